@@ -1,0 +1,952 @@
+/*
+ * xamg_oracle.c -- plain, slow, FP64 CPU oracle for the solve phase of an
+ * algebraic-multigrid-preconditioned Krylov solver with m right-hand sides.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline / reference leg of the benchmark may load this library.  The
+ * product path (the CUDA library under paper_2103_07329_gb300/) never calls
+ * it, links it or shares any code with it.
+ *
+ * What it follows (the paper names the methods; the algorithms are the
+ * textbook ones it cites):
+ *   - Problem A X = B, A n x n, X, B n x m, m << n ............ paper Sec. 1
+ *   - "blas2" multi-RHS SpMV-like product Y = A X ............. paper Sec. 2.2-2.3
+ *   - classical (Ruge-Stueben) AMG, used as a preconditioner .. paper Sec. 2.1, Tab. 1
+ *     (strength, RS first and second pass, classical interpolation,
+ *      Galerkin R A P with R = P^T: Trottenberg et al., Appendix A)
+ *   - Chebyshev smoother, polynomial order 2, pre and post ..... paper Sec. 2.1, Fig. 3
+ *   - MultiGrid with max_iters 1 as preconditioner ............. paper Fig. 3
+ *   - direct solver on the coarsest level (dense LU) .......... paper Sec. 2.1, Tab. 1
+ *   - CG (Hestenes-Stiefel) and BiCGStab (van der Vorst) ....... paper Sec. 2.1, Tab. 1
+ *   - per-column status flags .................................. paper Sec. 1, abstract
+ *
+ * Points where the paper is silent are fixed as follows (each is one
+ * "reading" of the method):
+ *   R1 strength: j in S_i iff j != i and -a_ij >= theta * max_{k != i}(-a_ik),
+ *      with max > 0; rows whose off-diagonals are all >= 0 have S_i empty.
+ *   R2 RS pass 1: lambda_i = |S_i^T cap U| + 2 |S_i^T cap F|; repeatedly the
+ *      undecided point of largest lambda (ties: smallest index) becomes C, its
+ *      undecided strong dependents become F.  Points with S_i empty start as F.
+ *   R3 RS pass 2: for F points i in index order, every strong F neighbour k
+ *      (in column order) must strongly depend on some point of C_i = S_i cap C;
+ *      otherwise k becomes C (and joins C_i at once).
+ *   R4 classical interpolation with weak connections lumped into the
+ *      diagonal and strong F connections distributed over C_i using only the
+ *      entries of row k whose sign is opposite to a_kk; a zero distribution
+ *      sum lumps a_ik into the diagonal.
+ *   R5 R = P^T, A_c = R A P accumulated row by row in the fixed order
+ *      (k in row I of R, l in row k of A, J in row l of P), all structural
+ *      entries kept.
+ *   R6 coarsening stops at n <= max_coarse, at max_levels, or when a level
+ *      would keep more than 0.9 n points; the last level is solved by dense
+ *      LU with partial pivoting.
+ *   R7 Chebyshev on D^-1 A over [a, b], b = min(1.1 * lambda_hat, Gershgorin
+ *      bound), a = 0.3 b, lambda_hat from power iterations started at a
+ *      SplitMix64 counter vector; "order 2" = two recurrence steps.
+ *   R8 stopping: a column freezes when its recursive residual norm is
+ *      <= tol * ||b_j||; once every column is frozen the true residuals are
+ *      computed and any column above tol restarts from its true residual.
+ *
+ * Compiled with -ffp-contract=off so that every product and sum is rounded
+ * as written.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXLEV 40
+
+enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_OOM = -3, ORC_ERR_NONFINITE = -4,
+       ORC_ERR_SETUP = -6, ORC_NOT_CONVERGED = 1, ORC_BREAKDOWN = 2 };
+
+/* per-column status codes reported by the solvers */
+enum { COL_CONVERGED = 0, COL_NOT_CONVERGED = 1, COL_BREAKDOWN = 2 };
+
+typedef struct {
+  int n, ncols;
+  int *rowptr;  /* n + 1 */
+  int *col;     /* nnz, ascending within a row */
+  double *val;  /* nnz */
+} ocsr;
+
+typedef struct {
+  int nlev;
+  ocsr A[ORC_MAXLEV];
+  ocsr P[ORC_MAXLEV];  /* n_l x n_{l+1}, l < nlev-1 */
+  ocsr R[ORC_MAXLEV];  /* n_{l+1} x n_l */
+  int *cf[ORC_MAXLEV]; /* 1 = C point, 0 = F point, l < nlev-1 */
+  double *dinv[ORC_MAXLEV];
+  double cheb_lo[ORC_MAXLEV], cheb_hi[ORC_MAXLEV], lam_hat[ORC_MAXLEV], gersh[ORC_MAXLEV];
+  int cheb_steps;
+  double *lu;  /* coarsest dense LU factors, row-major nc x nc */
+  int *piv;
+  int nc;
+} ohier;
+
+static int64_t nnz_of(const ocsr *a) { return a->rowptr[a->n]; }
+
+static void csr_free(ocsr *a) {
+  free(a->rowptr); free(a->col); free(a->val);
+  a->rowptr = NULL; a->col = NULL; a->val = NULL; a->n = a->ncols = 0;
+}
+
+static int csr_alloc(ocsr *a, int n, int ncols, int64_t nnz) {
+  a->n = n; a->ncols = ncols;
+  a->rowptr = (int *)calloc((size_t)n + 1, sizeof(int));
+  a->col = (int *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int));
+  a->val = (double *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+  if (!a->rowptr || !a->col || !a->val) { csr_free(a); return ORC_ERR_OOM; }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Y = A X for an n x m row-major block X (paper Sec. 2.2: one pass over A
+ * serves all m columns).  Row i of Y, column j: sum over the row's entries in
+ * storage order of a_ik * x_kj. */
+static void spmm(const ocsr *A, int m, const double *X, double *Y) {
+  int i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < A->n; ++i) {
+    double *y = Y + (size_t)i * m;
+    int j, p;
+    for (j = 0; j < m; ++j) y[j] = 0.0;
+    for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) {
+      const double a = A->val[p];
+      const double *x = X + (size_t)A->col[p] * m;
+      for (j = 0; j < m; ++j) y[j] = y[j] + a * x[j];
+    }
+  }
+}
+
+int orc_spmm(int n, int ncols, const int *rowptr, const int *col, const double *val,
+             int m, const double *X, double *Y) {
+  ocsr A;
+  if (n < 0 || ncols < 0 || m < 1 || !rowptr) return ORC_ERR_ARG;
+  A.n = n; A.ncols = ncols; A.rowptr = (int *)rowptr; A.col = (int *)col; A.val = (double *)val;
+  spmm(&A, m, X, Y);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Column dot products c_j = sum_i u_ij v_ij, summed in row order. */
+static void coldot(size_t n, int m, const double *U, const double *V, double *c) {
+  size_t i; int j;
+  for (j = 0; j < m; ++j) c[j] = 0.0;
+  for (i = 0; i < n; ++i)
+    for (j = 0; j < m; ++j) c[j] = c[j] + U[i * m + j] * V[i * m + j];
+}
+
+/* ------------------------------------------------------------------ */
+/* SplitMix64 (Steele, Lea, Flood 2014): output number i (i = 0, 1, ...) of the
+ * generator seeded with 0, mapped to a double in [-1, 1). */
+static double splitmix_uniform(uint64_t i) {
+  uint64_t z = (i + 1u) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+double orc_splitmix_uniform(uint64_t i) { return splitmix_uniform(i); }
+
+/* ------------------------------------------------------------------ */
+/* Reading R1: strong dependencies S (CSR pattern, columns ascending). */
+static int build_strength(const ocsr *A, double theta, ocsr *S) {
+  int i, p, cnt;
+  int64_t nnz = nnz_of(A);
+  if (csr_alloc(S, A->n, A->n, nnz) != ORC_OK) return ORC_ERR_OOM;
+  cnt = 0;
+  for (i = 0; i < A->n; ++i) {
+    double mx = 0.0;
+    for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p)
+      if (A->col[p] != i && -A->val[p] > mx) mx = -A->val[p];
+    if (mx > 0.0) {
+      for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p)
+        if (A->col[p] != i && -A->val[p] >= theta * mx) { S->col[cnt] = A->col[p]; S->val[cnt] = 1.0; ++cnt; }
+    }
+    S->rowptr[i + 1] = cnt;
+  }
+  return ORC_OK;
+}
+
+/* Transpose of a CSR matrix (columns of the result ascending). */
+static int transpose(const ocsr *A, ocsr *T) {
+  int i, p;
+  int64_t nnz = nnz_of(A);
+  int *next;
+  if (csr_alloc(T, A->ncols, A->n, nnz) != ORC_OK) return ORC_ERR_OOM;
+  for (p = 0; p < nnz; ++p) T->rowptr[A->col[p] + 1]++;
+  for (i = 0; i < A->ncols; ++i) T->rowptr[i + 1] += T->rowptr[i];
+  next = (int *)malloc(((size_t)A->ncols + 1) * sizeof(int));
+  if (!next) { csr_free(T); return ORC_ERR_OOM; }
+  memcpy(next, T->rowptr, ((size_t)A->ncols + 1) * sizeof(int));
+  for (i = 0; i < A->n; ++i)
+    for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) {
+      int q = next[A->col[p]]++;
+      T->col[q] = i; T->val[q] = A->val[p];
+    }
+  free(next);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* A binary max-heap of (lambda, index) pairs; order: larger lambda first,
+ * smaller index first on equal lambda.  Stale entries are skipped on pop. */
+typedef struct { int lam, idx; } hent;
+typedef struct { hent *a; size_t n, cap; } heap;
+
+static int hbefore(hent x, hent y) { return x.lam > y.lam || (x.lam == y.lam && x.idx < y.idx); }
+
+static int hpush(heap *h, int lam, int idx) {
+  size_t c;
+  if (h->n == h->cap) {
+    size_t nc = h->cap ? 2 * h->cap : 1024;
+    hent *na = (hent *)realloc(h->a, nc * sizeof(hent));
+    if (!na) return ORC_ERR_OOM;
+    h->a = na; h->cap = nc;
+  }
+  c = h->n++;
+  h->a[c].lam = lam; h->a[c].idx = idx;
+  while (c > 0) {
+    size_t par = (c - 1) / 2;
+    if (!hbefore(h->a[c], h->a[par])) break;
+    { hent t = h->a[c]; h->a[c] = h->a[par]; h->a[par] = t; }
+    c = par;
+  }
+  return ORC_OK;
+}
+
+static hent hpop(heap *h) {
+  hent top = h->a[0];
+  size_t c = 0;
+  h->a[0] = h->a[--h->n];
+  for (;;) {
+    size_t l = 2 * c + 1, r = l + 1, b = c;
+    if (l < h->n && hbefore(h->a[l], h->a[b])) b = l;
+    if (r < h->n && hbefore(h->a[r], h->a[b])) b = r;
+    if (b == c) break;
+    { hent t = h->a[c]; h->a[c] = h->a[b]; h->a[b] = t; }
+    c = b;
+  }
+  return top;
+}
+
+/* Readings R2 + R3: C/F splitting.  cf[i] = 1 (C) or 0 (F). */
+#define ST_U 0
+#define ST_C 1
+#define ST_F 2
+static int rs_split(const ocsr *S, const ocsr *ST, int *cf) {
+  int n = S->n, i, p, q;
+  int *st = (int *)malloc((size_t)n * sizeof(int));
+  int *lam = (int *)malloc((size_t)n * sizeof(int));
+  int *mark = (int *)malloc((size_t)n * sizeof(int));
+  heap h = {NULL, 0, 0};
+  int rc = ORC_OK;
+  if (!st || !lam || !mark) { rc = ORC_ERR_OOM; goto done; }
+  for (i = 0; i < n; ++i) {
+    lam[i] = ST->rowptr[i + 1] - ST->rowptr[i];
+    st[i] = (S->rowptr[i + 1] == S->rowptr[i]) ? ST_F : ST_U;
+  }
+  for (i = 0; i < n; ++i)
+    if (st[i] == ST_U && hpush(&h, lam[i], i) != ORC_OK) { rc = ORC_ERR_OOM; goto done; }
+  /* first pass */
+  while (h.n > 0) {
+    hent e = hpop(&h);
+    i = e.idx;
+    if (st[i] != ST_U || e.lam != lam[i]) continue; /* stale */
+    st[i] = ST_C;
+    /* undecided points that strongly depend on i become F */
+    for (p = ST->rowptr[i]; p < ST->rowptr[i + 1]; ++p) {
+      int j = ST->col[p];
+      if (st[j] != ST_U) continue;
+      st[j] = ST_F;
+      for (q = S->rowptr[j]; q < S->rowptr[j + 1]; ++q) {
+        int k = S->col[q];
+        if (st[k] == ST_U) {
+          lam[k] += 1;
+          if (hpush(&h, lam[k], k) != ORC_OK) { rc = ORC_ERR_OOM; goto done; }
+        }
+      }
+    }
+    /* i left U: the points i depends on lose one */
+    for (p = S->rowptr[i]; p < S->rowptr[i + 1]; ++p) {
+      int k = S->col[p];
+      if (st[k] == ST_U) {
+        lam[k] -= 1;
+        if (hpush(&h, lam[k], k) != ORC_OK) { rc = ORC_ERR_OOM; goto done; }
+      }
+    }
+  }
+  /* second pass */
+  for (i = 0; i < n; ++i) mark[i] = -1;
+  for (i = 0; i < n; ++i) {
+    if (st[i] != ST_F || S->rowptr[i + 1] == S->rowptr[i]) continue;
+    for (p = S->rowptr[i]; p < S->rowptr[i + 1]; ++p)
+      if (st[S->col[p]] == ST_C) mark[S->col[p]] = i;
+    for (p = S->rowptr[i]; p < S->rowptr[i + 1]; ++p) {
+      int k = S->col[p], found = 0;
+      if (st[k] != ST_F) continue;
+      for (q = S->rowptr[k]; q < S->rowptr[k + 1]; ++q)
+        if (mark[S->col[q]] == i) { found = 1; break; }
+      if (!found) { st[k] = ST_C; mark[k] = i; }
+    }
+  }
+  for (i = 0; i < n; ++i) cf[i] = (st[i] == ST_C) ? 1 : 0;
+done:
+  free(st); free(lam); free(mark); free(h.a);
+  return rc;
+}
+
+/* Reading R4: classical interpolation P (n x nc). */
+static int build_interp(const ocsr *A, const ocsr *S, const int *cf, ocsr *P) {
+  int n = A->n, i, p, q, nc = 0;
+  int64_t cnt = 0, cap;
+  int *cidx = (int *)malloc((size_t)n * sizeof(int));
+  int *smark = (int *)malloc((size_t)n * sizeof(int)); /* smark[j] == i: j in S_i */
+  int *cmark = (int *)malloc((size_t)n * sizeof(int)); /* cmark[j] == i: j in C_i */
+  double *num = (double *)malloc((size_t)n * sizeof(double));
+  int rc = ORC_OK;
+  if (!cidx || !smark || !cmark || !num) { rc = ORC_ERR_OOM; goto fail; }
+  for (i = 0; i < n; ++i) { cidx[i] = cf[i] ? nc++ : -1; smark[i] = -1; cmark[i] = -1; }
+  /* an upper bound on nnz(P): one per C row, |C_i| per F row */
+  cap = 0;
+  for (i = 0; i < n; ++i) cap += cf[i] ? 1 : (S->rowptr[i + 1] - S->rowptr[i]);
+  if (csr_alloc(P, n, nc, cap) != ORC_OK) { rc = ORC_ERR_OOM; goto fail; }
+  for (i = 0; i < n; ++i) {
+    if (cf[i]) {
+      P->col[cnt] = cidx[i]; P->val[cnt] = 1.0; ++cnt;
+    } else if (S->rowptr[i + 1] > S->rowptr[i]) {
+      double diag = 0.0;
+      for (p = S->rowptr[i]; p < S->rowptr[i + 1]; ++p) {
+        smark[S->col[p]] = i;
+        if (cf[S->col[p]]) { cmark[S->col[p]] = i; num[S->col[p]] = 0.0; }
+      }
+      for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p)
+        if (A->col[p] == i) diag = A->val[p];
+      /* weak connections (any neighbour not in S_i) go into the diagonal */
+      for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) {
+        int j = A->col[p];
+        if (j == i) continue;
+        if (smark[j] != i) diag = diag + A->val[p];
+        else if (cf[j]) num[j] = num[j] + A->val[p];
+      }
+      /* strong F neighbours are distributed over C_i */
+      for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) {
+        int k = A->col[p];
+        double aik = A->val[p], akk = 0.0, sum = 0.0;
+        if (k == i || smark[k] != i || cf[k]) continue;
+        for (q = A->rowptr[k]; q < A->rowptr[k + 1]; ++q)
+          if (A->col[q] == k) akk = A->val[q];
+        for (q = A->rowptr[k]; q < A->rowptr[k + 1]; ++q) {
+          int l = A->col[q];
+          if (cmark[l] == i && A->val[q] * akk < 0.0) sum = sum + A->val[q];
+        }
+        if (sum == 0.0) {
+          diag = diag + aik;
+        } else {
+          for (q = A->rowptr[k]; q < A->rowptr[k + 1]; ++q) {
+            int l = A->col[q];
+            if (cmark[l] == i && A->val[q] * akk < 0.0) num[l] = num[l] + aik * A->val[q] / sum;
+          }
+        }
+      }
+      if (diag == 0.0) { rc = ORC_ERR_SETUP; csr_free(P); goto fail; }
+      for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) {
+        int j = A->col[p];
+        if (j != i && cmark[j] == i) { P->col[cnt] = cidx[j]; P->val[cnt] = -num[j] / diag; ++cnt; }
+      }
+    }
+    P->rowptr[i + 1] = (int)cnt;
+  }
+fail:
+  free(cidx); free(smark); free(cmark); free(num);
+  return rc;
+}
+
+/* Reading R5: A_c = R A P, row by row in a fixed accumulation order. */
+static int galerkin(const ocsr *R, const ocsr *A, const ocsr *P, ocsr *Ac) {
+  int nc = R->n, I, p, q, s;
+  int *pos = (int *)malloc((size_t)(P->ncols > 0 ? P->ncols : 1) * sizeof(int));
+  double *acc = (double *)malloc((size_t)(P->ncols > 0 ? P->ncols : 1) * sizeof(double));
+  int *list = (int *)malloc((size_t)(P->ncols > 0 ? P->ncols : 1) * sizeof(int));
+  int64_t cnt = 0, cap = 1 << 20;
+  int rc = ORC_OK;
+  Ac->rowptr = NULL; Ac->col = NULL; Ac->val = NULL;
+  if (!pos || !acc || !list) { rc = ORC_ERR_OOM; goto fail; }
+  for (I = 0; I < P->ncols; ++I) pos[I] = -1;
+  Ac->n = nc; Ac->ncols = P->ncols;
+  Ac->rowptr = (int *)calloc((size_t)nc + 1, sizeof(int));
+  Ac->col = (int *)malloc((size_t)cap * sizeof(int));
+  Ac->val = (double *)malloc((size_t)cap * sizeof(double));
+  if (!Ac->rowptr || !Ac->col || !Ac->val) { rc = ORC_ERR_OOM; goto fail; }
+  for (I = 0; I < nc; ++I) {
+    int len = 0, a, b;
+    for (p = R->rowptr[I]; p < R->rowptr[I + 1]; ++p) {
+      int k = R->col[p];
+      double rik = R->val[p];
+      for (q = A->rowptr[k]; q < A->rowptr[k + 1]; ++q) {
+        int l = A->col[q];
+        double t = rik * A->val[q];
+        for (s = P->rowptr[l]; s < P->rowptr[l + 1]; ++s) {
+          int J = P->col[s];
+          if (pos[J] < 0) { pos[J] = len; list[len++] = J; acc[J] = 0.0; }
+          acc[J] = acc[J] + t * P->val[s];
+        }
+      }
+    }
+    /* insertion sort of the row's column list (rows are short) */
+    for (a = 1; a < len; ++a) {
+      int key = list[a];
+      b = a - 1;
+      while (b >= 0 && list[b] > key) { list[b + 1] = list[b]; --b; }
+      list[b + 1] = key;
+    }
+    if (cnt + len > cap) {
+      int64_t ncap = cap;
+      while (cnt + len > ncap) ncap *= 2;
+      {
+        int *nci = (int *)realloc(Ac->col, (size_t)ncap * sizeof(int));
+        double *ncv;
+        if (!nci) { rc = ORC_ERR_OOM; goto fail; }
+        Ac->col = nci;
+        ncv = (double *)realloc(Ac->val, (size_t)ncap * sizeof(double));
+        if (!ncv) { rc = ORC_ERR_OOM; goto fail; }
+        Ac->val = ncv;
+      }
+      cap = ncap;
+    }
+    for (a = 0; a < len; ++a) {
+      Ac->col[cnt] = list[a]; Ac->val[cnt] = acc[list[a]]; ++cnt;
+      pos[list[a]] = -1;
+    }
+    Ac->rowptr[I + 1] = (int)cnt;
+  }
+  free(pos); free(acc); free(list);
+  return ORC_OK;
+fail:
+  free(pos); free(acc); free(list);
+  csr_free(Ac);
+  return rc;
+}
+
+/* Reading R7: Chebyshev interval for D^-1 A. */
+static int cheb_bounds(const ocsr *A, const double *dinv, int power_iters, double hi_safety,
+                       double lo_frac, double *lo, double *hi, double *lam_hat, double *gersh) {
+  int n = A->n, i, p, it;
+  double g = 0.0, lam = 0.0;
+  double *v = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  double *w = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  if (!v || !w) { free(v); free(w); return ORC_ERR_OOM; }
+  for (i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) s = s + fabs(A->val[p]);
+    s = s * fabs(dinv[i]);
+    if (s > g) g = s;
+  }
+  for (i = 0; i < n; ++i) v[i] = splitmix_uniform((uint64_t)i);
+  for (it = 0; it < power_iters; ++it) {
+    double nv = 0.0, nw = 0.0;
+    spmm(A, 1, v, w);
+    for (i = 0; i < n; ++i) w[i] = dinv[i] * w[i];
+    for (i = 0; i < n; ++i) nv = nv + v[i] * v[i];
+    for (i = 0; i < n; ++i) nw = nw + w[i] * w[i];
+    nv = sqrt(nv); nw = sqrt(nw);
+    if (nw == 0.0 || nv == 0.0) break;
+    lam = nw / nv;
+    for (i = 0; i < n; ++i) v[i] = w[i] / nw;
+  }
+  *lam_hat = lam; *gersh = g;
+  *hi = hi_safety * lam;
+  if (*hi > g || lam == 0.0) *hi = g;
+  *lo = lo_frac * *hi;
+  free(v); free(w);
+  return ORC_OK;
+}
+
+/* Dense LU with partial pivoting (first row of largest |pivot|), in place. */
+static int lu_factor(int n, double *a, int *piv) {
+  int k, i, j;
+  for (k = 0; k < n; ++k) {
+    int pr = k;
+    double best = fabs(a[(size_t)k * n + k]);
+    for (i = k + 1; i < n; ++i)
+      if (fabs(a[(size_t)i * n + k]) > best) { best = fabs(a[(size_t)i * n + k]); pr = i; }
+    piv[k] = pr;
+    if (best == 0.0) return ORC_ERR_SETUP;
+    if (pr != k)
+      for (j = 0; j < n; ++j) { double t = a[(size_t)k * n + j]; a[(size_t)k * n + j] = a[(size_t)pr * n + j]; a[(size_t)pr * n + j] = t; }
+    for (i = k + 1; i < n; ++i) {
+      double l = a[(size_t)i * n + k] / a[(size_t)k * n + k];
+      a[(size_t)i * n + k] = l;
+      for (j = k + 1; j < n; ++j) a[(size_t)i * n + j] = a[(size_t)i * n + j] - l * a[(size_t)k * n + j];
+    }
+  }
+  return ORC_OK;
+}
+
+/* Solve with the factors for an n x m row-major block b (overwritten). */
+static void lu_solve(int n, const double *lu, const int *piv, int m, double *b) {
+  int k, i, j;
+  for (j = 0; j < m; ++j) {
+    for (k = 0; k < n; ++k)
+      if (piv[k] != k) { double t = b[(size_t)k * m + j]; b[(size_t)k * m + j] = b[(size_t)piv[k] * m + j]; b[(size_t)piv[k] * m + j] = t; }
+    for (i = 1; i < n; ++i) {
+      double s = b[(size_t)i * m + j];
+      for (k = 0; k < i; ++k) s = s - lu[(size_t)i * n + k] * b[(size_t)k * m + j];
+      b[(size_t)i * m + j] = s;
+    }
+    for (i = n - 1; i >= 0; --i) {
+      double s = b[(size_t)i * m + j];
+      for (k = i + 1; k < n; ++k) s = s - lu[(size_t)i * n + k] * b[(size_t)k * m + j];
+      b[(size_t)i * m + j] = s / lu[(size_t)i * n + i];
+    }
+  }
+}
+
+int orc_lu_factor(int n, double *a, int *piv) { return lu_factor(n, a, piv); }
+void orc_lu_solve(int n, const double *lu, const int *piv, int m, double *b) { lu_solve(n, lu, piv, m, b); }
+
+/* ------------------------------------------------------------------ */
+void orc_free(ohier *h) {
+  int l;
+  if (!h) return;
+  for (l = 0; l < ORC_MAXLEV; ++l) {
+    csr_free(&h->A[l]); csr_free(&h->P[l]); csr_free(&h->R[l]);
+    free(h->cf[l]); free(h->dinv[l]);
+  }
+  free(h->lu); free(h->piv);
+  free(h);
+}
+
+static int copy_csr(int n, int ncols, const int *rowptr, const int *col, const double *val, ocsr *a) {
+  int64_t nnz = rowptr[n];
+  if (csr_alloc(a, n, ncols, nnz) != ORC_OK) return ORC_ERR_OOM;
+  memcpy(a->rowptr, rowptr, ((size_t)n + 1) * sizeof(int));
+  memcpy(a->col, col, (size_t)nnz * sizeof(int));
+  memcpy(a->val, val, (size_t)nnz * sizeof(double));
+  return ORC_OK;
+}
+
+/* Builds the hierarchy (readings R1-R7).  Returns NULL and sets *err on error. */
+ohier *orc_setup(int n, const int *rowptr, const int *col, const double *val, double theta,
+                 int max_coarse, int max_levels, int cheb_steps, int power_iters,
+                 double lo_frac, double hi_safety, int max_dense, int *err) {
+  ohier *h;
+  int l, i, p, rc = ORC_OK;
+  *err = ORC_OK;
+  if (n < 1 || !rowptr || max_levels < 1 || max_levels > ORC_MAXLEV || cheb_steps < 1) { *err = ORC_ERR_ARG; return NULL; }
+  for (i = 0; i < n; ++i) {
+    int diag = 0;
+    if (rowptr[i + 1] < rowptr[i]) { *err = ORC_ERR_ARG; return NULL; }
+    for (p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      if (col[p] < 0 || col[p] >= n || (p > rowptr[i] && col[p] <= col[p - 1])) { *err = ORC_ERR_ARG; return NULL; }
+      if (!isfinite(val[p])) { *err = ORC_ERR_NONFINITE; return NULL; }
+      if (col[p] == i && val[p] != 0.0) diag = 1;
+    }
+    if (!diag) { *err = ORC_ERR_ARG; return NULL; }
+  }
+  h = (ohier *)calloc(1, sizeof(ohier));
+  if (!h) { *err = ORC_ERR_OOM; return NULL; }
+  h->cheb_steps = cheb_steps;
+  if (copy_csr(n, n, rowptr, col, val, &h->A[0]) != ORC_OK) { orc_free(h); *err = ORC_ERR_OOM; return NULL; }
+  for (l = 0;; ++l) {
+    ocsr *A = &h->A[l];
+    ocsr S, ST;
+    int nc;
+    h->dinv[l] = (double *)malloc((size_t)A->n * sizeof(double));
+    if (!h->dinv[l]) { rc = ORC_ERR_OOM; break; }
+    for (i = 0; i < A->n; ++i) {
+      double d = 0.0;
+      for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) if (A->col[p] == i) d = A->val[p];
+      if (d == 0.0) { rc = ORC_ERR_SETUP; break; }
+      h->dinv[l][i] = 1.0 / d;
+    }
+    if (rc != ORC_OK) break;
+    h->nlev = l + 1;
+    if (A->n <= max_coarse || l == max_levels - 1) break;
+    if (build_strength(A, theta, &S) != ORC_OK) { rc = ORC_ERR_OOM; break; }
+    if (transpose(&S, &ST) != ORC_OK) { csr_free(&S); rc = ORC_ERR_OOM; break; }
+    h->cf[l] = (int *)malloc((size_t)A->n * sizeof(int));
+    if (!h->cf[l]) { csr_free(&S); csr_free(&ST); rc = ORC_ERR_OOM; break; }
+    rc = rs_split(&S, &ST, h->cf[l]);
+    csr_free(&ST);
+    if (rc != ORC_OK) { csr_free(&S); break; }
+    nc = 0;
+    for (i = 0; i < A->n; ++i) nc += h->cf[l][i];
+    if (nc == 0 || (double)nc > 0.9 * (double)A->n) {
+      csr_free(&S); free(h->cf[l]); h->cf[l] = NULL;
+      break;
+    }
+    rc = build_interp(A, &S, h->cf[l], &h->P[l]);
+    csr_free(&S);
+    if (rc != ORC_OK) break;
+    if ((rc = transpose(&h->P[l], &h->R[l])) != ORC_OK) break;
+    if ((rc = galerkin(&h->R[l], A, &h->P[l], &h->A[l + 1])) != ORC_OK) break;
+  }
+  if (rc == ORC_OK) {
+    for (l = 0; l + 1 < h->nlev; ++l) {
+      rc = cheb_bounds(&h->A[l], h->dinv[l], power_iters, hi_safety, lo_frac,
+                       &h->cheb_lo[l], &h->cheb_hi[l], &h->lam_hat[l], &h->gersh[l]);
+      if (rc != ORC_OK) break;
+    }
+  }
+  if (rc == ORC_OK) {
+    ocsr *Ac = &h->A[h->nlev - 1];
+    h->nc = Ac->n;
+    if (Ac->n > max_dense) rc = ORC_ERR_SETUP;
+    else {
+      h->lu = (double *)calloc((size_t)Ac->n * Ac->n, sizeof(double));
+      h->piv = (int *)malloc((size_t)Ac->n * sizeof(int));
+      if (!h->lu || !h->piv) rc = ORC_ERR_OOM;
+      else {
+        for (i = 0; i < Ac->n; ++i)
+          for (p = Ac->rowptr[i]; p < Ac->rowptr[i + 1]; ++p) h->lu[(size_t)i * Ac->n + Ac->col[p]] = Ac->val[p];
+        rc = lu_factor(Ac->n, h->lu, h->piv);
+      }
+    }
+  }
+  if (rc != ORC_OK) { orc_free(h); *err = rc; return NULL; }
+  return h;
+}
+
+/* ---- accessors used by the tests ---- */
+int orc_nlev(const ohier *h) { return h->nlev; }
+int orc_cheb_steps(const ohier *h) { return h->cheb_steps; }
+void orc_level_sizes(const ohier *h, int l, int *n, int64_t *nnz_a, int64_t *nnz_p) {
+  *n = h->A[l].n; *nnz_a = nnz_of(&h->A[l]);
+  *nnz_p = (l + 1 < h->nlev) ? nnz_of(&h->P[l]) : 0;
+}
+/* which: 0 = A, 1 = P, 2 = R */
+void orc_level_csr(const ohier *h, int l, int which, int *rowptr, int *col, double *val) {
+  const ocsr *a = which == 0 ? &h->A[l] : which == 1 ? &h->P[l] : &h->R[l];
+  int64_t nnz = nnz_of(a);
+  memcpy(rowptr, a->rowptr, ((size_t)a->n + 1) * sizeof(int));
+  memcpy(col, a->col, (size_t)nnz * sizeof(int));
+  memcpy(val, a->val, (size_t)nnz * sizeof(double));
+}
+void orc_level_cf(const ohier *h, int l, int *cf) { memcpy(cf, h->cf[l], (size_t)h->A[l].n * sizeof(int)); }
+void orc_level_dinv(const ohier *h, int l, double *d) { memcpy(d, h->dinv[l], (size_t)h->A[l].n * sizeof(double)); }
+void orc_level_cheb(const ohier *h, int l, double *out4) {
+  out4[0] = h->cheb_lo[l]; out4[1] = h->cheb_hi[l]; out4[2] = h->lam_hat[l]; out4[3] = h->gersh[l];
+}
+void orc_coarse_lu(const ohier *h, double *lu, int *piv) {
+  memcpy(lu, h->lu, (size_t)h->nc * h->nc * sizeof(double));
+  memcpy(piv, h->piv, (size_t)h->nc * sizeof(int));
+}
+
+/* ------------------------------------------------------------------ */
+/* Chebyshev smoothing (reading R7) on level l for an n x m block: `steps`
+ * recurrence steps on x.  If x_zero, x is taken as 0 on entry and r0 = b.
+ * If r_out is not NULL the residual after the last step is written to it.
+ *   theta = (hi+lo)/2, delta = (hi-lo)/2, sigma = theta/delta, rho_0 = 1/sigma
+ *   d_0 = D^-1 r_0 / theta
+ *   r_k = r_{k-1} - A d_{k-1},  rho_k = 1 / (2 sigma - rho_{k-1})
+ *   d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) D^-1 r_k
+ *   x <- x + d_k after each step. */
+static int cheb_smooth(const ohier *h, int l, int m, const double *b, double *x, int x_zero,
+                       double *r_out) {
+  const ocsr *A = &h->A[l];
+  size_t N = (size_t)A->n * m, e;
+  int i, j, k, steps = h->cheb_steps;
+  double lo = h->cheb_lo[l], hi = h->cheb_hi[l];
+  double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  double rho = 1.0 / sigma, rho_new;
+  double *r = (double *)malloc(N * sizeof(double));
+  double *d = (double *)malloc(N * sizeof(double));
+  double *t = (double *)malloc(N * sizeof(double));
+  if (!r || !d || !t) { free(r); free(d); free(t); return ORC_ERR_OOM; }
+  if (x_zero) {
+    for (e = 0; e < N; ++e) { r[e] = b[e]; x[e] = 0.0; }
+  } else {
+    spmm(A, m, x, t);
+    for (e = 0; e < N; ++e) r[e] = b[e] - t[e];
+  }
+  for (i = 0; i < A->n; ++i)
+    for (j = 0; j < m; ++j) {
+      e = (size_t)i * m + j;
+      d[e] = h->dinv[l][i] * r[e] / theta;
+      x[e] = x[e] + d[e];
+    }
+  for (k = 1; k < steps; ++k) {
+    spmm(A, m, d, t);
+    for (e = 0; e < N; ++e) r[e] = r[e] - t[e];
+    rho_new = 1.0 / (2.0 * sigma - rho);
+    for (i = 0; i < A->n; ++i)
+      for (j = 0; j < m; ++j) {
+        e = (size_t)i * m + j;
+        d[e] = rho_new * rho * d[e] + 2.0 * rho_new / delta * (h->dinv[l][i] * r[e]);
+        x[e] = x[e] + d[e];
+      }
+    rho = rho_new;
+  }
+  if (r_out) {
+    spmm(A, m, d, t);
+    for (e = 0; e < N; ++e) r_out[e] = r[e] - t[e];
+  }
+  free(r); free(d); free(t);
+  return ORC_OK;
+}
+
+int orc_cheb_smooth(const ohier *h, int l, int m, const double *b, double *x, int x_zero, double *r_out) {
+  if (!h || l < 0 || l >= h->nlev - 1 || m < 1) return ORC_ERR_ARG;
+  return cheb_smooth(h, l, m, b, x, x_zero, r_out);
+}
+
+/* One V(1,1) cycle from x = 0 (paper Fig. 3: MultiGrid, max_iters 1, Chebyshev
+ * pre- and post-smoother; coarsest level by the direct solver). */
+static int vcycle(const ohier *h, int l, int m, const double *b, double *x) {
+  const ocsr *A = &h->A[l];
+  size_t N = (size_t)A->n * m, e;
+  int rc;
+  double *r, *bc, *xc, *t;
+  if (l == h->nlev - 1) {
+    memcpy(x, b, N * sizeof(double));
+    lu_solve(h->nc, h->lu, h->piv, m, x);
+    return ORC_OK;
+  }
+  r = (double *)malloc(N * sizeof(double));
+  t = (double *)malloc(N * sizeof(double));
+  bc = (double *)malloc((size_t)h->A[l + 1].n * m * sizeof(double));
+  xc = (double *)malloc((size_t)h->A[l + 1].n * m * sizeof(double));
+  if (!r || !t || !bc || !xc) { rc = ORC_ERR_OOM; goto done; }
+  if ((rc = cheb_smooth(h, l, m, b, x, 1, r)) != ORC_OK) goto done;
+  spmm(&h->R[l], m, r, bc);                       /* restriction */
+  if ((rc = vcycle(h, l + 1, m, bc, xc)) != ORC_OK) goto done;
+  spmm(&h->P[l], m, xc, t);                       /* prolongation */
+  for (e = 0; e < N; ++e) x[e] = x[e] + t[e];
+  rc = cheb_smooth(h, l, m, b, x, 0, NULL);       /* post-smoothing */
+done:
+  free(r); free(t); free(bc); free(xc);
+  return rc;
+}
+
+int orc_vcycle(const ohier *h, int m, const double *b, double *x) {
+  if (!h || m < 1) return ORC_ERR_ARG;
+  return vcycle(h, 0, m, b, x);
+}
+
+/* ------------------------------------------------------------------ */
+static int all_finite(size_t N, const double *v) {
+  size_t e;
+  for (e = 0; e < N; ++e) if (!isfinite(v[e])) return 0;
+  return 1;
+}
+
+/* true residual norms ||b_j - A x_j|| into tn[j]; t is scratch */
+static void true_resnorm(const ocsr *A, int m, const double *b, const double *x, double *t, double *tn) {
+  size_t N = (size_t)A->n * m, e;
+  spmm(A, m, x, t);
+  for (e = 0; e < N; ++e) t[e] = b[e] - t[e];
+  coldot((size_t)A->n, m, t, t, tn);
+  { int j; for (j = 0; j < m; ++j) tn[j] = sqrt(tn[j]); }
+}
+
+/* Reading R8 applied when every column is frozen: columns whose true
+ * residual is above tol restart from it.  Returns the number restarted. */
+static int confirm(const ocsr *A, int m, const double *b, const double *x, double *r, double *t,
+                   double *tn, const double *nb, double tol, int *state, int *restart) {
+  int j, cnt = 0;
+  size_t i, N = (size_t)A->n;
+  true_resnorm(A, m, b, x, t, tn);
+  for (j = 0; j < m; ++j) {
+    if (state[j] != 1) continue; /* only columns frozen by the residual test */
+    if (tn[j] <= tol * nb[j]) { state[j] = 2; continue; }
+    state[j] = 0; restart[j] = 1; ++cnt;
+    for (i = 0; i < N; ++i) r[i * m + j] = t[i * m + j];
+  }
+  return cnt;
+}
+
+/* state: 0 active, 1 frozen by the recursive residual, 2 confirmed converged,
+ * 3 breakdown, 4 zero right-hand side */
+
+/* Preconditioned CG (paper Sec. 2.1, Tab. 1; Hestenes-Stiefel), M = one V-cycle. */
+int orc_pcg(const ohier *h, int m, const double *b, double *x, double tol, int maxit,
+            int *iters, double *relres, int *status) {
+  const ocsr *A = &h->A[0];
+  size_t N = (size_t)A->n * m, i;
+  int j, k, rc = ORC_OK, any;
+  double *r = NULL, *z = NULL, *p = NULL, *q = NULL, *t = NULL;
+  double *nb = NULL, *rho = NULL, *c = NULL, *tn = NULL;
+  int *state = NULL, *restart = NULL;
+  if (!h || m < 1 || maxit < 0 || !(tol > 0.0)) return ORC_ERR_ARG;
+  if (!all_finite(N, b)) return ORC_ERR_NONFINITE;
+  r = (double *)malloc(N * sizeof(double)); z = (double *)malloc(N * sizeof(double));
+  p = (double *)malloc(N * sizeof(double)); q = (double *)malloc(N * sizeof(double));
+  t = (double *)malloc(N * sizeof(double));
+  nb = (double *)malloc((size_t)m * sizeof(double)); rho = (double *)malloc((size_t)m * sizeof(double));
+  c = (double *)malloc((size_t)m * sizeof(double)); tn = (double *)malloc((size_t)m * sizeof(double));
+  state = (int *)calloc((size_t)m, sizeof(int)); restart = (int *)calloc((size_t)m, sizeof(int));
+  if (!r || !z || !p || !q || !t || !nb || !rho || !c || !tn || !state || !restart) { rc = ORC_ERR_OOM; goto done; }
+  coldot((size_t)A->n, m, b, b, nb);
+  for (j = 0; j < m; ++j) { nb[j] = sqrt(nb[j]); iters[j] = 0; if (nb[j] == 0.0) state[j] = 4; }
+  for (i = 0; i < N; ++i) { x[i] = 0.0; r[i] = b[i]; }
+  if ((rc = vcycle(h, 0, m, r, z)) != ORC_OK) goto done;
+  memcpy(p, z, N * sizeof(double));
+  coldot((size_t)A->n, m, r, z, rho);
+  for (j = 0; j < m; ++j) if (state[j] == 0 && !(rho[j] > 0.0)) state[j] = 3;
+  for (k = 1; k <= maxit; ++k) {
+    any = 0;
+    for (j = 0; j < m; ++j) any |= (state[j] == 0);
+    if (!any) break;
+    spmm(A, m, p, q);
+    coldot((size_t)A->n, m, p, q, c);
+    for (j = 0; j < m; ++j) {
+      double alpha;
+      if (state[j] != 0) continue;
+      if (!(c[j] > 0.0)) { state[j] = 3; continue; }
+      alpha = rho[j] / c[j];
+      for (i = 0; i < (size_t)A->n; ++i) {
+        x[i * m + j] = x[i * m + j] + alpha * p[i * m + j];
+        r[i * m + j] = r[i * m + j] - alpha * q[i * m + j];
+      }
+      iters[j] = k;
+    }
+    coldot((size_t)A->n, m, r, r, c);
+    any = 0;
+    for (j = 0; j < m; ++j) {
+      if (state[j] != 0) continue;
+      if (sqrt(c[j]) <= tol * nb[j]) state[j] = 1;
+      else any = 1;
+    }
+    if (!any) {
+      if (confirm(A, m, b, x, r, t, tn, nb, tol, state, restart) == 0) break;
+    }
+    if ((rc = vcycle(h, 0, m, r, z)) != ORC_OK) goto done;
+    coldot((size_t)A->n, m, r, z, c);
+    for (j = 0; j < m; ++j) {
+      double beta;
+      if (state[j] != 0) continue;
+      if (!(c[j] > 0.0)) { state[j] = 3; continue; }
+      beta = restart[j] ? 0.0 : c[j] / rho[j];
+      restart[j] = 0;
+      for (i = 0; i < (size_t)A->n; ++i) p[i * m + j] = z[i * m + j] + beta * p[i * m + j];
+      rho[j] = c[j];
+    }
+  }
+  true_resnorm(A, m, b, x, t, tn);
+  rc = ORC_OK;
+  for (j = 0; j < m; ++j) {
+    relres[j] = nb[j] > 0.0 ? tn[j] / nb[j] : 0.0;
+    if (state[j] == 4) status[j] = COL_CONVERGED;
+    else if (state[j] == 3) status[j] = COL_BREAKDOWN;
+    else status[j] = relres[j] <= tol ? COL_CONVERGED : COL_NOT_CONVERGED;
+    if (status[j] == COL_BREAKDOWN) rc = ORC_BREAKDOWN;
+    else if (status[j] == COL_NOT_CONVERGED && rc == ORC_OK) rc = ORC_NOT_CONVERGED;
+  }
+done:
+  free(r); free(z); free(p); free(q); free(t); free(nb); free(rho); free(c); free(tn);
+  free(state); free(restart);
+  return rc;
+}
+
+/* Right-preconditioned BiCGStab (paper Sec. 2.1, Tab. 1; van der Vorst), M = one V-cycle. */
+int orc_bicgstab(const ohier *h, int m, const double *b, double *x, double tol, int maxit,
+                 int *iters, double *relres, int *status) {
+  const ocsr *A = &h->A[0];
+  size_t N = (size_t)A->n * m, i, n = (size_t)A->n;
+  int j, k, rc = ORC_OK, any;
+  double *r = NULL, *rh = NULL, *p = NULL, *v = NULL, *s = NULL, *t = NULL, *ph = NULL, *sh = NULL;
+  double *nb = NULL, *rho_old = NULL, *alpha = NULL, *omega = NULL, *c = NULL, *c2 = NULL, *tn = NULL;
+  int *state = NULL, *restart = NULL;
+  if (!h || m < 1 || maxit < 0 || !(tol > 0.0)) return ORC_ERR_ARG;
+  if (!all_finite(N, b)) return ORC_ERR_NONFINITE;
+  r = (double *)malloc(N * sizeof(double)); rh = (double *)malloc(N * sizeof(double));
+  p = (double *)malloc(N * sizeof(double)); v = (double *)malloc(N * sizeof(double));
+  s = (double *)malloc(N * sizeof(double)); t = (double *)malloc(N * sizeof(double));
+  ph = (double *)malloc(N * sizeof(double)); sh = (double *)malloc(N * sizeof(double));
+  nb = (double *)malloc((size_t)m * sizeof(double)); rho_old = (double *)malloc((size_t)m * sizeof(double));
+  alpha = (double *)malloc((size_t)m * sizeof(double)); omega = (double *)malloc((size_t)m * sizeof(double));
+  c = (double *)malloc((size_t)m * sizeof(double)); c2 = (double *)malloc((size_t)m * sizeof(double));
+  tn = (double *)malloc((size_t)m * sizeof(double));
+  state = (int *)calloc((size_t)m, sizeof(int)); restart = (int *)calloc((size_t)m, sizeof(int));
+  if (!r || !rh || !p || !v || !s || !t || !ph || !sh || !nb || !rho_old || !alpha || !omega || !c ||
+      !c2 || !tn || !state || !restart) { rc = ORC_ERR_OOM; goto done; }
+  coldot(n, m, b, b, nb);
+  for (j = 0; j < m; ++j) { nb[j] = sqrt(nb[j]); iters[j] = 0; if (nb[j] == 0.0) state[j] = 4; restart[j] = 1; }
+  for (i = 0; i < N; ++i) { x[i] = 0.0; r[i] = b[i]; rh[i] = b[i]; p[i] = 0.0; v[i] = 0.0; }
+  for (k = 1; k <= maxit; ++k) {
+    any = 0;
+    for (j = 0; j < m; ++j) any |= (state[j] == 0);
+    if (!any) break;
+    coldot(n, m, rh, r, c);                         /* rho_k = rhat . r */
+    for (j = 0; j < m; ++j) {
+      double beta;
+      if (state[j] != 0) continue;
+      if (c[j] == 0.0 || !isfinite(c[j])) { state[j] = 3; continue; }
+      if (restart[j]) {
+        for (i = 0; i < n; ++i) p[i * m + j] = r[i * m + j];
+        restart[j] = 0;
+      } else {
+        beta = (c[j] / rho_old[j]) * (alpha[j] / omega[j]);
+        for (i = 0; i < n; ++i)
+          p[i * m + j] = r[i * m + j] + beta * (p[i * m + j] - omega[j] * v[i * m + j]);
+      }
+      rho_old[j] = c[j];
+    }
+    if ((rc = vcycle(h, 0, m, p, ph)) != ORC_OK) goto done;
+    spmm(A, m, ph, v);
+    coldot(n, m, rh, v, c);
+    for (j = 0; j < m; ++j) {
+      if (state[j] != 0) continue;
+      if (c[j] == 0.0 || !isfinite(c[j])) { state[j] = 3; continue; }
+      alpha[j] = rho_old[j] / c[j];
+      for (i = 0; i < n; ++i) s[i * m + j] = r[i * m + j] - alpha[j] * v[i * m + j];
+    }
+    coldot(n, m, s, s, c);
+    any = 0;
+    for (j = 0; j < m; ++j) {
+      if (state[j] != 0) continue;
+      iters[j] = k;
+      if (sqrt(c[j]) <= tol * nb[j]) {            /* converged at the half step */
+        for (i = 0; i < n; ++i) {
+          x[i * m + j] = x[i * m + j] + alpha[j] * ph[i * m + j];
+          r[i * m + j] = s[i * m + j];
+        }
+        state[j] = 1;
+      } else any = 1;
+    }
+    if (any) {
+      if ((rc = vcycle(h, 0, m, s, sh)) != ORC_OK) goto done;
+      spmm(A, m, sh, t);
+      coldot(n, m, t, s, c);
+      coldot(n, m, t, t, c2);
+      for (j = 0; j < m; ++j) {
+        if (state[j] != 0) continue;
+        if (c2[j] == 0.0 || c[j] == 0.0 || !isfinite(c[j] / c2[j])) { state[j] = 3; continue; }
+        omega[j] = c[j] / c2[j];
+        for (i = 0; i < n; ++i) {
+          x[i * m + j] = x[i * m + j] + alpha[j] * ph[i * m + j] + omega[j] * sh[i * m + j];
+          r[i * m + j] = s[i * m + j] - omega[j] * t[i * m + j];
+        }
+      }
+      coldot(n, m, r, r, c);
+      for (j = 0; j < m; ++j)
+        if (state[j] == 0 && sqrt(c[j]) <= tol * nb[j]) state[j] = 1;
+    }
+    any = 0;
+    for (j = 0; j < m; ++j) any |= (state[j] == 0);
+    if (!any) {
+      if (confirm(A, m, b, x, r, t, tn, nb, tol, state, restart) == 0) break;
+      for (j = 0; j < m; ++j)          /* restarted columns take rhat = r */
+        if (state[j] == 0 && restart[j])
+          for (i = 0; i < n; ++i) rh[i * m + j] = r[i * m + j];
+    }
+  }
+  true_resnorm(A, m, b, x, t, tn);
+  rc = ORC_OK;
+  for (j = 0; j < m; ++j) {
+    relres[j] = nb[j] > 0.0 ? tn[j] / nb[j] : 0.0;
+    if (state[j] == 4) status[j] = COL_CONVERGED;
+    else if (state[j] == 3) status[j] = COL_BREAKDOWN;
+    else status[j] = relres[j] <= tol ? COL_CONVERGED : COL_NOT_CONVERGED;
+    if (status[j] == COL_BREAKDOWN) rc = ORC_BREAKDOWN;
+    else if (status[j] == COL_NOT_CONVERGED && rc == ORC_OK) rc = ORC_NOT_CONVERGED;
+  }
+done:
+  free(r); free(rh); free(p); free(v); free(s); free(t); free(ph); free(sh);
+  free(nb); free(rho_old); free(alpha); free(omega); free(c); free(c2); free(tn);
+  free(state); free(restart);
+  return rc;
+}

@@ -1,0 +1,106 @@
+"""Seeded synthetic inputs shared by the library, its tests and the benchmark.
+
+This module only *generates problems*: the sparse matrices of the paper's test
+systems and the random right-hand sides.  It holds none of the solver's
+arithmetic (no setup, smoothing, Krylov or multigrid step), so both the CUDA
+path and the CPU oracle can take their inputs from it.
+
+Matrices (paper Sec. 3, "Example case": the 3D Poisson equation on a cube,
+7-point stencil):
+  * ``poisson7(N)``: A = -Delta_h on an N^3 grid, unit spacing without the h^2
+    factor, Dirichlet boundary nodes eliminated (their couplings are simply
+    absent), diagonal 6, off-diagonals -1.  The sign makes A symmetric positive
+    definite, which CG needs.  Ordering is lexicographic, row index
+    i + N j + N^2 k with i fastest.
+  * ``poisson27(N)``: the 27-point analogue, diagonal 26, all 26 neighbours -1.
+
+Right-hand sides: entries i.i.d. uniform[-1, 1) from numpy's
+``default_rng(seed)``, n x m row-major (C order).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class CSR:
+    """A square sparse matrix in CSR form: int32 row pointers and column
+    indices (ascending within each row, diagonal included), float64 values."""
+
+    n: int
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+
+def _stencil(N: int, offsets, diag: float) -> CSR:
+    if N < 1:
+        raise ValueError("grid edge N must be >= 1")
+    n = N * N * N
+    idx = np.arange(n, dtype=np.int64)
+    i = idx % N
+    j = (idx // N) % N
+    k = idx // (N * N)
+    cols = np.empty((n, len(offsets)), dtype=np.int32)
+    valid = np.empty((n, len(offsets)), dtype=bool)
+    vals = np.empty((n, len(offsets)), dtype=np.float64)
+    for t, (dk, dj, di) in enumerate(offsets):
+        ok = ((i + di >= 0) & (i + di < N) & (j + dj >= 0) & (j + dj < N)
+              & (k + dk >= 0) & (k + dk < N))
+        cols[:, t] = (idx + di + N * dj + N * N * dk).astype(np.int32)
+        valid[:, t] = ok
+        vals[:, t] = diag if (dk, dj, di) == (0, 0, 0) else -1.0
+    counts = valid.sum(axis=1)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    if rowptr[-1] >= 2**31:
+        raise ValueError("nnz does not fit int32")
+    col = cols[valid]
+    val = vals[valid]
+    return CSR(n, rowptr.astype(np.int32), np.ascontiguousarray(col, dtype=np.int32),
+               np.ascontiguousarray(val, dtype=np.float64))
+
+
+def poisson7(N: int) -> CSR:
+    """7-point -Laplacian on an N^3 grid (Dirichlet nodes eliminated)."""
+    offs = [(-1, 0, 0), (0, -1, 0), (0, 0, -1), (0, 0, 0), (0, 0, 1), (0, 1, 0), (1, 0, 0)]
+    return _stencil(N, offs, 6.0)
+
+
+def poisson27(N: int) -> CSR:
+    """27-point Laplacian on an N^3 grid (Dirichlet nodes eliminated)."""
+    offs = [(dk, dj, di) for dk in (-1, 0, 1) for dj in (-1, 0, 1) for di in (-1, 0, 1)]
+    return _stencil(N, offs, 26.0)
+
+
+def rhs_uniform(n: int, m: int, seed: int = 0, m_draw: int | None = None) -> np.ndarray:
+    """n x m row-major block with entries i.i.d. uniform[-1, 1).
+
+    With ``m_draw`` the generator draws an n x m_draw block and the first m
+    columns are returned, so an m-sweep shares its columns across m."""
+    md = m if m_draw is None else m_draw
+    if m > md:
+        raise ValueError("m > m_draw")
+    B = np.random.default_rng(seed).uniform(-1.0, 1.0, size=(n, md))
+    return np.ascontiguousarray(B[:, :m])
+
+
+def csr_from_dense(A: np.ndarray) -> CSR:
+    """CSR of a dense square matrix, keeping its nonzeros and its diagonal."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    mask = (A != 0.0) | np.eye(n, dtype=bool)
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum(mask.sum(axis=1))
+    rows, cols = np.nonzero(mask)
+    return CSR(n, rowptr, cols.astype(np.int32), A[rows, cols].astype(np.float64))
+
+
+def grid_n(N: int) -> int:
+    return N * N * N
