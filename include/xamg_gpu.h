@@ -1,0 +1,249 @@
+/*
+ * xamg_gpu.h -- C ABI of the GB300 (sm_103a) solve-phase library for sparse
+ * systems A X = B with m right-hand sides (paper Sec. 1: A is n x n, X and B
+ * are n x m with m << n).
+ *
+ * The library builds a classical algebraic-multigrid hierarchy once on the
+ * host (the paper's MultiGrid setup, Sec. 2.3) and then runs the solve phase
+ * on one GPU: multi-column sparse products (the paper's "blas2" group,
+ * Sec. 2.2-2.3), Chebyshev smoothing, restriction, prolongation, the
+ * coarsest direct solve and the PCG / BiCGStab Krylov loops (Sec. 2.1,
+ * Tab. 1) with per-column status flags.
+ *
+ * Conventions shared by every entry point:
+ *   - Blocks of m columns are stored n x m ROW-MAJOR: element (i, j) of X is
+ *     X[i*m + j] (the columns of one row are adjacent).
+ *   - Return value 0 = success; negative = error (nothing usable written);
+ *     positive = numerical outcome of a solve (results written).
+ *   - "device" pointers are CUDA global-memory addresses on the current
+ *     device (e.g. from torch.empty(..., device="cuda").data_ptr()); "host"
+ *     pointers are ordinary process memory.  Pointers named const are only
+ *     read.  The library never frees memory it did not allocate.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Every entry point that takes a stream enqueues its
+ *     device work there and returns only after that work has finished.
+ *   - Input and output blocks of one call must not overlap.
+ *   - The handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef XAMG_GPU_H
+#define XAMG_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define XAMG_OK 0
+#define XAMG_ERR_INVALID_ARG (-1) /* bad size, pointer, layout or option       */
+#define XAMG_ERR_CUDA (-2)        /* a CUDA runtime call failed                 */
+#define XAMG_ERR_OOM (-3)         /* host or device allocation failed           */
+#define XAMG_ERR_NONFINITE (-4)   /* NaN or Inf in the matrix or in B           */
+#define XAMG_ERR_TIMEOUT (-5)     /* a bounded device wait ran out              */
+#define XAMG_ERR_SETUP (-6)       /* hierarchy could not be built (zero pivot,
+                                     zero diagonal, coarsest level too large)   */
+#define XAMG_NOT_CONVERGED 1      /* some column missed tol within maxit        */
+#define XAMG_BREAKDOWN 2          /* some column hit a Krylov breakdown         */
+
+/* per-column status written to xamg_stats.status[j] */
+#define XAMG_COL_CONVERGED 0
+#define XAMG_COL_NOT_CONVERGED 1
+#define XAMG_COL_BREAKDOWN 2
+
+/* solver methods (paper Tab. 1: CG and BiCGStab as solvers, MultiGrid as
+ * preconditioner, Chebyshev as pre-/post-smoother, Direct on the coarsest
+ * level) */
+#define XAMG_PCG 0
+#define XAMG_BICGSTAB 1
+
+/* largest m accepted by the solve entry points */
+#define XAMG_MAX_RHS 32
+
+typedef struct xamg_hier xamg_hier; /* opaque, owned by the library */
+
+/* A square sparse matrix in CSR form in HOST memory, read-only, owned by the
+ * caller: rowptr[n+1] (rowptr[0] = 0, non-decreasing), col[nnz] strictly
+ * ascending within each row and in [0, n), val[nnz].  Each row must hold a
+ * nonzero diagonal entry. */
+typedef struct {
+  int32_t n;
+  int64_t nnz;
+  const int32_t *rowptr;
+  const int32_t *col;
+  const double *val;
+} xamg_csr;
+
+/* AMG setup parameters (fill with xamg_amg_params_default first).
+ *   theta         strength threshold of classical Ruge-Stueben coarsening (0.25)
+ *   max_coarse    a level with at most this many rows is the coarsest (64)
+ *   max_levels    hard cap on the number of levels (25)
+ *   cheb_steps    Chebyshev recurrence steps per smoothing = polynomial
+ *                 order (2; paper Fig. 3 "polynomial_order 2"), in [1, 4]
+ *   power_iters   power iterations for the largest eigenvalue of D^-1 A (20)
+ *   cheb_lo_frac  lower end of the Chebyshev interval as a fraction of the
+ *                 upper end (0.3)
+ *   cheb_hi_safety  factor on the power-iteration estimate (1.1); the upper
+ *                 end is min(cheb_hi_safety * estimate, Gershgorin bound)
+ *   max_dense     largest coarsest level accepted for the dense LU (1024)
+ *   nthreads      host threads for the setup (0 = all hardware threads)
+ *   device_upload 1 (default): upload the hierarchy to the current CUDA
+ *                 device; 0: build the host-side hierarchy only (no CUDA
+ *                 call is made; only the xamg_*info / xamg_level_export
+ *                 entry points accept such a handle) */
+typedef struct {
+  double theta;
+  int32_t max_coarse;
+  int32_t max_levels;
+  int32_t cheb_steps;
+  int32_t power_iters;
+  double cheb_lo_frac;
+  double cheb_hi_safety;
+  int32_t max_dense;
+  int32_t nthreads;
+  int32_t device_upload;
+} xamg_amg_params;
+
+/* Solve options (fill with xamg_solve_opts_default first).
+ *   method       XAMG_PCG or XAMG_BICGSTAB
+ *   stream       cudaStream_t as void*, NULL = legacy default stream
+ *   workspace    optional caller-owned DEVICE buffer of workspace_bytes bytes
+ *                (at least xamg_workspace_bytes(); 256-byte aligned); NULL
+ *                makes the library allocate and cache one inside the handle
+ *   workspace_bytes  size of `workspace` */
+typedef struct {
+  int32_t method;
+  void *stream;
+  void *workspace;
+  size_t workspace_bytes;
+} xamg_solve_opts;
+
+/* Per-solve statistics (paper Fig. 2, "solver->stats").  The three arrays are
+ * caller-owned HOST arrays of length m; any of them may be NULL.
+ *   iters[j]   Krylov iterations of column j (one preconditioner application
+ *              per PCG iteration, two per BiCGStab iteration)
+ *   relres[j]  true relative residual ||b_j - A x_j|| / ||b_j|| at exit
+ *              (0 for a zero column)
+ *   status[j]  XAMG_COL_* code
+ *   iterations total loop iterations the call ran (max over columns)
+ *   vcycles    preconditioner applications the call ran */
+typedef struct {
+  int32_t *iters;
+  double *relres;
+  int32_t *status;
+  int32_t iterations;
+  int32_t vcycles;
+} xamg_stats;
+
+/* Human-readable text for a status code (static storage). */
+const char *xamg_strerror(int code);
+
+void xamg_amg_params_default(xamg_amg_params *p);
+void xamg_solve_opts_default(xamg_solve_opts *o);
+
+/* Builds the AMG hierarchy of A on the host (classical Ruge-Stueben
+ * coarsening, classical interpolation, Galerkin R A P with R = P^T, Chebyshev
+ * interval per level, dense LU of the coarsest level; paper Sec. 2.3: the
+ * MultiGrid setup()) and uploads it to the current CUDA device.  A is read
+ * only during the call.  On success *out holds a new handle owned by the
+ * caller, to be released with xamg_destroy.  Errors: INVALID_ARG (bad CSR,
+ * missing diagonal), NONFINITE, SETUP, OOM, CUDA. */
+int xamg_setup_hierarchy(const xamg_csr *A, const xamg_amg_params *p, xamg_hier **out);
+
+/* Releases the handle and every device buffer it owns.  NULL is accepted. */
+int xamg_destroy(xamg_hier *h);
+
+/* Number of levels and the row count, nnz of A, nnz of P of level `level`
+ * (nnz_p = 0 on the coarsest level).  Any output pointer may be NULL. */
+int xamg_hier_info(const xamg_hier *h, int32_t *levels, double *op_complexity);
+int xamg_level_info(const xamg_hier *h, int32_t level, int32_t *n, int64_t *nnz_a,
+                    int64_t *nnz_p);
+
+/* Copies the host-side setup results of one level into caller-owned HOST
+ * arrays (any may be NULL): rowptr[n+1], col[nnz_a], val[nnz_a] of A;
+ * p_rowptr[n+1], p_col[nnz_p], p_val[nnz_p] of P; cf[n] (1 = coarse point);
+ * cheb[4] = {lower, upper, power estimate, Gershgorin bound}. */
+int xamg_level_export(const xamg_hier *h, int32_t level, int32_t *rowptr, int32_t *col,
+                      double *val, int32_t *p_rowptr, int32_t *p_col, double *p_val,
+                      int32_t *cf, double *cheb);
+
+/* Copies the coarsest level's dense LU factors (row-major nc x nc, unit lower
+ * L below the diagonal, U on and above it) and pivot rows (row k was swapped
+ * with row piv[k]) into caller-owned HOST arrays; *nc receives the size. */
+int xamg_coarse_export(const xamg_hier *h, int32_t *nc, double *lu, int32_t *piv);
+
+/* Bytes of device workspace a solve of m columns with `method` needs. */
+int xamg_workspace_bytes(const xamg_hier *h, int32_t m, int32_t method, size_t *bytes);
+
+/* Solves A X = B to ||b_j - A x_j|| <= tol ||b_j|| for every column
+ * (paper Sec. 1 and 2.1; PCG or BiCGStab preconditioned by one V(1,1)
+ * Chebyshev cycle, paper Fig. 3).  B and X are DEVICE n x m row-major
+ * blocks, 1 <= m <= XAMG_MAX_RHS, caller-owned; X0 = 0.  Each column stops
+ * on its own (status flags); X always holds the last iterate.  Returns 0 when
+ * every column converged, XAMG_NOT_CONVERGED / XAMG_BREAKDOWN otherwise, or
+ * a negative error (NONFINITE if B holds NaN/Inf: X is then untouched).
+ * `stats` may be NULL. */
+int xamg_solve(xamg_hier *h, const double *B, double *X, int32_t m, double tol, int32_t maxit,
+               const xamg_solve_opts *opts, xamg_stats *stats);
+
+/* As xamg_solve with B and X in HOST memory: the call copies B to the device,
+ * solves, and copies X back, all on opts->stream. */
+int xamg_solve_host(xamg_hier *h, const double *B, double *X, int32_t m, double tol,
+                    int32_t maxit, const xamg_solve_opts *opts, xamg_stats *stats);
+
+/* ---- single steps of the solve phase, for testing and measurement ---- */
+
+/* Y = M X on level `level` for M = A (which = 0), P (which = 1, level <
+ * levels-1, X has n_{level+1} rows) or R = P^T (which = 2, Y has n_{level+1}
+ * rows): the multi-column sparse product of paper Sec. 2.2.  X, Y: DEVICE
+ * row-major blocks with m columns, 1 <= m <= XAMG_MAX_RHS. */
+int xamg_level_spmm(xamg_hier *h, int32_t level, int32_t which, const double *X, double *Y,
+                    int32_t m, void *stream);
+
+/* Chebyshev smoothing on level `level` (< levels-1): cheb_steps steps on X
+ * for right-hand side B.  x_zero = 1 takes X = 0 on entry (pre-smoothing)
+ * and then, if R is not NULL, writes the residual B - A X after the last
+ * step to R; x_zero = 0 smooths the given X (post-smoothing; R must be
+ * NULL).  DEVICE row-major blocks with m columns. */
+int xamg_smooth(xamg_hier *h, int32_t level, const double *B, double *X, double *R,
+                int32_t x_zero, int32_t m, void *stream);
+
+/* One V(1,1) cycle from X = 0 for right-hand side B (the preconditioner
+ * application z = M^-1 r of paper Fig. 3, MultiGrid with max_iters 1).
+ * DEVICE row-major blocks n x m. */
+int xamg_vcycle(xamg_hier *h, const double *B, double *X, int32_t m, void *stream);
+
+/* Coarsest-level direct solve X = A_L^-1 B with the LU factors of the setup
+ * (paper Tab. 1, Direct).  DEVICE row-major blocks n_L x m. */
+int xamg_coarse_solve(xamg_hier *h, const double *B, double *X, int32_t m, void *stream);
+
+/* Column dot products out[j] = sum_i U[i*m + j] * V[i*m + j] of two DEVICE
+ * n x m row-major blocks (the paper's "blas" dot products, Sec. 2.3), into the
+ * DEVICE array out[m].  The sum is reduced in a fixed order, so repeated
+ * calls give identical bits.  Allocates (and frees) its own device scratch
+ * for the per-block partial sums. */
+int xamg_coldot(const double *U, const double *V, int64_t n, int32_t m, double *out,
+                void *stream);
+
+/* ---- measurement ---- */
+
+/* Turns per-launch timing of the sparse row kernels on (1) or off (0).  When
+ * on, every launch of a row kernel (the fused SpMM-based steps) is bracketed
+ * by CUDA events on the launching stream; the results are accumulated per
+ * (level, operator) when the enclosing call finishes.  Off by default. */
+int xamg_timing_enable(xamg_hier *h, int32_t enable);
+
+/* Reads and clears nothing: launches and total device milliseconds of the
+ * timed row-kernel launches on `level` for operator `which` (0 = A, 1 = P,
+ * 2 = R) since timing was last enabled, plus the algorithmic flops and bytes
+ * of those launches (flops = 2 nnz m_padded; bytes = 12 nnz + 4 (rows+1) +
+ * 8 (cols_in + rows) m_padded per product plus the epilogue's block reads and
+ * writes).  Output pointers may be NULL. */
+int xamg_timing_read(const xamg_hier *h, int32_t level, int32_t which, int64_t *launches,
+                     double *total_ms, double *flops, double *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XAMG_GPU_H */

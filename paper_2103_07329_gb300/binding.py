@@ -1,0 +1,321 @@
+"""Thin ctypes binding of the C ABI in ``include/xamg_gpu.h``.
+
+Argument marshalling only: every step of the solve phase runs in the CUDA
+library.  Device blocks are passed as torch CUDA tensors (float64,
+contiguous, n x m row-major); streams as ``torch.cuda.Stream`` or raw handles.
+If the compiled library is missing this module raises at import time instead
+of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CUDA = -2
+ERR_OOM = -3
+ERR_NONFINITE = -4
+ERR_TIMEOUT = -5
+ERR_SETUP = -6
+NOT_CONVERGED = 1
+BREAKDOWN = 2
+PCG = 0
+BICGSTAB = 1
+MAX_RHS = 32
+
+# every entry point declared in include/xamg_gpu.h
+EXPORTS = [
+    "xamg_strerror", "xamg_amg_params_default", "xamg_solve_opts_default",
+    "xamg_setup_hierarchy", "xamg_destroy", "xamg_hier_info", "xamg_level_info",
+    "xamg_level_export", "xamg_coarse_export", "xamg_workspace_bytes", "xamg_solve",
+    "xamg_solve_host", "xamg_level_spmm", "xamg_smooth", "xamg_vcycle", "xamg_coarse_solve",
+    "xamg_coldot", "xamg_timing_enable", "xamg_timing_read",
+]
+
+
+class XamgError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class CsrT(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class AmgParamsT(C.Structure):
+    _fields_ = [("theta", C.c_double), ("max_coarse", C.c_int32), ("max_levels", C.c_int32),
+                ("cheb_steps", C.c_int32), ("power_iters", C.c_int32),
+                ("cheb_lo_frac", C.c_double), ("cheb_hi_safety", C.c_double),
+                ("max_dense", C.c_int32), ("nthreads", C.c_int32), ("device_upload", C.c_int32)]
+
+
+class SolveOptsT(C.Structure):
+    _fields_ = [("method", C.c_int32), ("stream", C.c_void_p), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_size_t)]
+
+
+class StatsT(C.Structure):
+    _fields_ = [("iters", C.c_void_p), ("relres", C.c_void_p), ("status", C.c_void_p),
+                ("iterations", C.c_int32), ("vcycles", C.c_int32)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library {LIB_PATH} is not built; run "
+                          "`python -m paper_2103_07329_gb300.build` (nvcc, sm_103a)")
+    try:  # let the library share torch's CUDA runtime when torch is present
+        import torch  # noqa: F401
+    except Exception:
+        pass
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "xamg_strerror": ([C.c_int], C.c_char_p),
+        "xamg_amg_params_default": ([C.POINTER(AmgParamsT)], None),
+        "xamg_solve_opts_default": ([C.POINTER(SolveOptsT)], None),
+        "xamg_setup_hierarchy": ([C.POINTER(CsrT), C.POINTER(AmgParamsT), C.POINTER(vp)], C.c_int),
+        "xamg_destroy": ([vp], C.c_int),
+        "xamg_hier_info": ([vp, C.POINTER(i32), C.POINTER(dbl)], C.c_int),
+        "xamg_level_info": ([vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64)], C.c_int),
+        "xamg_level_export": ([vp, i32, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
+        "xamg_coarse_export": ([vp, C.POINTER(i32), vp, vp], C.c_int),
+        "xamg_workspace_bytes": ([vp, i32, i32, C.POINTER(C.c_size_t)], C.c_int),
+        "xamg_solve": ([vp, vp, vp, i32, dbl, i32, C.POINTER(SolveOptsT), C.POINTER(StatsT)], C.c_int),
+        "xamg_solve_host": ([vp, vp, vp, i32, dbl, i32, C.POINTER(SolveOptsT), C.POINTER(StatsT)],
+                            C.c_int),
+        "xamg_level_spmm": ([vp, i32, i32, vp, vp, i32, vp], C.c_int),
+        "xamg_smooth": ([vp, i32, vp, vp, vp, i32, i32, vp], C.c_int),
+        "xamg_vcycle": ([vp, vp, vp, i32, vp], C.c_int),
+        "xamg_coarse_solve": ([vp, vp, vp, i32, vp], C.c_int),
+        "xamg_coldot": ([vp, vp, i64, i32, vp, vp], C.c_int),
+        "xamg_timing_enable": ([vp, i32], C.c_int),
+        "xamg_timing_read": ([vp, i32, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl),
+                              C.POINTER(dbl)], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def lib():
+    return _load()
+
+
+def strerror(code: int) -> str:
+    return _load().xamg_strerror(code).decode()
+
+
+def _check(rc: int, what: str, allow_positive=False) -> int:
+    if rc < 0 or (rc > 0 and not allow_positive):
+        raise XamgError(rc, what)
+    return rc
+
+
+def _ptr(t) -> int:
+    """Device address of a torch CUDA tensor (float64, contiguous) or an int."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def amg_params(**kw) -> AmgParamsT:
+    p = AmgParamsT()
+    _load().xamg_amg_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown AMG parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+class SolveStats:
+    def __init__(self, m):
+        self.iters = np.zeros(m, np.int32)
+        self.relres = np.zeros(m, np.float64)
+        self.status = np.zeros(m, np.int32)
+        self.iterations = 0
+        self.vcycles = 0
+        self.rc = 0
+
+    def struct(self) -> StatsT:
+        return StatsT(self.iters.ctypes.data, self.relres.ctypes.data, self.status.ctypes.data, 0, 0)
+
+
+class Hierarchy:
+    """Handle on the library's frozen AMG hierarchy (``xamg_setup_hierarchy``)."""
+
+    def __init__(self, A, **params):
+        L = _load()
+        self._keep = (np.ascontiguousarray(A.rowptr, np.int32), np.ascontiguousarray(A.col, np.int32),
+                      np.ascontiguousarray(A.val, np.float64))
+        rp, ci, v = self._keep
+        csr = CsrT(A.n, int(rp[-1]), rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+        prm = amg_params(**params)
+        h = C.c_void_p()
+        rc = L.xamg_setup_hierarchy(C.byref(csr), C.byref(prm), C.byref(h))
+        self._keep = None
+        _check(rc, "xamg_setup_hierarchy")
+        self._h = h
+        self.n = A.n
+        self.on_device = bool(prm.device_upload)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().xamg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def levels(self) -> int:
+        n = C.c_int32()
+        _check(_load().xamg_hier_info(self._h, C.byref(n), None), "xamg_hier_info")
+        return n.value
+
+    @property
+    def op_complexity(self) -> float:
+        oc = C.c_double()
+        _check(_load().xamg_hier_info(self._h, None, C.byref(oc)), "xamg_hier_info")
+        return oc.value
+
+    def level_info(self, l: int):
+        n = C.c_int32(); na = C.c_int64(); npn = C.c_int64()
+        _check(_load().xamg_level_info(self._h, l, C.byref(n), C.byref(na), C.byref(npn)),
+               "xamg_level_info")
+        return n.value, na.value, npn.value
+
+    def level_export(self, l: int):
+        n, na, npn = self.level_info(l)
+        rp = np.empty(n + 1, np.int32); ci = np.empty(max(na, 1), np.int32); v = np.empty(max(na, 1))
+        prp = np.empty(n + 1, np.int32); pci = np.empty(max(npn, 1), np.int32)
+        pv = np.empty(max(npn, 1)); cf = np.zeros(n, np.int32); ch = np.empty(4)
+        _check(_load().xamg_level_export(self._h, l, rp.ctypes.data, ci.ctypes.data, v.ctypes.data,
+                                         prp.ctypes.data, pci.ctypes.data, pv.ctypes.data,
+                                         cf.ctypes.data, ch.ctypes.data), "xamg_level_export")
+        last = l + 1 == self.levels
+        return dict(n=n, A=(rp, ci[:na], v[:na]),
+                    P=None if last else (prp, pci[:npn], pv[:npn]),
+                    cf=None if last else cf, cheb=None if last else ch)
+
+    def coarse_export(self):
+        nc = C.c_int32()
+        _check(_load().xamg_coarse_export(self._h, C.byref(nc), None, None), "xamg_coarse_export")
+        lu = np.empty(nc.value * nc.value); piv = np.empty(nc.value, np.int32)
+        _check(_load().xamg_coarse_export(self._h, C.byref(nc), lu.ctypes.data, piv.ctypes.data),
+               "xamg_coarse_export")
+        return lu.reshape(nc.value, nc.value), piv
+
+    def workspace_bytes(self, m: int, method: int = PCG) -> int:
+        b = C.c_size_t()
+        _check(_load().xamg_workspace_bytes(self._h, m, method, C.byref(b)), "xamg_workspace_bytes")
+        return b.value
+
+    def _opts(self, method, stream, workspace):
+        o = SolveOptsT()
+        _load().xamg_solve_opts_default(C.byref(o))
+        o.method = method
+        o.stream = _stream(stream)
+        if workspace is not None:
+            o.workspace = _ptr(workspace)
+            o.workspace_bytes = workspace.numel() * workspace.element_size()
+        return o
+
+    def solve(self, B, X, tol=1e-8, maxit=200, method=PCG, stream=None, workspace=None) -> SolveStats:
+        """xamg_solve on device blocks B, X (torch float64 CUDA tensors, n x m)."""
+        m = B.shape[1] if B.dim() == 2 else 1
+        st = SolveStats(m)
+        s = st.struct()
+        o = self._opts(method, stream, workspace)
+        rc = _load().xamg_solve(self._h, _ptr(B), _ptr(X), m, tol, maxit, C.byref(o), C.byref(s))
+        _check(rc, "xamg_solve", allow_positive=True)
+        st.iterations, st.vcycles, st.rc = s.iterations, s.vcycles, rc
+        return st
+
+    def solve_host(self, B: np.ndarray, X: np.ndarray, tol=1e-8, maxit=200, method=PCG,
+                   stream=None) -> SolveStats:
+        """xamg_solve_host on host arrays (float64, C order, n x m)."""
+        assert B.flags.c_contiguous and X.flags.c_contiguous and B.dtype == np.float64
+        m = B.shape[1]
+        st = SolveStats(m)
+        s = st.struct()
+        o = self._opts(method, stream, None)
+        rc = _load().xamg_solve_host(self._h, B.ctypes.data, X.ctypes.data, m, tol, maxit,
+                                     C.byref(o), C.byref(s))
+        _check(rc, "xamg_solve_host", allow_positive=True)
+        st.iterations, st.vcycles, st.rc = s.iterations, s.vcycles, rc
+        return st
+
+    def spmm(self, level: int, which: int, X, Y, stream=None):
+        m = X.shape[1]
+        _check(_load().xamg_level_spmm(self._h, level, which, _ptr(X), _ptr(Y), m, _stream(stream)),
+               "xamg_level_spmm")
+
+    def smooth(self, level: int, B, X, R=None, x_zero=True, stream=None):
+        m = B.shape[1]
+        _check(_load().xamg_smooth(self._h, level, _ptr(B), _ptr(X), _ptr(R), 1 if x_zero else 0, m,
+                                   _stream(stream)), "xamg_smooth")
+
+    def vcycle(self, B, X, stream=None):
+        _check(_load().xamg_vcycle(self._h, _ptr(B), _ptr(X), B.shape[1], _stream(stream)),
+               "xamg_vcycle")
+
+    def coarse_solve(self, B, X, stream=None):
+        _check(_load().xamg_coarse_solve(self._h, _ptr(B), _ptr(X), B.shape[1], _stream(stream)),
+               "xamg_coarse_solve")
+
+    def timing_enable(self, on: bool = True):
+        _check(_load().xamg_timing_enable(self._h, 1 if on else 0), "xamg_timing_enable")
+
+    def timing_read(self, level: int, which: int):
+        n = C.c_int64(); ms = C.c_double(); fl = C.c_double(); by = C.c_double()
+        _check(_load().xamg_timing_read(self._h, level, which, C.byref(n), C.byref(ms), C.byref(fl),
+                                        C.byref(by)), "xamg_timing_read")
+        return dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value)
+
+
+def coldot(U, V, out, stream=None):
+    """xamg_coldot: out[j] = sum_i U[i, j] V[i, j] on device tensors."""
+    n, m = U.shape
+    _check(_load().xamg_coldot(_ptr(U), _ptr(V), n, m, _ptr(out), _stream(stream)), "xamg_coldot")

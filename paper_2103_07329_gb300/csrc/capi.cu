@@ -1,0 +1,974 @@
+// capi.cu -- the library's C entry points: device upload of the hierarchy, the
+// V(1,1) Chebyshev cycle, the PCG and BiCGStab drivers and the single-step
+// entry points.  Declarations and contracts: include/xamg_gpu.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hier_host.h"
+#include "launch.h"
+
+using namespace xamg;
+
+namespace {
+
+struct DevCsr {
+  int n = 0, ncols = 0;
+  int64_t nnz = 0;
+  int32_t *rowptr = nullptr;
+  int32_t *col = nullptr;
+  double *val = nullptr;
+};
+
+struct DevLevel {
+  DevCsr A, P, R;
+  double *w[4] = {nullptr, nullptr, nullptr, nullptr};  // Chebyshev row weights per step
+  double c1[4] = {0, 0, 0, 0};                          // Chebyshev step coefficients
+};
+
+struct TimerRec {
+  cudaEvent_t a, b;
+  int level, which;
+  double flops, bytes;
+};
+
+struct TimeAcc {
+  int64_t launches = 0;
+  double ms = 0, flops = 0, bytes = 0;
+};
+
+// Device blocks of one solve (n x nv row-major unless noted).
+struct Work {
+  int nv = 0;
+  double *Bn = nullptr, *X = nullptr, *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr;
+  double *RH = nullptr, *V = nullptr, *S = nullptr, *T = nullptr, *PH = nullptr, *SH = nullptr;
+  std::vector<double *> vb, vx, vr, vd, vd2;  // V-cycle blocks per level
+  double *part[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  ColState *cs = nullptr;
+};
+
+}  // namespace
+
+struct xamg_hier {
+  HostHier host;
+  xamg_amg_params prm{};
+  bool on_device = false;
+  int device = 0;
+  std::vector<DevLevel> lv;
+  double *lu = nullptr;
+  int32_t *piv = nullptr;
+  std::vector<void *> owned;  // device allocations of the hierarchy
+  void *ws = nullptr;         // cached solve workspace
+  size_t ws_bytes = 0;
+  double *hb = nullptr;       // staging blocks of xamg_solve_host
+  size_t hb_bytes = 0;
+  Flags *flags_h = nullptr;   // mapped pinned counters
+  Flags *flags_d = nullptr;
+  bool timing = false;
+  std::vector<TimerRec> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<TimeAcc> tacc;  // [level * 3 + which]
+};
+
+namespace {
+
+#define XCK(call)                              \
+  do {                                         \
+    cudaError_t e__ = (call);                  \
+    if (e__ != cudaSuccess) {                  \
+      return e__ == cudaErrorMemoryAllocation ? XAMG_ERR_OOM : XAMG_ERR_CUDA; \
+    }                                          \
+  } while (0)
+
+int pad_nv(int m) {
+  int v = 1;
+  while (v < m) v <<= 1;
+  return v;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <class T>
+int dev_upload(xamg_hier *h, T **dst, const T *src, size_t count) {
+  *dst = nullptr;
+  if (count == 0) return XAMG_OK;
+  void *p = nullptr;
+  XCK(cudaMalloc(&p, count * sizeof(T)));
+  h->owned.push_back(p);
+  XCK(cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice));
+  *dst = (T *)p;
+  return XAMG_OK;
+}
+
+int upload_csr(xamg_hier *h, const HostCsr &a, DevCsr &d) {
+  d.n = a.n;
+  d.ncols = a.ncols;
+  d.nnz = a.nnz();
+  int rc;
+  if ((rc = dev_upload(h, &d.rowptr, a.rowptr.data(), a.rowptr.size())) != XAMG_OK) return rc;
+  if ((rc = dev_upload(h, &d.col, a.col.data(), a.col.size())) != XAMG_OK) return rc;
+  return dev_upload(h, &d.val, a.val.data(), a.val.size());
+}
+
+// Chebyshev coefficients of level l (interval [lo, hi] of D^-1 A):
+//   theta = (hi+lo)/2, delta = (hi-lo)/2, sigma = theta/delta, rho_0 = 1/sigma
+//   step 0: d_0 = (D^-1 / theta) r_0
+//   step k: rho_k = 1/(2 sigma - rho_{k-1}), d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k/delta) D^-1 r_k
+int upload_level(xamg_hier *h, int l) {
+  const HostLevel &H = h->host.lv[l];
+  DevLevel &D = h->lv[l];
+  int rc;
+  if ((rc = upload_csr(h, H.A, D.A)) != XAMG_OK) return rc;
+  const bool coarsest = l + 1 == (int)h->host.lv.size();
+  if (coarsest) return XAMG_OK;
+  if ((rc = upload_csr(h, H.P, D.P)) != XAMG_OK) return rc;
+  if ((rc = upload_csr(h, H.R, D.R)) != XAMG_OK) return rc;
+  const double theta = 0.5 * (H.hi + H.lo), delta = 0.5 * (H.hi - H.lo), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  std::vector<double> w(H.dinv.size());
+  for (int k = 0; k < h->host.cheb_steps; ++k) {
+    double coef;
+    if (k == 0) {
+      coef = 1.0 / theta;
+      D.c1[0] = 0.0;
+    } else {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      D.c1[k] = rn * rho;
+      coef = 2.0 * rn / delta;
+      rho = rn;
+    }
+    for (size_t i = 0; i < w.size(); ++i) w[i] = coef * H.dinv[i];
+    if ((rc = dev_upload(h, &D.w[k], w.data(), w.size())) != XAMG_OK) return rc;
+  }
+  return XAMG_OK;
+}
+
+void free_device(xamg_hier *h) {
+  for (void *p : h->owned) cudaFree(p);
+  h->owned.clear();
+  if (h->ws) cudaFree(h->ws);
+  h->ws = nullptr;
+  h->ws_bytes = 0;
+  if (h->hb) cudaFree(h->hb);
+  h->hb = nullptr;
+  h->hb_bytes = 0;
+  if (h->flags_h) cudaFreeHost(h->flags_h);
+  h->flags_h = nullptr;
+  h->flags_d = nullptr;
+  for (auto &p : h->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  h->pending.clear();
+  for (auto e : h->event_pool) cudaEventDestroy(e);
+  h->event_pool.clear();
+}
+
+// ---- workspace ----
+size_t plan(const xamg_hier *h, int nv, int method, Work *w, char *base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char * {
+    char *p = base ? base + off : nullptr;
+    off += align256(bytes);
+    return p;
+  };
+  const size_t n0 = (size_t)h->host.lv[0].A.n;
+  const size_t blk = n0 * nv * sizeof(double);
+  Work tmp;
+  Work &W = w ? *w : tmp;
+  W.nv = nv;
+  W.Bn = (double *)take(blk);
+  W.X = (double *)take(blk);
+  W.R = (double *)take(blk);
+  W.P = (double *)take(blk);
+  if (method == XAMG_PCG) {
+    W.Z = (double *)take(blk);
+    W.Q = (double *)take(blk);
+  } else {
+    W.RH = (double *)take(blk);
+    W.V = (double *)take(blk);
+    W.S = (double *)take(blk);
+    W.T = (double *)take(blk);
+    W.PH = (double *)take(blk);
+    W.SH = (double *)take(blk);
+  }
+  const int L = (int)h->host.lv.size();
+  const bool dd = h->host.cheb_steps >= 3;
+  W.vb.assign(L, nullptr);
+  W.vx.assign(L, nullptr);
+  W.vr.assign(L, nullptr);
+  W.vd.assign(L, nullptr);
+  W.vd2.assign(L, nullptr);
+  for (int l = 0; l < L; ++l) {
+    const size_t b = (size_t)h->host.lv[l].A.n * nv * sizeof(double);
+    if (l > 0) {
+      W.vb[l] = (double *)take(b);
+      W.vx[l] = (double *)take(b);
+    }
+    if (l + 1 < L) {
+      W.vr[l] = (double *)take(b);
+      W.vd[l] = (double *)take(b);
+      if (dd) W.vd2[l] = (double *)take(b);
+    }
+  }
+  for (int i = 0; i < 5; ++i) W.part[i] = (double *)take((size_t)kMaxGrid * 32 * sizeof(double));
+  W.cs = (ColState *)take(sizeof(ColState));
+  return off;
+}
+
+int ensure_workspace(xamg_hier *h, int nv, int method, const xamg_solve_opts *o, Work &w) {
+  const size_t need = plan(h, nv, method, nullptr, nullptr);
+  char *base;
+  if (o && o->workspace) {
+    if (o->workspace_bytes < need || ((uintptr_t)o->workspace & 255)) return XAMG_ERR_INVALID_ARG;
+    base = (char *)o->workspace;
+  } else {
+    if (h->ws_bytes < need) {
+      if (h->ws) cudaFree(h->ws);
+      h->ws = nullptr;
+      h->ws_bytes = 0;
+      XCK(cudaMalloc(&h->ws, need));
+      h->ws_bytes = need;
+    }
+    base = (char *)h->ws;
+  }
+  plan(h, nv, method, &w, base);
+  return XAMG_OK;
+}
+
+// ---- timing ----
+cudaEvent_t pool_event(xamg_hier *h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void flush_timing(xamg_hier *h) {
+  for (auto &p : h->pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      TimeAcc &t = h->tacc[(size_t)p.level * 3 + p.which];
+      t.launches++;
+      t.ms += ms;
+      t.flops += p.flops;
+      t.bytes += p.bytes;
+    }
+    h->event_pool.push_back(p.a);
+    h->event_pool.push_back(p.b);
+  }
+  h->pending.clear();
+}
+
+// ---- row kernel wrapper ----
+int slices_for(const DevCsr &M, int nv) {
+  if (nv != 1 || M.n == 0) return 1;
+  const double avg = (double)M.nnz / M.n;
+  return avg >= 24.0 ? 16 : 4;
+}
+
+// Algorithmic bytes of one fused row launch: the matrix once, the operand
+// block once, and every block the epilogue reads or writes once.
+double row_bytes(const DevCsr &M, const RowOp &op, int nv) {
+  const double blk = (double)M.n * nv * 8.0;
+  double b = 12.0 * (double)M.nnz + 4.0 * (M.n + 1) + (double)M.ncols * nv * 8.0;
+  if (op.init) b += blk;
+  if (op.y) b += blk;
+  if (op.dp) b += blk;
+  if (op.w) b += (double)M.n * 8.0;
+  if (op.dnext) b += blk;
+  if (op.x) b += 2 * blk;
+  if (op.partials) b += (op.dot_u ? blk : 0);
+  return b;
+}
+
+int rows(xamg_hier *h, int level, int which, const DevCsr &M, RowOp op, int nv, bool neg,
+         cudaStream_t st) {
+  op.n = M.n;
+  op.rowptr = M.rowptr;
+  op.col = M.col;
+  op.val = M.val;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (h->timing) {
+    a = pool_event(h);
+    b = pool_event(h);
+    cudaEventRecord(a, st);
+  }
+  const int g = launch_rows(op, nv, slices_for(M, nv), neg, st);
+  if (h->timing) {
+    cudaEventRecord(b, st);
+    h->pending.push_back({a, b, level, which, 2.0 * (double)M.nnz * nv, row_bytes(M, op, nv)});
+  }
+  return g;
+}
+
+RowOp blank() {
+  RowOp o;
+  std::memset(&o, 0, sizeof(o));
+  return o;
+}
+
+// ---- V(1,1) Chebyshev cycle ----
+// On entry x holds w0 .* b (the first smoother iterate) unless `level` is the
+// coarsest.  If dot_part is set, the partial sums of dot_u . x_final are
+// written there and *dot_grid receives their block count.
+int vcycle(xamg_hier *h, Work &W, int l, const double *b, double *x, cudaStream_t st,
+           const double *dot_u, double *dot_part, int *dot_grid) {
+  const int nv = W.nv;
+  const int L = (int)h->lv.size();
+  const int s = h->host.cheb_steps;
+  if (l == L - 1) {
+    launch_coarse(nv, h->host.nc, h->lu, h->piv, b, x, st);
+    if (dot_part) {
+      const int g = elem_grid(h->host.nc, nv);
+      launch_coldot(nv, h->host.nc, dot_u, x, dot_part, g, st);
+      *dot_grid = g;
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
+  }
+  DevLevel &D = h->lv[l];
+  double *r = W.vr[l];
+  double *dA = W.vd[l], *dB = W.vd2[l];
+  // pre-smoothing from x = 0 (x already holds d_0)
+  if (s == 1) {
+    RowOp o = blank();
+    o.init = b; o.src = x; o.y = r;
+    if (rows(h, l, 0, D.A, o, nv, true, st) < 0) return XAMG_ERR_CUDA;
+  } else {
+    RowOp o = blank();
+    o.init = b; o.src = x; o.y = r; o.dp = x; o.w = D.w[1]; o.c1 = D.c1[1]; o.dnext = dA;
+    if (rows(h, l, 0, D.A, o, nv, true, st) < 0) return XAMG_ERR_CUDA;
+    double *dprev = dA, *dnext = dB;
+    for (int k = 2; k < s; ++k) {
+      RowOp m = blank();
+      m.init = r; m.src = dprev; m.y = r; m.dp = dprev; m.w = D.w[k]; m.c1 = D.c1[k];
+      m.dnext = dnext; m.x = x; m.x_dp = 1;
+      if (rows(h, l, 0, D.A, m, nv, true, st) < 0) return XAMG_ERR_CUDA;
+      std::swap(dprev, dnext);
+    }
+    RowOp f = blank();
+    f.init = r; f.src = dprev; f.y = r; f.dp = dprev; f.x = x; f.x_dp = 1;
+    if (rows(h, l, 0, D.A, f, nv, true, st) < 0) return XAMG_ERR_CUDA;
+  }
+  // restriction b_c = R r (and the coarse level's first smoother iterate)
+  {
+    const bool next_coarsest = l + 2 == L;
+    RowOp o = blank();
+    o.src = r; o.y = W.vb[l + 1];
+    if (!next_coarsest) {
+      o.w = h->lv[l + 1].w[0];
+      o.dnext = W.vx[l + 1];
+    }
+    if (rows(h, l, 2, D.R, o, nv, false, st) < 0) return XAMG_ERR_CUDA;
+  }
+  int rc = vcycle(h, W, l + 1, W.vb[l + 1], W.vx[l + 1], st, nullptr, nullptr, nullptr);
+  if (rc != XAMG_OK) return rc;
+  // prolongation and correction x += P x_c
+  {
+    RowOp o = blank();
+    o.init = x; o.src = W.vx[l + 1]; o.y = x;
+    if (rows(h, l, 1, D.P, o, nv, false, st) < 0) return XAMG_ERR_CUDA;
+  }
+  // post-smoothing from x
+  {
+    RowOp o = blank();
+    o.init = b; o.src = x; o.y = r; o.w = D.w[0]; o.dnext = dA;
+    if (rows(h, l, 0, D.A, o, nv, true, st) < 0) return XAMG_ERR_CUDA;
+  }
+  if (s == 1) {
+    const int g = elem_grid(D.A.n, nv);
+    launch_axpy_dot(nv, D.A.n, x, dA, dot_part ? dot_u : nullptr, dot_part, g, st);
+    if (dot_part) *dot_grid = g;
+  } else {
+    double *dprev = dA, *dnext = dB;
+    for (int k = 1; k < s; ++k) {
+      const bool last = k == s - 1;
+      RowOp o = blank();
+      o.init = r; o.src = dprev; o.dp = dprev; o.w = D.w[k]; o.c1 = D.c1[k];
+      o.x = x; o.x_dp = 1;
+      if (last) {
+        o.x_dn = 1;
+        if (dot_part) {
+          o.dot_u = dot_u; o.dot_of = 1; o.partials = dot_part;
+        }
+      } else {
+        o.y = r; o.dnext = dnext;
+      }
+      const int g = rows(h, l, 0, D.A, o, nv, true, st);
+      if (g < 0) return XAMG_ERR_CUDA;
+      if (last && dot_part) *dot_grid = g;
+      std::swap(dprev, dnext);
+    }
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
+}
+
+int sync_read(cudaStream_t st) {
+  XCK(cudaStreamSynchronize(st));
+  return XAMG_OK;
+}
+
+// true residual t = b - A x with partial ||t||^2 in part; returns the grid
+int true_residual(xamg_hier *h, Work &W, double *T, double *part, cudaStream_t st) {
+  RowOp o = blank();
+  o.init = W.Bn; o.src = W.X; o.y = T; o.partials2 = part;
+  return rows(h, 0, 0, h->lv[0].A, o, W.nv, true, st);
+}
+
+struct SolveCtx {
+  xamg_hier *h;
+  Work W;
+  int m, nv;
+  double tol;
+  int maxit;
+  cudaStream_t st;
+  int iterations = 0, vcycles = 0;
+};
+
+int finish(SolveCtx &c, double *Xuser, xamg_stats *stats) {
+  xamg_hier *h = c.h;
+  Work &W = c.W;
+  const int64_t n = h->lv[0].A.n;
+  double *T = W.Q ? W.Q : W.T;
+  const int g = true_residual(h, W, T, W.part[4], c.st);
+  if (g < 0) return XAMG_ERR_CUDA;
+  launch_scalar(c.nv, SM_FINAL, W.cs, W.part[4], nullptr, g, c.tol, 0, nullptr, c.st);
+  launch_copy_out(c.nv, n, W.X, Xuser, c.m, elem_grid(n, c.nv), c.st);
+  ColState cs;
+  XCK(cudaMemcpyAsync(&cs, W.cs, sizeof(cs), cudaMemcpyDeviceToHost, c.st));
+  XCK(cudaStreamSynchronize(c.st));
+  XCK(cudaGetLastError());
+  if (h->timing) flush_timing(h);
+  int rc = XAMG_OK;
+  int maxits = 0;
+  for (int j = 0; j < c.m; ++j) {
+    int status;
+    double rel = 0.0;
+    if (cs.state[j] == 4) {
+      status = XAMG_COL_CONVERGED;
+    } else {
+      rel = cs.tn[j] / cs.nb[j];
+      if (cs.state[j] == 3) status = XAMG_COL_BREAKDOWN;
+      else status = rel <= c.tol ? XAMG_COL_CONVERGED : XAMG_COL_NOT_CONVERGED;
+    }
+    if (status == XAMG_COL_BREAKDOWN) rc = XAMG_BREAKDOWN;
+    else if (status == XAMG_COL_NOT_CONVERGED && rc == XAMG_OK) rc = XAMG_NOT_CONVERGED;
+    maxits = std::max(maxits, (int)cs.iters[j]);
+    if (stats) {
+      if (stats->iters) stats->iters[j] = cs.iters[j];
+      if (stats->relres) stats->relres[j] = rel;
+      if (stats->status) stats->status[j] = status;
+    }
+  }
+  if (stats) {
+    stats->iterations = maxits;
+    stats->vcycles = c.vcycles;
+  }
+  return rc;
+}
+
+int check_init(SolveCtx &c) {
+  int rc = sync_read(c.st);
+  if (rc != XAMG_OK) return rc;
+  XCK(cudaGetLastError());
+  if (c.h->flags_h->breakdown < 0) return XAMG_ERR_NONFINITE;
+  return XAMG_OK;
+}
+
+int solve_pcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
+  xamg_hier *h = c.h;
+  Work &W = c.W;
+  const int nv = c.nv;
+  const int64_t n = h->lv[0].A.n;
+  const int ge = elem_grid(n, nv);
+  const bool single = h->lv.size() == 1;
+  const double *w0 = single ? nullptr : h->lv[0].w[0];
+  Flags *fl = h->flags_d;
+  cudaStream_t st = c.st;
+  int g;
+  launch_init_pcg(nv, n, B, c.m, W.Bn, W.R, W.X, W.Z, w0, W.part[0], ge, st);
+  launch_scalar(nv, SM_INIT, W.cs, W.part[0], nullptr, ge, c.tol, 0, fl, st);
+  int rc = check_init(c);
+  if (rc != XAMG_OK) return rc;
+  if (h->flags_h->active > 0) {
+    if ((rc = vcycle(h, W, 0, W.R, W.Z, st, W.R, W.part[1], &g)) != XAMG_OK) return rc;
+    c.vcycles++;
+    launch_scalar(nv, SM_PCG_BETA, W.cs, W.part[1], nullptr, g, c.tol, 0, fl, st);
+    launch_pcg_p(nv, n, W.P, W.Z, W.cs, ge, st);
+  }
+  for (int k = 1; k <= c.maxit && h->flags_h->active > 0; ++k) {
+    c.iterations = k;
+    RowOp o = blank();
+    o.src = W.P; o.y = W.Q; o.dot_u = W.P; o.dot_of = 0; o.partials = W.part[0];
+    if ((g = rows(h, 0, 0, h->lv[0].A, o, nv, false, st)) < 0) return XAMG_ERR_CUDA;
+    launch_scalar(nv, SM_PCG_ALPHA, W.cs, W.part[0], nullptr, g, c.tol, k, fl, st);
+    launch_pcg_xr(nv, n, W.X, W.R, W.P, W.Q, W.cs, w0, W.Z, W.part[1], ge, st);
+    launch_scalar(nv, SM_PCG_CONV, W.cs, W.part[1], nullptr, ge, c.tol, k, fl, st);
+    if ((rc = sync_read(st)) != XAMG_OK) return rc;
+    if (h->flags_h->active == 0) {
+      if ((g = true_residual(h, W, W.Q, W.part[2], st)) < 0) return XAMG_ERR_CUDA;
+      launch_scalar(nv, SM_CONFIRM, W.cs, W.part[2], nullptr, g, c.tol, k, fl, st);
+      if ((rc = sync_read(st)) != XAMG_OK) return rc;
+      if (h->flags_h->reactivated == 0) break;
+      launch_copy_cols(nv, n, W.R, W.Q, W.cs, ge, st);
+      if (w0) launch_scale_rows(nv, n, w0, W.R, W.Z, ge, st);
+    }
+    if ((rc = vcycle(h, W, 0, W.R, W.Z, st, W.R, W.part[1], &g)) != XAMG_OK) return rc;
+    c.vcycles++;
+    launch_scalar(nv, SM_PCG_BETA, W.cs, W.part[1], nullptr, g, c.tol, k, fl, st);
+    launch_pcg_p(nv, n, W.P, W.Z, W.cs, ge, st);
+  }
+  return finish(c, Xuser, stats);
+}
+
+int solve_bicgstab(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
+  xamg_hier *h = c.h;
+  Work &W = c.W;
+  const int nv = c.nv;
+  const int64_t n = h->lv[0].A.n;
+  const int ge = elem_grid(n, nv);
+  const bool single = h->lv.size() == 1;
+  const double *w0 = single ? nullptr : h->lv[0].w[0];
+  Flags *fl = h->flags_d;
+  cudaStream_t st = c.st;
+  int g;
+  const size_t blk = (size_t)n * nv * sizeof(double);
+  XCK(cudaMemsetAsync(W.T, 0, blk, st));
+  XCK(cudaMemsetAsync(W.SH, 0, blk, st));
+  launch_init_bicg(nv, n, B, c.m, W.Bn, W.R, W.RH, W.X, W.P, W.V, W.part[0], ge, st);
+  launch_scalar(nv, SM_INIT, W.cs, W.part[0], nullptr, ge, c.tol, 0, fl, st);
+  int rc = check_init(c);
+  if (rc != XAMG_OK) return rc;
+  double *prh = W.part[0];  // partial sums of rhat . r
+  int grh = ge;
+  for (int k = 1; k <= c.maxit && h->flags_h->active > 0; ++k) {
+    c.iterations = k;
+    launch_scalar(nv, SM_BI_RHO, W.cs, prh, nullptr, grh, c.tol, k, fl, st);
+    launch_bicg_p(nv, n, W.P, W.R, W.V, W.cs, w0, W.PH, ge, st);
+    if ((rc = vcycle(h, W, 0, W.P, W.PH, st, nullptr, nullptr, nullptr)) != XAMG_OK) return rc;
+    c.vcycles++;
+    RowOp o = blank();
+    o.src = W.PH; o.y = W.V; o.dot_u = W.RH; o.dot_of = 0; o.partials = W.part[1];
+    if ((g = rows(h, 0, 0, h->lv[0].A, o, nv, false, st)) < 0) return XAMG_ERR_CUDA;
+    launch_scalar(nv, SM_BI_ALPHA, W.cs, W.part[1], nullptr, g, c.tol, k, fl, st);
+    launch_bicg_s(nv, n, W.S, W.R, W.V, W.cs, w0, W.SH, W.part[2], ge, st);
+    launch_scalar(nv, SM_BI_HALF, W.cs, W.part[2], nullptr, ge, c.tol, k, fl, st);
+    if ((rc = sync_read(st)) != XAMG_OK) return rc;
+    if (h->flags_h->active > 0) {
+      if ((rc = vcycle(h, W, 0, W.S, W.SH, st, nullptr, nullptr, nullptr)) != XAMG_OK) return rc;
+      c.vcycles++;
+      RowOp t = blank();
+      t.src = W.SH; t.y = W.T; t.dot_u = W.S; t.dot_of = 0; t.partials = W.part[1];
+      t.partials2 = W.part[2];
+      if ((g = rows(h, 0, 0, h->lv[0].A, t, nv, false, st)) < 0) return XAMG_ERR_CUDA;
+      launch_scalar(nv, SM_BI_OMEGA, W.cs, W.part[1], W.part[2], g, c.tol, k, fl, st);
+    }
+    launch_bicg_xr(nv, n, W.X, W.R, W.S, W.T, W.PH, W.SH, W.RH, W.cs, W.part[3], W.part[0], ge, st);
+    prh = W.part[0];
+    grh = ge;
+    launch_scalar(nv, SM_BI_CONV, W.cs, W.part[3], nullptr, ge, c.tol, k, fl, st);
+    if ((rc = sync_read(st)) != XAMG_OK) return rc;
+    if (h->flags_h->active == 0) {
+      if ((g = true_residual(h, W, W.T, W.part[2], st)) < 0) return XAMG_ERR_CUDA;
+      launch_scalar(nv, SM_CONFIRM, W.cs, W.part[2], nullptr, g, c.tol, k, fl, st);
+      if ((rc = sync_read(st)) != XAMG_OK) return rc;
+      if (h->flags_h->reactivated == 0) break;
+      launch_copy_cols(nv, n, W.R, W.T, W.cs, ge, st);
+      launch_copy_cols(nv, n, W.RH, W.T, W.cs, ge, st);
+      launch_coldot(nv, n, W.RH, W.R, W.part[0], ge, st);
+    }
+  }
+  return finish(c, Xuser, stats);
+}
+
+int solve_impl(xamg_hier *h, const double *B, double *X, int m, double tol, int maxit,
+               const xamg_solve_opts *opts, xamg_stats *stats) {
+  if (!h || !h->on_device || !B || !X || m < 1 || m > XAMG_MAX_RHS || !(tol > 0.0) || maxit < 0)
+    return XAMG_ERR_INVALID_ARG;
+  xamg_solve_opts o;
+  xamg_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.method != XAMG_PCG && o.method != XAMG_BICGSTAB) return XAMG_ERR_INVALID_ARG;
+  XCK(cudaSetDevice(h->device));
+  SolveCtx c;
+  c.h = h;
+  c.m = m;
+  c.nv = pad_nv(m);
+  c.tol = tol;
+  c.maxit = maxit;
+  c.st = (cudaStream_t)o.stream;
+  int rc = ensure_workspace(h, c.nv, o.method, &o, c.W);
+  if (rc != XAMG_OK) return rc;
+  h->flags_h->active = 0;
+  rc = o.method == XAMG_PCG ? solve_pcg(c, B, X, stats) : solve_bicgstab(c, B, X, stats);
+  if (h->timing && rc < 0) {
+    cudaStreamSynchronize(c.st);
+    flush_timing(h);
+  }
+  return rc;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+const char *xamg_strerror(int code) {
+  switch (code) {
+    case XAMG_OK: return "success";
+    case XAMG_ERR_INVALID_ARG: return "invalid argument";
+    case XAMG_ERR_CUDA: return "CUDA runtime error";
+    case XAMG_ERR_OOM: return "out of memory";
+    case XAMG_ERR_NONFINITE: return "non-finite value in the input";
+    case XAMG_ERR_TIMEOUT: return "bounded device wait timed out";
+    case XAMG_ERR_SETUP: return "hierarchy setup failed";
+    case XAMG_NOT_CONVERGED: return "some columns did not converge";
+    case XAMG_BREAKDOWN: return "some columns broke down";
+    default: return "unknown status";
+  }
+}
+
+void xamg_amg_params_default(xamg_amg_params *p) {
+  if (!p) return;
+  p->theta = 0.25;
+  p->max_coarse = 64;
+  p->max_levels = 25;
+  p->cheb_steps = 2;
+  p->power_iters = 20;
+  p->cheb_lo_frac = 0.3;
+  p->cheb_hi_safety = 1.1;
+  p->max_dense = 1024;
+  p->nthreads = 0;
+  p->device_upload = 1;
+}
+
+void xamg_solve_opts_default(xamg_solve_opts *o) {
+  if (!o) return;
+  o->method = XAMG_PCG;
+  o->stream = nullptr;
+  o->workspace = nullptr;
+  o->workspace_bytes = 0;
+}
+
+int xamg_setup_hierarchy(const xamg_csr *A, const xamg_amg_params *p, xamg_hier **out) {
+  if (!A || !out) return XAMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  xamg_amg_params prm;
+  xamg_amg_params_default(&prm);
+  if (p) prm = *p;
+  xamg_hier *h = new (std::nothrow) xamg_hier();
+  if (!h) return XAMG_ERR_OOM;
+  h->prm = prm;
+  int rc = build_hierarchy(*A, prm, h->host);
+  if (rc != XAMG_OK) {
+    delete h;
+    return rc;
+  }
+  if (prm.device_upload) {
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+      delete h;
+      return XAMG_ERR_CUDA;
+    }
+    const int L = (int)h->host.lv.size();
+    h->lv.resize(L);
+    for (int l = 0; l < L && rc == XAMG_OK; ++l) rc = upload_level(h, l);
+    if (rc == XAMG_OK) rc = dev_upload(h, &h->lu, h->host.lu.data(), h->host.lu.size());
+    if (rc == XAMG_OK) rc = dev_upload(h, &h->piv, h->host.piv.data(), h->host.piv.size());
+    if (rc == XAMG_OK) {
+      if (cudaHostAlloc((void **)&h->flags_h, sizeof(Flags), cudaHostAllocMapped) != cudaSuccess ||
+          cudaHostGetDevicePointer((void **)&h->flags_d, h->flags_h, 0) != cudaSuccess)
+        rc = XAMG_ERR_CUDA;
+      else
+        std::memset(h->flags_h, 0, sizeof(Flags));
+    }
+    if (rc != XAMG_OK) {
+      free_device(h);
+      delete h;
+      return rc;
+    }
+    h->tacc.assign((size_t)L * 3, TimeAcc());
+    h->on_device = true;
+  }
+  *out = h;
+  return XAMG_OK;
+}
+
+int xamg_destroy(xamg_hier *h) {
+  if (!h) return XAMG_OK;
+  if (h->on_device) {
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    free_device(h);
+  }
+  delete h;
+  return XAMG_OK;
+}
+
+int xamg_hier_info(const xamg_hier *h, int32_t *levels, double *op_complexity) {
+  if (!h) return XAMG_ERR_INVALID_ARG;
+  if (levels) *levels = (int32_t)h->host.lv.size();
+  if (op_complexity) {
+    double s = 0;
+    for (auto &L : h->host.lv) s += (double)L.A.nnz();
+    *op_complexity = s / (double)h->host.lv[0].A.nnz();
+  }
+  return XAMG_OK;
+}
+
+int xamg_level_info(const xamg_hier *h, int32_t level, int32_t *n, int64_t *nnz_a, int64_t *nnz_p) {
+  if (!h || level < 0 || level >= (int)h->host.lv.size()) return XAMG_ERR_INVALID_ARG;
+  const HostLevel &L = h->host.lv[level];
+  if (n) *n = L.A.n;
+  if (nnz_a) *nnz_a = L.A.nnz();
+  if (nnz_p) *nnz_p = L.P.nnz();
+  return XAMG_OK;
+}
+
+int xamg_level_export(const xamg_hier *h, int32_t level, int32_t *rowptr, int32_t *col, double *val,
+                      int32_t *p_rowptr, int32_t *p_col, double *p_val, int32_t *cf, double *cheb) {
+  if (!h || level < 0 || level >= (int)h->host.lv.size()) return XAMG_ERR_INVALID_ARG;
+  const HostLevel &L = h->host.lv[level];
+  if (rowptr) std::memcpy(rowptr, L.A.rowptr.data(), L.A.rowptr.size() * sizeof(int32_t));
+  if (col) std::memcpy(col, L.A.col.data(), L.A.col.size() * sizeof(int32_t));
+  if (val) std::memcpy(val, L.A.val.data(), L.A.val.size() * sizeof(double));
+  if (!L.P.rowptr.empty()) {
+    if (p_rowptr) std::memcpy(p_rowptr, L.P.rowptr.data(), L.P.rowptr.size() * sizeof(int32_t));
+    if (p_col) std::memcpy(p_col, L.P.col.data(), L.P.col.size() * sizeof(int32_t));
+    if (p_val) std::memcpy(p_val, L.P.val.data(), L.P.val.size() * sizeof(double));
+  }
+  if (cf && !L.cf.empty()) std::memcpy(cf, L.cf.data(), L.cf.size() * sizeof(int32_t));
+  if (cheb) {
+    cheb[0] = L.lo;
+    cheb[1] = L.hi;
+    cheb[2] = L.lam;
+    cheb[3] = L.gersh;
+  }
+  return XAMG_OK;
+}
+
+int xamg_coarse_export(const xamg_hier *h, int32_t *nc, double *lu, int32_t *piv) {
+  if (!h) return XAMG_ERR_INVALID_ARG;
+  if (nc) *nc = h->host.nc;
+  if (lu) std::memcpy(lu, h->host.lu.data(), h->host.lu.size() * sizeof(double));
+  if (piv) std::memcpy(piv, h->host.piv.data(), h->host.piv.size() * sizeof(int32_t));
+  return XAMG_OK;
+}
+
+int xamg_workspace_bytes(const xamg_hier *h, int32_t m, int32_t method, size_t *bytes) {
+  if (!h || !bytes || m < 1 || m > XAMG_MAX_RHS || (method != XAMG_PCG && method != XAMG_BICGSTAB))
+    return XAMG_ERR_INVALID_ARG;
+  *bytes = plan(h, pad_nv(m), method, nullptr, nullptr);
+  return XAMG_OK;
+}
+
+int xamg_solve(xamg_hier *h, const double *B, double *X, int32_t m, double tol, int32_t maxit,
+               const xamg_solve_opts *opts, xamg_stats *stats) {
+  return solve_impl(h, B, X, m, tol, maxit, opts, stats);
+}
+
+int xamg_solve_host(xamg_hier *h, const double *B, double *X, int32_t m, double tol, int32_t maxit,
+                    const xamg_solve_opts *opts, xamg_stats *stats) {
+  if (!h || !h->on_device || !B || !X || m < 1 || m > XAMG_MAX_RHS) return XAMG_ERR_INVALID_ARG;
+  XCK(cudaSetDevice(h->device));
+  const size_t bytes = (size_t)h->host.lv[0].A.n * m * sizeof(double);
+  if (h->hb_bytes < 2 * align256(bytes)) {
+    if (h->hb) cudaFree(h->hb);
+    h->hb = nullptr;
+    h->hb_bytes = 0;
+    XCK(cudaMalloc((void **)&h->hb, 2 * align256(bytes)));
+    h->hb_bytes = 2 * align256(bytes);
+  }
+  double *db = h->hb, *dx = (double *)((char *)h->hb + align256(bytes));
+  cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
+  XCK(cudaMemcpyAsync(db, B, bytes, cudaMemcpyHostToDevice, st));
+  int rc = solve_impl(h, db, dx, m, tol, maxit, opts, stats);
+  if (rc < 0) return rc;
+  XCK(cudaMemcpyAsync(X, dx, bytes, cudaMemcpyDeviceToHost, st));
+  XCK(cudaStreamSynchronize(st));
+  return rc;
+}
+
+int xamg_level_spmm(xamg_hier *h, int32_t level, int32_t which, const double *X, double *Y,
+                    int32_t m, void *stream) {
+  if (!h || !h->on_device || !X || !Y || m < 1 || m > XAMG_MAX_RHS || level < 0 ||
+      level >= (int)h->lv.size() || which < 0 || which > 2)
+    return XAMG_ERR_INVALID_ARG;
+  if (which > 0 && level + 1 >= (int)h->lv.size()) return XAMG_ERR_INVALID_ARG;
+  XCK(cudaSetDevice(h->device));
+  DevLevel &D = h->lv[level];
+  const DevCsr &M = which == 0 ? D.A : which == 1 ? D.P : D.R;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nv = pad_nv(m);
+  const double *src = X;
+  double *dst = Y;
+  Work W;
+  if (nv != m) {
+    int rc = ensure_workspace(h, nv, XAMG_PCG, nullptr, W);
+    if (rc != XAMG_OK) return rc;
+    src = W.Bn;
+    dst = W.X;
+    launch_pad_in(nv, M.ncols, X, m, W.Bn, elem_grid(M.ncols, nv), st);
+  }
+  RowOp o = blank();
+  o.src = src;
+  o.y = dst;
+  if (rows(h, level, which, M, o, nv, false, st) < 0) return XAMG_ERR_CUDA;
+  if (nv != m) launch_copy_out(nv, M.n, W.X, Y, m, elem_grid(M.n, nv), st);
+  XCK(cudaStreamSynchronize(st));
+  XCK(cudaGetLastError());
+  if (h->timing) flush_timing(h);
+  return XAMG_OK;
+}
+
+int xamg_smooth(xamg_hier *h, int32_t level, const double *B, double *X, double *R, int32_t x_zero,
+                int32_t m, void *stream) {
+  if (!h || !h->on_device || !B || !X || m < 1 || m > XAMG_MAX_RHS || level < 0 ||
+      level + 1 >= (int)h->lv.size() || (!x_zero && R))
+    return XAMG_ERR_INVALID_ARG;
+  XCK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nv = pad_nv(m);
+  Work W;
+  int rc = ensure_workspace(h, nv, XAMG_PCG, nullptr, W);
+  if (rc != XAMG_OK) return rc;
+  DevLevel &D = h->lv[level];
+  const int64_t n = D.A.n;
+  const int ge = elem_grid(n, nv);
+  const int s = h->host.cheb_steps;
+  // padded copies of B and X in Bn / X, residual in vr, directions in vd/vd2
+  launch_pad_in(nv, n, B, m, W.Bn, ge, st);
+  double *x = W.X, *r = W.vr[level], *dA = W.vd[level], *dB = W.vd2[level];
+  if (x_zero) {
+    launch_scale_rows(nv, n, D.w[0], W.Bn, x, ge, st);
+    if (s == 1) {
+      RowOp o = blank();
+      o.init = W.Bn; o.src = x; o.y = r;
+      if (rows(h, level, 0, D.A, o, nv, true, st) < 0) return XAMG_ERR_CUDA;
+    } else {
+      RowOp o = blank();
+      o.init = W.Bn; o.src = x; o.y = r; o.dp = x; o.w = D.w[1]; o.c1 = D.c1[1]; o.dnext = dA;
+      if (rows(h, level, 0, D.A, o, nv, true, st) < 0) return XAMG_ERR_CUDA;
+      double *dprev = dA, *dnext = dB;
+      for (int k = 2; k < s; ++k) {
+        RowOp q = blank();
+        q.init = r; q.src = dprev; q.y = r; q.dp = dprev; q.w = D.w[k]; q.c1 = D.c1[k];
+        q.dnext = dnext; q.x = x; q.x_dp = 1;
+        if (rows(h, level, 0, D.A, q, nv, true, st) < 0) return XAMG_ERR_CUDA;
+        std::swap(dprev, dnext);
+      }
+      RowOp f = blank();
+      f.init = r; f.src = dprev; f.y = r; f.dp = dprev; f.x = x; f.x_dp = 1;
+      if (rows(h, level, 0, D.A, f, nv, true, st) < 0) return XAMG_ERR_CUDA;
+    }
+    if (R) launch_copy_out(nv, n, r, R, m, ge, st);
+  } else {
+    launch_pad_in(nv, n, X, m, x, ge, st);
+    RowOp o = blank();
+    o.init = W.Bn; o.src = x; o.y = r; o.w = D.w[0]; o.dnext = dA;
+    if (rows(h, level, 0, D.A, o, nv, true, st) < 0) return XAMG_ERR_CUDA;
+    if (s == 1) {
+      launch_axpy_dot(nv, n, x, dA, nullptr, nullptr, ge, st);
+    } else {
+      double *dprev = dA, *dnext = dB;
+      for (int k = 1; k < s; ++k) {
+        const bool last = k == s - 1;
+        RowOp q = blank();
+        q.init = r; q.src = dprev; q.dp = dprev; q.w = D.w[k]; q.c1 = D.c1[k]; q.x = x; q.x_dp = 1;
+        if (last) q.x_dn = 1;
+        else {
+          q.y = r;
+          q.dnext = dnext;
+        }
+        if (rows(h, level, 0, D.A, q, nv, true, st) < 0) return XAMG_ERR_CUDA;
+        std::swap(dprev, dnext);
+      }
+    }
+  }
+  launch_copy_out(nv, n, x, X, m, ge, st);
+  XCK(cudaStreamSynchronize(st));
+  XCK(cudaGetLastError());
+  if (h->timing) flush_timing(h);
+  return XAMG_OK;
+}
+
+int xamg_vcycle(xamg_hier *h, const double *B, double *X, int32_t m, void *stream) {
+  if (!h || !h->on_device || !B || !X || m < 1 || m > XAMG_MAX_RHS) return XAMG_ERR_INVALID_ARG;
+  XCK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nv = pad_nv(m);
+  Work W;
+  int rc = ensure_workspace(h, nv, XAMG_PCG, nullptr, W);
+  if (rc != XAMG_OK) return rc;
+  const int64_t n = h->lv[0].A.n;
+  const int ge = elem_grid(n, nv);
+  launch_pad_in(nv, n, B, m, W.Bn, ge, st);
+  if (h->lv.size() > 1) launch_scale_rows(nv, n, h->lv[0].w[0], W.Bn, W.X, ge, st);
+  if ((rc = vcycle(h, W, 0, W.Bn, W.X, st, nullptr, nullptr, nullptr)) != XAMG_OK) return rc;
+  launch_copy_out(nv, n, W.X, X, m, ge, st);
+  XCK(cudaStreamSynchronize(st));
+  XCK(cudaGetLastError());
+  if (h->timing) flush_timing(h);
+  return XAMG_OK;
+}
+
+int xamg_coarse_solve(xamg_hier *h, const double *B, double *X, int32_t m, void *stream) {
+  if (!h || !h->on_device || !B || !X || m < 1 || m > XAMG_MAX_RHS) return XAMG_ERR_INVALID_ARG;
+  XCK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nv = pad_nv(m);
+  Work W;
+  int rc = ensure_workspace(h, nv, XAMG_PCG, nullptr, W);
+  if (rc != XAMG_OK) return rc;
+  const int nc = h->host.nc;
+  const int ge = elem_grid(nc, nv);
+  launch_pad_in(nv, nc, B, m, W.Bn, ge, st);
+  launch_coarse(nv, nc, h->lu, h->piv, W.Bn, W.X, st);
+  launch_copy_out(nv, nc, W.X, X, m, ge, st);
+  XCK(cudaStreamSynchronize(st));
+  XCK(cudaGetLastError());
+  return XAMG_OK;
+}
+
+int xamg_coldot(const double *U, const double *V, int64_t n, int32_t m, double *out, void *stream) {
+  if (!U || !V || !out || n < 0 || m < 1 || m > XAMG_MAX_RHS) return XAMG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int grid = coldot_rt_grid(n, m);
+  double *part = nullptr;
+  XCK(cudaMallocAsync((void **)&part, (size_t)grid * m * sizeof(double), st));
+  launch_coldot_rt(n, m, U, V, part, grid, st);
+  launch_reduce_rt(m, part, grid, out, st);
+  cudaError_t e1 = cudaGetLastError();
+  cudaError_t e2 = cudaFreeAsync(part, st);
+  cudaError_t e3 = cudaStreamSynchronize(st);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return XAMG_ERR_CUDA;
+  return XAMG_OK;
+}
+
+int xamg_timing_enable(xamg_hier *h, int32_t enable) {
+  if (!h || !h->on_device) return XAMG_ERR_INVALID_ARG;
+  h->timing = enable != 0;
+  if (h->timing) h->tacc.assign(h->lv.size() * 3, TimeAcc());
+  return XAMG_OK;
+}
+
+int xamg_timing_read(const xamg_hier *h, int32_t level, int32_t which, int64_t *launches,
+                     double *total_ms, double *flops, double *bytes) {
+  if (!h || !h->on_device || level < 0 || level >= (int)h->lv.size() || which < 0 || which > 2)
+    return XAMG_ERR_INVALID_ARG;
+  const TimeAcc &t = h->tacc[(size_t)level * 3 + which];
+  if (launches) *launches = t.launches;
+  if (total_ms) *total_ms = t.ms;
+  if (flops) *flops = t.flops;
+  if (bytes) *bytes = t.bytes;
+  return XAMG_OK;
+}
+
+}  // extern "C"

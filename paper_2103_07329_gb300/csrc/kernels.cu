@@ -1,0 +1,578 @@
+// kernels.cu -- solve-phase kernels and their launchers (sm_103a).
+//
+// Every reduction in this file is deterministic: per-block partial sums are
+// formed in a fixed thread order and reduced by one block in a fixed order,
+// so repeated runs of the same solve give identical bits.
+#include <algorithm>
+#include <cmath>
+
+#include "launch.h"
+
+namespace xamg {
+
+int device_sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 1;
+  }
+  return sms;
+}
+
+int elem_grid(int64_t n, int nv) {
+  const int64_t need = (n * nv + kBlock - 1) / kBlock;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)device_sm_count() * 8));
+}
+
+// ------------------------------------------------------------------ rows
+template <int NV, int S, bool NEG>
+static int rows_t(const RowOp &op, cudaStream_t st) {
+  static int max_grid = 0;
+  if (!max_grid) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rows<NV, S, NEG>, kBlock, 0) != cudaSuccess || b < 1)
+      b = 1;
+    max_grid = std::min(kMaxGrid, b * device_sm_count());
+  }
+  constexpr int rows_per_block = kWarps * (32 / (NV * S));
+  const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
+  k_rows<NV, S, NEG><<<grid, kBlock, 0, st>>>(op);
+  return cudaPeekAtLastError() == cudaSuccess ? grid : -1;
+}
+
+template <int NV, bool NEG>
+static int rows_s(const RowOp &op, int slices, cudaStream_t st) {
+  if constexpr (NV == 1) {
+    if (slices >= 16) return rows_t<1, 16, NEG>(op, st);
+    if (slices >= 4) return rows_t<1, 4, NEG>(op, st);
+  } else if constexpr (NV <= 8) {
+    if (slices >= 4) return rows_t<NV, 4, NEG>(op, st);
+  }
+  return rows_t<NV, 1, NEG>(op, st);
+}
+
+int launch_rows(const RowOp &op, int nv, int slices, bool neg, cudaStream_t st) {
+  switch (nv) {
+#define XAMG_ROWS_CASE(V) \
+  case V:                 \
+    return neg ? rows_s<V, true>(op, slices, st) : rows_s<V, false>(op, slices, st);
+    XAMG_ROWS_CASE(1)
+    XAMG_ROWS_CASE(2)
+    XAMG_ROWS_CASE(4)
+    XAMG_ROWS_CASE(8)
+    XAMG_ROWS_CASE(16)
+    XAMG_ROWS_CASE(32)
+#undef XAMG_ROWS_CASE
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------------ elementwise
+#define XAMG_ELEM_LOOP(NV, n)                                                            \
+  for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x, total__ = (n) * (NV); e < total__; \
+       e += (int64_t)gridDim.x * kBlock)
+
+// R, Bn = B (padded to NV columns), X = 0, Z = w0 * R (first smoother
+// iterate of the preconditioner), partial ||R||^2.
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_init_pcg(int64_t n, const double *B, int m, double *Bn,
+                                                     double *R, double *X, double *Z,
+                                                     const double *w0, double *part) {
+  const int c = threadIdx.x % NV;
+  double acc = 0.0;
+  XAMG_ELEM_LOOP(NV, n) {
+    const int64_t i = e / NV;
+    const double b = c < m ? B[i * m + c] : 0.0;
+    Bn[e] = b;
+    R[e] = b;
+    X[e] = 0.0;
+    Z[e] = w0 ? w0[i] * b : 0.0;
+    acc = fma(b, b, acc);
+  }
+  block_colsum_store<NV>(acc, part);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_init_bicg(int64_t n, const double *B, int m, double *Bn,
+                                                      double *R, double *RH, double *X, double *P,
+                                                      double *V, double *part) {
+  const int c = threadIdx.x % NV;
+  double acc = 0.0;
+  XAMG_ELEM_LOOP(NV, n) {
+    const int64_t i = e / NV;
+    const double b = c < m ? B[i * m + c] : 0.0;
+    Bn[e] = b;
+    R[e] = b;
+    RH[e] = b;
+    X[e] = 0.0;
+    P[e] = 0.0;
+    V[e] = 0.0;
+    acc = fma(b, b, acc);
+  }
+  block_colsum_store<NV>(acc, part);
+}
+
+// x += alpha p ; r -= alpha q ; z = w0 r ; partial ||r||^2
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_pcg_xr(int64_t n, double *X, double *R, const double *P,
+                                                   const double *Q, const ColState *cs,
+                                                   const double *w0, double *Z, double *part) {
+  const int c = threadIdx.x % NV;
+  const double a = cs->alpha[c];
+  double acc = 0.0;
+  XAMG_ELEM_LOOP(NV, n) {
+    const double r = fma(-a, Q[e], R[e]);
+    X[e] = fma(a, P[e], X[e]);
+    R[e] = r;
+    if (w0) Z[e] = w0[e / NV] * r;
+    acc = fma(r, r, acc);
+  }
+  block_colsum_store<NV>(acc, part);
+}
+
+// p = z + beta p
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_pcg_p(int64_t n, double *P, const double *Z,
+                                                  const ColState *cs) {
+  const int c = threadIdx.x % NV;
+  const double b = cs->beta[c];
+  if (b == 0.0) {
+    XAMG_ELEM_LOOP(NV, n) { P[e] = Z[e]; }
+  } else {
+    XAMG_ELEM_LOOP(NV, n) { P[e] = fma(b, P[e], Z[e]); }
+  }
+}
+
+// p = r + beta (p - omega v) ; ph = w0 p
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_bicg_p(int64_t n, double *P, const double *R,
+                                                   const double *V, const ColState *cs,
+                                                   const double *w0, double *PH) {
+  const int c = threadIdx.x % NV;
+  const double b = cs->beta[c], om = cs->omega[c];
+  XAMG_ELEM_LOOP(NV, n) {
+    const double p = fma(b, fma(-om, V[e], P[e]), R[e]);
+    P[e] = p;
+    if (w0) PH[e] = w0[e / NV] * p;
+  }
+}
+
+// s = r - alpha v ; sh = w0 s ; partial ||s||^2
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_bicg_s(int64_t n, double *S, const double *R,
+                                                   const double *V, const ColState *cs,
+                                                   const double *w0, double *SH, double *part) {
+  const int c = threadIdx.x % NV;
+  const double a = cs->alpha[c];
+  double acc = 0.0;
+  XAMG_ELEM_LOOP(NV, n) {
+    const double s = fma(-a, V[e], R[e]);
+    S[e] = s;
+    if (w0) SH[e] = w0[e / NV] * s;
+    acc = fma(s, s, acc);
+  }
+  block_colsum_store<NV>(acc, part);
+}
+
+// x += alpha ph + omega sh ; r = s - omega t ; partials ||r||^2 and rhat.r
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_bicg_xr(int64_t n, double *X, double *R, const double *S,
+                                                    const double *T, const double *PH,
+                                                    const double *SH, const double *RH,
+                                                    const ColState *cs, double *part_rr,
+                                                    double *part_rhr) {
+  const int c = threadIdx.x % NV;
+  const double a = cs->alpha[c], om = cs->omega[c];
+  double rr = 0.0, rhr = 0.0;
+  XAMG_ELEM_LOOP(NV, n) {
+    X[e] = fma(om, SH[e], fma(a, PH[e], X[e]));
+    const double r = fma(-om, T[e], S[e]);
+    R[e] = r;
+    rr = fma(r, r, rr);
+    rhr = fma(RH[e], r, rhr);
+  }
+  block_colsum_store<NV>(rr, part_rr);
+  __syncthreads();
+  block_colsum_store<NV>(rhr, part_rhr);
+}
+
+// dst[:, c] = src[:, c] for the columns restarted by the last confirmation
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_copy_cols(int64_t n, double *dst, const double *src,
+                                                      const ColState *cs) {
+  const int c = threadIdx.x % NV;
+  if (!cs->reac[c]) return;
+  XAMG_ELEM_LOOP(NV, n) { dst[e] = src[e]; }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_copy_out(int64_t n, const double *Xin, double *Xu, int m) {
+  const int c = threadIdx.x % NV;
+  XAMG_ELEM_LOOP(NV, n) {
+    if (c < m) Xu[(e / NV) * m + c] = Xin[e];
+  }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_pad_in(int64_t n, const double *Xu, int m, double *Xp) {
+  const int c = threadIdx.x % NV;
+  XAMG_ELEM_LOOP(NV, n) { Xp[e] = c < m ? Xu[(e / NV) * m + c] : 0.0; }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_scale_rows(int64_t n, const double *w, const double *B,
+                                                       double *X) {
+  XAMG_ELEM_LOOP(NV, n) { X[e] = w[e / NV] * B[e]; }
+}
+
+// x += d ; optional partial u.x
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_axpy_dot(int64_t n, double *X, const double *D,
+                                                     const double *U, double *part) {
+  double acc = 0.0;
+  XAMG_ELEM_LOOP(NV, n) {
+    const double x = X[e] + D[e];
+    X[e] = x;
+    if (U) acc = fma(U[e], x, acc);
+  }
+  if (part) block_colsum_store<NV>(acc, part);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_coldot(int64_t n, const double *U, const double *V,
+                                                   double *part) {
+  double acc = 0.0;
+  XAMG_ELEM_LOOP(NV, n) { acc = fma(U[e], V[e], acc); }
+  block_colsum_store<NV>(acc, part);
+}
+
+// ------------------------------------------------------------------ scalars
+// One block of 1024 threads.  Warp c reduces column c of the partial sums
+// (lane t takes blocks t, t+32, ... in order, then a fixed xor tree); thread c
+// then applies the per-column step of the Krylov method.
+template <int NV>
+__global__ void __launch_bounds__(1024) k_scalar(int mode, ColState *cs, const double *p0,
+                                                 const double *p1, int nblk, double tol, int k,
+                                                 Flags *fl) {
+  __shared__ double s0[32], s1[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < NV) {
+    double a = 0.0, b = 0.0;
+    if (p0)
+      for (int g = lane; g < nblk; g += 32) a += p0[(size_t)g * NV + warp];
+    if (p1)
+      for (int g = lane; g < nblk; g += 32) b += p1[(size_t)g * NV + warp];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      s0[warp] = a;
+      s1[warp] = b;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const int c = threadIdx.x;
+    const double d0 = s0[c], d1 = s1[c];
+    const int st = cs->state[c];
+    switch (mode) {
+      case SM_INIT: {
+        const double nb = sqrt(d0);
+        cs->nb[c] = nb;
+        cs->state[c] = nb > 0.0 ? 0 : 4;
+        cs->restart[c] = 1;
+        cs->iters[c] = 0;
+        cs->reac[c] = 0;
+        cs->alpha[c] = cs->beta[c] = cs->omega[c] = cs->rho[c] = cs->tn[c] = 0.0;
+        break;
+      }
+      case SM_PCG_ALPHA:
+        if (st == 0) {
+          if (!(d0 > 0.0)) {
+            cs->state[c] = 3;
+            cs->alpha[c] = 0.0;
+          } else {
+            cs->alpha[c] = cs->rho[c] / d0;
+            cs->iters[c] = k;
+          }
+        } else {
+          cs->alpha[c] = 0.0;
+        }
+        break;
+      case SM_PCG_CONV:
+      case SM_BI_CONV:
+        if (st == 0 && sqrt(d0) <= tol * cs->nb[c]) cs->state[c] = 1;
+        break;
+      case SM_PCG_BETA:
+        if (st == 0) {
+          if (!(d0 > 0.0)) {
+            cs->state[c] = 3;
+            cs->beta[c] = 0.0;
+          } else {
+            cs->beta[c] = cs->restart[c] ? 0.0 : d0 / cs->rho[c];
+            cs->restart[c] = 0;
+            cs->rho[c] = d0;
+          }
+        } else {
+          cs->beta[c] = 0.0;
+        }
+        break;
+      case SM_CONFIRM: {
+        const double tn = sqrt(d0);
+        cs->tn[c] = tn;
+        cs->reac[c] = 0;
+        if (st == 1) {
+          if (tn <= tol * cs->nb[c]) {
+            cs->state[c] = 2;
+          } else {
+            cs->state[c] = 0;
+            cs->restart[c] = 1;
+            cs->reac[c] = 1;
+          }
+        }
+        break;
+      }
+      case SM_FINAL:
+        cs->tn[c] = sqrt(d0);
+        break;
+      case SM_BI_RHO:
+        if (st == 0) {
+          if (d0 == 0.0 || !isfinite(d0)) {
+            cs->state[c] = 3;
+            cs->beta[c] = 0.0;
+          } else {
+            cs->beta[c] = cs->restart[c] ? 0.0 : (d0 / cs->rho[c]) * (cs->alpha[c] / cs->omega[c]);
+            cs->restart[c] = 0;
+            cs->rho[c] = d0;
+          }
+        } else {
+          cs->beta[c] = 0.0;
+        }
+        break;
+      case SM_BI_ALPHA:
+        if (st == 0) {
+          if (d0 == 0.0 || !isfinite(d0)) {
+            cs->state[c] = 3;
+            cs->alpha[c] = 0.0;
+            cs->omega[c] = 0.0;
+          } else {
+            cs->alpha[c] = cs->rho[c] / d0;
+          }
+        } else {
+          cs->alpha[c] = 0.0;
+          cs->omega[c] = 0.0;
+        }
+        break;
+      case SM_BI_HALF:
+        if (st == 0) {
+          cs->iters[c] = k;
+          if (sqrt(d0) <= tol * cs->nb[c]) {
+            cs->state[c] = 1;
+            cs->omega[c] = 0.0;
+          }
+        }
+        break;
+      case SM_BI_OMEGA:
+        if (st == 0) {
+          const double om = d0 / d1;
+          if (d1 == 0.0 || d0 == 0.0 || !isfinite(om)) {
+            cs->state[c] = 3;
+            cs->alpha[c] = 0.0;
+            cs->omega[c] = 0.0;
+          } else {
+            cs->omega[c] = om;
+          }
+        }
+        break;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && fl) {
+    int act = 0, fr = 0, re = 0, br = 0;
+    for (int c = 0; c < NV; ++c) {
+      act += cs->state[c] == 0;
+      fr += cs->state[c] == 1;
+      re += cs->reac[c];
+      br += cs->state[c] == 3;
+    }
+    volatile Flags *vf = fl;
+    vf->active = act;
+    vf->frozen = fr;
+    vf->reactivated = re;
+    vf->breakdown = br;
+    if (mode == SM_INIT) {
+      int nonfinite = 0;
+      for (int c = 0; c < NV; ++c) nonfinite |= !isfinite(s0[c]);
+      vf->breakdown = nonfinite ? -1 : 0;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ coarsest
+// X = A_c^-1 B with the LU factors (unit lower L, partial pivoting): one block
+// works through the rows in order; the forward sweep subtracts in the same
+// order as the row form of forward substitution.
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_coarse(int nc, const double *lu, const int32_t *piv,
+                                                   const double *B, double *X) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nc * NV; e += kBlock) X[e] = B[e];
+  __syncthreads();
+  if (tid < NV)
+    for (int k = 0; k < nc; ++k) {
+      const int p = piv[k];
+      if (p != k) {
+        const double t = X[k * NV + tid];
+        X[k * NV + tid] = X[p * NV + tid];
+        X[p * NV + tid] = t;
+      }
+    }
+  __syncthreads();
+  for (int k = 0; k + 1 < nc; ++k) {
+    for (int e = tid; e < (nc - k - 1) * NV; e += kBlock) {
+      const int i = k + 1 + e / NV, c = e % NV;
+      X[i * NV + c] = __dsub_rn(X[i * NV + c], __dmul_rn(lu[(size_t)i * nc + k], X[k * NV + c]));
+    }
+    __syncthreads();
+  }
+  for (int i = nc - 1; i >= 0; --i) {
+    if (tid < NV) X[i * NV + tid] = X[i * NV + tid] / lu[(size_t)i * nc + i];
+    __syncthreads();
+    for (int e = tid; e < i * NV; e += kBlock) {
+      const int r = e / NV, c = e % NV;
+      X[r * NV + c] = __dsub_rn(X[r * NV + c], __dmul_rn(lu[(size_t)r * nc + i], X[i * NV + c]));
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ runtime-m dots
+// Thread t of a block owns column t % m for t < (kBlock / m) * m; rows are
+// strided over the grid.  Partials: per block and column, summed over the
+// block's threads of that column in thread order.
+__global__ void __launch_bounds__(kBlock) k_coldot_rt(int64_t n, int m, const double *U,
+                                                      const double *V, double *part) {
+  __shared__ double sh[kBlock];
+  const int per = kBlock / m;
+  const int t = threadIdx.x;
+  double acc = 0.0;
+  if (t < per * m) {
+    const int c = t % m, r0 = t / m;
+    for (int64_t i = (int64_t)blockIdx.x * per + r0; i < n; i += (int64_t)gridDim.x * per)
+      acc = fma(U[i * m + c], V[i * m + c], acc);
+  }
+  sh[t] = acc;
+  __syncthreads();
+  if (t < m) {
+    double s = 0.0;
+    for (int r = 0; r < per; ++r) s += sh[r * m + t];
+    part[(size_t)blockIdx.x * m + t] = s;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_reduce_rt(int m, const double *part, int nblk, double *out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp >= m) return;
+  double a = 0.0;
+  for (int g = lane; g < nblk; g += 32) a += part[(size_t)g * m + warp];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (lane == 0) out[warp] = a;
+}
+
+// ------------------------------------------------------------------ dispatch
+#define XAMG_NV_SWITCH(nv, CALL) \
+  switch (nv) {                  \
+    case 1: { constexpr int NV = 1; CALL; } break;   \
+    case 2: { constexpr int NV = 2; CALL; } break;   \
+    case 4: { constexpr int NV = 4; CALL; } break;   \
+    case 8: { constexpr int NV = 8; CALL; } break;   \
+    case 16: { constexpr int NV = 16; CALL; } break; \
+    case 32: { constexpr int NV = 32; CALL; } break; \
+    default: break;              \
+  }
+
+void launch_init_pcg(int nv, int64_t n, const double *B, int m, double *Bn, double *R, double *X,
+                     double *Z, const double *w0, double *part, int grid, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_init_pcg<NV><<<grid, kBlock, 0, st>>>(n, B, m, Bn, R, X, Z, w0, part)));
+}
+void launch_init_bicg(int nv, int64_t n, const double *B, int m, double *Bn, double *R, double *RH,
+                      double *X, double *P, double *V, double *part, int grid, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_init_bicg<NV><<<grid, kBlock, 0, st>>>(n, B, m, Bn, R, RH, X, P, V, part)));
+}
+void launch_pcg_xr(int nv, int64_t n, double *X, double *R, const double *P, const double *Q,
+                   const ColState *cs, const double *w0, double *Z, double *part, int grid,
+                   cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_pcg_xr<NV><<<grid, kBlock, 0, st>>>(n, X, R, P, Q, cs, w0, Z, part)));
+}
+void launch_pcg_p(int nv, int64_t n, double *P, const double *Z, const ColState *cs, int grid,
+                  cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_pcg_p<NV><<<grid, kBlock, 0, st>>>(n, P, Z, cs)));
+}
+void launch_bicg_p(int nv, int64_t n, double *P, const double *R, const double *V,
+                   const ColState *cs, const double *w0, double *PH, int grid, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_bicg_p<NV><<<grid, kBlock, 0, st>>>(n, P, R, V, cs, w0, PH)));
+}
+void launch_bicg_s(int nv, int64_t n, double *S, const double *R, const double *V,
+                   const ColState *cs, const double *w0, double *SH, double *part, int grid,
+                   cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_bicg_s<NV><<<grid, kBlock, 0, st>>>(n, S, R, V, cs, w0, SH, part)));
+}
+void launch_bicg_xr(int nv, int64_t n, double *X, double *R, const double *S, const double *T,
+                    const double *PH, const double *SH, const double *RH, const ColState *cs,
+                    double *part_rr, double *part_rhr, int grid, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_bicg_xr<NV><<<grid, kBlock, 0, st>>>(n, X, R, S, T, PH, SH, RH, cs, part_rr,
+                                                              part_rhr)));
+}
+void launch_copy_cols(int nv, int64_t n, double *dst, const double *src, const ColState *cs,
+                      int grid, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_copy_cols<NV><<<grid, kBlock, 0, st>>>(n, dst, src, cs)));
+}
+void launch_copy_out(int nv, int64_t n, const double *Xin, double *Xuser, int m, int grid,
+                     cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_copy_out<NV><<<grid, kBlock, 0, st>>>(n, Xin, Xuser, m)));
+}
+void launch_pad_in(int nv, int64_t n, const double *Xuser, int m, double *Xp, int grid,
+                   cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_pad_in<NV><<<grid, kBlock, 0, st>>>(n, Xuser, m, Xp)));
+}
+void launch_scale_rows(int nv, int64_t n, const double *w, const double *B, double *X, int grid,
+                       cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_scale_rows<NV><<<grid, kBlock, 0, st>>>(n, w, B, X)));
+}
+void launch_axpy_dot(int nv, int64_t n, double *X, const double *D, const double *U, double *part,
+                     int grid, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_axpy_dot<NV><<<grid, kBlock, 0, st>>>(n, X, D, U, part)));
+}
+void launch_coldot(int nv, int64_t n, const double *U, const double *V, double *part, int grid,
+                   cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_coldot<NV><<<grid, kBlock, 0, st>>>(n, U, V, part)));
+}
+void launch_scalar(int nv, int mode, ColState *cs, const double *p0, const double *p1, int nblk,
+                   double tol, int k, Flags *flags, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_scalar<NV><<<1, 1024, 0, st>>>(mode, cs, p0, p1, nblk, tol, k, flags)));
+}
+void launch_coarse(int nv, int nc, const double *lu, const int32_t *piv, const double *B, double *X,
+                   cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_coarse<NV><<<1, kBlock, 0, st>>>(nc, lu, piv, B, X)));
+}
+
+int coldot_rt_grid(int64_t n, int m) {
+  const int per = kBlock / m;
+  const int64_t need = (n + per - 1) / per;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)device_sm_count() * 8));
+}
+void launch_coldot_rt(int64_t n, int m, const double *U, const double *V, double *part, int grid,
+                      cudaStream_t st) {
+  k_coldot_rt<<<grid, kBlock, 0, st>>>(n, m, U, V, part);
+}
+void launch_reduce_rt(int m, const double *part, int nblk, double *out, cudaStream_t st) {
+  k_reduce_rt<<<1, 1024, 0, st>>>(m, part, nblk, out);
+}
+
+}  // namespace xamg

@@ -1,0 +1,98 @@
+// launch.h -- host-side launchers of the solve-phase kernels (runtime NV
+// dispatch onto the compile-time NV kernels of kernels.cu).  Internal.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace xamg {
+
+constexpr int kMaxGrid = 4096;  // upper bound on blocks of any reducing launch
+
+// Per-column solver state on the device (NV <= 32 columns are used).
+struct ColState {
+  double nb[32];       // ||b_j||
+  double rho[32];      // PCG: r.z ; BiCGStab: rhat.r of the last iteration
+  double alpha[32];
+  double beta[32];
+  double omega[32];
+  double tn[32];       // true residual norms
+  int32_t state[32];   // 0 active, 1 frozen by the residual test, 2 confirmed,
+                       // 3 breakdown, 4 zero right-hand side
+  int32_t restart[32]; // next direction update starts afresh
+  int32_t iters[32];
+  int32_t reac[32];    // 1: column restarted by the last confirmation
+};
+
+// Host-visible counters written by the scalar kernels (mapped pinned memory).
+struct Flags {
+  int32_t active;       // columns still iterating
+  int32_t frozen;       // columns frozen by the recursive residual test
+  int32_t reactivated;  // columns restarted by the last confirmation
+  int32_t breakdown;
+};
+
+enum ScalarMode : int {
+  SM_INIT = 0,       // p0: ||b||^2 partials -> nb, state, restart = 1
+  SM_PCG_ALPHA = 1,  // p0: p.q -> alpha, iters = k
+  SM_PCG_CONV = 2,   // p0: r.r -> freeze
+  SM_PCG_BETA = 3,   // p0: r.z -> beta, rho
+  SM_CONFIRM = 4,    // p0: true residual^2 -> confirm or restart
+  SM_FINAL = 5,      // p0: true residual^2 -> tn
+  SM_BI_RHO = 6,     // p0: rhat.r -> beta, rho
+  SM_BI_ALPHA = 7,   // p0: rhat.v -> alpha
+  SM_BI_HALF = 8,    // p0: s.s -> iters = k, half-step freeze
+  SM_BI_OMEGA = 9,   // p0: t.s, p1: t.t -> omega
+  SM_BI_CONV = 10,   // p0: r.r -> freeze
+};
+
+int device_sm_count();
+
+// Fused row operation; returns the grid size used (needed to reduce
+// op.partials), or -1 on a launch error.
+int launch_rows(const RowOp &op, int nv, int slices, bool neg, cudaStream_t st);
+
+// Elementwise grid size for n rows of nv columns.
+int elem_grid(int64_t n, int nv);
+
+void launch_init_pcg(int nv, int64_t n, const double *B, int m, double *Bn, double *R, double *X,
+                     double *Z, const double *w0, double *part, int grid, cudaStream_t st);
+void launch_init_bicg(int nv, int64_t n, const double *B, int m, double *Bn, double *R, double *RH,
+                      double *X, double *P, double *V, double *part, int grid, cudaStream_t st);
+void launch_pcg_xr(int nv, int64_t n, double *X, double *R, const double *P, const double *Q,
+                   const ColState *cs, const double *w0, double *Z, double *part, int grid,
+                   cudaStream_t st);
+void launch_pcg_p(int nv, int64_t n, double *P, const double *Z, const ColState *cs, int grid,
+                  cudaStream_t st);
+void launch_bicg_p(int nv, int64_t n, double *P, const double *R, const double *V,
+                   const ColState *cs, const double *w0, double *PH, int grid, cudaStream_t st);
+void launch_bicg_s(int nv, int64_t n, double *S, const double *R, const double *V,
+                   const ColState *cs, const double *w0, double *SH, double *part, int grid,
+                   cudaStream_t st);
+void launch_bicg_xr(int nv, int64_t n, double *X, double *R, const double *S, const double *T,
+                    const double *PH, const double *SH, const double *RH, const ColState *cs,
+                    double *part_rr, double *part_rhr, int grid, cudaStream_t st);
+void launch_copy_cols(int nv, int64_t n, double *dst, const double *src, const ColState *cs,
+                      int grid, cudaStream_t st);
+void launch_copy_out(int nv, int64_t n, const double *Xin, double *Xuser, int m, int grid,
+                     cudaStream_t st);
+void launch_pad_in(int nv, int64_t n, const double *Xuser, int m, double *Xp, int grid,
+                   cudaStream_t st);
+void launch_scale_rows(int nv, int64_t n, const double *w, const double *B, double *X, int grid,
+                       cudaStream_t st);
+void launch_axpy_dot(int nv, int64_t n, double *X, const double *D, const double *U, double *part,
+                     int grid, cudaStream_t st);
+void launch_coldot(int nv, int64_t n, const double *U, const double *V, double *part, int grid,
+                   cudaStream_t st);
+void launch_scalar(int nv, int mode, ColState *cs, const double *p0, const double *p1, int nblk,
+                   double tol, int k, Flags *flags, cudaStream_t st);
+void launch_coarse(int nv, int nc, const double *lu, const int32_t *piv, const double *B, double *X,
+                   cudaStream_t st);
+// Runtime-m column dots for the public entry point: partials then reduce.
+int coldot_rt_grid(int64_t n, int m);
+void launch_coldot_rt(int64_t n, int m, const double *U, const double *V, double *part, int grid,
+                      cudaStream_t st);
+void launch_reduce_rt(int m, const double *part, int nblk, double *out, cudaStream_t st);
+
+}  // namespace xamg

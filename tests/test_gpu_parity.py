@@ -1,0 +1,287 @@
+"""GPU parity: every step of the solve phase, called through the C ABI, against
+the CPU oracle on the same seeded inputs.
+
+Tolerances (FP64 on both sides; the products agree up to summation order and
+fused multiply-adds):
+  * SpMM on integer-valued data: bitwise (every partial sum is exact);
+  * SpMM, smoother, coarse solve, V-cycle: per-column ||g - o|| / ||o|| <= 1e-12;
+  * solves: true residual <= 1e-8 per column, iteration counts within +-1.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_07329_gb300 import binding as B
+from paper_2103_07329_gb300 import build as build_mod
+from paper_2103_07329_gb300 import problems as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build_mod.build()
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def colrel(g, o):
+    g = np.asarray(g).reshape(o.shape[0], -1)
+    o = o.reshape(o.shape[0], -1)
+    num = np.linalg.norm(g - o, axis=0)
+    den = np.linalg.norm(o, axis=0)
+    return np.where(den > 0, num / np.where(den > 0, den, 1), num)
+
+
+def csr_of(t, rows):
+    rp, ci, v = t
+    return P.CSR(rows, rp, ci, v)
+
+
+class Pair:
+    """Library and oracle hierarchies of one matrix."""
+
+    def __init__(self, A, **kw):
+        self.A = A
+        self.g = B.Hierarchy(A, **kw)
+        self.o = oracle.Hierarchy(A, **kw)
+
+
+_pairs = {}
+
+
+def pair(name, N, **kw):
+    key = (name, N, tuple(sorted(kw.items())))
+    if key not in _pairs:
+        A = P.poisson7(N) if name == "p7" else P.poisson27(N)
+        _pairs[key] = Pair(A, **kw)
+    return _pairs[key]
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    return pair("p7", 32)
+
+
+# ---------------------------------------------------------------- SpMM
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 8, 16, 32])
+def test_spmm_fine_level_integer_bitwise(cfg0, m):
+    A = cfg0.A
+    X = np.random.default_rng(m).integers(-1000, 1001, size=(A.n, m)).astype(np.float64)
+    Y = torch.empty((A.n, m), dtype=torch.float64, device="cuda")
+    cfg0.g.spmm(0, 0, dev(X), Y)
+    assert np.array_equal(Y.cpu().numpy(), oracle.spmm(A, X))
+
+
+@pytest.mark.parametrize("m", [1, 4, 5, 32])
+def test_spmm_all_levels_and_operators(cfg0, m):
+    rng = np.random.default_rng(10 + m)
+    for l in range(cfg0.o.nlev):
+        lv = cfg0.o.level(l)
+        ops = [(0, csr_of(lv.A, lv.n), lv.n)]
+        if lv.P is not None:
+            nc = cfg0.o.level(l + 1).n
+            ops += [(1, P.CSR(lv.n, *lv.P), nc), (2, P.CSR(nc, *lv.R), lv.n)]
+        for which, M, ncols in ops:
+            X = rng.uniform(-1, 1, size=(ncols, m))
+            Y = torch.empty((M.n, m), dtype=torch.float64, device="cuda")
+            cfg0.g.spmm(l, which, dev(X), Y)
+            ref = oracle.spmm(M, X, ncols=ncols)
+            assert colrel(Y.cpu().numpy(), ref).max() <= RTOL, (l, which)
+
+
+@pytest.mark.parametrize("N", [5, 17, 33])
+def test_spmm_ragged_sizes(N):
+    # n not a multiple of any tile: 125, 4913, 35937 rows
+    pr = pair("p7", N)
+    for m in (1, 2, 32):
+        X = np.random.default_rng(N).integers(-50, 51, size=(pr.A.n, m)).astype(np.float64)
+        Y = torch.empty((pr.A.n, m), dtype=torch.float64, device="cuda")
+        pr.g.spmm(0, 0, dev(X), Y)
+        assert np.array_equal(Y.cpu().numpy(), oracle.spmm(pr.A, X))
+
+
+def test_spmm_27pt_long_rows():
+    pr = pair("p27", 20)
+    for m in (1, 8):
+        X = np.random.default_rng(3).integers(-99, 100, size=(pr.A.n, m)).astype(np.float64)
+        Y = torch.empty((pr.A.n, m), dtype=torch.float64, device="cuda")
+        pr.g.spmm(0, 0, dev(X), Y)
+        assert np.array_equal(Y.cpu().numpy(), oracle.spmm(pr.A, X))
+
+
+# ---------------------------------------------------------------- smoother / coarse / V-cycle
+@pytest.mark.parametrize("m", [1, 4, 7])
+def test_chebyshev_pre_and_post(cfg0, m):
+    rng = np.random.default_rng(20 + m)
+    for l in range(cfg0.o.nlev - 1):
+        n = cfg0.o.level(l).n
+        Bm = rng.uniform(-1, 1, size=(n, m))
+        X = torch.empty((n, m), dtype=torch.float64, device="cuda")
+        R = torch.empty((n, m), dtype=torch.float64, device="cuda")
+        cfg0.g.smooth(l, dev(Bm), X, R, x_zero=True)
+        xo, ro = cfg0.o.cheb_smooth(l, Bm)
+        assert colrel(X.cpu().numpy(), xo).max() <= RTOL
+        assert colrel(R.cpu().numpy(), ro).max() <= 1e-11
+        X0 = rng.uniform(-1, 1, size=(n, m))
+        X = dev(X0)
+        cfg0.g.smooth(l, dev(Bm), X, None, x_zero=False)
+        xo, _ = cfg0.o.cheb_smooth(l, Bm, X0=X0, want_residual=False)
+        assert colrel(X.cpu().numpy(), xo).max() <= RTOL
+
+
+def test_coarse_solve(cfg0):
+    lu, piv = cfg0.o.coarse_lu()
+    nc = lu.shape[0]
+    Bm = np.random.default_rng(1).uniform(-1, 1, size=(nc, 6))
+    X = torch.empty((nc, 6), dtype=torch.float64, device="cuda")
+    cfg0.g.coarse_solve(dev(Bm), X)
+    ref = oracle.lu_solve(lu, piv, Bm)
+    assert colrel(X.cpu().numpy(), ref).max() <= RTOL
+
+
+@pytest.mark.parametrize("m", [1, 4, 32])
+def test_vcycle_parity(cfg0, m):
+    Bm = P.rhs_uniform(cfg0.A.n, m, 0)
+    X = torch.empty_like(dev(Bm))
+    cfg0.g.vcycle(dev(Bm), X)
+    assert colrel(X.cpu().numpy(), cfg0.o.vcycle(Bm)).max() <= RTOL
+
+
+def test_vcycle_parity_27pt():
+    pr = pair("p27", 16)
+    Bm = P.rhs_uniform(pr.A.n, 3, 0)
+    X = torch.empty_like(dev(Bm))
+    pr.g.vcycle(dev(Bm), X)
+    assert colrel(X.cpu().numpy(), pr.o.vcycle(Bm)).max() <= RTOL
+
+
+def test_vcycle_single_level_is_exact():
+    pr = pair("p7", 4)          # n = 64 <= max_coarse: one level
+    assert pr.g.levels == 1
+    Bm = P.rhs_uniform(pr.A.n, 2, 0)
+    X = torch.empty_like(dev(Bm))
+    pr.g.vcycle(dev(Bm), X)
+    assert colrel(X.cpu().numpy(), pr.o.vcycle(Bm)).max() <= RTOL
+
+
+# ---------------------------------------------------------------- solves
+def true_relres(A, Bm, X):
+    R = Bm - oracle.spmm(A, X)
+    return np.linalg.norm(R, axis=0) / np.linalg.norm(Bm, axis=0)
+
+
+@pytest.mark.parametrize("method", [B.PCG, B.BICGSTAB])
+def test_solve_cfg0(cfg0, method):
+    Bm = P.rhs_uniform(cfg0.A.n, 4, 0)
+    X = torch.empty_like(dev(Bm))
+    st = cfg0.g.solve(dev(Bm), X, tol=1e-8, maxit=100, method=method)
+    ref = cfg0.o.pcg(Bm) if method == B.PCG else cfg0.o.bicgstab(Bm)
+    assert st.rc == 0 and np.all(st.status == 0)
+    Xg = X.cpu().numpy()
+    rr = true_relres(cfg0.A, Bm, Xg)
+    assert np.all(rr <= 1e-8), rr
+    assert np.allclose(st.relres, rr, rtol=1e-6, atol=0)
+    assert np.all(np.abs(st.iters - ref.iters) <= 1), (st.iters, ref.iters)
+    assert colrel(Xg, ref.X).max() <= 1e-6
+
+
+@pytest.mark.parametrize("method", [B.PCG, B.BICGSTAB])
+def test_solve_27pt(method):
+    pr = pair("p27", 24)
+    Bm = P.rhs_uniform(pr.A.n, 5, 0)
+    X = torch.empty_like(dev(Bm))
+    st = pr.g.solve(dev(Bm), X, method=method)
+    ref = pr.o.pcg(Bm) if method == B.PCG else pr.o.bicgstab(Bm)
+    assert np.all(true_relres(pr.A, Bm, X.cpu().numpy()) <= 1e-8)
+    assert np.all(np.abs(st.iters - ref.iters) <= 1)
+
+
+def test_m1_equals_single_column(cfg0):
+    Bm = P.rhs_uniform(cfg0.A.n, 4, 0)
+    Xb = torch.empty_like(dev(Bm))
+    sb = cfg0.g.solve(dev(Bm), Xb)
+    for j in range(4):
+        X1 = torch.empty((cfg0.A.n, 1), dtype=torch.float64, device="cuda")
+        s1 = cfg0.g.solve(dev(Bm[:, j:j + 1]), X1)
+        assert s1.iters[0] == sb.iters[j]
+        assert colrel(X1.cpu().numpy(), Xb.cpu().numpy()[:, j:j + 1]).max() <= 1e-12
+
+
+def test_repeatable_bits(cfg0):
+    Bm = dev(P.rhs_uniform(cfg0.A.n, 8, 1))
+    X1 = torch.empty_like(Bm)
+    X2 = torch.empty_like(Bm)
+    cfg0.g.solve(Bm, X1, method=B.BICGSTAB)
+    cfg0.g.solve(Bm, X2, method=B.BICGSTAB)
+    assert torch.equal(X1, X2)
+
+
+def test_edge_cases(cfg0):
+    n = cfg0.A.n
+    Bm = P.rhs_uniform(n, 3, 2)
+    Bm[:, 1] = 0.0
+    X = torch.full((n, 3), 7.0, dtype=torch.float64, device="cuda")
+    st = cfg0.g.solve(dev(Bm), X)
+    Xg = X.cpu().numpy()
+    assert st.iters[1] == 0 and np.all(Xg[:, 1] == 0.0) and st.status[1] == 0
+    assert np.all(true_relres(cfg0.A, Bm[:, [0, 2]], Xg[:, [0, 2]]) <= 1e-8)
+    # non-finite right-hand side: error, X untouched
+    Bm[5, 2] = np.nan
+    X = torch.full((n, 3), 7.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.XamgError) as e:
+        cfg0.g.solve(dev(Bm), X)
+    assert e.value.code == B.ERR_NONFINITE
+    assert torch.all(X == 7.0)
+    # iteration limit
+    Bm = P.rhs_uniform(n, 2, 3)
+    st = cfg0.g.solve(dev(Bm), torch.empty((n, 2), dtype=torch.float64, device="cuda"),
+                      tol=1e-14, maxit=2)
+    assert st.rc == B.NOT_CONVERGED and np.all(st.status == 1) and np.all(st.iters == 2)
+    ref = cfg0.o.pcg(Bm, tol=1e-14, maxit=2)
+    assert np.all(ref.iters == 2)
+    # bad arguments
+    with pytest.raises(B.XamgError):
+        cfg0.g.solve(dev(np.zeros((n, 33))), torch.empty((n, 33), dtype=torch.float64, device="cuda"))
+
+
+def test_host_buffers_match_device(cfg0):
+    Bm = P.rhs_uniform(cfg0.A.n, 4, 5)
+    Xd = torch.empty_like(dev(Bm))
+    sd = cfg0.g.solve(dev(Bm), Xd)
+    Xh = np.empty_like(Bm)
+    sh = cfg0.g.solve_host(Bm, Xh)
+    assert np.array_equal(Xh, Xd.cpu().numpy())
+    assert np.array_equal(sh.iters, sd.iters)
+
+
+def test_caller_workspace(cfg0):
+    Bm = dev(P.rhs_uniform(cfg0.A.n, 4, 6))
+    nb = cfg0.g.workspace_bytes(4, B.PCG)
+    ws = torch.empty(nb // 8 + 64, dtype=torch.float64, device="cuda")
+    X1 = torch.empty_like(Bm)
+    X2 = torch.empty_like(Bm)
+    cfg0.g.solve(Bm, X1)
+    cfg0.g.solve(Bm, X2, workspace=ws)
+    assert torch.equal(X1, X2)
+
+
+@pytest.mark.parametrize("m", [1, 3, 32])
+def test_coldot(m):
+    rng = np.random.default_rng(m)
+    U = rng.uniform(-1, 1, size=(10007, m))
+    V = rng.uniform(-1, 1, size=(10007, m))
+    out = torch.empty(m, dtype=torch.float64, device="cuda")
+    B.coldot(dev(U), dev(V), out)
+    ref = (U * V).sum(axis=0)
+    assert np.allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-12)
+    out2 = torch.empty(m, dtype=torch.float64, device="cuda")
+    B.coldot(dev(U), dev(V), out2)
+    assert torch.equal(out, out2)
