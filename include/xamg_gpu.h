@@ -243,6 +243,10 @@ int xamg_timing_enable(xamg_hier *h, int32_t enable);
 int xamg_timing_read(const xamg_hier *h, int32_t level, int32_t which, int64_t *launches,
                      double *total_ms, double *flops, double *bytes);
 
+/* Number of kernel launches the library has issued in this process (all
+ * handles, all devices) since it was loaded. */
+int64_t xamg_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

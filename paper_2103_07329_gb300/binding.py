@@ -36,7 +36,7 @@ EXPORTS = [
     "xamg_setup_hierarchy", "xamg_destroy", "xamg_hier_info", "xamg_level_info",
     "xamg_level_export", "xamg_coarse_export", "xamg_workspace_bytes", "xamg_solve",
     "xamg_solve_host", "xamg_level_spmm", "xamg_smooth", "xamg_vcycle", "xamg_coarse_solve",
-    "xamg_coldot", "xamg_timing_enable", "xamg_timing_read",
+    "xamg_coldot", "xamg_timing_enable", "xamg_timing_read", "xamg_kernel_launches",
 ]
 
 
@@ -104,6 +104,7 @@ def _load():
         "xamg_coarse_solve": ([vp, vp, vp, i32, vp], C.c_int),
         "xamg_coldot": ([vp, vp, i64, i32, vp, vp], C.c_int),
         "xamg_timing_enable": ([vp, i32], C.c_int),
+        "xamg_kernel_launches": ([], C.c_int64),
         "xamg_timing_read": ([vp, i32, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl),
                               C.POINTER(dbl)], C.c_int),
     }
@@ -313,6 +314,11 @@ class Hierarchy:
         _check(_load().xamg_timing_read(self._h, level, which, C.byref(n), C.byref(ms), C.byref(fl),
                                         C.byref(by)), "xamg_timing_read")
         return dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value)
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(_load().xamg_kernel_launches())
 
 
 def coldot(U, V, out, stream=None):

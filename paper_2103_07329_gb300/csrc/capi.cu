@@ -952,6 +952,8 @@ int xamg_coldot(const double *U, const double *V, int64_t n, int32_t m, double *
   return XAMG_OK;
 }
 
+int64_t xamg_kernel_launches(void) { return g_launches.load(); }
+
 int xamg_timing_enable(xamg_hier *h, int32_t enable) {
   if (!h || !h->on_device) return XAMG_ERR_INVALID_ARG;
   h->timing = enable != 0;

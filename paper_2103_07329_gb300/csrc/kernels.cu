@@ -4,11 +4,14 @@
 // formed in a fixed thread order and reduced by one block in a fixed order,
 // so repeated runs of the same solve give identical bits.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "launch.h"
 
 namespace xamg {
+
+std::atomic<int64_t> g_launches{0};
 
 int device_sm_count() {
   static int sms = 0;
@@ -40,6 +43,7 @@ static int rows_t(const RowOp &op, cudaStream_t st) {
   const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
   k_rows<NV, S, NEG><<<grid, kBlock, 0, st>>>(op);
+  g_launches++;
   return cudaPeekAtLastError() == cudaSuccess ? grid : -1;
 }
 
@@ -487,6 +491,7 @@ __global__ void __launch_bounds__(1024) k_reduce_rt(int m, const double *part, i
 
 // ------------------------------------------------------------------ dispatch
 #define XAMG_NV_SWITCH(nv, CALL) \
+  g_launches++;                  \
   switch (nv) {                  \
     case 1: { constexpr int NV = 1; CALL; } break;   \
     case 2: { constexpr int NV = 2; CALL; } break;   \
@@ -570,9 +575,11 @@ int coldot_rt_grid(int64_t n, int m) {
 void launch_coldot_rt(int64_t n, int m, const double *U, const double *V, double *part, int grid,
                       cudaStream_t st) {
   k_coldot_rt<<<grid, kBlock, 0, st>>>(n, m, U, V, part);
+  g_launches++;
 }
 void launch_reduce_rt(int m, const double *part, int nblk, double *out, cudaStream_t st) {
   k_reduce_rt<<<1, 1024, 0, st>>>(m, part, nblk, out);
+  g_launches++;
 }
 
 }  // namespace xamg

@@ -2,6 +2,8 @@
 // dispatch onto the compile-time NV kernels of kernels.cu).  Internal.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -48,6 +50,7 @@ enum ScalarMode : int {
 };
 
 int device_sm_count();
+extern std::atomic<int64_t> g_launches;  // kernels launched by the library
 
 // Fused row operation; returns the grid size used (needed to reduce
 // op.partials), or -1 on a launch error.
