@@ -226,6 +226,29 @@ int xamg_coarse_solve(xamg_hier *h, const double *B, double *X, int32_t m, void 
 int xamg_coldot(const double *U, const double *V, int64_t n, int32_t m, double *out,
                 void *stream);
 
+/* Column dot products like xamg_coldot, for callers that must not allocate
+ * device memory during the call: for example a host framework that has
+ * reserved all device memory for its own pool (so cudaMalloc would fail), or
+ * a latency-critical loop that must not enter the CUDA allocator, which may
+ * synchronize the device.  There is no counterpart in the paper.
+ *
+ * U, V: DEVICE n x m row-major blocks; out: DEVICE array of m doubles; all
+ * caller-owned.  The per-block partial sums live in one file-scope device
+ * array of the library (1024 blocks x 32 columns of doubles, 256 KiB), which
+ * every GPU that loads the library keeps until the process exits; the call
+ * uses at most 1024 blocks, so any n >= 0 is accepted, and m must be in
+ * [1, XAMG_MAX_RHS] (else XAMG_ERR_INVALID_ARG, nothing launched).  The call
+ * makes no cudaMalloc, cudaFree or other allocating call.  Its first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents: calls whose
+ * device work overlaps (other streams, other threads) race on it and must be
+ * serialised by the caller.  Results are reduced in a fixed order; they may
+ * differ from xamg_coldot's in the last bits because the block count differs.
+ * Returns after the work on `stream` has finished. */
+int xamg_coldot_noalloc(const double *U, const double *V, int64_t n, int32_t m, double *out,
+                        void *stream);
+
 /* ---- measurement ---- */
 
 /* Turns per-launch timing of the sparse row kernels on (1) or off (0).  When

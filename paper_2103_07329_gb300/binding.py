@@ -37,6 +37,7 @@ EXPORTS = [
     "xamg_level_export", "xamg_coarse_export", "xamg_workspace_bytes", "xamg_solve",
     "xamg_solve_host", "xamg_level_spmm", "xamg_smooth", "xamg_vcycle", "xamg_coarse_solve",
     "xamg_coldot", "xamg_timing_enable", "xamg_timing_read", "xamg_kernel_launches",
+    "xamg_coldot_noalloc",
 ]
 
 
@@ -103,6 +104,7 @@ def _load():
         "xamg_vcycle": ([vp, vp, vp, i32, vp], C.c_int),
         "xamg_coarse_solve": ([vp, vp, vp, i32, vp], C.c_int),
         "xamg_coldot": ([vp, vp, i64, i32, vp, vp], C.c_int),
+        "xamg_coldot_noalloc": ([vp, vp, i64, i32, vp, vp], C.c_int),
         "xamg_timing_enable": ([vp, i32], C.c_int),
         "xamg_kernel_launches": ([], C.c_int64),
         "xamg_timing_read": ([vp, i32, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl),
@@ -325,3 +327,13 @@ def coldot(U, V, out, stream=None):
     """xamg_coldot: out[j] = sum_i U[i, j] V[i, j] on device tensors."""
     n, m = U.shape
     _check(_load().xamg_coldot(_ptr(U), _ptr(V), n, m, _ptr(out), _stream(stream)), "xamg_coldot")
+
+
+def coldot_noalloc(U, V, out, stream=None):
+    """xamg_coldot_noalloc: the same column dots as ``coldot`` for callers that
+    must not allocate device memory during the call; the partial sums go to a
+    fixed 256 KiB array inside the library.  Calls that overlap on the GPU race
+    on that array."""
+    n, m = U.shape
+    _check(_load().xamg_coldot_noalloc(_ptr(U), _ptr(V), n, m, _ptr(out), _stream(stream)),
+           "xamg_coldot_noalloc")

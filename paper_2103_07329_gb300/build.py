@@ -30,7 +30,7 @@ def _nvcc() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("setup.cpp", "kernels.cu", "capi.cu")]
+    return [os.path.join(CSRC, f) for f in ("setup.cpp", "kernels.cu", "capi.cu", "noalloc.cu")]
 
 
 def _deps():
