@@ -30,11 +30,14 @@ def _nvcc() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("setup.cpp", "kernels.cu", "capi.cu", "noalloc.cu")]
+    return [os.path.join(CSRC, f) for f in ("setup.cpp", "kernels.cu", "capi.cu", "noalloc.cu",
+                                            "rows_nv1.cu", "rows_nv2.cu", "rows_nv4.cu",
+                                            "rows_nv8.cu", "rows_nv16.cu", "rows_nv32.cu")]
 
 
 def _deps():
-    return sources() + [os.path.join(CSRC, f) for f in ("hier_host.h", "launch.h", "kernels.cuh")] + [
+    return sources() + [os.path.join(CSRC, f) for f in ("hier_host.h", "launch.h", "kernels.cuh",
+                                                              "rows_inst.cuh")] + [
         os.path.join(ROOT, "include", "xamg_gpu.h")]
 
 

@@ -290,7 +290,7 @@ double row_bytes(const DevCsr &M, const RowOp &op, int nv) {
   return b;
 }
 
-int rows(xamg_hier *h, int level, int which, const DevCsr &M, RowOp op, int nv, bool neg,
+int rows(xamg_hier *h, int level, int which, const DevCsr &M, RowOp op, int nv, bool neg, int epi,
          cudaStream_t st) {
   op.n = M.n;
   op.rowptr = M.rowptr;
@@ -302,7 +302,7 @@ int rows(xamg_hier *h, int level, int which, const DevCsr &M, RowOp op, int nv, 
     b = pool_event(h);
     cudaEventRecord(a, st);
   }
-  const int g = launch_rows(op, nv, slices_for(M, nv), neg, st);
+  const int g = launch_rows(op, nv, slices_for(M, nv), neg, epi, st);
   if (h->timing) {
     cudaEventRecord(b, st);
     h->pending.push_back({a, b, level, which, 2.0 * (double)M.nnz * nv, row_bytes(M, op, nv)});
@@ -316,6 +316,79 @@ RowOp blank() {
   return o;
 }
 
+// ---- Chebyshev smoothing (cheb_steps steps) on level l ----
+// Pre-smoothing from x = 0: on entry x holds d_0 = w_0 .* b (= x_1); on exit
+// x holds the smoothed iterate and r = b - A x.
+int presmooth(xamg_hier *h, Work &W, int l, const double *b, double *x, double *r, cudaStream_t st) {
+  const int nv = W.nv;
+  const int s = h->host.cheb_steps;
+  DevLevel &D = h->lv[l];
+  double *dA = W.vd[l], *dB = W.vd2[l];
+  if (s == 1) {
+    RowOp o = blank();
+    o.init = b; o.src = x; o.y = r;
+    return rows(h, l, 0, D.A, o, nv, true, EPI_Y, st) < 0 ? XAMG_ERR_CUDA : XAMG_OK;
+  }
+  RowOp o = blank();
+  o.init = b; o.src = x; o.y = r; o.dp = x; o.w = D.w[1]; o.c1 = D.c1[1]; o.dnext = dA;
+  if (rows(h, l, 0, D.A, o, nv, true, EPI_Y_DN, st) < 0) return XAMG_ERR_CUDA;
+  double *dprev = dA, *dnext = dB;
+  for (int k = 2; k < s; ++k) {
+    RowOp m = blank();
+    m.init = r; m.src = dprev; m.y = r; m.dp = dprev; m.w = D.w[k]; m.c1 = D.c1[k];
+    m.dnext = dnext; m.x = x;
+    if (rows(h, l, 0, D.A, m, nv, true, EPI_MID, st) < 0) return XAMG_ERR_CUDA;
+    std::swap(dprev, dnext);
+  }
+  RowOp f = blank();
+  f.init = r; f.src = dprev; f.y = r; f.dp = dprev; f.x = x;
+  return rows(h, l, 0, D.A, f, nv, true, EPI_Y_XDP, st) < 0 ? XAMG_ERR_CUDA : XAMG_OK;
+}
+
+// Post-smoothing of x (r is scratch).  If dot_part is set, the partial sums of
+// dot_u . x_final go there and *dot_grid receives their block count.
+int postsmooth(xamg_hier *h, Work &W, int l, const double *b, double *x, double *r, cudaStream_t st,
+               const double *dot_u, double *dot_part, int *dot_grid) {
+  const int nv = W.nv;
+  const int s = h->host.cheb_steps;
+  DevLevel &D = h->lv[l];
+  double *dA = W.vd[l], *dB = W.vd2[l];
+  {
+    RowOp o = blank();
+    o.init = b; o.src = x; o.y = r; o.w = D.w[0]; o.dnext = dA;
+    if (rows(h, l, 0, D.A, o, nv, true, EPI_Y_D0, st) < 0) return XAMG_ERR_CUDA;
+  }
+  if (s == 1) {
+    const int g = elem_grid(D.A.n, nv);
+    launch_axpy_dot(nv, D.A.n, x, dA, dot_part ? dot_u : nullptr, dot_part, g, st);
+    if (dot_part) *dot_grid = g;
+    return XAMG_OK;
+  }
+  double *dprev = dA, *dnext = dB;
+  for (int k = 1; k < s; ++k) {
+    const bool last = k == s - 1;
+    RowOp o = blank();
+    o.init = r; o.src = dprev; o.dp = dprev; o.w = D.w[k]; o.c1 = D.c1[k]; o.x = x;
+    int epi = EPI_MID;
+    if (last) {
+      epi = EPI_XLAST;
+      if (dot_part) {
+        o.dot_u = dot_u;
+        o.partials = dot_part;
+        epi = EPI_XLAST_DOT;
+      }
+    } else {
+      o.y = r;
+      o.dnext = dnext;
+    }
+    const int g = rows(h, l, 0, D.A, o, nv, true, epi, st);
+    if (g < 0) return XAMG_ERR_CUDA;
+    if (last && dot_part) *dot_grid = g;
+    std::swap(dprev, dnext);
+  }
+  return XAMG_OK;
+}
+
 // ---- V(1,1) Chebyshev cycle ----
 // On entry x holds w0 .* b (the first smoother iterate) unless `level` is the
 // coarsest.  If dot_part is set, the partial sums of dot_u . x_final are
@@ -324,7 +397,6 @@ int vcycle(xamg_hier *h, Work &W, int l, const double *b, double *x, cudaStream_
            const double *dot_u, double *dot_part, int *dot_grid) {
   const int nv = W.nv;
   const int L = (int)h->lv.size();
-  const int s = h->host.cheb_steps;
   if (l == L - 1) {
     launch_coarse(nv, h->host.nc, h->lu, h->piv, b, x, st);
     if (dot_part) {
@@ -336,28 +408,8 @@ int vcycle(xamg_hier *h, Work &W, int l, const double *b, double *x, cudaStream_
   }
   DevLevel &D = h->lv[l];
   double *r = W.vr[l];
-  double *dA = W.vd[l], *dB = W.vd2[l];
-  // pre-smoothing from x = 0 (x already holds d_0)
-  if (s == 1) {
-    RowOp o = blank();
-    o.init = b; o.src = x; o.y = r;
-    if (rows(h, l, 0, D.A, o, nv, true, st) < 0) return XAMG_ERR_CUDA;
-  } else {
-    RowOp o = blank();
-    o.init = b; o.src = x; o.y = r; o.dp = x; o.w = D.w[1]; o.c1 = D.c1[1]; o.dnext = dA;
-    if (rows(h, l, 0, D.A, o, nv, true, st) < 0) return XAMG_ERR_CUDA;
-    double *dprev = dA, *dnext = dB;
-    for (int k = 2; k < s; ++k) {
-      RowOp m = blank();
-      m.init = r; m.src = dprev; m.y = r; m.dp = dprev; m.w = D.w[k]; m.c1 = D.c1[k];
-      m.dnext = dnext; m.x = x; m.x_dp = 1;
-      if (rows(h, l, 0, D.A, m, nv, true, st) < 0) return XAMG_ERR_CUDA;
-      std::swap(dprev, dnext);
-    }
-    RowOp f = blank();
-    f.init = r; f.src = dprev; f.y = r; f.dp = dprev; f.x = x; f.x_dp = 1;
-    if (rows(h, l, 0, D.A, f, nv, true, st) < 0) return XAMG_ERR_CUDA;
-  }
+  int rc = presmooth(h, W, l, b, x, r, st);
+  if (rc != XAMG_OK) return rc;
   // restriction b_c = R r (and the coarse level's first smoother iterate)
   {
     const bool next_coarsest = l + 2 == L;
@@ -367,47 +419,19 @@ int vcycle(xamg_hier *h, Work &W, int l, const double *b, double *x, cudaStream_
       o.w = h->lv[l + 1].w[0];
       o.dnext = W.vx[l + 1];
     }
-    if (rows(h, l, 2, D.R, o, nv, false, st) < 0) return XAMG_ERR_CUDA;
+    if (rows(h, l, 2, D.R, o, nv, false, next_coarsest ? EPI_Y : EPI_Y_D0, st) < 0)
+      return XAMG_ERR_CUDA;
   }
-  int rc = vcycle(h, W, l + 1, W.vb[l + 1], W.vx[l + 1], st, nullptr, nullptr, nullptr);
+  rc = vcycle(h, W, l + 1, W.vb[l + 1], W.vx[l + 1], st, nullptr, nullptr, nullptr);
   if (rc != XAMG_OK) return rc;
   // prolongation and correction x += P x_c
   {
     RowOp o = blank();
     o.init = x; o.src = W.vx[l + 1]; o.y = x;
-    if (rows(h, l, 1, D.P, o, nv, false, st) < 0) return XAMG_ERR_CUDA;
+    if (rows(h, l, 1, D.P, o, nv, false, EPI_Y, st) < 0) return XAMG_ERR_CUDA;
   }
-  // post-smoothing from x
-  {
-    RowOp o = blank();
-    o.init = b; o.src = x; o.y = r; o.w = D.w[0]; o.dnext = dA;
-    if (rows(h, l, 0, D.A, o, nv, true, st) < 0) return XAMG_ERR_CUDA;
-  }
-  if (s == 1) {
-    const int g = elem_grid(D.A.n, nv);
-    launch_axpy_dot(nv, D.A.n, x, dA, dot_part ? dot_u : nullptr, dot_part, g, st);
-    if (dot_part) *dot_grid = g;
-  } else {
-    double *dprev = dA, *dnext = dB;
-    for (int k = 1; k < s; ++k) {
-      const bool last = k == s - 1;
-      RowOp o = blank();
-      o.init = r; o.src = dprev; o.dp = dprev; o.w = D.w[k]; o.c1 = D.c1[k];
-      o.x = x; o.x_dp = 1;
-      if (last) {
-        o.x_dn = 1;
-        if (dot_part) {
-          o.dot_u = dot_u; o.dot_of = 1; o.partials = dot_part;
-        }
-      } else {
-        o.y = r; o.dnext = dnext;
-      }
-      const int g = rows(h, l, 0, D.A, o, nv, true, st);
-      if (g < 0) return XAMG_ERR_CUDA;
-      if (last && dot_part) *dot_grid = g;
-      std::swap(dprev, dnext);
-    }
-  }
+  rc = postsmooth(h, W, l, b, x, r, st, dot_u, dot_part, dot_grid);
+  if (rc != XAMG_OK) return rc;
   return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
 }
 
@@ -420,7 +444,7 @@ int sync_read(cudaStream_t st) {
 int true_residual(xamg_hier *h, Work &W, double *T, double *part, cudaStream_t st) {
   RowOp o = blank();
   o.init = W.Bn; o.src = W.X; o.y = T; o.partials2 = part;
-  return rows(h, 0, 0, h->lv[0].A, o, W.nv, true, st);
+  return rows(h, 0, 0, h->lv[0].A, o, W.nv, true, EPI_Y_DOT2, st);
 }
 
 struct SolveCtx {
@@ -507,8 +531,8 @@ int solve_pcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
   for (int k = 1; k <= c.maxit && h->flags_h->active > 0; ++k) {
     c.iterations = k;
     RowOp o = blank();
-    o.src = W.P; o.y = W.Q; o.dot_u = W.P; o.dot_of = 0; o.partials = W.part[0];
-    if ((g = rows(h, 0, 0, h->lv[0].A, o, nv, false, st)) < 0) return XAMG_ERR_CUDA;
+    o.src = W.P; o.y = W.Q; o.dot_u = W.P; o.partials = W.part[0];
+    if ((g = rows(h, 0, 0, h->lv[0].A, o, nv, false, EPI_Y_DOT, st)) < 0) return XAMG_ERR_CUDA;
     launch_scalar(nv, SM_PCG_ALPHA, W.cs, W.part[0], nullptr, g, c.tol, k, fl, st);
     launch_pcg_xr(nv, n, W.X, W.R, W.P, W.Q, W.cs, w0, W.Z, W.part[1], ge, st);
     launch_scalar(nv, SM_PCG_CONV, W.cs, W.part[1], nullptr, ge, c.tol, k, fl, st);
@@ -556,8 +580,8 @@ int solve_bicgstab(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stat
     if ((rc = vcycle(h, W, 0, W.P, W.PH, st, nullptr, nullptr, nullptr)) != XAMG_OK) return rc;
     c.vcycles++;
     RowOp o = blank();
-    o.src = W.PH; o.y = W.V; o.dot_u = W.RH; o.dot_of = 0; o.partials = W.part[1];
-    if ((g = rows(h, 0, 0, h->lv[0].A, o, nv, false, st)) < 0) return XAMG_ERR_CUDA;
+    o.src = W.PH; o.y = W.V; o.dot_u = W.RH; o.partials = W.part[1];
+    if ((g = rows(h, 0, 0, h->lv[0].A, o, nv, false, EPI_Y_DOT, st)) < 0) return XAMG_ERR_CUDA;
     launch_scalar(nv, SM_BI_ALPHA, W.cs, W.part[1], nullptr, g, c.tol, k, fl, st);
     launch_bicg_s(nv, n, W.S, W.R, W.V, W.cs, w0, W.SH, W.part[2], ge, st);
     launch_scalar(nv, SM_BI_HALF, W.cs, W.part[2], nullptr, ge, c.tol, k, fl, st);
@@ -566,9 +590,9 @@ int solve_bicgstab(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stat
       if ((rc = vcycle(h, W, 0, W.S, W.SH, st, nullptr, nullptr, nullptr)) != XAMG_OK) return rc;
       c.vcycles++;
       RowOp t = blank();
-      t.src = W.SH; t.y = W.T; t.dot_u = W.S; t.dot_of = 0; t.partials = W.part[1];
+      t.src = W.SH; t.y = W.T; t.dot_u = W.S; t.partials = W.part[1];
       t.partials2 = W.part[2];
-      if ((g = rows(h, 0, 0, h->lv[0].A, t, nv, false, st)) < 0) return XAMG_ERR_CUDA;
+      if ((g = rows(h, 0, 0, h->lv[0].A, t, nv, false, EPI_Y_DOT2, st)) < 0) return XAMG_ERR_CUDA;
       launch_scalar(nv, SM_BI_OMEGA, W.cs, W.part[1], W.part[2], g, c.tol, k, fl, st);
     }
     launch_bicg_xr(nv, n, W.X, W.R, W.S, W.T, W.PH, W.SH, W.RH, W.cs, W.part[3], W.part[0], ge, st);
@@ -820,7 +844,7 @@ int xamg_level_spmm(xamg_hier *h, int32_t level, int32_t which, const double *X,
   RowOp o = blank();
   o.src = src;
   o.y = dst;
-  if (rows(h, level, which, M, o, nv, false, st) < 0) return XAMG_ERR_CUDA;
+  if (rows(h, level, which, M, o, nv, false, EPI_Y, st) < 0) return XAMG_ERR_CUDA;
   if (nv != m) launch_copy_out(nv, M.n, W.X, Y, m, elem_grid(M.n, nv), st);
   XCK(cudaStreamSynchronize(st));
   XCK(cudaGetLastError());
@@ -842,55 +866,17 @@ int xamg_smooth(xamg_hier *h, int32_t level, const double *B, double *X, double 
   DevLevel &D = h->lv[level];
   const int64_t n = D.A.n;
   const int ge = elem_grid(n, nv);
-  const int s = h->host.cheb_steps;
   // padded copies of B and X in Bn / X, residual in vr, directions in vd/vd2
   launch_pad_in(nv, n, B, m, W.Bn, ge, st);
-  double *x = W.X, *r = W.vr[level], *dA = W.vd[level], *dB = W.vd2[level];
+  double *x = W.X, *r = W.vr[level];
   if (x_zero) {
     launch_scale_rows(nv, n, D.w[0], W.Bn, x, ge, st);
-    if (s == 1) {
-      RowOp o = blank();
-      o.init = W.Bn; o.src = x; o.y = r;
-      if (rows(h, level, 0, D.A, o, nv, true, st) < 0) return XAMG_ERR_CUDA;
-    } else {
-      RowOp o = blank();
-      o.init = W.Bn; o.src = x; o.y = r; o.dp = x; o.w = D.w[1]; o.c1 = D.c1[1]; o.dnext = dA;
-      if (rows(h, level, 0, D.A, o, nv, true, st) < 0) return XAMG_ERR_CUDA;
-      double *dprev = dA, *dnext = dB;
-      for (int k = 2; k < s; ++k) {
-        RowOp q = blank();
-        q.init = r; q.src = dprev; q.y = r; q.dp = dprev; q.w = D.w[k]; q.c1 = D.c1[k];
-        q.dnext = dnext; q.x = x; q.x_dp = 1;
-        if (rows(h, level, 0, D.A, q, nv, true, st) < 0) return XAMG_ERR_CUDA;
-        std::swap(dprev, dnext);
-      }
-      RowOp f = blank();
-      f.init = r; f.src = dprev; f.y = r; f.dp = dprev; f.x = x; f.x_dp = 1;
-      if (rows(h, level, 0, D.A, f, nv, true, st) < 0) return XAMG_ERR_CUDA;
-    }
+    if ((rc = presmooth(h, W, level, W.Bn, x, r, st)) != XAMG_OK) return rc;
     if (R) launch_copy_out(nv, n, r, R, m, ge, st);
   } else {
     launch_pad_in(nv, n, X, m, x, ge, st);
-    RowOp o = blank();
-    o.init = W.Bn; o.src = x; o.y = r; o.w = D.w[0]; o.dnext = dA;
-    if (rows(h, level, 0, D.A, o, nv, true, st) < 0) return XAMG_ERR_CUDA;
-    if (s == 1) {
-      launch_axpy_dot(nv, n, x, dA, nullptr, nullptr, ge, st);
-    } else {
-      double *dprev = dA, *dnext = dB;
-      for (int k = 1; k < s; ++k) {
-        const bool last = k == s - 1;
-        RowOp q = blank();
-        q.init = r; q.src = dprev; q.dp = dprev; q.w = D.w[k]; q.c1 = D.c1[k]; q.x = x; q.x_dp = 1;
-        if (last) q.x_dn = 1;
-        else {
-          q.y = r;
-          q.dnext = dnext;
-        }
-        if (rows(h, level, 0, D.A, q, nv, true, st) < 0) return XAMG_ERR_CUDA;
-        std::swap(dprev, dnext);
-      }
-    }
+    if ((rc = postsmooth(h, W, level, W.Bn, x, r, st, nullptr, nullptr, nullptr)) != XAMG_OK)
+      return rc;
   }
   launch_copy_out(nv, n, x, X, m, ge, st);
   XCK(cudaStreamSynchronize(st));

@@ -30,46 +30,14 @@ int elem_grid(int64_t n, int nv) {
 }
 
 // ------------------------------------------------------------------ rows
-template <int NV, int S, bool NEG>
-static int rows_t(const RowOp &op, cudaStream_t st) {
-  static int max_grid = 0;
-  if (!max_grid) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rows<NV, S, NEG>, kBlock, 0) != cudaSuccess || b < 1)
-      b = 1;
-    max_grid = std::min(kMaxGrid, b * device_sm_count());
-  }
-  constexpr int rows_per_block = kWarps * (32 / (NV * S));
-  const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
-  k_rows<NV, S, NEG><<<grid, kBlock, 0, st>>>(op);
-  g_launches++;
-  return cudaPeekAtLastError() == cudaSuccess ? grid : -1;
-}
-
-template <int NV, bool NEG>
-static int rows_s(const RowOp &op, int slices, cudaStream_t st) {
-  if constexpr (NV == 1) {
-    if (slices >= 16) return rows_t<1, 16, NEG>(op, st);
-    if (slices >= 4) return rows_t<1, 4, NEG>(op, st);
-  } else if constexpr (NV <= 8) {
-    if (slices >= 4) return rows_t<NV, 4, NEG>(op, st);
-  }
-  return rows_t<NV, 1, NEG>(op, st);
-}
-
-int launch_rows(const RowOp &op, int nv, int slices, bool neg, cudaStream_t st) {
+int launch_rows(const RowOp &op, int nv, int slices, bool neg, int epi, cudaStream_t st) {
   switch (nv) {
-#define XAMG_ROWS_CASE(V) \
-  case V:                 \
-    return neg ? rows_s<V, true>(op, slices, st) : rows_s<V, false>(op, slices, st);
-    XAMG_ROWS_CASE(1)
-    XAMG_ROWS_CASE(2)
-    XAMG_ROWS_CASE(4)
-    XAMG_ROWS_CASE(8)
-    XAMG_ROWS_CASE(16)
-    XAMG_ROWS_CASE(32)
-#undef XAMG_ROWS_CASE
+    case 1: return launch_rows_nv1(op, slices, neg, epi, st);
+    case 2: return launch_rows_nv2(op, slices, neg, epi, st);
+    case 4: return launch_rows_nv4(op, slices, neg, epi, st);
+    case 8: return launch_rows_nv8(op, slices, neg, epi, st);
+    case 16: return launch_rows_nv16(op, slices, neg, epi, st);
+    case 32: return launch_rows_nv32(op, slices, neg, epi, st);
   }
   return -1;
 }

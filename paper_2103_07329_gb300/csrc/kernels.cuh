@@ -20,9 +20,9 @@ constexpr int kWarps = kBlock / 32;
 //   y[i,c] = v                                                 (if y)
 //   dn     = c1 * dp[i,c] + w[i] * v                           (if w; dp may be null)
 //   dnext[i,c] = dn                                            (if dnext)
-//   x[i,c] += dp[i,c] (if x_dp) + dn (if x_dn)                 (if x)
-//   partial dot: sum over the block's rows of dot_u[i,c] * t with t = v, the
-//   new x or dn (dot_of = 0, 1, 2), written to partials[block*NV + c].
+//   x[i,c] += dp[i,c] and/or dn
+//   partial dots over the block's rows, written to partials[block*NV + c]
+// which of these apply is the kernel's compile-time epilogue (enum Epi).
 // All pointers except rowptr/col/val/src may alias each other only at the
 // same element (own-row reads before own-row writes); src never aliases an
 // output.
@@ -39,11 +39,9 @@ struct RowOp {
   double c1;
   double *dnext;
   double *x;
-  int x_dp, x_dn;
   const double *dot_u;
-  int dot_of;
   double *partials;
-  double *partials2;  // if set: partial sums of v * v (second reduction)
+  double *partials2;  // partial sums of v * v (EPI_Y_DOT2)
 };
 
 // Sum over the lanes of a warp that hold the same column c = lane % NV, in a
@@ -72,15 +70,177 @@ __device__ __forceinline__ void block_colsum_store(double v, double *out) {
   }
 }
 
-// Row kernel.  A group of G = NV*S lanes owns one row: lane -> column
-// c = lane % NV and slice s = (lane / NV) % S; slice s takes the row's
-// entries s, s+S, s+2S, ...  With S = 1 every lane does exactly the row's
-// FMAs for its column (no reduction adds); S > 1 splits long rows or narrow
-// blocks over more lanes and adds the slices with shuffles.  Warps walk the
-// rows in a grid-stride loop, so the row -> block map (and with it the order
-// of the partial dot sums) depends only on n and the grid size.
-template <int NV, int S, bool NEG>
-__global__ void __launch_bounds__(kBlock) k_rows(RowOp op) {
+// Epilogue of a row kernel, fixed at compile time so that no floating-point
+// operation of an unused branch is executed (v is the row's product sum):
+enum Epi : int {
+  EPI_Y = 0,       // y = v
+  EPI_Y_D0,        // y = v ; dnext = w v                         (first smoother step)
+  EPI_Y_DN,        // y = v ; dnext = c1 dp + w v                 (Chebyshev step, x untouched)
+  EPI_Y_XDP,       // y = v ; x += dp                             (last pre-smoothing step)
+  EPI_MID,         // y = v ; dnext = c1 dp + w v ; x += dp       (middle Chebyshev step)
+  EPI_XLAST,       // x += dp + (c1 dp + w v)                     (last post-smoothing step)
+  EPI_XLAST_DOT,   // EPI_XLAST and partial dot_u . x_new
+  EPI_Y_DOT,       // y = v ; partial dot_u . v
+  EPI_Y_DOT2,      // y = v ; partial dot_u . v (if dot_u) and v . v
+  EPI_COUNT
+};
+
+// dpv, wv, xv, du are the own-row operands loaded before the product loop.
+template <int NV, int EPI>
+__device__ __forceinline__ void row_epilogue(const RowOp &op, int64_t i, int c, double acc,
+                                             double dpv, double wv, double xv, double du,
+                                             double &dsum, double &dsum2) {
+  const int64_t e = i * NV + c;
+  if constexpr (EPI != EPI_XLAST && EPI != EPI_XLAST_DOT) {
+    if (op.y) op.y[e] = acc;
+  }
+  if constexpr (EPI == EPI_Y_D0) op.dnext[e] = wv * acc;
+  if constexpr (EPI == EPI_Y_DN) op.dnext[e] = fma(op.c1, dpv, wv * acc);
+  if constexpr (EPI == EPI_Y_XDP) op.x[e] = xv + dpv;
+  if constexpr (EPI == EPI_MID) {
+    op.dnext[e] = fma(op.c1, dpv, wv * acc);
+    op.x[e] = xv + dpv;
+  }
+  if constexpr (EPI == EPI_XLAST || EPI == EPI_XLAST_DOT) {
+    const double xn = (xv + dpv) + fma(op.c1, dpv, wv * acc);
+    op.x[e] = xn;
+    if constexpr (EPI == EPI_XLAST_DOT) dsum = fma(du, xn, dsum);
+  }
+  if constexpr (EPI == EPI_Y_DOT) dsum = fma(du, acc, dsum);
+  if constexpr (EPI == EPI_Y_DOT2) {
+    if (op.dot_u) dsum = fma(du, acc, dsum);
+    dsum2 = fma(acc, acc, dsum2);
+  }
+}
+
+template <int EPI>
+__device__ __forceinline__ constexpr bool epi_has_dot() {
+  return EPI == EPI_XLAST_DOT || EPI == EPI_Y_DOT || EPI == EPI_Y_DOT2;
+}
+
+// Own-row operands of the epilogue.
+template <int NV, int EPI>
+__device__ __forceinline__ void row_operands(const RowOp &op, int64_t i, int c, double &dpv,
+                                             double &wv, double &xv, double &du) {
+  const int64_t e = i * NV + c;
+  if constexpr (EPI == EPI_Y_DN || EPI == EPI_Y_XDP || EPI == EPI_MID || EPI == EPI_XLAST ||
+                EPI == EPI_XLAST_DOT)
+    dpv = op.dp[e];
+  if constexpr (EPI == EPI_Y_D0 || EPI == EPI_Y_DN || EPI == EPI_MID || EPI == EPI_XLAST ||
+                EPI == EPI_XLAST_DOT)
+    wv = op.w[i];
+  if constexpr (EPI == EPI_Y_XDP || EPI == EPI_MID || EPI == EPI_XLAST || EPI == EPI_XLAST_DOT)
+    xv = op.x[e];
+  if constexpr (EPI == EPI_XLAST_DOT || EPI == EPI_Y_DOT) du = op.dot_u[e];
+  if constexpr (EPI == EPI_Y_DOT2) du = op.dot_u ? op.dot_u[e] : 0.0;
+}
+
+template <bool NEG>
+__device__ __forceinline__ double fmadd(double a, double x, double acc) {
+  return NEG ? fma(-a, x, acc) : fma(a, x, acc);
+}
+
+// Exactly `rem` (1..7) further products of one chunk, in order.
+template <bool NEG>
+__device__ __forceinline__ double tail_fma(int rem, const double (&as)[8], const double (&xs)[8],
+                                           double acc) {
+  switch (rem) {
+    case 7: acc = fmadd<NEG>(as[0], xs[0], acc); acc = fmadd<NEG>(as[1], xs[1], acc);
+            acc = fmadd<NEG>(as[2], xs[2], acc); acc = fmadd<NEG>(as[3], xs[3], acc);
+            acc = fmadd<NEG>(as[4], xs[4], acc); acc = fmadd<NEG>(as[5], xs[5], acc);
+            acc = fmadd<NEG>(as[6], xs[6], acc); break;
+    case 6: acc = fmadd<NEG>(as[0], xs[0], acc); acc = fmadd<NEG>(as[1], xs[1], acc);
+            acc = fmadd<NEG>(as[2], xs[2], acc); acc = fmadd<NEG>(as[3], xs[3], acc);
+            acc = fmadd<NEG>(as[4], xs[4], acc); acc = fmadd<NEG>(as[5], xs[5], acc); break;
+    case 5: acc = fmadd<NEG>(as[0], xs[0], acc); acc = fmadd<NEG>(as[1], xs[1], acc);
+            acc = fmadd<NEG>(as[2], xs[2], acc); acc = fmadd<NEG>(as[3], xs[3], acc);
+            acc = fmadd<NEG>(as[4], xs[4], acc); break;
+    case 4: acc = fmadd<NEG>(as[0], xs[0], acc); acc = fmadd<NEG>(as[1], xs[1], acc);
+            acc = fmadd<NEG>(as[2], xs[2], acc); acc = fmadd<NEG>(as[3], xs[3], acc); break;
+    case 3: acc = fmadd<NEG>(as[0], xs[0], acc); acc = fmadd<NEG>(as[1], xs[1], acc);
+            acc = fmadd<NEG>(as[2], xs[2], acc); break;
+    case 2: acc = fmadd<NEG>(as[0], xs[0], acc); acc = fmadd<NEG>(as[1], xs[1], acc); break;
+    case 1: acc = fmadd<NEG>(as[0], xs[0], acc); break;
+    default: break;
+  }
+  return acc;
+}
+
+// Row kernel, one lane per column (S = 1).  A group of NV lanes owns one row
+// (32/NV rows per warp).  The group reads the row's column indices and values
+// NV at a time with one coalesced load each and passes them around with
+// shuffles, so all operand-row gathers of a chunk of eight entries are issued
+// before their FMAs: the dependent chain per row is row pointer -> index/value
+// -> operand rows, independent of the row length.  Each lane adds its
+// column's products in the row's storage order (no reduction adds), and a
+// chunk's tail takes exactly as many FMAs as it has entries.
+template <int NV, bool NEG, int EPI>
+__device__ __forceinline__ void rows_lane_per_column(const RowOp &op) {
+  constexpr int RPW = 32 / NV;
+  const int lane = threadIdx.x & 31;
+  const int c = lane % NV;
+  const int grp = lane / NV;
+  const int gbase = grp * NV;
+  const int64_t warp0 = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t wstride = (int64_t)gridDim.x * kWarps;
+  const double *__restrict__ val = op.val;
+  const int32_t *__restrict__ col = op.col;
+  const double *__restrict__ src = op.src;
+  double dsum = 0.0, dsum2 = 0.0;
+  for (int64_t base = warp0 * RPW; base < op.n; base += wstride * RPW) {
+    const int64_t i = base + grp;
+    const bool valid = i < op.n;
+    int start = 0, len = 0;
+    double acc = 0.0, dpv = 0.0, wv = 0.0, xv = 0.0, du = 0.0;
+    if (valid) {
+      start = __ldg(op.rowptr + i);
+      len = __ldg(op.rowptr + i + 1) - start;
+      if (op.init) acc = op.init[i * NV + c];
+      row_operands<NV, EPI>(op, i, c, dpv, wv, xv, du);
+    }
+    const int maxlen = RPW == 1 ? len : __reduce_max_sync(0xffffffffu, len);
+    for (int kb = 0; kb < maxlen; kb += NV) {
+      const bool own = kb + c < len;
+      const int cl = own ? __ldg(col + start + kb + c) : 0;
+      const double av = own ? __ldg(val + start + kb + c) : 0.0;
+      const int cnt = min(NV, maxlen - kb);
+      for (int t = 0; t < cnt; t += 8) {
+        double xs[8], as[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int from = (gbase + t + u) & 31;
+          const int cc = __shfl_sync(0xffffffffu, cl, from);
+          as[u] = __shfl_sync(0xffffffffu, av, from);
+          xs[u] = (t + u < cnt && kb + t + u < len) ? __ldg(src + (int64_t)cc * NV + c) : 0.0;
+        }
+        // entries past this row's own end carry a = x = 0 (rows of one warp
+        // may differ in length when NV < 32)
+        const int rem = min(8, cnt - t);
+        if (rem == 8) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc = fmadd<NEG>(as[u], xs[u], acc);
+        } else {
+          acc = tail_fma<NEG>(rem, as, xs, acc);
+        }
+      }
+    }
+    if (valid) row_epilogue<NV, EPI>(op, i, c, acc, dpv, wv, xv, du, dsum, dsum2);
+  }
+  if constexpr (epi_has_dot<EPI>()) {
+    if (EPI != EPI_Y_DOT2 || op.dot_u) block_colsum_store<NV>(dsum, op.partials);
+    if constexpr (EPI == EPI_Y_DOT2) {
+      __syncthreads();
+      block_colsum_store<NV>(dsum2, op.partials2);
+    }
+  }
+}
+
+// Row kernel with S > 1 slices per column (narrow blocks, m = 1): a group of
+// G = NV*S lanes owns one row, lane -> column c = lane % NV and slice
+// s = (lane / NV) % S; slice s takes the row's entries s, s+S, ... and the
+// slices are added with shuffles.
+template <int NV, int S, bool NEG, int EPI>
+__device__ __forceinline__ void rows_sliced(const RowOp &op) {
   constexpr int G = NV * S;
   constexpr int RPW = 32 / G;
   const int lane = threadIdx.x & 31;
@@ -96,9 +256,10 @@ __global__ void __launch_bounds__(kBlock) k_rows(RowOp op) {
   for (int64_t base = warp0 * RPW; base < op.n; base += wstride * RPW) {
     const int64_t i = base + grp;
     const bool valid = i < op.n;
-    double acc = 0.0;
+    double acc = 0.0, dpv = 0.0, wv = 0.0, xv = 0.0, du = 0.0;
     if (valid) {
       if (op.init && s == 0) acc = op.init[i * NV + c];
+      row_operands<NV, EPI>(op, i, c, dpv, wv, xv, du);
       int k = __ldg(op.rowptr + i) + s;
       const int end = __ldg(op.rowptr + i + 1);
       for (; k + 3 * S < end; k += 4 * S) {
@@ -108,51 +269,40 @@ __global__ void __launch_bounds__(kBlock) k_rows(RowOp op) {
                      a3 = __ldg(val + k + 3 * S);
         const double x0 = __ldg(src + (int64_t)k0 * NV + c), x1 = __ldg(src + (int64_t)k1 * NV + c),
                      x2 = __ldg(src + (int64_t)k2 * NV + c), x3 = __ldg(src + (int64_t)k3 * NV + c);
-        if (NEG) {
-          acc = fma(-a0, x0, acc); acc = fma(-a1, x1, acc);
-          acc = fma(-a2, x2, acc); acc = fma(-a3, x3, acc);
-        } else {
-          acc = fma(a0, x0, acc); acc = fma(a1, x1, acc);
-          acc = fma(a2, x2, acc); acc = fma(a3, x3, acc);
-        }
+        acc = fmadd<NEG>(a0, x0, acc);
+        acc = fmadd<NEG>(a1, x1, acc);
+        acc = fmadd<NEG>(a2, x2, acc);
+        acc = fmadd<NEG>(a3, x3, acc);
       }
       for (; k < end; k += S) {
         const double a = __ldg(val + k);
-        const double xv = __ldg(src + (int64_t)__ldg(col + k) * NV + c);
-        acc = NEG ? fma(-a, xv, acc) : fma(a, xv, acc);
+        acc = fmadd<NEG>(a, __ldg(src + (int64_t)__ldg(col + k) * NV + c), acc);
       }
     }
-    if (S > 1) {
 #pragma unroll
-      for (int o = NV; o < G; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    }
-    if (valid && s == 0) {
-      const int64_t e = i * NV + c;
-      if (op.y) op.y[e] = acc;
-      double dn = 0.0, dpv = 0.0, xn = 0.0;
-      if (op.dp) dpv = op.dp[e];
-      if (op.w) {
-        const double wr = op.w[i] * acc;
-        dn = op.dp ? fma(op.c1, dpv, wr) : wr;
-        if (op.dnext) op.dnext[e] = dn;
-      }
-      if (op.x) {
-        xn = op.x[e];
-        if (op.x_dp) xn += dpv;
-        if (op.x_dn) xn += dn;
-        op.x[e] = xn;
-      }
-      if (op.partials) {
-        const double t = op.dot_of == 0 ? acc : (op.dot_of == 1 ? xn : dn);
-        dsum = fma(op.dot_u[e], t, dsum);
-      }
-      if (op.partials2) dsum2 = fma(acc, acc, dsum2);
+    for (int o = NV; o < G; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (valid && s == 0) row_epilogue<NV, EPI>(op, i, c, acc, dpv, wv, xv, du, dsum, dsum2);
+  }
+  if constexpr (epi_has_dot<EPI>()) {
+    if (EPI != EPI_Y_DOT2 || op.dot_u) block_colsum_store<NV>(dsum, op.partials);
+    if constexpr (EPI == EPI_Y_DOT2) {
+      __syncthreads();
+      block_colsum_store<NV>(dsum2, op.partials2);
     }
   }
-  if (op.partials) block_colsum_store<NV>(dsum, op.partials);
-  if (op.partials2) {
-    __syncthreads();
-    block_colsum_store<NV>(dsum2, op.partials2);
+}
+
+// The fused row kernel.  Warps walk the rows in a grid-stride loop, so the
+// row -> block map (and with it the order of the partial dot sums) depends
+// only on n and the grid size.  At most 64 registers per thread (four
+// 256-thread blocks per SM): measured faster than the uncapped build, whose
+// wider epilogues took 80 registers and three blocks per SM.
+template <int NV, int S, bool NEG, int EPI>
+__global__ void __launch_bounds__(kBlock, 4) k_rows(RowOp op) {
+  if constexpr (S == 1) {
+    rows_lane_per_column<NV, NEG, EPI>(op);
+  } else {
+    rows_sliced<NV, S, NEG, EPI>(op);
   }
 }
 

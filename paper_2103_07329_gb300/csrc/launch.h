@@ -52,9 +52,16 @@ enum ScalarMode : int {
 int device_sm_count();
 extern std::atomic<int64_t> g_launches;  // kernels launched by the library
 
-// Fused row operation; returns the grid size used (needed to reduce
-// op.partials), or -1 on a launch error.
-int launch_rows(const RowOp &op, int nv, int slices, bool neg, cudaStream_t st);
+// Fused row operation with epilogue `epi` (enum Epi); returns the grid size
+// used (needed to reduce op.partials), or -1 on a launch error or an
+// unsupported combination.  One translation unit per NV (rows_nv*.cu).
+int launch_rows(const RowOp &op, int nv, int slices, bool neg, int epi, cudaStream_t st);
+int launch_rows_nv1(const RowOp &op, int slices, bool neg, int epi, cudaStream_t st);
+int launch_rows_nv2(const RowOp &op, int slices, bool neg, int epi, cudaStream_t st);
+int launch_rows_nv4(const RowOp &op, int slices, bool neg, int epi, cudaStream_t st);
+int launch_rows_nv8(const RowOp &op, int slices, bool neg, int epi, cudaStream_t st);
+int launch_rows_nv16(const RowOp &op, int slices, bool neg, int epi, cudaStream_t st);
+int launch_rows_nv32(const RowOp &op, int slices, bool neg, int epi, cudaStream_t st);
 
 // Elementwise grid size for n rows of nv columns.
 int elem_grid(int64_t n, int nv);

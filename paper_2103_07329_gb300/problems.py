@@ -14,6 +14,10 @@ Matrices (paper Sec. 3, "Example case": the 3D Poisson equation on a cube,
     i + N j + N^2 k with i fastest.
   * ``poisson27(N)``: the 27-point analogue, diagonal 26, all 26 neighbours -1.
 
+  * ``diffusion7(N, k)``: cell-centred finite volumes for -div(k grad u) with
+    cell coefficients k (e.g. lognormal, ``lognormal_cells``), the
+    variable-coefficient systems the mixed-precision and batched forms use.
+
 Right-hand sides: entries i.i.d. uniform[-1, 1) from numpy's
 ``default_rng(seed)``, n x m row-major (C order).
 """
@@ -77,6 +81,54 @@ def poisson27(N: int) -> CSR:
     """27-point Laplacian on an N^3 grid (Dirichlet nodes eliminated)."""
     offs = [(dk, dj, di) for dk in (-1, 0, 1) for dj in (-1, 0, 1) for di in (-1, 0, 1)]
     return _stencil(N, offs, 26.0)
+
+
+def lognormal_cells(N: int, sigma: float, seed: int) -> np.ndarray:
+    """Cell coefficients k = exp(sigma g), g i.i.d. standard normal from
+    numpy's default_rng(seed), one per cell in lexicographic order."""
+    return np.exp(sigma * np.random.default_rng(seed).standard_normal(N * N * N))
+
+
+def diffusion7(N: int, kcell: np.ndarray) -> CSR:
+    """Cell-centred finite-volume -div(k grad u) on an N^3 grid of unit cells.
+
+    Face transmissibility between cells a and b is the harmonic mean
+    2 k_a k_b / (k_a + k_b); a boundary face carries the Dirichlet value at the
+    face, half a cell away, so its transmissibility is 2 k_c.  Off-diagonals
+    are -T, the diagonal the sum of the cell's six face transmissibilities.
+    Rows are lexicographic with i fastest, columns ascending."""
+    n = N * N * N
+    k = np.asarray(kcell, dtype=np.float64).reshape(-1)
+    if k.size != n or np.any(k <= 0) or not np.all(np.isfinite(k)):
+        raise ValueError("need N^3 positive finite cell coefficients")
+    idx = np.arange(n, dtype=np.int64)
+    i = idx % N
+    j = (idx // N) % N
+    kk = idx // (N * N)
+    offs = [(-1, 0, 0), (0, -1, 0), (0, 0, -1), (0, 0, 0), (0, 0, 1), (0, 1, 0), (1, 0, 0)]
+    cols = np.empty((n, 7), dtype=np.int64)
+    valid = np.empty((n, 7), dtype=bool)
+    vals = np.zeros((n, 7), dtype=np.float64)
+    diag = np.zeros(n, dtype=np.float64)
+    for t, (dk, dj, di) in enumerate(offs):
+        if (dk, dj, di) == (0, 0, 0):
+            continue
+        ok = ((i + di >= 0) & (i + di < N) & (j + dj >= 0) & (j + dj < N)
+              & (kk + dk >= 0) & (kk + dk < N))
+        nb = idx + di + N * dj + N * N * dk
+        T = np.where(ok, 2.0 * k * k[np.where(ok, nb, idx)] / (k + k[np.where(ok, nb, idx)]), 2.0 * k)
+        diag += T
+        cols[:, t] = nb
+        valid[:, t] = ok
+        vals[:, t] = -T
+    cols[:, 3] = idx
+    valid[:, 3] = True
+    vals[:, 3] = diag
+    counts = valid.sum(axis=1)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    return CSR(n, rowptr.astype(np.int32), np.ascontiguousarray(cols[valid], dtype=np.int32),
+               np.ascontiguousarray(vals[valid], dtype=np.float64))
 
 
 def rhs_uniform(n: int, m: int, seed: int = 0, m_draw: int | None = None) -> np.ndarray:

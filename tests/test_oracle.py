@@ -61,7 +61,30 @@ def test_poisson27_closed_forms(N):
     assert np.all(S.diagonal() == 26.0)
 
 
+def test_diffusion7_hand_cases():
+    # constant k = 1: interior faces T = 1, boundary faces T = 2 (half-cell
+    # Dirichlet distance), so the row sum is 2 x (number of boundary faces)
+    N = 4
+    A = P.diffusion7(N, np.ones(N ** 3))
+    S = to_scipy(A)
+    assert (S != S.T).nnz == 0
+    idx = np.arange(A.n)
+    i, j, k = idx % N, (idx // N) % N, idx // (N * N)
+    bfaces = sum((c == 0).astype(int) + (c == N - 1).astype(int) for c in (i, j, k))
+    assert np.array_equal(np.asarray(S.sum(axis=1)).ravel(), 2.0 * bfaces)
+    assert np.array_equal(S.diagonal(), 6.0 + bfaces)
+    assert A.nnz == P.poisson7(N).nnz
+    # two cells with k = 1 and 3 in a 2x2x2 block: harmonic mean 2*1*3/4 = 1.5
+    kc = np.ones(8)
+    kc[1] = 3.0
+    B = to_scipy(P.diffusion7(2, kc)).toarray()
+    assert B[0, 1] == -1.5 and B[1, 0] == -1.5
+    # cell 1 has three interior faces (T = 1.5) and three boundary faces (T = 2 k = 6)
+    assert B[1, 1] == 3 * 1.5 + 3 * 2 * 3.0
+
+
 def eigvec7(N, p, q, r):
+
     g = np.arange(1, N + 1)
     s = lambda a: np.sin(np.pi * a * g / (N + 1))
     v = np.einsum("k,j,i->kji", s(r), s(q), s(p)).reshape(-1)
