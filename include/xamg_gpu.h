@@ -58,6 +58,18 @@ extern "C" {
 #define XAMG_PCG 0
 #define XAMG_BICGSTAB 1
 
+/* preconditioner precision (paper Sec. 2.3, "mixed-precision": reduced
+ * precision in the multigrid hierarchy only, basic precision for the result)
+ *   XAMG_PREC_FP64  V-cycle in FP64, standard PCG / BiCGStab
+ *   XAMG_PREC_FP32  V-cycle on FP32 blocks with FP32 values of A, P, R and
+ *                   FP32 accumulation; FP64 coarsest solve; PCG becomes
+ *                   flexible PCG (FP64 outer loop, FP64 dots and residuals)
+ *   XAMG_PREC_BF16  as FP32, but A's values are bf16 relative to a per-row
+ *                   FP32 scale s_i = max_j |a_ij|: a_ij ~ s_i bf16(a_ij / s_i) */
+#define XAMG_PREC_FP64 0
+#define XAMG_PREC_FP32 1
+#define XAMG_PREC_BF16 2
+
 /* largest m accepted by the solve entry points */
 #define XAMG_MAX_RHS 32
 
@@ -107,6 +119,7 @@ typedef struct {
 
 /* Solve options (fill with xamg_solve_opts_default first).
  *   method       XAMG_PCG or XAMG_BICGSTAB
+ *   precond      XAMG_PREC_FP64 (default), XAMG_PREC_FP32 or XAMG_PREC_BF16
  *   stream       cudaStream_t as void*, NULL = legacy default stream
  *   workspace    optional caller-owned DEVICE buffer of workspace_bytes bytes
  *                (at least xamg_workspace_bytes(); 256-byte aligned); NULL
@@ -114,6 +127,7 @@ typedef struct {
  *   workspace_bytes  size of `workspace` */
 typedef struct {
   int32_t method;
+  int32_t precond;
   void *stream;
   void *workspace;
   size_t workspace_bytes;
@@ -173,8 +187,10 @@ int xamg_level_export(const xamg_hier *h, int32_t level, int32_t *rowptr, int32_
  * with row piv[k]) into caller-owned HOST arrays; *nc receives the size. */
 int xamg_coarse_export(const xamg_hier *h, int32_t *nc, double *lu, int32_t *piv);
 
-/* Bytes of device workspace a solve of m columns with `method` needs. */
-int xamg_workspace_bytes(const xamg_hier *h, int32_t m, int32_t method, size_t *bytes);
+/* Bytes of device workspace a solve of m columns with `method` and
+ * preconditioner precision `precond` needs. */
+int xamg_workspace_bytes(const xamg_hier *h, int32_t m, int32_t method, int32_t precond,
+                         size_t *bytes);
 
 /* Solves A X = B to ||b_j - A x_j|| <= tol ||b_j|| for every column
  * (paper Sec. 1 and 2.1; PCG or BiCGStab preconditioned by one V(1,1)
@@ -213,6 +229,14 @@ int xamg_smooth(xamg_hier *h, int32_t level, const double *B, double *X, double 
  * application z = M^-1 r of paper Fig. 3, MultiGrid with max_iters 1).
  * DEVICE row-major blocks n x m. */
 int xamg_vcycle(xamg_hier *h, const double *B, double *X, int32_t m, void *stream);
+
+/* One V(1,1) cycle in preconditioner precision `precond` (XAMG_PREC_*): B is
+ * rounded to the FP32 block, the cycle runs on FP32 blocks (FP64 coarsest
+ * solve) and its result is widened into X.  DEVICE FP64 row-major blocks
+ * n x m.  XAMG_PREC_FP64 is xamg_vcycle.  The first reduced-precision call
+ * uploads the FP32/bf16 copies of the hierarchy (kept until xamg_destroy). */
+int xamg_vcycle_precond(xamg_hier *h, int32_t precond, const double *B, double *X, int32_t m,
+                        void *stream);
 
 /* Coarsest-level direct solve X = A_L^-1 B with the LU factors of the setup
  * (paper Tab. 1, Direct).  DEVICE row-major blocks n_L x m. */
@@ -259,7 +283,8 @@ int xamg_timing_enable(xamg_hier *h, int32_t enable);
 
 /* Reads and clears nothing: launches and total device milliseconds of the
  * timed row-kernel launches on `level` for operator `which` (0 = A, 1 = P,
- * 2 = R) since timing was last enabled, plus the algorithmic flops and bytes
+ * 2 = R on FP64 blocks; 3, 4, 5 = the same on FP32 blocks) since timing was
+ * last enabled, plus the algorithmic flops and bytes
  * of those launches (flops = 2 nnz m_padded; bytes = 12 nnz + 4 (rows+1) +
  * 8 (cols_in + rows) m_padded per product plus the epilogue's block reads and
  * writes).  Output pointers may be NULL. */

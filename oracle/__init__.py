@@ -69,6 +69,18 @@ def lib():
         L.orc_cheb_smooth.restype = C.c_int
         L.orc_vcycle.argtypes = [C.c_void_p, C.c_int, _f64p, _f64p]
         L.orc_vcycle.restype = C.c_int
+        L.orc_vcycle_prec.argtypes = [C.c_void_p, C.c_int, C.c_int, _f64p, _f64p]
+        L.orc_vcycle_prec.restype = C.c_int
+        _f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+        L.orc_spmm_f.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, _f32p, _f32p]
+        L.orc_spmm_f.restype = C.c_int
+        L.orc_bf16_bits.argtypes = [C.c_float]
+        L.orc_bf16_bits.restype = C.c_uint16
+        for name in ("orc_pcg_prec", "orc_bicgstab_prec"):
+            f = getattr(L, name)
+            f.argtypes = [C.c_void_p, C.c_int, C.c_int, _f64p, _f64p, C.c_double, C.c_int, _i32p,
+                          _f64p, _i32p]
+            f.restype = C.c_int
         for name in ("orc_pcg", "orc_bicgstab"):
             f = getattr(L, name)
             f.argtypes = [C.c_void_p, C.c_int, _f64p, _f64p, C.c_double, C.c_int, _i32p, _f64p,
@@ -190,20 +202,48 @@ class Hierarchy:
             raise RuntimeError(f"orc_vcycle failed: {rc}")
         return X
 
-    def _solve(self, fn, B, tol, maxit):
+    def vcycle_prec(self, prec: int, B: np.ndarray) -> np.ndarray:
+        """One V-cycle with the preconditioner precision prec (0 FP64, 1 FP32, 2 bf16 A)."""
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        X = np.empty_like(B)
+        rc = lib().orc_vcycle_prec(self._h, prec, B.shape[1], B, X)
+        if rc != 0:
+            raise RuntimeError(f"orc_vcycle_prec failed: {rc}")
+        return X
+
+    def spmm_f(self, l: int, which: int, X: np.ndarray, bf16: bool = False) -> np.ndarray:
+        """FP32 product of level l's operator (0 A, 1 P, 2 R) with an FP32 block."""
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        rows = self.level(l).n if which != 2 else self.level(l + 1).n
+        Y = np.empty((rows, X.shape[1]), dtype=np.float32)
+        rc = lib().orc_spmm_f(self._h, l, which, 1 if bf16 else 0, X.shape[1], X, Y)
+        if rc != 0:
+            raise RuntimeError(f"orc_spmm_f failed: {rc}")
+        return Y
+
+    def _solve(self, fn, B, tol, maxit, prec=None):
         B = np.ascontiguousarray(B, dtype=np.float64)
         m = B.shape[1]
         X = np.empty_like(B)
         it = np.zeros(m, np.int32); rr = np.zeros(m, np.float64); st = np.zeros(m, np.int32)
-        rc = fn(self._h, m, B, X, tol, maxit, it, rr, st)
+        if prec is None:
+            rc = fn(self._h, m, B, X, tol, maxit, it, rr, st)
+        else:
+            rc = fn(self._h, prec, m, B, X, tol, maxit, it, rr, st)
         if rc < 0:
             raise RuntimeError(f"oracle solve failed: {rc}")
         return SolveResult(X, it, rr, st, rc)
 
-    def pcg(self, B, tol=1e-8, maxit=200):
+    def pcg(self, B, tol=1e-8, maxit=200, prec=0):
+        """PCG; with prec 1 (FP32) or 2 (bf16 A) the preconditioner is the
+        reduced-precision V-cycle and the iteration is flexible PCG."""
+        if prec:
+            return self._solve(lib().orc_pcg_prec, B, tol, maxit, prec)
         return self._solve(lib().orc_pcg, B, tol, maxit)
 
-    def bicgstab(self, B, tol=1e-8, maxit=200):
+    def bicgstab(self, B, tol=1e-8, maxit=200, prec=0):
+        if prec:
+            return self._solve(lib().orc_bicgstab_prec, B, tol, maxit, prec)
         return self._solve(lib().orc_bicgstab, B, tol, maxit)
 
 
@@ -231,6 +271,11 @@ def lu_solve(lu: np.ndarray, piv: np.ndarray, B: np.ndarray) -> np.ndarray:
         b = b[:, None]
     lib().orc_lu_solve(lu.shape[0], np.ascontiguousarray(lu).reshape(-1), piv, b.shape[1], b.reshape(-1))
     return b
+
+
+def bf16_bits(f: float) -> int:
+    """bf16 bits of an FP32 value, round to nearest even."""
+    return int(lib().orc_bf16_bits(f))
 
 
 def splitmix_uniform(i: int) -> float:

@@ -82,6 +82,11 @@ typedef struct {
   double *lu;  /* coarsest dense LU factors, row-major nc x nc */
   int *piv;
   int nc;
+  /* reduced-precision copies for the FP32 preconditioner (built on first use) */
+  int lp_ready;
+  float *af[ORC_MAXLEV], *pf[ORC_MAXLEV], *rf[ORC_MAXLEV], *dinvf[ORC_MAXLEV];
+  uint16_t *aq[ORC_MAXLEV];  /* bf16 bits of fl32(a_ij) / s_i */
+  float *as[ORC_MAXLEV];     /* s_i = fl32(max_j |a_ij|) */
 } ohier;
 
 static int64_t nnz_of(const ocsr *a) { return a->rowptr[a->n]; }
@@ -514,6 +519,7 @@ void orc_free(ohier *h) {
   for (l = 0; l < ORC_MAXLEV; ++l) {
     csr_free(&h->A[l]); csr_free(&h->P[l]); csr_free(&h->R[l]);
     free(h->cf[l]); free(h->dinv[l]);
+    free(h->af[l]); free(h->pf[l]); free(h->rf[l]); free(h->dinvf[l]); free(h->aq[l]); free(h->as[l]);
   }
   free(h->lu); free(h->piv);
   free(h);
@@ -695,6 +701,7 @@ int orc_cheb_smooth(const ohier *h, int l, int m, const double *b, double *x, in
 
 /* One V(1,1) cycle from x = 0 (paper Fig. 3: MultiGrid, max_iters 1, Chebyshev
  * pre- and post-smoother; coarsest level by the direct solver). */
+static int vcycle(const ohier *h, int l, int m, const double *b, double *x);
 static int vcycle(const ohier *h, int l, int m, const double *b, double *x) {
   const ocsr *A = &h->A[l];
   size_t N = (size_t)A->n * m, e;
@@ -724,6 +731,204 @@ done:
 int orc_vcycle(const ohier *h, int m, const double *b, double *x) {
   if (!h || m < 1) return ORC_ERR_ARG;
   return vcycle(h, 0, m, b, x);
+}
+
+/* ------------------------------------------------------------------ */
+/* Reduced-precision preconditioner (paper Sec. 2.3, "mixed-precision": a
+ * reduced floating-point type inside part of the multigrid hierarchy, the
+ * basic precision for the result).  Reading: every value of A, P, R, D^-1 and
+ * every Chebyshev coefficient is rounded once to FP32 and the V-cycle runs in
+ * FP32 arithmetic (each operation rounded to FP32), except the coarsest
+ * solve, which widens its FP32 input, solves with the FP64 LU factors and
+ * rounds the result back.  In the bf16 variant A's values are stored as
+ * q_ij = bf16(fl32(a_ij) / s_i), s_i = fl32(max_j |a_ij|), and a row product
+ * is s_i * sum_j q_ij x_j. */
+
+/* bf16 bits of a float: IEEE 754 roundTiesToEven on the 16 dropped
+ * mantissa bits (NaN stays NaN). */
+static uint16_t bf16_bits(float f) {
+  uint32_t u, lsb;
+  memcpy(&u, &f, sizeof(u));
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x0040u);
+  lsb = (u >> 16) & 1u;
+  u = u + 0x7fffu + lsb;
+  return (uint16_t)(u >> 16);
+}
+
+static float bf16_value(uint16_t b) {
+  uint32_t u = (uint32_t)b << 16;
+  float f;
+  memcpy(&f, &u, sizeof(f));
+  return f;
+}
+
+uint16_t orc_bf16_bits(float f) { return bf16_bits(f); }
+
+static float *to_f32(const double *v, int64_t n) {
+  int64_t k;
+  float *o = (float *)malloc((size_t)(n > 0 ? n : 1) * sizeof(float));
+  if (!o) return NULL;
+  for (k = 0; k < n; ++k) o[k] = (float)v[k];
+  return o;
+}
+
+static int build_lowp(ohier *h) {
+  int l, i, p;
+  if (h->lp_ready) return ORC_OK;
+  for (l = 0; l < h->nlev; ++l) {
+    const ocsr *A = &h->A[l];
+    h->af[l] = to_f32(A->val, nnz_of(A));
+    h->dinvf[l] = to_f32(h->dinv[l], A->n);
+    h->aq[l] = (uint16_t *)malloc((size_t)(nnz_of(A) > 0 ? nnz_of(A) : 1) * sizeof(uint16_t));
+    h->as[l] = (float *)malloc((size_t)A->n * sizeof(float));
+    if (!h->af[l] || !h->dinvf[l] || !h->aq[l] || !h->as[l]) return ORC_ERR_OOM;
+    for (i = 0; i < A->n; ++i) {
+      double mx = 0.0;
+      for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) if (fabs(A->val[p]) > mx) mx = fabs(A->val[p]);
+      h->as[l][i] = mx > 0.0 ? (float)mx : 1.0f;
+      for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) h->aq[l][p] = bf16_bits(h->af[l][p] / h->as[l][i]);
+    }
+    if (l + 1 < h->nlev) {
+      h->pf[l] = to_f32(h->P[l].val, nnz_of(&h->P[l]));
+      h->rf[l] = to_f32(h->R[l].val, nnz_of(&h->R[l]));
+      if (!h->pf[l] || !h->rf[l]) return ORC_ERR_OOM;
+    }
+  }
+  h->lp_ready = 1;
+  return ORC_OK;
+}
+
+/* y = A x in FP32 for an n x m block; which: 0 = A, 1 = P, 2 = R; bf16 = 1
+ * uses A's bf16 values and row scales. */
+static void spmm_f(const ohier *h, int l, int which, int bf16, int m, const float *X, float *Y) {
+  const ocsr *M = which == 0 ? &h->A[l] : which == 1 ? &h->P[l] : &h->R[l];
+  const float *v = which == 0 ? h->af[l] : which == 1 ? h->pf[l] : h->rf[l];
+  int i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < M->n; ++i) {
+    float *y = Y + (size_t)i * m;
+    int j, p;
+    for (j = 0; j < m; ++j) y[j] = 0.0f;
+    for (p = M->rowptr[i]; p < M->rowptr[i + 1]; ++p) {
+      const float a = (which == 0 && bf16) ? bf16_value(h->aq[l][p]) : v[p];
+      const float *x = X + (size_t)M->col[p] * m;
+      for (j = 0; j < m; ++j) y[j] = y[j] + a * x[j];
+    }
+    if (which == 0 && bf16)
+      for (j = 0; j < m; ++j) y[j] = h->as[l][i] * y[j];
+  }
+}
+
+/* FP32 Chebyshev smoothing: the recurrence of cheb_smooth with FP32 data. */
+static int cheb_smooth_f(const ohier *h, int l, int bf16, int m, const float *b, float *x, int x_zero,
+                         float *r_out) {
+  const ocsr *A = &h->A[l];
+  size_t N = (size_t)A->n * m, e;
+  int i, j, k, steps = h->cheb_steps;
+  double lo = h->cheb_lo[l], hi = h->cheb_hi[l];
+  double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  double rho = 1.0 / sigma, rho_new;
+  const float c0 = (float)(1.0 / theta);
+  const float *dv = h->dinvf[l];
+  float *r = (float *)malloc(N * sizeof(float));
+  float *d = (float *)malloc(N * sizeof(float));
+  float *t = (float *)malloc(N * sizeof(float));
+  if (!r || !d || !t) { free(r); free(d); free(t); return ORC_ERR_OOM; }
+  if (x_zero) {
+    for (e = 0; e < N; ++e) { r[e] = b[e]; x[e] = 0.0f; }
+  } else {
+    spmm_f(h, l, 0, bf16, m, x, t);
+    for (e = 0; e < N; ++e) r[e] = b[e] - t[e];
+  }
+  for (i = 0; i < A->n; ++i)
+    for (j = 0; j < m; ++j) {
+      e = (size_t)i * m + j;
+      d[e] = c0 * (dv[i] * r[e]);
+      x[e] = x[e] + d[e];
+    }
+  for (k = 1; k < steps; ++k) {
+    float c1, c2;
+    spmm_f(h, l, 0, bf16, m, d, t);
+    for (e = 0; e < N; ++e) r[e] = r[e] - t[e];
+    rho_new = 1.0 / (2.0 * sigma - rho);
+    c1 = (float)(rho_new * rho);
+    c2 = (float)(2.0 * rho_new / delta);
+    for (i = 0; i < A->n; ++i)
+      for (j = 0; j < m; ++j) {
+        e = (size_t)i * m + j;
+        d[e] = c1 * d[e] + c2 * (dv[i] * r[e]);
+        x[e] = x[e] + d[e];
+      }
+    rho = rho_new;
+  }
+  if (r_out) {
+    spmm_f(h, l, 0, bf16, m, d, t);
+    for (e = 0; e < N; ++e) r_out[e] = r[e] - t[e];
+  }
+  free(r); free(d); free(t);
+  return ORC_OK;
+}
+
+static int vcycle_f(const ohier *h, int l, int bf16, int m, const float *b, float *x) {
+  const ocsr *A = &h->A[l];
+  size_t N = (size_t)A->n * m, e;
+  int rc;
+  float *r, *bc, *xc, *t;
+  if (l == h->nlev - 1) {
+    double *w = (double *)malloc(N * sizeof(double));
+    if (!w) return ORC_ERR_OOM;
+    for (e = 0; e < N; ++e) w[e] = (double)b[e];
+    lu_solve(h->nc, h->lu, h->piv, m, w);
+    for (e = 0; e < N; ++e) x[e] = (float)w[e];
+    free(w);
+    return ORC_OK;
+  }
+  r = (float *)malloc(N * sizeof(float));
+  t = (float *)malloc(N * sizeof(float));
+  bc = (float *)malloc((size_t)h->A[l + 1].n * m * sizeof(float));
+  xc = (float *)malloc((size_t)h->A[l + 1].n * m * sizeof(float));
+  if (!r || !t || !bc || !xc) { rc = ORC_ERR_OOM; goto done; }
+  if ((rc = cheb_smooth_f(h, l, bf16, m, b, x, 1, r)) != ORC_OK) goto done;
+  spmm_f(h, l, 2, 0, m, r, bc);
+  if ((rc = vcycle_f(h, l + 1, bf16, m, bc, xc)) != ORC_OK) goto done;
+  spmm_f(h, l, 1, 0, m, xc, t);
+  for (e = 0; e < N; ++e) x[e] = x[e] + t[e];
+  rc = cheb_smooth_f(h, l, bf16, m, b, x, 0, NULL);
+done:
+  free(r); free(t); free(bc); free(xc);
+  return rc;
+}
+
+/* z = M r for an FP64 block r: prec 0 = the FP64 V-cycle; 1 = FP32 values;
+ * 2 = bf16 values of A.  The reduced forms round r to FP32 and widen z. */
+static int apply_M(ohier *h, int prec, int m, const double *r, double *z) {
+  size_t N = (size_t)h->A[0].n * m, e;
+  float *rf, *zf;
+  int rc;
+  if (prec == 0) return vcycle(h, 0, m, r, z);
+  if ((rc = build_lowp(h)) != ORC_OK) return rc;
+  rf = (float *)malloc(N * sizeof(float));
+  zf = (float *)malloc(N * sizeof(float));
+  if (!rf || !zf) { free(rf); free(zf); return ORC_ERR_OOM; }
+  for (e = 0; e < N; ++e) rf[e] = (float)r[e];
+  rc = vcycle_f(h, 0, prec == 2, m, rf, zf);
+  for (e = 0; e < N; ++e) z[e] = (double)zf[e];
+  free(rf); free(zf);
+  return rc;
+}
+
+int orc_vcycle_prec(ohier *h, int prec, int m, const double *b, double *x) {
+  if (!h || m < 1 || prec < 0 || prec > 2) return ORC_ERR_ARG;
+  return apply_M(h, prec, m, b, x);
+}
+
+/* FP32 products of one level (tests): which 0 = A (bf16 values if bf16), 1 = P, 2 = R. */
+int orc_spmm_f(ohier *h, int l, int which, int bf16, int m, const float *X, float *Y) {
+  int rc;
+  if (!h || l < 0 || l >= h->nlev || which < 0 || which > 2 || (which && l + 1 >= h->nlev)) return ORC_ERR_ARG;
+  if ((rc = build_lowp(h)) != ORC_OK) return rc;
+  spmm_f(h, l, which, bf16, m, X, Y);
+  return ORC_OK;
 }
 
 /* ------------------------------------------------------------------ */
@@ -761,17 +966,23 @@ static int confirm(const ocsr *A, int m, const double *b, const double *x, doubl
 /* state: 0 active, 1 frozen by the recursive residual, 2 confirmed converged,
  * 3 breakdown, 4 zero right-hand side */
 
-/* Preconditioned CG (paper Sec. 2.1, Tab. 1; Hestenes-Stiefel), M = one V-cycle. */
-int orc_pcg(const ohier *h, int m, const double *b, double *x, double tol, int maxit,
-            int *iters, double *relres, int *status) {
+/* Preconditioned CG (paper Sec. 2.1, Tab. 1; Hestenes-Stiefel), M = one
+ * V-cycle.  With a reduced-precision preconditioner (prec 1, 2) M is only
+ * approximately symmetric, and the direction update takes the flexible form
+ * beta = z_{k+1} . (r_{k+1} - r_k) / (z_k . r_k) (Notay 2000; Golub and
+ * Ye 1999), for which the previous residual is kept. */
+int orc_pcg_prec(ohier *h, int prec, int m, const double *b, double *x, double tol, int maxit,
+                 int *iters, double *relres, int *status) {
   const ocsr *A = &h->A[0];
   size_t N = (size_t)A->n * m, i;
   int j, k, rc = ORC_OK, any;
-  double *r = NULL, *z = NULL, *p = NULL, *q = NULL, *t = NULL;
-  double *nb = NULL, *rho = NULL, *c = NULL, *tn = NULL;
+  double *r = NULL, *z = NULL, *p = NULL, *q = NULL, *t = NULL, *ro = NULL;
+  double *nb = NULL, *rho = NULL, *c = NULL, *c2 = NULL, *tn = NULL;
   int *state = NULL, *restart = NULL;
-  if (!h || m < 1 || maxit < 0 || !(tol > 0.0)) return ORC_ERR_ARG;
+  if (!h || m < 1 || maxit < 0 || !(tol > 0.0) || prec < 0 || prec > 2) return ORC_ERR_ARG;
   if (!all_finite(N, b)) return ORC_ERR_NONFINITE;
+  ro = (double *)malloc(N * sizeof(double)); c2 = (double *)malloc((size_t)m * sizeof(double));
+  if (!ro || !c2) { rc = ORC_ERR_OOM; goto done; }
   r = (double *)malloc(N * sizeof(double)); z = (double *)malloc(N * sizeof(double));
   p = (double *)malloc(N * sizeof(double)); q = (double *)malloc(N * sizeof(double));
   t = (double *)malloc(N * sizeof(double));
@@ -782,7 +993,7 @@ int orc_pcg(const ohier *h, int m, const double *b, double *x, double tol, int m
   coldot((size_t)A->n, m, b, b, nb);
   for (j = 0; j < m; ++j) { nb[j] = sqrt(nb[j]); iters[j] = 0; if (nb[j] == 0.0) state[j] = 4; }
   for (i = 0; i < N; ++i) { x[i] = 0.0; r[i] = b[i]; }
-  if ((rc = vcycle(h, 0, m, r, z)) != ORC_OK) goto done;
+  if ((rc = apply_M(h, prec, m, r, z)) != ORC_OK) goto done;
   memcpy(p, z, N * sizeof(double));
   coldot((size_t)A->n, m, r, z, rho);
   for (j = 0; j < m; ++j) if (state[j] == 0 && !(rho[j] > 0.0)) state[j] = 3;
@@ -792,6 +1003,7 @@ int orc_pcg(const ohier *h, int m, const double *b, double *x, double tol, int m
     if (!any) break;
     spmm(A, m, p, q);
     coldot((size_t)A->n, m, p, q, c);
+    memcpy(ro, r, N * sizeof(double));
     for (j = 0; j < m; ++j) {
       double alpha;
       if (state[j] != 0) continue;
@@ -813,13 +1025,16 @@ int orc_pcg(const ohier *h, int m, const double *b, double *x, double tol, int m
     if (!any) {
       if (confirm(A, m, b, x, r, t, tn, nb, tol, state, restart) == 0) break;
     }
-    if ((rc = vcycle(h, 0, m, r, z)) != ORC_OK) goto done;
+    if ((rc = apply_M(h, prec, m, r, z)) != ORC_OK) goto done;
     coldot((size_t)A->n, m, r, z, c);
+    if (prec) coldot((size_t)A->n, m, z, ro, c2);
     for (j = 0; j < m; ++j) {
       double beta;
       if (state[j] != 0) continue;
       if (!(c[j] > 0.0)) { state[j] = 3; continue; }
-      beta = restart[j] ? 0.0 : c[j] / rho[j];
+      if (restart[j]) beta = 0.0;
+      else if (prec) beta = (c[j] - c2[j]) / rho[j];
+      else beta = c[j] / rho[j];
       restart[j] = 0;
       for (i = 0; i < (size_t)A->n; ++i) p[i * m + j] = z[i * m + j] + beta * p[i * m + j];
       rho[j] = c[j];
@@ -837,20 +1052,26 @@ int orc_pcg(const ohier *h, int m, const double *b, double *x, double tol, int m
   }
 done:
   free(r); free(z); free(p); free(q); free(t); free(nb); free(rho); free(c); free(tn);
-  free(state); free(restart);
+  free(state); free(restart); free(ro); free(c2);
   return rc;
 }
 
+int orc_pcg(ohier *h, int m, const double *b, double *x, double tol, int maxit, int *iters,
+            double *relres, int *status) {
+  return orc_pcg_prec(h, 0, m, b, x, tol, maxit, iters, relres, status);
+}
+
+
 /* Right-preconditioned BiCGStab (paper Sec. 2.1, Tab. 1; van der Vorst), M = one V-cycle. */
-int orc_bicgstab(const ohier *h, int m, const double *b, double *x, double tol, int maxit,
-                 int *iters, double *relres, int *status) {
+int orc_bicgstab_prec(ohier *h, int prec, int m, const double *b, double *x, double tol,
+                      int maxit, int *iters, double *relres, int *status) {
   const ocsr *A = &h->A[0];
   size_t N = (size_t)A->n * m, i, n = (size_t)A->n;
   int j, k, rc = ORC_OK, any;
   double *r = NULL, *rh = NULL, *p = NULL, *v = NULL, *s = NULL, *t = NULL, *ph = NULL, *sh = NULL;
   double *nb = NULL, *rho_old = NULL, *alpha = NULL, *omega = NULL, *c = NULL, *c2 = NULL, *tn = NULL;
   int *state = NULL, *restart = NULL;
-  if (!h || m < 1 || maxit < 0 || !(tol > 0.0)) return ORC_ERR_ARG;
+  if (!h || m < 1 || maxit < 0 || !(tol > 0.0) || prec < 0 || prec > 2) return ORC_ERR_ARG;
   if (!all_finite(N, b)) return ORC_ERR_NONFINITE;
   r = (double *)malloc(N * sizeof(double)); rh = (double *)malloc(N * sizeof(double));
   p = (double *)malloc(N * sizeof(double)); v = (double *)malloc(N * sizeof(double));
@@ -885,7 +1106,7 @@ int orc_bicgstab(const ohier *h, int m, const double *b, double *x, double tol, 
       }
       rho_old[j] = c[j];
     }
-    if ((rc = vcycle(h, 0, m, p, ph)) != ORC_OK) goto done;
+    if ((rc = apply_M(h, prec, m, p, ph)) != ORC_OK) goto done;
     spmm(A, m, ph, v);
     coldot(n, m, rh, v, c);
     for (j = 0; j < m; ++j) {
@@ -908,7 +1129,7 @@ int orc_bicgstab(const ohier *h, int m, const double *b, double *x, double tol, 
       } else any = 1;
     }
     if (any) {
-      if ((rc = vcycle(h, 0, m, s, sh)) != ORC_OK) goto done;
+      if ((rc = apply_M(h, prec, m, s, sh)) != ORC_OK) goto done;
       spmm(A, m, sh, t);
       coldot(n, m, t, s, c);
       coldot(n, m, t, t, c2);
@@ -949,4 +1170,9 @@ done:
   free(nb); free(rho_old); free(alpha); free(omega); free(c); free(c2); free(tn);
   free(state); free(restart);
   return rc;
+}
+
+int orc_bicgstab(ohier *h, int m, const double *b, double *x, double tol, int maxit, int *iters,
+                 double *relres, int *status) {
+  return orc_bicgstab_prec(h, 0, m, b, x, tol, maxit, iters, relres, status);
 }

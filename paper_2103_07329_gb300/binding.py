@@ -28,6 +28,9 @@ NOT_CONVERGED = 1
 BREAKDOWN = 2
 PCG = 0
 BICGSTAB = 1
+PREC_FP64 = 0
+PREC_FP32 = 1
+PREC_BF16 = 2
 MAX_RHS = 32
 
 # every entry point declared in include/xamg_gpu.h
@@ -35,7 +38,8 @@ EXPORTS = [
     "xamg_strerror", "xamg_amg_params_default", "xamg_solve_opts_default",
     "xamg_setup_hierarchy", "xamg_destroy", "xamg_hier_info", "xamg_level_info",
     "xamg_level_export", "xamg_coarse_export", "xamg_workspace_bytes", "xamg_solve",
-    "xamg_solve_host", "xamg_level_spmm", "xamg_smooth", "xamg_vcycle", "xamg_coarse_solve",
+    "xamg_solve_host", "xamg_level_spmm", "xamg_smooth", "xamg_vcycle", "xamg_vcycle_precond",
+    "xamg_coarse_solve",
     "xamg_coldot", "xamg_timing_enable", "xamg_timing_read", "xamg_kernel_launches",
     "xamg_coldot_noalloc",
 ]
@@ -60,8 +64,8 @@ class AmgParamsT(C.Structure):
 
 
 class SolveOptsT(C.Structure):
-    _fields_ = [("method", C.c_int32), ("stream", C.c_void_p), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t)]
+    _fields_ = [("method", C.c_int32), ("precond", C.c_int32), ("stream", C.c_void_p),
+                ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
 
 
 class StatsT(C.Structure):
@@ -95,13 +99,14 @@ def _load():
         "xamg_level_info": ([vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64)], C.c_int),
         "xamg_level_export": ([vp, i32, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "xamg_coarse_export": ([vp, C.POINTER(i32), vp, vp], C.c_int),
-        "xamg_workspace_bytes": ([vp, i32, i32, C.POINTER(C.c_size_t)], C.c_int),
+        "xamg_workspace_bytes": ([vp, i32, i32, i32, C.POINTER(C.c_size_t)], C.c_int),
         "xamg_solve": ([vp, vp, vp, i32, dbl, i32, C.POINTER(SolveOptsT), C.POINTER(StatsT)], C.c_int),
         "xamg_solve_host": ([vp, vp, vp, i32, dbl, i32, C.POINTER(SolveOptsT), C.POINTER(StatsT)],
                             C.c_int),
         "xamg_level_spmm": ([vp, i32, i32, vp, vp, i32, vp], C.c_int),
         "xamg_smooth": ([vp, i32, vp, vp, vp, i32, i32, vp], C.c_int),
         "xamg_vcycle": ([vp, vp, vp, i32, vp], C.c_int),
+        "xamg_vcycle_precond": ([vp, i32, vp, vp, i32, vp], C.c_int),
         "xamg_coarse_solve": ([vp, vp, vp, i32, vp], C.c_int),
         "xamg_coldot": ([vp, vp, i64, i32, vp, vp], C.c_int),
         "xamg_coldot_noalloc": ([vp, vp, i64, i32, vp, vp], C.c_int),
@@ -250,40 +255,43 @@ class Hierarchy:
                "xamg_coarse_export")
         return lu.reshape(nc.value, nc.value), piv
 
-    def workspace_bytes(self, m: int, method: int = PCG) -> int:
+    def workspace_bytes(self, m: int, method: int = PCG, precond: int = PREC_FP64) -> int:
         b = C.c_size_t()
-        _check(_load().xamg_workspace_bytes(self._h, m, method, C.byref(b)), "xamg_workspace_bytes")
+        _check(_load().xamg_workspace_bytes(self._h, m, method, precond, C.byref(b)),
+               "xamg_workspace_bytes")
         return b.value
 
-    def _opts(self, method, stream, workspace):
+    def _opts(self, method, stream, workspace, precond=PREC_FP64):
         o = SolveOptsT()
         _load().xamg_solve_opts_default(C.byref(o))
         o.method = method
+        o.precond = precond
         o.stream = _stream(stream)
         if workspace is not None:
             o.workspace = _ptr(workspace)
             o.workspace_bytes = workspace.numel() * workspace.element_size()
         return o
 
-    def solve(self, B, X, tol=1e-8, maxit=200, method=PCG, stream=None, workspace=None) -> SolveStats:
+    def solve(self, B, X, tol=1e-8, maxit=200, method=PCG, stream=None, workspace=None,
+              precond=PREC_FP64) -> SolveStats:
         """xamg_solve on device blocks B, X (torch float64 CUDA tensors, n x m)."""
         m = B.shape[1] if B.dim() == 2 else 1
         st = SolveStats(m)
         s = st.struct()
-        o = self._opts(method, stream, workspace)
+        o = self._opts(method, stream, workspace, precond)
         rc = _load().xamg_solve(self._h, _ptr(B), _ptr(X), m, tol, maxit, C.byref(o), C.byref(s))
         _check(rc, "xamg_solve", allow_positive=True)
         st.iterations, st.vcycles, st.rc = s.iterations, s.vcycles, rc
         return st
 
     def solve_host(self, B: np.ndarray, X: np.ndarray, tol=1e-8, maxit=200, method=PCG,
-                   stream=None) -> SolveStats:
+                   stream=None, precond=PREC_FP64) -> SolveStats:
         """xamg_solve_host on host arrays (float64, C order, n x m)."""
         assert B.flags.c_contiguous and X.flags.c_contiguous and B.dtype == np.float64
         m = B.shape[1]
         st = SolveStats(m)
         s = st.struct()
-        o = self._opts(method, stream, None)
+        o = self._opts(method, stream, None, precond)
         rc = _load().xamg_solve_host(self._h, B.ctypes.data, X.ctypes.data, m, tol, maxit,
                                      C.byref(o), C.byref(s))
         _check(rc, "xamg_solve_host", allow_positive=True)
@@ -303,6 +311,10 @@ class Hierarchy:
     def vcycle(self, B, X, stream=None):
         _check(_load().xamg_vcycle(self._h, _ptr(B), _ptr(X), B.shape[1], _stream(stream)),
                "xamg_vcycle")
+
+    def vcycle_precond(self, precond, B, X, stream=None):
+        _check(_load().xamg_vcycle_precond(self._h, precond, _ptr(B), _ptr(X), B.shape[1],
+                                           _stream(stream)), "xamg_vcycle_precond")
 
     def coarse_solve(self, B, X, stream=None):
         _check(_load().xamg_coarse_solve(self._h, _ptr(B), _ptr(X), B.shape[1], _stream(stream)),

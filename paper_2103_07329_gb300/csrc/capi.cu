@@ -1,6 +1,7 @@
 // capi.cu -- the library's C entry points: device upload of the hierarchy, the
 // V(1,1) Chebyshev cycle, the PCG and BiCGStab drivers and the single-step
 // entry points.  Declarations and contracts: include/xamg_gpu.h.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +29,12 @@ struct DevLevel {
   DevCsr A, P, R;
   double *w[4] = {nullptr, nullptr, nullptr, nullptr};  // Chebyshev row weights per step
   double c1[4] = {0, 0, 0, 0};                          // Chebyshev step coefficients
+  // reduced-precision copies for the FP32-block preconditioner (same index arrays)
+  float *a32 = nullptr, *p32 = nullptr, *r32 = nullptr;
+  __nv_bfloat16 *a16 = nullptr;  // bf16(fl32(a_ij) / s_i)
+  float *a16s = nullptr;         // s_i = fl32(max_j |a_ij|)
+  float *w32[4] = {nullptr, nullptr, nullptr, nullptr};
+  float c1f[4] = {0, 0, 0, 0};
 };
 
 struct TimerRec {
@@ -47,8 +54,33 @@ struct Work {
   double *Bn = nullptr, *X = nullptr, *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr;
   double *RH = nullptr, *V = nullptr, *S = nullptr, *T = nullptr, *PH = nullptr, *SH = nullptr;
   std::vector<double *> vb, vx, vr, vd, vd2;  // V-cycle blocks per level
+  // FP32-block preconditioner: level-0 input/output and per-level blocks
+  float *R32 = nullptr, *Z32 = nullptr;
+  std::vector<float *> fb, fx, fr, fd, fd2;
+  double *cw = nullptr;  // FP64 working copy of the coarsest block
   double *part[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   ColState *cs = nullptr;
+};
+
+// The block scalar's view of the hierarchy and the work blocks.
+template <class TB> struct Blocks;
+template <> struct Blocks<double> {
+  static double *b(Work &W, int l) { return W.vb[l]; }
+  static double *x(Work &W, int l) { return W.vx[l]; }
+  static double *r(Work &W, int l) { return W.vr[l]; }
+  static double *d(Work &W, int l) { return W.vd[l]; }
+  static double *d2(Work &W, int l) { return W.vd2[l]; }
+  static const double *w(const DevLevel &D, int k) { return D.w[k]; }
+  static double c1(const DevLevel &D, int k) { return D.c1[k]; }
+};
+template <> struct Blocks<float> {
+  static float *b(Work &W, int l) { return W.fb[l]; }
+  static float *x(Work &W, int l) { return W.fx[l]; }
+  static float *r(Work &W, int l) { return W.fr[l]; }
+  static float *d(Work &W, int l) { return W.fd[l]; }
+  static float *d2(Work &W, int l) { return W.fd2[l]; }
+  static const float *w(const DevLevel &D, int k) { return D.w32[k]; }
+  static float c1(const DevLevel &D, int k) { return D.c1f[k]; }
 };
 
 }  // namespace
@@ -68,6 +100,7 @@ struct xamg_hier {
   size_t hb_bytes = 0;
   Flags *flags_h = nullptr;   // mapped pinned counters
   Flags *flags_d = nullptr;
+  bool lowp_ready = false;    // reduced-precision copies uploaded
   bool timing = false;
   std::vector<TimerRec> pending;
   std::vector<cudaEvent_t> event_pool;
@@ -147,6 +180,58 @@ int upload_level(xamg_hier *h, int l) {
   return XAMG_OK;
 }
 
+// Reduced-precision copies of the hierarchy for the FP32-block preconditioner:
+// fl32 of every value of A, P, R; bf16 values of A relative to the row scale
+// s_i = fl32(max_j |a_ij|), q_ij = bf16_rne(fl32(a_ij) / s_i); the Chebyshev
+// row weights and step coefficients rounded to FP32.
+int upload_lowp(xamg_hier *h) {
+  if (h->lowp_ready) return XAMG_OK;
+  const int L = (int)h->host.lv.size();
+  int rc;
+  for (int l = 0; l < L; ++l) {
+    const HostLevel &H = h->host.lv[l];
+    DevLevel &D = h->lv[l];
+    std::vector<float> f(H.A.val.size());
+    for (size_t k = 0; k < f.size(); ++k) f[k] = (float)H.A.val[k];
+    if ((rc = dev_upload(h, &D.a32, f.data(), f.size())) != XAMG_OK) return rc;
+    std::vector<float> s((size_t)H.A.n);
+    std::vector<__nv_bfloat16> q(H.A.val.size());
+    for (int i = 0; i < H.A.n; ++i) {
+      double mx = 0.0;
+      for (int p = H.A.rowptr[i]; p < H.A.rowptr[i + 1]; ++p) mx = std::max(mx, std::fabs(H.A.val[p]));
+      s[i] = mx > 0.0 ? (float)mx : 1.0f;
+      for (int p = H.A.rowptr[i]; p < H.A.rowptr[i + 1]; ++p) q[p] = __float2bfloat16_rn(f[p] / s[i]);
+    }
+    if ((rc = dev_upload(h, &D.a16, q.data(), q.size())) != XAMG_OK) return rc;
+    if ((rc = dev_upload(h, &D.a16s, s.data(), s.size())) != XAMG_OK) return rc;
+    if (l + 1 == L) continue;
+    std::vector<float> pf(H.P.val.size()), rf(H.R.val.size());
+    for (size_t k = 0; k < pf.size(); ++k) pf[k] = (float)H.P.val[k];
+    for (size_t k = 0; k < rf.size(); ++k) rf[k] = (float)H.R.val[k];
+    if ((rc = dev_upload(h, &D.p32, pf.data(), pf.size())) != XAMG_OK) return rc;
+    if ((rc = dev_upload(h, &D.r32, rf.data(), rf.size())) != XAMG_OK) return rc;
+    const double theta = 0.5 * (H.hi + H.lo), delta = 0.5 * (H.hi - H.lo), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    std::vector<float> w(H.dinv.size());
+    for (int k = 0; k < h->host.cheb_steps; ++k) {
+      double coef;
+      if (k == 0) {
+        coef = 1.0 / theta;
+        D.c1f[0] = 0.0f;
+      } else {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        D.c1f[k] = (float)(rn * rho);
+        coef = 2.0 * rn / delta;
+        rho = rn;
+      }
+      for (size_t i = 0; i < w.size(); ++i) w[i] = (float)(coef * H.dinv[i]);
+      if ((rc = dev_upload(h, &D.w32[k], w.data(), w.size())) != XAMG_OK) return rc;
+    }
+  }
+  h->lowp_ready = true;
+  return XAMG_OK;
+}
+
 void free_device(xamg_hier *h) {
   for (void *p : h->owned) cudaFree(p);
   h->owned.clear();
@@ -169,7 +254,7 @@ void free_device(xamg_hier *h) {
 }
 
 // ---- workspace ----
-size_t plan(const xamg_hier *h, int nv, int method, Work *w, char *base) {
+size_t plan(const xamg_hier *h, int nv, int method, int prec, Work *w, char *base) {
   size_t off = 0;
   auto take = [&](size_t bytes) -> char * {
     char *p = base ? base + off : nullptr;
@@ -215,13 +300,45 @@ size_t plan(const xamg_hier *h, int nv, int method, Work *w, char *base) {
       if (dd) W.vd2[l] = (double *)take(b);
     }
   }
+  W.fb.assign(L, nullptr);
+  W.fx.assign(L, nullptr);
+  W.fr.assign(L, nullptr);
+  W.fd.assign(L, nullptr);
+  W.fd2.assign(L, nullptr);
+  W.R32 = W.Z32 = nullptr;
+  W.cw = nullptr;
+  if (prec != XAMG_PREC_FP64) {
+    const size_t fblk = n0 * nv * sizeof(float);
+    W.R32 = (float *)take(fblk);
+    W.Z32 = (float *)take(fblk);
+    W.fb[0] = W.R32;
+    W.fx[0] = W.Z32;
+    for (int l = 0; l < L; ++l) {
+      const size_t b = (size_t)h->host.lv[l].A.n * nv * sizeof(float);
+      if (l > 0) {
+        W.fb[l] = (float *)take(b);
+        W.fx[l] = (float *)take(b);
+      }
+      if (l + 1 < L) {
+        W.fr[l] = (float *)take(b);
+        W.fd[l] = (float *)take(b);
+        if (dd) W.fd2[l] = (float *)take(b);
+      }
+    }
+    W.cw = (double *)take((size_t)h->host.nc * nv * sizeof(double));
+  }
   for (int i = 0; i < 5; ++i) W.part[i] = (double *)take((size_t)kMaxGrid * 32 * sizeof(double));
   W.cs = (ColState *)take(sizeof(ColState));
   return off;
 }
 
-int ensure_workspace(xamg_hier *h, int nv, int method, const xamg_solve_opts *o, Work &w) {
-  const size_t need = plan(h, nv, method, nullptr, nullptr);
+int ensure_workspace(xamg_hier *h, int nv, int method, int prec, const xamg_solve_opts *o,
+                     Work &w) {
+  if (prec != XAMG_PREC_FP64) {
+    const int rc = upload_lowp(h);
+    if (rc != XAMG_OK) return rc;
+  }
+  const size_t need = plan(h, nv, method, prec, nullptr, nullptr);
   char *base;
   if (o && o->workspace) {
     if (o->workspace_bytes < need || ((uintptr_t)o->workspace & 255)) return XAMG_ERR_INVALID_ARG;
@@ -236,7 +353,7 @@ int ensure_workspace(xamg_hier *h, int nv, int method, const xamg_solve_opts *o,
     }
     base = (char *)h->ws;
   }
-  plan(h, nv, method, &w, base);
+  plan(h, nv, method, prec, &w, base);
   return XAMG_OK;
 }
 
@@ -256,7 +373,7 @@ void flush_timing(xamg_hier *h) {
   for (auto &p : h->pending) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-      TimeAcc &t = h->tacc[(size_t)p.level * 3 + p.which];
+      TimeAcc &t = h->tacc[(size_t)p.level * 6 + p.which];
       t.launches++;
       t.ms += ms;
       t.flops += p.flops;
@@ -277,41 +394,71 @@ int slices_for(const DevCsr &M, int nv) {
 
 // Algorithmic bytes of one fused row launch: the matrix once, the operand
 // block once, and every block the epilogue reads or writes once.
-double row_bytes(const DevCsr &M, const RowOp &op, int nv) {
-  const double blk = (double)M.n * nv * 8.0;
-  double b = 12.0 * (double)M.nnz + 4.0 * (M.n + 1) + (double)M.ncols * nv * 8.0;
+template <class TB>
+double row_bytes(const DevCsr &M, const RowOpT<TB> &op, int nv, double val_bytes) {
+  const double blk = (double)M.n * nv * sizeof(TB);
+  double b = (4.0 + val_bytes) * (double)M.nnz + 4.0 * (M.n + 1) + (double)M.ncols * nv * sizeof(TB);
+  if (op.rscale) b += 4.0 * M.n;
   if (op.init) b += blk;
   if (op.y) b += blk;
   if (op.dp) b += blk;
-  if (op.w) b += (double)M.n * 8.0;
+  if (op.w) b += (double)M.n * sizeof(TB);
   if (op.dnext) b += blk;
   if (op.x) b += 2 * blk;
-  if (op.partials) b += (op.dot_u ? blk : 0);
+  if (op.dot_u) b += (double)M.n * nv * 8.0;
+  if (op.dot_u2) b += (double)M.n * nv * 8.0;
   return b;
 }
 
-int rows(xamg_hier *h, int level, int which, const DevCsr &M, RowOp op, int nv, bool neg, int epi,
+// Operator `which` (0 = A, 1 = P, 2 = R) of level `level` with the values of
+// block scalar TB and preconditioner precision `prec`.
+template <class TB>
+int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bool neg, int epi,
          cudaStream_t st) {
+  const DevLevel &D = h->lv[level];
+  const DevCsr &M = which == 0 ? D.A : which == 1 ? D.P : D.R;
   op.n = M.n;
   op.rowptr = M.rowptr;
   op.col = M.col;
-  op.val = M.val;
+  int vt = 0;
+  double vbytes = 8.0;
+  if constexpr (sizeof(TB) == 8) {
+    op.val = M.val;
+    op.rscale = nullptr;
+  } else {
+    vbytes = 4.0;
+    if (which == 0 && prec == XAMG_PREC_BF16) {
+      op.val = D.a16;
+      op.rscale = D.a16s;
+      vt = 1;
+      vbytes = 2.0;
+    } else {
+      op.val = which == 0 ? D.a32 : which == 1 ? D.p32 : D.r32;
+      op.rscale = nullptr;
+    }
+  }
   cudaEvent_t a = nullptr, b = nullptr;
   if (h->timing) {
     a = pool_event(h);
     b = pool_event(h);
     cudaEventRecord(a, st);
   }
-  const int g = launch_rows(op, nv, slices_for(M, nv), neg, epi, st);
+  int g;
+  if constexpr (sizeof(TB) == 8)
+    g = launch_rows(op, nv, slices_for(M, nv), neg, epi, st);
+  else
+    g = launch_rows_f(op, nv, slices_for(M, nv), neg, epi, vt, st);
   if (h->timing) {
     cudaEventRecord(b, st);
-    h->pending.push_back({a, b, level, which, 2.0 * (double)M.nnz * nv, row_bytes(M, op, nv)});
+    const int slot = which + (sizeof(TB) == 8 ? 0 : 3);
+    h->pending.push_back({a, b, level, slot, 2.0 * (double)M.nnz * nv, row_bytes(M, op, nv, vbytes)});
   }
   return g;
 }
 
-RowOp blank() {
-  RowOp o;
+template <class TB>
+RowOpT<TB> blank() {
+  RowOpT<TB> o;
   std::memset(&o, 0, sizeof(o));
   return o;
 }
@@ -319,71 +466,93 @@ RowOp blank() {
 // ---- Chebyshev smoothing (cheb_steps steps) on level l ----
 // Pre-smoothing from x = 0: on entry x holds d_0 = w_0 .* b (= x_1); on exit
 // x holds the smoothed iterate and r = b - A x.
-int presmooth(xamg_hier *h, Work &W, int l, const double *b, double *x, double *r, cudaStream_t st) {
+template <class TB>
+int presmooth(xamg_hier *h, Work &W, int prec, int l, const TB *b, TB *x, TB *r, cudaStream_t st) {
+  using BL = Blocks<TB>;
   const int nv = W.nv;
   const int s = h->host.cheb_steps;
-  DevLevel &D = h->lv[l];
-  double *dA = W.vd[l], *dB = W.vd2[l];
+  const DevLevel &D = h->lv[l];
+  TB *dA = BL::d(W, l), *dB = BL::d2(W, l);
   if (s == 1) {
-    RowOp o = blank();
+    RowOpT<TB> o = blank<TB>();
     o.init = b; o.src = x; o.y = r;
-    return rows(h, l, 0, D.A, o, nv, true, EPI_Y, st) < 0 ? XAMG_ERR_CUDA : XAMG_OK;
+    return rows<TB>(h, l, 0, prec, o, nv, true, EPI_Y, st) < 0 ? XAMG_ERR_CUDA : XAMG_OK;
   }
-  RowOp o = blank();
-  o.init = b; o.src = x; o.y = r; o.dp = x; o.w = D.w[1]; o.c1 = D.c1[1]; o.dnext = dA;
-  if (rows(h, l, 0, D.A, o, nv, true, EPI_Y_DN, st) < 0) return XAMG_ERR_CUDA;
-  double *dprev = dA, *dnext = dB;
+  RowOpT<TB> o = blank<TB>();
+  o.init = b; o.src = x; o.y = r; o.dp = x; o.w = BL::w(D, 1); o.c1 = BL::c1(D, 1); o.dnext = dA;
+  if (rows<TB>(h, l, 0, prec, o, nv, true, EPI_Y_DN, st) < 0) return XAMG_ERR_CUDA;
+  TB *dprev = dA, *dnext = dB;
   for (int k = 2; k < s; ++k) {
-    RowOp m = blank();
-    m.init = r; m.src = dprev; m.y = r; m.dp = dprev; m.w = D.w[k]; m.c1 = D.c1[k];
+    RowOpT<TB> m = blank<TB>();
+    m.init = r; m.src = dprev; m.y = r; m.dp = dprev; m.w = BL::w(D, k); m.c1 = BL::c1(D, k);
     m.dnext = dnext; m.x = x;
-    if (rows(h, l, 0, D.A, m, nv, true, EPI_MID, st) < 0) return XAMG_ERR_CUDA;
+    if (rows<TB>(h, l, 0, prec, m, nv, true, EPI_MID, st) < 0) return XAMG_ERR_CUDA;
     std::swap(dprev, dnext);
   }
-  RowOp f = blank();
+  RowOpT<TB> f = blank<TB>();
   f.init = r; f.src = dprev; f.y = r; f.dp = dprev; f.x = x;
-  return rows(h, l, 0, D.A, f, nv, true, EPI_Y_XDP, st) < 0 ? XAMG_ERR_CUDA : XAMG_OK;
+  return rows<TB>(h, l, 0, prec, f, nv, true, EPI_Y_XDP, st) < 0 ? XAMG_ERR_CUDA : XAMG_OK;
 }
 
-// Post-smoothing of x (r is scratch).  If dot_part is set, the partial sums of
-// dot_u . x_final go there and *dot_grid receives their block count.
-int postsmooth(xamg_hier *h, Work &W, int l, const double *b, double *x, double *r, cudaStream_t st,
-               const double *dot_u, double *dot_part, int *dot_grid) {
+// FP64 partial dots of the final iterate: dot_u . x into dot_part and, when
+// dot_u2 is set, dot_u2 . x into dot_part2; *dot_grid gets their block count.
+struct Dots {
+  const double *u = nullptr, *u2 = nullptr;
+  double *part = nullptr, *part2 = nullptr;
+  int *grid = nullptr;
+};
+
+// Post-smoothing of x (r is scratch).
+template <class TB>
+int postsmooth(xamg_hier *h, Work &W, int prec, int l, const TB *b, TB *x, TB *r, cudaStream_t st,
+               const Dots &dots) {
+  using BL = Blocks<TB>;
   const int nv = W.nv;
   const int s = h->host.cheb_steps;
-  DevLevel &D = h->lv[l];
-  double *dA = W.vd[l], *dB = W.vd2[l];
+  const DevLevel &D = h->lv[l];
+  TB *dA = BL::d(W, l), *dB = BL::d2(W, l);
   {
-    RowOp o = blank();
-    o.init = b; o.src = x; o.y = r; o.w = D.w[0]; o.dnext = dA;
-    if (rows(h, l, 0, D.A, o, nv, true, EPI_Y_D0, st) < 0) return XAMG_ERR_CUDA;
+    RowOpT<TB> o = blank<TB>();
+    o.init = b; o.src = x; o.y = r; o.w = BL::w(D, 0); o.dnext = dA;
+    if (rows<TB>(h, l, 0, prec, o, nv, true, EPI_Y_D0, st) < 0) return XAMG_ERR_CUDA;
   }
   if (s == 1) {
     const int g = elem_grid(D.A.n, nv);
-    launch_axpy_dot(nv, D.A.n, x, dA, dot_part ? dot_u : nullptr, dot_part, g, st);
-    if (dot_part) *dot_grid = g;
+    if constexpr (sizeof(TB) == 8) {
+      launch_axpy_dot(nv, D.A.n, x, dA, dots.part ? dots.u : nullptr, dots.part, g, st);
+      if (dots.part2) launch_coldot(nv, D.A.n, dots.u2, x, dots.part2, g, st);
+    } else {
+      launch_axpy_dot_f(nv, D.A.n, x, dA, dots.part ? dots.u : nullptr,
+                        dots.part2 ? dots.u2 : nullptr, dots.part, dots.part2, g, st);
+    }
+    if (dots.part) *dots.grid = g;
     return XAMG_OK;
   }
-  double *dprev = dA, *dnext = dB;
+  TB *dprev = dA, *dnext = dB;
   for (int k = 1; k < s; ++k) {
     const bool last = k == s - 1;
-    RowOp o = blank();
-    o.init = r; o.src = dprev; o.dp = dprev; o.w = D.w[k]; o.c1 = D.c1[k]; o.x = x;
+    RowOpT<TB> o = blank<TB>();
+    o.init = r; o.src = dprev; o.dp = dprev; o.w = BL::w(D, k); o.c1 = BL::c1(D, k); o.x = x;
     int epi = EPI_MID;
     if (last) {
       epi = EPI_XLAST;
-      if (dot_part) {
-        o.dot_u = dot_u;
-        o.partials = dot_part;
+      if (dots.part) {
+        o.dot_u = dots.u;
+        o.partials = dots.part;
         epi = EPI_XLAST_DOT;
+        if (dots.part2) {
+          o.dot_u2 = dots.u2;
+          o.partials2 = dots.part2;
+          epi = EPI_XLAST_DOT2;
+        }
       }
     } else {
       o.y = r;
       o.dnext = dnext;
     }
-    const int g = rows(h, l, 0, D.A, o, nv, true, epi, st);
+    const int g = rows<TB>(h, l, 0, prec, o, nv, true, epi, st);
     if (g < 0) return XAMG_ERR_CUDA;
-    if (last && dot_part) *dot_grid = g;
+    if (last && dots.part) *dots.grid = g;
     std::swap(dprev, dnext);
   }
   return XAMG_OK;
@@ -391,48 +560,68 @@ int postsmooth(xamg_hier *h, Work &W, int l, const double *b, double *x, double 
 
 // ---- V(1,1) Chebyshev cycle ----
 // On entry x holds w0 .* b (the first smoother iterate) unless `level` is the
-// coarsest.  If dot_part is set, the partial sums of dot_u . x_final are
-// written there and *dot_grid receives their block count.
-int vcycle(xamg_hier *h, Work &W, int l, const double *b, double *x, cudaStream_t st,
-           const double *dot_u, double *dot_part, int *dot_grid) {
+// coarsest.  TB = double: the FP64 preconditioner; TB = float: the
+// reduced-precision one (FP32 blocks, FP32 or bf16 values of A, FP64 coarsest
+// solve).  Optional FP64 dots of the final iterate (see Dots).
+template <class TB>
+int vcycle(xamg_hier *h, Work &W, int prec, int l, const TB *b, TB *x, cudaStream_t st,
+           const Dots &dots) {
+  using BL = Blocks<TB>;
   const int nv = W.nv;
   const int L = (int)h->lv.size();
   if (l == L - 1) {
-    launch_coarse(nv, h->host.nc, h->lu, h->piv, b, x, st);
-    if (dot_part) {
-      const int g = elem_grid(h->host.nc, nv);
-      launch_coldot(nv, h->host.nc, dot_u, x, dot_part, g, st);
-      *dot_grid = g;
+    const int nc = h->host.nc;
+    const double *xd;
+    if constexpr (sizeof(TB) == 8) {
+      launch_coarse(nv, nc, h->lu, h->piv, b, x, st);
+      xd = x;
+    } else {
+      launch_coarse_f(nv, nc, h->lu, h->piv, b, x, W.cw, st);
+      launch_to_f64(nv, nc, x, W.cw, elem_grid(nc, nv), st);  // the dots read the FP32 result
+      xd = W.cw;
+    }
+    if (dots.part) {
+      const int g = elem_grid(nc, nv);
+      launch_coldot(nv, nc, dots.u, xd, dots.part, g, st);
+      if (dots.part2) launch_coldot(nv, nc, dots.u2, xd, dots.part2, g, st);
+      *dots.grid = g;
     }
     return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
   }
-  DevLevel &D = h->lv[l];
-  double *r = W.vr[l];
-  int rc = presmooth(h, W, l, b, x, r, st);
+  TB *r = BL::r(W, l);
+  int rc = presmooth<TB>(h, W, prec, l, b, x, r, st);
   if (rc != XAMG_OK) return rc;
   // restriction b_c = R r (and the coarse level's first smoother iterate)
   {
     const bool next_coarsest = l + 2 == L;
-    RowOp o = blank();
-    o.src = r; o.y = W.vb[l + 1];
+    RowOpT<TB> o = blank<TB>();
+    o.src = r; o.y = BL::b(W, l + 1);
     if (!next_coarsest) {
-      o.w = h->lv[l + 1].w[0];
-      o.dnext = W.vx[l + 1];
+      o.w = BL::w(h->lv[l + 1], 0);
+      o.dnext = BL::x(W, l + 1);
     }
-    if (rows(h, l, 2, D.R, o, nv, false, next_coarsest ? EPI_Y : EPI_Y_D0, st) < 0)
+    if (rows<TB>(h, l, 2, prec, o, nv, false, next_coarsest ? EPI_Y : EPI_Y_D0, st) < 0)
       return XAMG_ERR_CUDA;
   }
-  rc = vcycle(h, W, l + 1, W.vb[l + 1], W.vx[l + 1], st, nullptr, nullptr, nullptr);
+  rc = vcycle<TB>(h, W, prec, l + 1, BL::b(W, l + 1), BL::x(W, l + 1), st, Dots());
   if (rc != XAMG_OK) return rc;
   // prolongation and correction x += P x_c
   {
-    RowOp o = blank();
-    o.init = x; o.src = W.vx[l + 1]; o.y = x;
-    if (rows(h, l, 1, D.P, o, nv, false, EPI_Y, st) < 0) return XAMG_ERR_CUDA;
+    RowOpT<TB> o = blank<TB>();
+    o.init = x; o.src = BL::x(W, l + 1); o.y = x;
+    if (rows<TB>(h, l, 1, prec, o, nv, false, EPI_Y, st) < 0) return XAMG_ERR_CUDA;
   }
-  rc = postsmooth(h, W, l, b, x, r, st, dot_u, dot_part, dot_grid);
+  rc = postsmooth<TB>(h, W, prec, l, b, x, r, st, dots);
   if (rc != XAMG_OK) return rc;
   return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
+}
+
+Dots dot1(const double *u, double *part, int *grid) {
+  Dots d;
+  d.u = u;
+  d.part = part;
+  d.grid = grid;
+  return d;
 }
 
 int sync_read(cudaStream_t st) {
@@ -442,9 +631,9 @@ int sync_read(cudaStream_t st) {
 
 // true residual t = b - A x with partial ||t||^2 in part; returns the grid
 int true_residual(xamg_hier *h, Work &W, double *T, double *part, cudaStream_t st) {
-  RowOp o = blank();
+  RowOp o = blank<double>();
   o.init = W.Bn; o.src = W.X; o.y = T; o.partials2 = part;
-  return rows(h, 0, 0, h->lv[0].A, o, W.nv, true, EPI_Y_DOT2, st);
+  return rows<double>(h, 0, 0, XAMG_PREC_FP64, o, W.nv, true, EPI_Y_DOT2, st);
 }
 
 struct SolveCtx {
@@ -453,9 +642,28 @@ struct SolveCtx {
   int m, nv;
   double tol;
   int maxit;
+  int prec = XAMG_PREC_FP64;
   cudaStream_t st;
   int iterations = 0, vcycles = 0;
 };
+
+// z = M r for the FP64 Krylov loops.  FP64 preconditioner: on entry z holds
+// w0 .* r (written by the kernel that produced r).  Reduced precision: r is
+// rounded to the FP32 block, the FP32 V-cycle runs, z is widened back.
+int apply_precond(SolveCtx &c, const double *r, double *z) {
+  xamg_hier *h = c.h;
+  Work &W = c.W;
+  c.vcycles++;
+  if (c.prec == XAMG_PREC_FP64) return vcycle<double>(h, W, c.prec, 0, r, z, c.st, Dots());
+  const int64_t n = h->lv[0].A.n;
+  const int ge = elem_grid(n, c.nv);
+  const float *w0f = h->lv.size() > 1 ? h->lv[0].w32[0] : nullptr;
+  launch_to_f32(c.nv, n, r, W.R32, w0f, W.Z32, ge, c.st);
+  const int rc = vcycle<float>(h, W, c.prec, 0, W.R32, W.Z32, c.st, Dots());
+  if (rc != XAMG_OK) return rc;
+  launch_to_f64(c.nv, n, W.Z32, z, ge, c.st);
+  return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
+}
 
 int finish(SolveCtx &c, double *Xuser, xamg_stats *stats) {
   xamg_hier *h = c.h;
@@ -523,16 +731,17 @@ int solve_pcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
   int rc = check_init(c);
   if (rc != XAMG_OK) return rc;
   if (h->flags_h->active > 0) {
-    if ((rc = vcycle(h, W, 0, W.R, W.Z, st, W.R, W.part[1], &g)) != XAMG_OK) return rc;
+    if ((rc = vcycle<double>(h, W, XAMG_PREC_FP64, 0, W.R, W.Z, st, dot1(W.R, W.part[1], &g))) != XAMG_OK)
+      return rc;
     c.vcycles++;
     launch_scalar(nv, SM_PCG_BETA, W.cs, W.part[1], nullptr, g, c.tol, 0, fl, st);
     launch_pcg_p(nv, n, W.P, W.Z, W.cs, ge, st);
   }
   for (int k = 1; k <= c.maxit && h->flags_h->active > 0; ++k) {
     c.iterations = k;
-    RowOp o = blank();
+    RowOp o = blank<double>();
     o.src = W.P; o.y = W.Q; o.dot_u = W.P; o.partials = W.part[0];
-    if ((g = rows(h, 0, 0, h->lv[0].A, o, nv, false, EPI_Y_DOT, st)) < 0) return XAMG_ERR_CUDA;
+    if ((g = rows<double>(h, 0, 0, XAMG_PREC_FP64, o, nv, false, EPI_Y_DOT, st)) < 0) return XAMG_ERR_CUDA;
     launch_scalar(nv, SM_PCG_ALPHA, W.cs, W.part[0], nullptr, g, c.tol, k, fl, st);
     launch_pcg_xr(nv, n, W.X, W.R, W.P, W.Q, W.cs, w0, W.Z, W.part[1], ge, st);
     launch_scalar(nv, SM_PCG_CONV, W.cs, W.part[1], nullptr, ge, c.tol, k, fl, st);
@@ -545,10 +754,66 @@ int solve_pcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
       launch_copy_cols(nv, n, W.R, W.Q, W.cs, ge, st);
       if (w0) launch_scale_rows(nv, n, w0, W.R, W.Z, ge, st);
     }
-    if ((rc = vcycle(h, W, 0, W.R, W.Z, st, W.R, W.part[1], &g)) != XAMG_OK) return rc;
+    if ((rc = vcycle<double>(h, W, XAMG_PREC_FP64, 0, W.R, W.Z, st, dot1(W.R, W.part[1], &g))) != XAMG_OK)
+      return rc;
     c.vcycles++;
     launch_scalar(nv, SM_PCG_BETA, W.cs, W.part[1], nullptr, g, c.tol, k, fl, st);
     launch_pcg_p(nv, n, W.P, W.Z, W.cs, ge, st);
+  }
+  return finish(c, Xuser, stats);
+}
+
+// Flexible PCG in FP64 around the reduced-precision preconditioner: the
+// rounding of the FP32 V-cycle makes M slightly non-symmetric, so the
+// direction update uses beta = z_new . (r_new - r_old) / (z_old . r_old)
+// (r_new - r_old = -alpha q, so only q . z is needed).  FP64 is kept for the
+// residual update, the dots and the coarsest solve.
+int solve_fpcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
+  xamg_hier *h = c.h;
+  Work &W = c.W;
+  const int nv = c.nv;
+  const int64_t n = h->lv[0].A.n;
+  const int ge = elem_grid(n, nv);
+  const float *w0f = h->lv.size() > 1 ? h->lv[0].w32[0] : nullptr;
+  Flags *fl = h->flags_d;
+  cudaStream_t st = c.st;
+  const int prec = c.prec;
+  int g;
+  launch_init_fpcg(nv, n, B, c.m, W.Bn, W.R, W.X, W.R32, W.Z32, w0f, W.part[0], ge, st);
+  launch_scalar(nv, SM_INIT, W.cs, W.part[0], nullptr, ge, c.tol, 0, fl, st);
+  int rc = check_init(c);
+  if (rc != XAMG_OK) return rc;
+  if (h->flags_h->active > 0) {
+    if ((rc = vcycle<float>(h, W, prec, 0, W.R32, W.Z32, st, dot1(W.R, W.part[1], &g))) != XAMG_OK)
+      return rc;
+    c.vcycles++;
+    launch_scalar(nv, SM_PCG_BETA, W.cs, W.part[1], nullptr, g, c.tol, 0, fl, st);
+    launch_fpcg_p(nv, n, W.P, W.Z32, W.cs, ge, st);
+  }
+  for (int k = 1; k <= c.maxit && h->flags_h->active > 0; ++k) {
+    c.iterations = k;
+    RowOp o = blank<double>();
+    o.src = W.P; o.y = W.Q; o.dot_u = W.P; o.partials = W.part[0];
+    if ((g = rows<double>(h, 0, 0, XAMG_PREC_FP64, o, nv, false, EPI_Y_DOT, st)) < 0) return XAMG_ERR_CUDA;
+    launch_scalar(nv, SM_PCG_ALPHA, W.cs, W.part[0], nullptr, g, c.tol, k, fl, st);
+    launch_fpcg_xr(nv, n, W.X, W.R, W.P, W.Q, W.cs, w0f, W.R32, W.Z32, W.part[1], ge, st);
+    launch_scalar(nv, SM_PCG_CONV, W.cs, W.part[1], nullptr, ge, c.tol, k, fl, st);
+    if ((rc = sync_read(st)) != XAMG_OK) return rc;
+    if (h->flags_h->active == 0) {
+      if ((g = true_residual(h, W, W.Q, W.part[2], st)) < 0) return XAMG_ERR_CUDA;
+      launch_scalar(nv, SM_CONFIRM, W.cs, W.part[2], nullptr, g, c.tol, k, fl, st);
+      if ((rc = sync_read(st)) != XAMG_OK) return rc;
+      if (h->flags_h->reactivated == 0) break;
+      launch_copy_cols(nv, n, W.R, W.Q, W.cs, ge, st);
+      launch_to_f32(nv, n, W.R, W.R32, w0f, W.Z32, ge, st);
+    }
+    Dots d = dot1(W.R, W.part[1], &g);
+    d.u2 = W.Q;
+    d.part2 = W.part[2];
+    if ((rc = vcycle<float>(h, W, prec, 0, W.R32, W.Z32, st, d)) != XAMG_OK) return rc;
+    c.vcycles++;
+    launch_scalar(nv, SM_FPCG_BETA, W.cs, W.part[1], W.part[2], g, c.tol, k, fl, st);
+    launch_fpcg_p(nv, n, W.P, W.Z32, W.cs, ge, st);
   }
   return finish(c, Xuser, stats);
 }
@@ -560,7 +825,9 @@ int solve_bicgstab(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stat
   const int64_t n = h->lv[0].A.n;
   const int ge = elem_grid(n, nv);
   const bool single = h->lv.size() == 1;
-  const double *w0 = single ? nullptr : h->lv[0].w[0];
+  // the FP64 preconditioner takes its first smoother iterate from the kernels
+  // that produce p and s; the reduced-precision one forms it while rounding
+  const double *w0 = (single || c.prec != XAMG_PREC_FP64) ? nullptr : h->lv[0].w[0];
   Flags *fl = h->flags_d;
   cudaStream_t st = c.st;
   int g;
@@ -577,22 +844,20 @@ int solve_bicgstab(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stat
     c.iterations = k;
     launch_scalar(nv, SM_BI_RHO, W.cs, prh, nullptr, grh, c.tol, k, fl, st);
     launch_bicg_p(nv, n, W.P, W.R, W.V, W.cs, w0, W.PH, ge, st);
-    if ((rc = vcycle(h, W, 0, W.P, W.PH, st, nullptr, nullptr, nullptr)) != XAMG_OK) return rc;
-    c.vcycles++;
-    RowOp o = blank();
+    if ((rc = apply_precond(c, W.P, W.PH)) != XAMG_OK) return rc;
+    RowOp o = blank<double>();
     o.src = W.PH; o.y = W.V; o.dot_u = W.RH; o.partials = W.part[1];
-    if ((g = rows(h, 0, 0, h->lv[0].A, o, nv, false, EPI_Y_DOT, st)) < 0) return XAMG_ERR_CUDA;
+    if ((g = rows<double>(h, 0, 0, XAMG_PREC_FP64, o, nv, false, EPI_Y_DOT, st)) < 0) return XAMG_ERR_CUDA;
     launch_scalar(nv, SM_BI_ALPHA, W.cs, W.part[1], nullptr, g, c.tol, k, fl, st);
     launch_bicg_s(nv, n, W.S, W.R, W.V, W.cs, w0, W.SH, W.part[2], ge, st);
     launch_scalar(nv, SM_BI_HALF, W.cs, W.part[2], nullptr, ge, c.tol, k, fl, st);
     if ((rc = sync_read(st)) != XAMG_OK) return rc;
     if (h->flags_h->active > 0) {
-      if ((rc = vcycle(h, W, 0, W.S, W.SH, st, nullptr, nullptr, nullptr)) != XAMG_OK) return rc;
-      c.vcycles++;
-      RowOp t = blank();
+      if ((rc = apply_precond(c, W.S, W.SH)) != XAMG_OK) return rc;
+      RowOp t = blank<double>();
       t.src = W.SH; t.y = W.T; t.dot_u = W.S; t.partials = W.part[1];
       t.partials2 = W.part[2];
-      if ((g = rows(h, 0, 0, h->lv[0].A, t, nv, false, EPI_Y_DOT2, st)) < 0) return XAMG_ERR_CUDA;
+      if ((g = rows<double>(h, 0, 0, XAMG_PREC_FP64, t, nv, false, EPI_Y_DOT2, st)) < 0) return XAMG_ERR_CUDA;
       launch_scalar(nv, SM_BI_OMEGA, W.cs, W.part[1], W.part[2], g, c.tol, k, fl, st);
     }
     launch_bicg_xr(nv, n, W.X, W.R, W.S, W.T, W.PH, W.SH, W.RH, W.cs, W.part[3], W.part[0], ge, st);
@@ -621,6 +886,8 @@ int solve_impl(xamg_hier *h, const double *B, double *X, int m, double tol, int 
   xamg_solve_opts_default(&o);
   if (opts) o = *opts;
   if (o.method != XAMG_PCG && o.method != XAMG_BICGSTAB) return XAMG_ERR_INVALID_ARG;
+  if (o.precond != XAMG_PREC_FP64 && o.precond != XAMG_PREC_FP32 && o.precond != XAMG_PREC_BF16)
+    return XAMG_ERR_INVALID_ARG;
   XCK(cudaSetDevice(h->device));
   SolveCtx c;
   c.h = h;
@@ -628,11 +895,15 @@ int solve_impl(xamg_hier *h, const double *B, double *X, int m, double tol, int 
   c.nv = pad_nv(m);
   c.tol = tol;
   c.maxit = maxit;
+  c.prec = o.precond;
   c.st = (cudaStream_t)o.stream;
-  int rc = ensure_workspace(h, c.nv, o.method, &o, c.W);
+  int rc = ensure_workspace(h, c.nv, o.method, c.prec, &o, c.W);
   if (rc != XAMG_OK) return rc;
   h->flags_h->active = 0;
-  rc = o.method == XAMG_PCG ? solve_pcg(c, B, X, stats) : solve_bicgstab(c, B, X, stats);
+  if (o.method == XAMG_PCG)
+    rc = c.prec == XAMG_PREC_FP64 ? solve_pcg(c, B, X, stats) : solve_fpcg(c, B, X, stats);
+  else
+    rc = solve_bicgstab(c, B, X, stats);
   if (h->timing && rc < 0) {
     cudaStreamSynchronize(c.st);
     flush_timing(h);
@@ -677,6 +948,7 @@ void xamg_amg_params_default(xamg_amg_params *p) {
 void xamg_solve_opts_default(xamg_solve_opts *o) {
   if (!o) return;
   o->method = XAMG_PCG;
+  o->precond = XAMG_PREC_FP64;
   o->stream = nullptr;
   o->workspace = nullptr;
   o->workspace_bytes = 0;
@@ -718,7 +990,7 @@ int xamg_setup_hierarchy(const xamg_csr *A, const xamg_amg_params *p, xamg_hier 
       delete h;
       return rc;
     }
-    h->tacc.assign((size_t)L * 3, TimeAcc());
+    h->tacc.assign((size_t)L * 6, TimeAcc());
     h->on_device = true;
   }
   *out = h;
@@ -786,10 +1058,12 @@ int xamg_coarse_export(const xamg_hier *h, int32_t *nc, double *lu, int32_t *piv
   return XAMG_OK;
 }
 
-int xamg_workspace_bytes(const xamg_hier *h, int32_t m, int32_t method, size_t *bytes) {
-  if (!h || !bytes || m < 1 || m > XAMG_MAX_RHS || (method != XAMG_PCG && method != XAMG_BICGSTAB))
+int xamg_workspace_bytes(const xamg_hier *h, int32_t m, int32_t method, int32_t precond,
+                         size_t *bytes) {
+  if (!h || !bytes || m < 1 || m > XAMG_MAX_RHS || (method != XAMG_PCG && method != XAMG_BICGSTAB) ||
+      precond < XAMG_PREC_FP64 || precond > XAMG_PREC_BF16)
     return XAMG_ERR_INVALID_ARG;
-  *bytes = plan(h, pad_nv(m), method, nullptr, nullptr);
+  *bytes = plan(h, pad_nv(m), method, precond, nullptr, nullptr);
   return XAMG_OK;
 }
 
@@ -835,16 +1109,16 @@ int xamg_level_spmm(xamg_hier *h, int32_t level, int32_t which, const double *X,
   double *dst = Y;
   Work W;
   if (nv != m) {
-    int rc = ensure_workspace(h, nv, XAMG_PCG, nullptr, W);
+    int rc = ensure_workspace(h, nv, XAMG_PCG, XAMG_PREC_FP64, nullptr, W);
     if (rc != XAMG_OK) return rc;
     src = W.Bn;
     dst = W.X;
     launch_pad_in(nv, M.ncols, X, m, W.Bn, elem_grid(M.ncols, nv), st);
   }
-  RowOp o = blank();
+  RowOp o = blank<double>();
   o.src = src;
   o.y = dst;
-  if (rows(h, level, which, M, o, nv, false, EPI_Y, st) < 0) return XAMG_ERR_CUDA;
+  if (rows<double>(h, level, which, XAMG_PREC_FP64, o, nv, false, EPI_Y, st) < 0) return XAMG_ERR_CUDA;
   if (nv != m) launch_copy_out(nv, M.n, W.X, Y, m, elem_grid(M.n, nv), st);
   XCK(cudaStreamSynchronize(st));
   XCK(cudaGetLastError());
@@ -861,7 +1135,7 @@ int xamg_smooth(xamg_hier *h, int32_t level, const double *B, double *X, double 
   cudaStream_t st = (cudaStream_t)stream;
   const int nv = pad_nv(m);
   Work W;
-  int rc = ensure_workspace(h, nv, XAMG_PCG, nullptr, W);
+  int rc = ensure_workspace(h, nv, XAMG_PCG, XAMG_PREC_FP64, nullptr, W);
   if (rc != XAMG_OK) return rc;
   DevLevel &D = h->lv[level];
   const int64_t n = D.A.n;
@@ -871,11 +1145,11 @@ int xamg_smooth(xamg_hier *h, int32_t level, const double *B, double *X, double 
   double *x = W.X, *r = W.vr[level];
   if (x_zero) {
     launch_scale_rows(nv, n, D.w[0], W.Bn, x, ge, st);
-    if ((rc = presmooth(h, W, level, W.Bn, x, r, st)) != XAMG_OK) return rc;
+    if ((rc = presmooth<double>(h, W, XAMG_PREC_FP64, level, W.Bn, x, r, st)) != XAMG_OK) return rc;
     if (R) launch_copy_out(nv, n, r, R, m, ge, st);
   } else {
     launch_pad_in(nv, n, X, m, x, ge, st);
-    if ((rc = postsmooth(h, W, level, W.Bn, x, r, st, nullptr, nullptr, nullptr)) != XAMG_OK)
+    if ((rc = postsmooth<double>(h, W, XAMG_PREC_FP64, level, W.Bn, x, r, st, Dots())) != XAMG_OK)
       return rc;
   }
   launch_copy_out(nv, n, x, X, m, ge, st);
@@ -891,13 +1165,37 @@ int xamg_vcycle(xamg_hier *h, const double *B, double *X, int32_t m, void *strea
   cudaStream_t st = (cudaStream_t)stream;
   const int nv = pad_nv(m);
   Work W;
-  int rc = ensure_workspace(h, nv, XAMG_PCG, nullptr, W);
+  int rc = ensure_workspace(h, nv, XAMG_PCG, XAMG_PREC_FP64, nullptr, W);
   if (rc != XAMG_OK) return rc;
   const int64_t n = h->lv[0].A.n;
   const int ge = elem_grid(n, nv);
   launch_pad_in(nv, n, B, m, W.Bn, ge, st);
   if (h->lv.size() > 1) launch_scale_rows(nv, n, h->lv[0].w[0], W.Bn, W.X, ge, st);
-  if ((rc = vcycle(h, W, 0, W.Bn, W.X, st, nullptr, nullptr, nullptr)) != XAMG_OK) return rc;
+  if ((rc = vcycle<double>(h, W, XAMG_PREC_FP64, 0, W.Bn, W.X, st, Dots())) != XAMG_OK) return rc;
+  launch_copy_out(nv, n, W.X, X, m, ge, st);
+  XCK(cudaStreamSynchronize(st));
+  XCK(cudaGetLastError());
+  if (h->timing) flush_timing(h);
+  return XAMG_OK;
+}
+
+int xamg_vcycle_precond(xamg_hier *h, int32_t precond, const double *B, double *X, int32_t m,
+                        void *stream) {
+  if (!h || !h->on_device || !B || !X || m < 1 || m > XAMG_MAX_RHS) return XAMG_ERR_INVALID_ARG;
+  if (precond == XAMG_PREC_FP64) return xamg_vcycle(h, B, X, m, stream);
+  if (precond != XAMG_PREC_FP32 && precond != XAMG_PREC_BF16) return XAMG_ERR_INVALID_ARG;
+  XCK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nv = pad_nv(m);
+  Work W;
+  int rc = ensure_workspace(h, nv, XAMG_PCG, precond, nullptr, W);
+  if (rc != XAMG_OK) return rc;
+  const int64_t n = h->lv[0].A.n;
+  const int ge = elem_grid(n, nv);
+  launch_pad_in(nv, n, B, m, W.Bn, ge, st);
+  launch_to_f32(nv, n, W.Bn, W.R32, h->lv.size() > 1 ? h->lv[0].w32[0] : nullptr, W.Z32, ge, st);
+  if ((rc = vcycle<float>(h, W, precond, 0, W.R32, W.Z32, st, Dots())) != XAMG_OK) return rc;
+  launch_to_f64(nv, n, W.Z32, W.X, ge, st);
   launch_copy_out(nv, n, W.X, X, m, ge, st);
   XCK(cudaStreamSynchronize(st));
   XCK(cudaGetLastError());
@@ -911,7 +1209,7 @@ int xamg_coarse_solve(xamg_hier *h, const double *B, double *X, int32_t m, void 
   cudaStream_t st = (cudaStream_t)stream;
   const int nv = pad_nv(m);
   Work W;
-  int rc = ensure_workspace(h, nv, XAMG_PCG, nullptr, W);
+  int rc = ensure_workspace(h, nv, XAMG_PCG, XAMG_PREC_FP64, nullptr, W);
   if (rc != XAMG_OK) return rc;
   const int nc = h->host.nc;
   const int ge = elem_grid(nc, nv);
@@ -943,15 +1241,15 @@ int64_t xamg_kernel_launches(void) { return g_launches.load(); }
 int xamg_timing_enable(xamg_hier *h, int32_t enable) {
   if (!h || !h->on_device) return XAMG_ERR_INVALID_ARG;
   h->timing = enable != 0;
-  if (h->timing) h->tacc.assign(h->lv.size() * 3, TimeAcc());
+  if (h->timing) h->tacc.assign(h->lv.size() * 6, TimeAcc());
   return XAMG_OK;
 }
 
 int xamg_timing_read(const xamg_hier *h, int32_t level, int32_t which, int64_t *launches,
                      double *total_ms, double *flops, double *bytes) {
-  if (!h || !h->on_device || level < 0 || level >= (int)h->lv.size() || which < 0 || which > 2)
+  if (!h || !h->on_device || level < 0 || level >= (int)h->lv.size() || which < 0 || which > 5)
     return XAMG_ERR_INVALID_ARG;
-  const TimeAcc &t = h->tacc[(size_t)level * 3 + which];
+  const TimeAcc &t = h->tacc[(size_t)level * 6 + which];
   if (launches) *launches = t.launches;
   if (total_ms) *total_ms = t.ms;
   if (flops) *flops = t.flops;

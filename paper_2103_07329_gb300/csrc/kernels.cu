@@ -42,6 +42,18 @@ int launch_rows(const RowOp &op, int nv, int slices, bool neg, int epi, cudaStre
   return -1;
 }
 
+int launch_rows_f(const RowOpF &op, int nv, int slices, bool neg, int epi, int vt, cudaStream_t st) {
+  switch (nv) {
+    case 1: return launch_rowsf_nv1(op, slices, neg, epi, vt, st);
+    case 2: return launch_rowsf_nv2(op, slices, neg, epi, vt, st);
+    case 4: return launch_rowsf_nv4(op, slices, neg, epi, vt, st);
+    case 8: return launch_rowsf_nv8(op, slices, neg, epi, vt, st);
+    case 16: return launch_rowsf_nv16(op, slices, neg, epi, vt, st);
+    case 32: return launch_rowsf_nv32(op, slices, neg, epi, vt, st);
+  }
+  return -1;
+}
+
 // ------------------------------------------------------------------ elementwise
 #define XAMG_ELEM_LOOP(NV, n)                                                            \
   for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x, total__ = (n) * (NV); e < total__; \
@@ -312,6 +324,22 @@ __global__ void __launch_bounds__(1024) k_scalar(int mode, ColState *cs, const d
       case SM_FINAL:
         cs->tn[c] = sqrt(d0);
         break;
+      case SM_FPCG_BETA:
+        // flexible CG (FP32 preconditioner): beta = z_new . (r_new - r_old) / (z_old . r_old)
+        // with r_new - r_old = -alpha q, i.e. beta = -alpha (z_new . q) / rho_old
+        if (st == 0) {
+          if (!(d0 > 0.0)) {
+            cs->state[c] = 3;
+            cs->beta[c] = 0.0;
+          } else {
+            cs->beta[c] = cs->restart[c] ? 0.0 : -cs->alpha[c] * d1 / cs->rho[c];
+            cs->restart[c] = 0;
+            cs->rho[c] = d0;
+          }
+        } else {
+          cs->beta[c] = 0.0;
+        }
+        break;
       case SM_BI_RHO:
         if (st == 0) {
           if (d0 == 0.0 || !isfinite(d0)) {
@@ -421,6 +449,138 @@ __global__ void __launch_bounds__(kBlock) k_coarse(int nc, const double *lu, con
     }
     __syncthreads();
   }
+}
+
+// ------------------------------------------------------------------ mixed precision
+// Kernels of the outer FP64 loop around a reduced-precision (FP32 block)
+// preconditioner: FP64 vectors are rounded once to FP32 for the V-cycle and
+// its FP32 result is widened again where the FP64 loop reads it.
+
+// Bn = R = B (padded), X = 0, R32 = fl32(B), Z32 = w0 * R32, partial ||B||^2.
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_init_fpcg(int64_t n, const double *B, int m, double *Bn,
+                                                      double *R, double *X, float *R32, float *Z32,
+                                                      const float *w0, double *part) {
+  const int c = threadIdx.x % NV;
+  double acc = 0.0;
+  XAMG_ELEM_LOOP(NV, n) {
+    const int64_t i = e / NV;
+    const double b = c < m ? B[i * m + c] : 0.0;
+    Bn[e] = b;
+    R[e] = b;
+    X[e] = 0.0;
+    const float b32 = (float)b;
+    R32[e] = b32;
+    Z32[e] = w0 ? w0[i] * b32 : 0.0f;
+    acc = fma(b, b, acc);
+  }
+  block_colsum_store<NV>(acc, part);
+}
+
+// x += alpha p ; r -= alpha q ; R32 = fl32(r) ; Z32 = w0 * R32 ; partial ||r||^2
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_fpcg_xr(int64_t n, double *X, double *R, const double *P,
+                                                    const double *Q, const ColState *cs,
+                                                    const float *w0, float *R32, float *Z32,
+                                                    double *part) {
+  const int c = threadIdx.x % NV;
+  const double a = cs->alpha[c];
+  double acc = 0.0;
+  XAMG_ELEM_LOOP(NV, n) {
+    const double r = fma(-a, Q[e], R[e]);
+    X[e] = fma(a, P[e], X[e]);
+    R[e] = r;
+    const float r32 = (float)r;
+    R32[e] = r32;
+    if (w0) Z32[e] = w0[e / NV] * r32;
+    acc = fma(r, r, acc);
+  }
+  block_colsum_store<NV>(acc, part);
+}
+
+// p = z + beta p with z the preconditioner's FP32 output
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_fpcg_p(int64_t n, double *P, const float *Z32,
+                                                   const ColState *cs) {
+  const int c = threadIdx.x % NV;
+  const double b = cs->beta[c];
+  if (b == 0.0) {
+    XAMG_ELEM_LOOP(NV, n) { P[e] = (double)Z32[e]; }
+  } else {
+    XAMG_ELEM_LOOP(NV, n) { P[e] = fma(b, P[e], (double)Z32[e]); }
+  }
+}
+
+// Y32 = fl32(X) and, if w0, Z32 = w0 * Y32
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_to_f32(int64_t n, const double *X, float *Y32,
+                                                   const float *w0, float *Z32) {
+  XAMG_ELEM_LOOP(NV, n) {
+    const float y = (float)X[e];
+    Y32[e] = y;
+    if (w0) Z32[e] = w0[e / NV] * y;
+  }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_to_f64(int64_t n, const float *X32, double *Y) {
+  XAMG_ELEM_LOOP(NV, n) { Y[e] = (double)X32[e]; }
+}
+
+// x += d (FP32) ; optional FP64 partials u . x and u2 . x
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_axpy_dot_f(int64_t n, float *X, const float *D,
+                                                       const double *U, const double *U2,
+                                                       double *part, double *part2) {
+  double acc = 0.0, acc2 = 0.0;
+  XAMG_ELEM_LOOP(NV, n) {
+    const float x = X[e] + D[e];
+    X[e] = x;
+    if (U) acc = fma(U[e], (double)x, acc);
+    if (U2) acc2 = fma(U2[e], (double)x, acc2);
+  }
+  if (part) block_colsum_store<NV>(acc, part);
+  if (part2) {
+    __syncthreads();
+    block_colsum_store<NV>(acc2, part2);
+  }
+}
+
+// Coarsest level with FP32 blocks: the FP64 LU solve of k_coarse on an FP64
+// working copy W (nc x NV), rounded back to FP32.
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_coarse_f(int nc, const double *lu, const int32_t *piv,
+                                                     const float *B, float *X, double *W) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nc * NV; e += kBlock) W[e] = (double)B[e];
+  __syncthreads();
+  if (tid < NV)
+    for (int k = 0; k < nc; ++k) {
+      const int p = piv[k];
+      if (p != k) {
+        const double t = W[k * NV + tid];
+        W[k * NV + tid] = W[p * NV + tid];
+        W[p * NV + tid] = t;
+      }
+    }
+  __syncthreads();
+  for (int k = 0; k + 1 < nc; ++k) {
+    for (int e = tid; e < (nc - k - 1) * NV; e += kBlock) {
+      const int i = k + 1 + e / NV, c = e % NV;
+      W[i * NV + c] = __dsub_rn(W[i * NV + c], __dmul_rn(lu[(size_t)i * nc + k], W[k * NV + c]));
+    }
+    __syncthreads();
+  }
+  for (int i = nc - 1; i >= 0; --i) {
+    if (tid < NV) W[i * NV + tid] = W[i * NV + tid] / lu[(size_t)i * nc + i];
+    __syncthreads();
+    for (int e = tid; e < i * NV; e += kBlock) {
+      const int r = e / NV, c = e % NV;
+      W[r * NV + c] = __dsub_rn(W[r * NV + c], __dmul_rn(lu[(size_t)r * nc + i], W[i * NV + c]));
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < nc * NV; e += kBlock) X[e] = (float)W[e];
 }
 
 // ------------------------------------------------------------------ runtime-m dots
@@ -533,6 +693,36 @@ void launch_scalar(int nv, int mode, ColState *cs, const double *p0, const doubl
 void launch_coarse(int nv, int nc, const double *lu, const int32_t *piv, const double *B, double *X,
                    cudaStream_t st) {
   XAMG_NV_SWITCH(nv, (k_coarse<NV><<<1, kBlock, 0, st>>>(nc, lu, piv, B, X)));
+}
+
+void launch_init_fpcg(int nv, int64_t n, const double *B, int m, double *Bn, double *R, double *X,
+                      float *R32, float *Z32, const float *w0, double *part, int grid,
+                      cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_init_fpcg<NV><<<grid, kBlock, 0, st>>>(n, B, m, Bn, R, X, R32, Z32, w0, part)));
+}
+void launch_fpcg_xr(int nv, int64_t n, double *X, double *R, const double *P, const double *Q,
+                    const ColState *cs, const float *w0, float *R32, float *Z32, double *part,
+                    int grid, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_fpcg_xr<NV><<<grid, kBlock, 0, st>>>(n, X, R, P, Q, cs, w0, R32, Z32, part)));
+}
+void launch_fpcg_p(int nv, int64_t n, double *P, const float *Z32, const ColState *cs, int grid,
+                   cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_fpcg_p<NV><<<grid, kBlock, 0, st>>>(n, P, Z32, cs)));
+}
+void launch_to_f32(int nv, int64_t n, const double *X, float *Y32, const float *w0, float *Z32,
+                   int grid, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_to_f32<NV><<<grid, kBlock, 0, st>>>(n, X, Y32, w0, Z32)));
+}
+void launch_to_f64(int nv, int64_t n, const float *X32, double *Y, int grid, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_to_f64<NV><<<grid, kBlock, 0, st>>>(n, X32, Y)));
+}
+void launch_axpy_dot_f(int nv, int64_t n, float *X, const float *D, const double *U,
+                       const double *U2, double *part, double *part2, int grid, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_axpy_dot_f<NV><<<grid, kBlock, 0, st>>>(n, X, D, U, U2, part, part2)));
+}
+void launch_coarse_f(int nv, int nc, const double *lu, const int32_t *piv, const float *B, float *X,
+                     double *W, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_coarse_f<NV><<<1, kBlock, 0, st>>>(nc, lu, piv, B, X, W)));
 }
 
 int coldot_rt_grid(int64_t n, int m) {

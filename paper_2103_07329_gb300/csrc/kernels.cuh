@@ -3,9 +3,14 @@
 // Blocks of NV columns are n x NV row-major (element (i, c) at i*NV + c); NV
 // is a compile-time power of two in {1, 2, 4, 8, 16, 32}, the counterpart of
 // the paper's compile-time RHS count (Sec. 2.3: "The number of RHSs is also
-// given as a template parameter").
+// given as a template parameter").  The block scalar TB is double (the FP64
+// solve) or float (the reduced-precision preconditioner of paper Sec. 2.3,
+// "mixed-precision"); the matrix values TV are double, float, or bf16 with a
+// per-row FP32 scale.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
 #include <cstdint>
 
 namespace xamg {
@@ -18,31 +23,37 @@ constexpr int kWarps = kBlock / 32;
 // column c:
 //   v      = init[i,c] (or 0)  +/-  sum_k M_ik * src[k,c]      (sign: template NEG)
 //   y[i,c] = v                                                 (if y)
-//   dn     = c1 * dp[i,c] + w[i] * v                           (if w; dp may be null)
-//   dnext[i,c] = dn                                            (if dnext)
+//   dn     = c1 * dp[i,c] + w[i] * v
+//   dnext[i,c] = dn
 //   x[i,c] += dp[i,c] and/or dn
 //   partial dots over the block's rows, written to partials[block*NV + c]
 // which of these apply is the kernel's compile-time epilogue (enum Epi).
 // All pointers except rowptr/col/val/src may alias each other only at the
 // same element (own-row reads before own-row writes); src never aliases an
-// output.
-struct RowOp {
+// output.  Dots are always accumulated in FP64 (dot_u, dot_u2 are FP64
+// blocks).
+template <class TB>
+struct RowOpT {
   int n;
   const int32_t *rowptr;
   const int32_t *col;
-  const double *val;
-  const double *src;
-  const double *init;
-  double *y;
-  const double *dp;
-  const double *w;
-  double c1;
-  double *dnext;
-  double *x;
+  const void *val;       // matrix values (TV)
+  const float *rscale;   // per-row scale of bf16 values
+  const TB *src;
+  const TB *init;
+  TB *y;
+  const TB *dp;
+  const TB *w;
+  TB c1;
+  TB *dnext;
+  TB *x;
   const double *dot_u;
+  const double *dot_u2;
   double *partials;
-  double *partials2;  // partial sums of v * v (EPI_Y_DOT2)
+  double *partials2;  // second reduction (EPI_Y_DOT2: v . v; EPI_XLAST_DOT2: dot_u2 . x)
 };
+using RowOp = RowOpT<double>;
+using RowOpF = RowOpT<float>;
 
 // Sum over the lanes of a warp that hold the same column c = lane % NV, in a
 // fixed xor-tree order; the result is valid in every lane.
@@ -82,16 +93,17 @@ enum Epi : int {
   EPI_XLAST_DOT,   // EPI_XLAST and partial dot_u . x_new
   EPI_Y_DOT,       // y = v ; partial dot_u . v
   EPI_Y_DOT2,      // y = v ; partial dot_u . v (if dot_u) and v . v
+  EPI_XLAST_DOT2,  // EPI_XLAST and partials dot_u . x_new, dot_u2 . x_new
   EPI_COUNT
 };
 
-// dpv, wv, xv, du are the own-row operands loaded before the product loop.
-template <int NV, int EPI>
-__device__ __forceinline__ void row_epilogue(const RowOp &op, int64_t i, int c, double acc,
-                                             double dpv, double wv, double xv, double du,
+// dpv, wv, xv, du, du2 are the own-row operands loaded before the product loop.
+template <class TB, int NV, int EPI>
+__device__ __forceinline__ void row_epilogue(const RowOpT<TB> &op, int64_t i, int c, TB acc,
+                                             TB dpv, TB wv, TB xv, double du, double du2,
                                              double &dsum, double &dsum2) {
   const int64_t e = i * NV + c;
-  if constexpr (EPI != EPI_XLAST && EPI != EPI_XLAST_DOT) {
+  if constexpr (EPI != EPI_XLAST && EPI != EPI_XLAST_DOT && EPI != EPI_XLAST_DOT2) {
     if (op.y) op.y[e] = acc;
   }
   if constexpr (EPI == EPI_Y_D0) op.dnext[e] = wv * acc;
@@ -101,49 +113,68 @@ __device__ __forceinline__ void row_epilogue(const RowOp &op, int64_t i, int c, 
     op.dnext[e] = fma(op.c1, dpv, wv * acc);
     op.x[e] = xv + dpv;
   }
-  if constexpr (EPI == EPI_XLAST || EPI == EPI_XLAST_DOT) {
-    const double xn = (xv + dpv) + fma(op.c1, dpv, wv * acc);
+  if constexpr (EPI == EPI_XLAST || EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2) {
+    const TB xn = (xv + dpv) + fma(op.c1, dpv, wv * acc);
     op.x[e] = xn;
-    if constexpr (EPI == EPI_XLAST_DOT) dsum = fma(du, xn, dsum);
+    if constexpr (EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2) dsum = fma(du, (double)xn, dsum);
+    if constexpr (EPI == EPI_XLAST_DOT2) dsum2 = fma(du2, (double)xn, dsum2);
   }
-  if constexpr (EPI == EPI_Y_DOT) dsum = fma(du, acc, dsum);
+  if constexpr (EPI == EPI_Y_DOT) dsum = fma(du, (double)acc, dsum);
   if constexpr (EPI == EPI_Y_DOT2) {
-    if (op.dot_u) dsum = fma(du, acc, dsum);
-    dsum2 = fma(acc, acc, dsum2);
+    if (op.dot_u) dsum = fma(du, (double)acc, dsum);
+    dsum2 = fma((double)acc, (double)acc, dsum2);
   }
 }
 
 template <int EPI>
 __device__ __forceinline__ constexpr bool epi_has_dot() {
-  return EPI == EPI_XLAST_DOT || EPI == EPI_Y_DOT || EPI == EPI_Y_DOT2;
+  return EPI == EPI_XLAST_DOT || EPI == EPI_Y_DOT || EPI == EPI_Y_DOT2 || EPI == EPI_XLAST_DOT2;
 }
 
 // Own-row operands of the epilogue.
-template <int NV, int EPI>
-__device__ __forceinline__ void row_operands(const RowOp &op, int64_t i, int c, double &dpv,
-                                             double &wv, double &xv, double &du) {
+template <class TB, int NV, int EPI>
+__device__ __forceinline__ void row_operands(const RowOpT<TB> &op, int64_t i, int c, TB &dpv,
+                                             TB &wv, TB &xv, double &du, double &du2) {
   const int64_t e = i * NV + c;
-  if constexpr (EPI == EPI_Y_DN || EPI == EPI_Y_XDP || EPI == EPI_MID || EPI == EPI_XLAST ||
-                EPI == EPI_XLAST_DOT)
-    dpv = op.dp[e];
-  if constexpr (EPI == EPI_Y_D0 || EPI == EPI_Y_DN || EPI == EPI_MID || EPI == EPI_XLAST ||
-                EPI == EPI_XLAST_DOT)
-    wv = op.w[i];
-  if constexpr (EPI == EPI_Y_XDP || EPI == EPI_MID || EPI == EPI_XLAST || EPI == EPI_XLAST_DOT)
-    xv = op.x[e];
-  if constexpr (EPI == EPI_XLAST_DOT || EPI == EPI_Y_DOT) du = op.dot_u[e];
+  constexpr bool xlast = EPI == EPI_XLAST || EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2;
+  if constexpr (EPI == EPI_Y_DN || EPI == EPI_Y_XDP || EPI == EPI_MID || xlast) dpv = op.dp[e];
+  if constexpr (EPI == EPI_Y_D0 || EPI == EPI_Y_DN || EPI == EPI_MID || xlast) wv = op.w[i];
+  if constexpr (EPI == EPI_Y_XDP || EPI == EPI_MID || xlast) xv = op.x[e];
+  if constexpr (EPI == EPI_XLAST_DOT || EPI == EPI_Y_DOT || EPI == EPI_XLAST_DOT2) du = op.dot_u[e];
+  if constexpr (EPI == EPI_XLAST_DOT2) du2 = op.dot_u2[e];
   if constexpr (EPI == EPI_Y_DOT2) du = op.dot_u ? op.dot_u[e] : 0.0;
 }
 
-template <bool NEG>
-__device__ __forceinline__ double fmadd(double a, double x, double acc) {
+// Matrix value storage: TV = double / float (value as stored) or bf16 (value
+// relative to the row's FP32 scale, applied once per row).
+template <class TV> struct ValueLoad;
+template <> struct ValueLoad<double> {
+  static constexpr bool scaled = false;
+  __device__ __forceinline__ static double get(const void *v, int k) {
+    return __ldg(static_cast<const double *>(v) + k);
+  }
+};
+template <> struct ValueLoad<float> {
+  static constexpr bool scaled = false;
+  __device__ __forceinline__ static float get(const void *v, int k) {
+    return __ldg(static_cast<const float *>(v) + k);
+  }
+};
+template <> struct ValueLoad<__nv_bfloat16> {
+  static constexpr bool scaled = true;
+  __device__ __forceinline__ static float get(const void *v, int k) {
+    return __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(v) + k));
+  }
+};
+
+template <bool NEG, class TB>
+__device__ __forceinline__ TB fmadd(TB a, TB x, TB acc) {
   return NEG ? fma(-a, x, acc) : fma(a, x, acc);
 }
 
 // Exactly `rem` (1..7) further products of one chunk, in order.
-template <bool NEG>
-__device__ __forceinline__ double tail_fma(int rem, const double (&as)[8], const double (&xs)[8],
-                                           double acc) {
+template <bool NEG, class TB>
+__device__ __forceinline__ TB tail_fma(int rem, const TB (&as)[8], const TB (&xs)[8], TB acc) {
   switch (rem) {
     case 7: acc = fmadd<NEG>(as[0], xs[0], acc); acc = fmadd<NEG>(as[1], xs[1], acc);
             acc = fmadd<NEG>(as[2], xs[2], acc); acc = fmadd<NEG>(as[3], xs[3], acc);
@@ -173,9 +204,12 @@ __device__ __forceinline__ double tail_fma(int rem, const double (&as)[8], const
 // before their FMAs: the dependent chain per row is row pointer -> index/value
 // -> operand rows, independent of the row length.  Each lane adds its
 // column's products in the row's storage order (no reduction adds), and a
-// chunk's tail takes exactly as many FMAs as it has entries.
-template <int NV, bool NEG, int EPI>
-__device__ __forceinline__ void rows_lane_per_column(const RowOp &op) {
+// chunk's tail takes exactly as many FMAs as it has entries.  With scaled
+// (bf16) values the products are summed first and the row scale applied once:
+// v = init +/- s_i * sum_k q_ik x_k.
+template <class TB, class TV, int NV, bool NEG, int EPI>
+__device__ __forceinline__ void rows_lane_per_column(const RowOpT<TB> &op) {
+  using VL = ValueLoad<TV>;
   constexpr int RPW = 32 / NV;
   const int lane = threadIdx.x & 31;
   const int c = lane % NV;
@@ -183,35 +217,35 @@ __device__ __forceinline__ void rows_lane_per_column(const RowOp &op) {
   const int gbase = grp * NV;
   const int64_t warp0 = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t wstride = (int64_t)gridDim.x * kWarps;
-  const double *__restrict__ val = op.val;
   const int32_t *__restrict__ col = op.col;
-  const double *__restrict__ src = op.src;
+  const TB *__restrict__ src = op.src;
   double dsum = 0.0, dsum2 = 0.0;
   for (int64_t base = warp0 * RPW; base < op.n; base += wstride * RPW) {
     const int64_t i = base + grp;
     const bool valid = i < op.n;
     int start = 0, len = 0;
-    double acc = 0.0, dpv = 0.0, wv = 0.0, xv = 0.0, du = 0.0;
+    TB acc = 0, dpv = 0, wv = 0, xv = 0;
+    double du = 0.0, du2 = 0.0;
     if (valid) {
       start = __ldg(op.rowptr + i);
       len = __ldg(op.rowptr + i + 1) - start;
-      if (op.init) acc = op.init[i * NV + c];
-      row_operands<NV, EPI>(op, i, c, dpv, wv, xv, du);
+      if (!VL::scaled && op.init) acc = op.init[i * NV + c];
+      row_operands<TB, NV, EPI>(op, i, c, dpv, wv, xv, du, du2);
     }
     const int maxlen = RPW == 1 ? len : __reduce_max_sync(0xffffffffu, len);
     for (int kb = 0; kb < maxlen; kb += NV) {
       const bool own = kb + c < len;
       const int cl = own ? __ldg(col + start + kb + c) : 0;
-      const double av = own ? __ldg(val + start + kb + c) : 0.0;
+      const TB av = own ? (TB)VL::get(op.val, start + kb + c) : (TB)0;
       const int cnt = min(NV, maxlen - kb);
       for (int t = 0; t < cnt; t += 8) {
-        double xs[8], as[8];
+        TB xs[8], as[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int from = (gbase + t + u) & 31;
           const int cc = __shfl_sync(0xffffffffu, cl, from);
           as[u] = __shfl_sync(0xffffffffu, av, from);
-          xs[u] = (t + u < cnt && kb + t + u < len) ? __ldg(src + (int64_t)cc * NV + c) : 0.0;
+          xs[u] = (t + u < cnt && kb + t + u < len) ? __ldg(src + (int64_t)cc * NV + c) : (TB)0;
         }
         // entries past this row's own end carry a = x = 0 (rows of one warp
         // may differ in length when NV < 32)
@@ -224,11 +258,14 @@ __device__ __forceinline__ void rows_lane_per_column(const RowOp &op) {
         }
       }
     }
-    if (valid) row_epilogue<NV, EPI>(op, i, c, acc, dpv, wv, xv, du, dsum, dsum2);
+    if constexpr (VL::scaled) {
+      if (valid) acc = fma((TB)op.rscale[i], acc, op.init ? op.init[i * NV + c] : (TB)0);
+    }
+    if (valid) row_epilogue<TB, NV, EPI>(op, i, c, acc, dpv, wv, xv, du, du2, dsum, dsum2);
   }
   if constexpr (epi_has_dot<EPI>()) {
     if (EPI != EPI_Y_DOT2 || op.dot_u) block_colsum_store<NV>(dsum, op.partials);
-    if constexpr (EPI == EPI_Y_DOT2) {
+    if constexpr (EPI == EPI_Y_DOT2 || EPI == EPI_XLAST_DOT2) {
       __syncthreads();
       block_colsum_store<NV>(dsum2, op.partials2);
     }
@@ -239,8 +276,9 @@ __device__ __forceinline__ void rows_lane_per_column(const RowOp &op) {
 // G = NV*S lanes owns one row, lane -> column c = lane % NV and slice
 // s = (lane / NV) % S; slice s takes the row's entries s, s+S, ... and the
 // slices are added with shuffles.
-template <int NV, int S, bool NEG, int EPI>
-__device__ __forceinline__ void rows_sliced(const RowOp &op) {
+template <class TB, class TV, int NV, int S, bool NEG, int EPI>
+__device__ __forceinline__ void rows_sliced(const RowOpT<TB> &op) {
+  using VL = ValueLoad<TV>;
   constexpr int G = NV * S;
   constexpr int RPW = 32 / G;
   const int lane = threadIdx.x & 31;
@@ -249,43 +287,46 @@ __device__ __forceinline__ void rows_sliced(const RowOp &op) {
   const int grp = lane / G;
   const int64_t warp0 = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t wstride = (int64_t)gridDim.x * kWarps;
-  const double *__restrict__ val = op.val;
   const int32_t *__restrict__ col = op.col;
-  const double *__restrict__ src = op.src;
+  const TB *__restrict__ src = op.src;
   double dsum = 0.0, dsum2 = 0.0;
   for (int64_t base = warp0 * RPW; base < op.n; base += wstride * RPW) {
     const int64_t i = base + grp;
     const bool valid = i < op.n;
-    double acc = 0.0, dpv = 0.0, wv = 0.0, xv = 0.0, du = 0.0;
+    TB acc = 0, dpv = 0, wv = 0, xv = 0;
+    double du = 0.0, du2 = 0.0;
     if (valid) {
-      if (op.init && s == 0) acc = op.init[i * NV + c];
-      row_operands<NV, EPI>(op, i, c, dpv, wv, xv, du);
+      if (!VL::scaled && op.init && s == 0) acc = op.init[i * NV + c];
+      row_operands<TB, NV, EPI>(op, i, c, dpv, wv, xv, du, du2);
       int k = __ldg(op.rowptr + i) + s;
       const int end = __ldg(op.rowptr + i + 1);
       for (; k + 3 * S < end; k += 4 * S) {
         const int k0 = __ldg(col + k), k1 = __ldg(col + k + S), k2 = __ldg(col + k + 2 * S),
                   k3 = __ldg(col + k + 3 * S);
-        const double a0 = __ldg(val + k), a1 = __ldg(val + k + S), a2 = __ldg(val + k + 2 * S),
-                     a3 = __ldg(val + k + 3 * S);
-        const double x0 = __ldg(src + (int64_t)k0 * NV + c), x1 = __ldg(src + (int64_t)k1 * NV + c),
-                     x2 = __ldg(src + (int64_t)k2 * NV + c), x3 = __ldg(src + (int64_t)k3 * NV + c);
+        const TB a0 = VL::get(op.val, k), a1 = VL::get(op.val, k + S),
+                 a2 = VL::get(op.val, k + 2 * S), a3 = VL::get(op.val, k + 3 * S);
+        const TB x0 = __ldg(src + (int64_t)k0 * NV + c), x1 = __ldg(src + (int64_t)k1 * NV + c),
+                 x2 = __ldg(src + (int64_t)k2 * NV + c), x3 = __ldg(src + (int64_t)k3 * NV + c);
         acc = fmadd<NEG>(a0, x0, acc);
         acc = fmadd<NEG>(a1, x1, acc);
         acc = fmadd<NEG>(a2, x2, acc);
         acc = fmadd<NEG>(a3, x3, acc);
       }
       for (; k < end; k += S) {
-        const double a = __ldg(val + k);
+        const TB a = VL::get(op.val, k);
         acc = fmadd<NEG>(a, __ldg(src + (int64_t)__ldg(col + k) * NV + c), acc);
       }
     }
 #pragma unroll
     for (int o = NV; o < G; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (valid && s == 0) row_epilogue<NV, EPI>(op, i, c, acc, dpv, wv, xv, du, dsum, dsum2);
+    if constexpr (VL::scaled) {
+      if (valid) acc = fma((TB)op.rscale[i], acc, op.init ? op.init[i * NV + c] : (TB)0);
+    }
+    if (valid && s == 0) row_epilogue<TB, NV, EPI>(op, i, c, acc, dpv, wv, xv, du, du2, dsum, dsum2);
   }
   if constexpr (epi_has_dot<EPI>()) {
     if (EPI != EPI_Y_DOT2 || op.dot_u) block_colsum_store<NV>(dsum, op.partials);
-    if constexpr (EPI == EPI_Y_DOT2) {
+    if constexpr (EPI == EPI_Y_DOT2 || EPI == EPI_XLAST_DOT2) {
       __syncthreads();
       block_colsum_store<NV>(dsum2, op.partials2);
     }
@@ -297,12 +338,12 @@ __device__ __forceinline__ void rows_sliced(const RowOp &op) {
 // only on n and the grid size.  At most 64 registers per thread (four
 // 256-thread blocks per SM): measured faster than the uncapped build, whose
 // wider epilogues took 80 registers and three blocks per SM.
-template <int NV, int S, bool NEG, int EPI>
-__global__ void __launch_bounds__(kBlock, 4) k_rows(RowOp op) {
+template <class TB, class TV, int NV, int S, bool NEG, int EPI>
+__global__ void __launch_bounds__(kBlock, 4) k_rows(RowOpT<TB> op) {
   if constexpr (S == 1) {
-    rows_lane_per_column<NV, NEG, EPI>(op);
+    rows_lane_per_column<TB, TV, NV, NEG, EPI>(op);
   } else {
-    rows_sliced<NV, S, NEG, EPI>(op);
+    rows_sliced<TB, TV, NV, S, NEG, EPI>(op);
   }
 }
 

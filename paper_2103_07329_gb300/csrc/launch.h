@@ -47,6 +47,7 @@ enum ScalarMode : int {
   SM_BI_HALF = 8,    // p0: s.s -> iters = k, half-step freeze
   SM_BI_OMEGA = 9,   // p0: t.s, p1: t.t -> omega
   SM_BI_CONV = 10,   // p0: r.r -> freeze
+  SM_FPCG_BETA = 11, // p0: r.z, p1: q.z -> flexible beta, rho
 };
 
 int device_sm_count();
@@ -62,6 +63,14 @@ int launch_rows_nv4(const RowOp &op, int slices, bool neg, int epi, cudaStream_t
 int launch_rows_nv8(const RowOp &op, int slices, bool neg, int epi, cudaStream_t st);
 int launch_rows_nv16(const RowOp &op, int slices, bool neg, int epi, cudaStream_t st);
 int launch_rows_nv32(const RowOp &op, int slices, bool neg, int epi, cudaStream_t st);
+// FP32 blocks; vt 0 = float values, 1 = bf16 values with per-row FP32 scale.
+int launch_rows_f(const RowOpF &op, int nv, int slices, bool neg, int epi, int vt, cudaStream_t st);
+int launch_rowsf_nv1(const RowOpF &op, int slices, bool neg, int epi, int vt, cudaStream_t st);
+int launch_rowsf_nv2(const RowOpF &op, int slices, bool neg, int epi, int vt, cudaStream_t st);
+int launch_rowsf_nv4(const RowOpF &op, int slices, bool neg, int epi, int vt, cudaStream_t st);
+int launch_rowsf_nv8(const RowOpF &op, int slices, bool neg, int epi, int vt, cudaStream_t st);
+int launch_rowsf_nv16(const RowOpF &op, int slices, bool neg, int epi, int vt, cudaStream_t st);
+int launch_rowsf_nv32(const RowOpF &op, int slices, bool neg, int epi, int vt, cudaStream_t st);
 
 // Elementwise grid size for n rows of nv columns.
 int elem_grid(int64_t n, int nv);
@@ -99,6 +108,22 @@ void launch_scalar(int nv, int mode, ColState *cs, const double *p0, const doubl
                    double tol, int k, Flags *flags, cudaStream_t st);
 void launch_coarse(int nv, int nc, const double *lu, const int32_t *piv, const double *B, double *X,
                    cudaStream_t st);
+// Outer FP64 loop around an FP32-block preconditioner.
+void launch_init_fpcg(int nv, int64_t n, const double *B, int m, double *Bn, double *R, double *X,
+                      float *R32, float *Z32, const float *w0, double *part, int grid,
+                      cudaStream_t st);
+void launch_fpcg_xr(int nv, int64_t n, double *X, double *R, const double *P, const double *Q,
+                    const ColState *cs, const float *w0, float *R32, float *Z32, double *part,
+                    int grid, cudaStream_t st);
+void launch_fpcg_p(int nv, int64_t n, double *P, const float *Z32, const ColState *cs, int grid,
+                   cudaStream_t st);
+void launch_to_f32(int nv, int64_t n, const double *X, float *Y32, const float *w0, float *Z32,
+                   int grid, cudaStream_t st);
+void launch_to_f64(int nv, int64_t n, const float *X32, double *Y, int grid, cudaStream_t st);
+void launch_axpy_dot_f(int nv, int64_t n, float *X, const float *D, const double *U,
+                       const double *U2, double *part, double *part2, int grid, cudaStream_t st);
+void launch_coarse_f(int nv, int nc, const double *lu, const int32_t *piv, const float *B, float *X,
+                     double *W, cudaStream_t st);
 // Runtime-m column dots for the public entry point: partials then reduce.
 int coldot_rt_grid(int64_t n, int m);
 void launch_coldot_rt(int64_t n, int m, const double *U, const double *V, double *part, int grid,

@@ -1,5 +1,7 @@
 // rows_inst.cuh -- instantiations and launcher of the fused row kernel for one
-// NV (XAMG_NV), included by rows_nv*.cu so that the NVs compile in parallel.
+// block width NV (XAMG_NV) and one block scalar (XAMG_FLOAT: float blocks with
+// float or bf16 values; otherwise double blocks and values).  Included by the
+// rows_nv*.cu / rowsf_nv*.cu units so that the variants compile in parallel.
 #include <algorithm>
 
 #include "launch.h"
@@ -11,13 +13,19 @@
 namespace xamg {
 namespace {
 
-template <int NV, int S, bool NEG, int EPI>
-int rows_t(const RowOp &op, cudaStream_t st) {
+#if XAMG_FLOAT
+using TBx = float;
+#else
+using TBx = double;
+#endif
+
+template <class TV, int NV, int S, bool NEG, int EPI>
+int rows_t(const RowOpT<TBx> &op, cudaStream_t st) {
   static int max_grid = 0;
   if (!max_grid) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rows<NV, S, NEG, EPI>, kBlock, 0) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rows<TBx, TV, NV, S, NEG, EPI>, kBlock,
+                                                      0) != cudaSuccess ||
         b < 1)
       b = 1;
     max_grid = std::min(kMaxGrid, b * device_sm_count());
@@ -25,34 +33,52 @@ int rows_t(const RowOp &op, cudaStream_t st) {
   constexpr int rows_per_block = kWarps * (32 / (NV * S));
   const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
-  k_rows<NV, S, NEG, EPI><<<grid, kBlock, 0, st>>>(op);
+  k_rows<TBx, TV, NV, S, NEG, EPI><<<grid, kBlock, 0, st>>>(op);
   g_launches++;
   return cudaPeekAtLastError() == cudaSuccess ? grid : -1;
 }
 
 // The (sign, epilogue) pairs the solver uses.
-template <int NV, int S>
-int rows_e(const RowOp &op, bool neg, int epi, cudaStream_t st) {
+template <class TV, int NV, int S>
+int rows_e(const RowOpT<TBx> &op, bool neg, int epi, cudaStream_t st) {
   if (neg) {
     switch (epi) {
-      case EPI_Y: return rows_t<NV, S, true, EPI_Y>(op, st);
-      case EPI_Y_D0: return rows_t<NV, S, true, EPI_Y_D0>(op, st);
-      case EPI_Y_DN: return rows_t<NV, S, true, EPI_Y_DN>(op, st);
-      case EPI_Y_XDP: return rows_t<NV, S, true, EPI_Y_XDP>(op, st);
-      case EPI_MID: return rows_t<NV, S, true, EPI_MID>(op, st);
-      case EPI_XLAST: return rows_t<NV, S, true, EPI_XLAST>(op, st);
-      case EPI_XLAST_DOT: return rows_t<NV, S, true, EPI_XLAST_DOT>(op, st);
-      case EPI_Y_DOT2: return rows_t<NV, S, true, EPI_Y_DOT2>(op, st);
+      case EPI_Y: return rows_t<TV, NV, S, true, EPI_Y>(op, st);
+      case EPI_Y_D0: return rows_t<TV, NV, S, true, EPI_Y_D0>(op, st);
+      case EPI_Y_DN: return rows_t<TV, NV, S, true, EPI_Y_DN>(op, st);
+      case EPI_Y_XDP: return rows_t<TV, NV, S, true, EPI_Y_XDP>(op, st);
+      case EPI_MID: return rows_t<TV, NV, S, true, EPI_MID>(op, st);
+      case EPI_XLAST: return rows_t<TV, NV, S, true, EPI_XLAST>(op, st);
+      case EPI_XLAST_DOT: return rows_t<TV, NV, S, true, EPI_XLAST_DOT>(op, st);
+#if XAMG_FLOAT
+      case EPI_XLAST_DOT2: return rows_t<TV, NV, S, true, EPI_XLAST_DOT2>(op, st);
+#else
+      case EPI_Y_DOT2: return rows_t<TV, NV, S, true, EPI_Y_DOT2>(op, st);
+#endif
       default: return -1;
     }
   }
   switch (epi) {
-    case EPI_Y: return rows_t<NV, S, false, EPI_Y>(op, st);
-    case EPI_Y_D0: return rows_t<NV, S, false, EPI_Y_D0>(op, st);
-    case EPI_Y_DOT: return rows_t<NV, S, false, EPI_Y_DOT>(op, st);
-    case EPI_Y_DOT2: return rows_t<NV, S, false, EPI_Y_DOT2>(op, st);
+    case EPI_Y: return rows_t<TV, NV, S, false, EPI_Y>(op, st);
+    case EPI_Y_D0: return rows_t<TV, NV, S, false, EPI_Y_D0>(op, st);
+#if !XAMG_FLOAT
+    case EPI_Y_DOT: return rows_t<TV, NV, S, false, EPI_Y_DOT>(op, st);
+    case EPI_Y_DOT2: return rows_t<TV, NV, S, false, EPI_Y_DOT2>(op, st);
+#endif
     default: return -1;
   }
+}
+
+// m = 1 splits rows over 4 or 16 lanes; wider blocks use one lane per column.
+template <class TV>
+int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t st) {
+#if XAMG_NV == 1
+  if (slices >= 16) return rows_e<TV, 1, 16>(op, neg, epi, st);
+  return rows_e<TV, 1, 4>(op, neg, epi, st);
+#else
+  (void)slices;
+  return rows_e<TV, XAMG_NV, 1>(op, neg, epi, st);
+#endif
 }
 
 }  // namespace
@@ -60,16 +86,18 @@ int rows_e(const RowOp &op, bool neg, int epi, cudaStream_t st) {
 #define XAMG_CAT2(a, b) a##b
 #define XAMG_CAT(a, b) XAMG_CAT2(a, b)
 
-// m = 1 splits rows over 4 or 16 lanes; wider blocks use one lane per column.
+#if XAMG_FLOAT
+// vt: 0 = float values, 1 = bf16 values with per-row scale
+int XAMG_CAT(launch_rowsf_nv, XAMG_NV)(const RowOpF &op, int slices, bool neg, int epi, int vt,
+                                        cudaStream_t st) {
+  return vt == 1 ? rows_any<__nv_bfloat16>(op, slices, neg, epi, st)
+                 : rows_any<float>(op, slices, neg, epi, st);
+}
+#else
 int XAMG_CAT(launch_rows_nv, XAMG_NV)(const RowOp &op, int slices, bool neg, int epi,
                                        cudaStream_t st) {
-#if XAMG_NV == 1
-  if (slices >= 16) return rows_e<1, 16>(op, neg, epi, st);
-  return rows_e<1, 4>(op, neg, epi, st);
-#else
-  (void)slices;
-  return rows_e<XAMG_NV, 1>(op, neg, epi, st);
-#endif
+  return rows_any<double>(op, slices, neg, epi, st);
 }
+#endif
 
 }  // namespace xamg

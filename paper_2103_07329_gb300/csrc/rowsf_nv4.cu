@@ -1,0 +1,4 @@
+// Fused row kernels, FP32 blocks (float or bf16 values), 4 column(s).
+#define XAMG_NV 4
+#define XAMG_FLOAT 1
+#include "rows_inst.cuh"

@@ -1,0 +1,96 @@
+"""GPU parity of the reduced-precision preconditioner (paper Sec. 2.3,
+"mixed-precision") against the oracle's FP32 / bf16 V-cycle, and of the
+FP64 outer solves around it against the FP64 oracle solution.
+
+Tolerances: both sides compute the FP32 V-cycle from identical FP32 / bf16
+data; they differ in FP32 rounding (fused multiply-adds, the order of the
+Chebyshev coefficient products), so per-column ||g - o|| / ||o|| <= 2e-5.
+Solves: true residual <= 1e-8 per column (checked in FP64 by the oracle),
+iteration counts within +-1 of the oracle's reduced-precision solve."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_07329_gb300 import binding as B
+from paper_2103_07329_gb300 import build as build_mod
+from paper_2103_07329_gb300 import problems as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build_mod.build()
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def colrel(g, o):
+    return np.linalg.norm(g - o, axis=0) / np.linalg.norm(o, axis=0)
+
+
+_cache = {}
+
+
+def pair(key):
+    if key not in _cache:
+        if key == "p7_32":
+            A = P.poisson7(32)
+        elif key == "var_24":
+            A = P.diffusion7(24, P.lognormal_cells(24, 1.0, 1))
+        else:
+            A = P.poisson27(16)
+        _cache[key] = (A, B.Hierarchy(A), oracle.Hierarchy(A))
+    return _cache[key]
+
+
+@pytest.mark.parametrize("key", ["p7_32", "var_24", "p27_16"])
+@pytest.mark.parametrize("prec", [B.PREC_FP32, B.PREC_BF16])
+@pytest.mark.parametrize("m", [1, 4, 32])
+def test_reduced_vcycle_parity(key, prec, m):
+    A, g, o = pair(key)
+    Bm = P.rhs_uniform(A.n, m, 0, m_draw=32)
+    X = torch.empty((A.n, m), dtype=torch.float64, device="cuda")
+    g.vcycle_precond(prec, dev(Bm), X)
+    ref = o.vcycle_prec(prec, Bm)
+    assert colrel(X.cpu().numpy(), ref).max() <= 2e-5
+
+
+@pytest.mark.parametrize("key", ["p7_32", "var_24"])
+@pytest.mark.parametrize("prec", [B.PREC_FP32, B.PREC_BF16])
+@pytest.mark.parametrize("method", [B.PCG, B.BICGSTAB])
+def test_reduced_precision_solve(key, prec, method):
+    A, g, o = pair(key)
+    Bm = P.rhs_uniform(A.n, 8, 0, m_draw=32)
+    X = torch.empty_like(dev(Bm))
+    st = g.solve(dev(Bm), X, tol=1e-8, maxit=100, method=method, precond=prec)
+    Xg = X.cpu().numpy()
+    rr = np.linalg.norm(Bm - oracle.spmm(A, Xg), axis=0) / np.linalg.norm(Bm, axis=0)
+    assert st.rc == 0 and np.all(st.status == 0)
+    assert np.all(rr <= 1e-8), rr
+    ref = (o.pcg if method == B.PCG else o.bicgstab)(Bm, tol=1e-8, prec=prec)
+    assert np.all(np.abs(st.iters - ref.iters) <= 1), (st.iters, ref.iters)
+    # error against the FP64 oracle solution
+    x64 = (o.pcg if method == B.PCG else o.bicgstab)(Bm, tol=1e-8).X
+    assert colrel(Xg, x64).max() <= 1e-6
+
+
+def test_reduced_precision_edge_cases():
+    A, g, o = pair("p7_32")
+    Bm = P.rhs_uniform(A.n, 3, 4, m_draw=32)
+    Bm[:, 1] = 0.0
+    X = torch.full((A.n, 3), 5.0, dtype=torch.float64, device="cuda")
+    st = g.solve(dev(Bm), X, precond=B.PREC_FP32)
+    assert st.iters[1] == 0 and torch.all(X[:, 1] == 0)
+    Bm[0, 0] = np.inf
+    X = torch.full((A.n, 3), 5.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.XamgError) as e:
+        g.solve(dev(Bm), X, precond=B.PREC_BF16)
+    assert e.value.code == B.ERR_NONFINITE and torch.all(X == 5.0)
+    with pytest.raises(B.XamgError):
+        g.solve(dev(Bm), X, precond=7)
