@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--cpu-cols", type=int, default=1, help="columns in the oracle's sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision forms")
     a = ap.parse_args()
     if a.grid is None:
         a.grid = 192 if a.matrix == "poisson7" else 160
@@ -308,6 +309,43 @@ def run_ours(a):
                         "frac": round(achieved_gbs / hbm, 4), "peak_kind": hbm_kind},
                 "share_of_step": round(tot["ms"] / ms, 4)}
 
+    # the same workload with the reduced-precision preconditioner (FP32 blocks;
+    # FP32 or bf16 values of A) inside the FP64 outer loop, same tolerance
+    forms = None
+    if not a.no_forms:
+        forms = {}
+        for name, prec in (("mixed_fp32", B.PREC_FP32), ("mixed_bf16", B.PREC_BF16)):
+            h.solve(Bd, X, a.tol, a.maxit, method, precond=prec)
+            h.timing_enable(True)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s3 = 0
+            for _ in range(a.steps):
+                st = h.solve(Bd, X, a.tol, a.maxit, method, precond=prec)
+                s3 += int(np.sum((st.status == 0) & (st.relres <= a.tol)))
+            e1.record(stream)
+            barrier()
+            fv, ft, _ = MR.job_throughput(e0.elapsed_time(e1) / 1e3, s3, dist, "cuda")
+            f32 = dict(launches=0, ms=0.0, flops=0.0, bytes=0.0)
+            for l in range(h.levels):
+                for which in (3, 4, 5):
+                    if which > 3 and l + 1 == h.levels:
+                        continue
+                    r = h.timing_read(l, which)
+                    for k in f32:
+                        f32[k] += r[k]
+            h.timing_enable(False)
+            gbs = f32["bytes"] / f32["ms"] / 1e6 if f32["ms"] > 0 else 0.0
+            forms[name] = {"value": fv, "speedup_vs_fp64": fv / value, "ms_per_step": 1e3 * ft / a.steps,
+                           "iters": st.iters.tolist()[:4], "max_relres": float(st.relres.max()),
+                           "precond_row_kernel": {"bound": "hbm", "achieved_gbs": round(gbs, 1),
+                                                  "peak_gbs": measured_hbm()[0],
+                                                  "frac": round(gbs / measured_hbm()[0], 4),
+                                                  "launches": f32["launches"],
+                                                  "share_of_step": round(f32["ms"] / (1e3 * ft), 4)}}
+
     # end to end through the host-buffer entry point: H2D of B and D2H of X inside
     e2e = None
     if not a.no_e2e:
@@ -351,7 +389,8 @@ def run_ours(a):
                 "iters": stats[-1].iters.tolist(), "vcycles_per_step": stats[-1].vcycles,
                 "max_relres": float(stats[-1].relres.max()),
                 "roofline": roofline, "roofline_levels": per_level,
-                "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": int(launches)}
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": int(launches),
+                "forms": forms}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
