@@ -386,10 +386,14 @@ void flush_timing(xamg_hier *h) {
 }
 
 // ---- row kernel wrapper ----
-int slices_for(const DevCsr &M, int nv) {
-  if (nv != 1 || M.n == 0) return 1;
+// m = 1: 4 or 16 lanes per row.  FP32 blocks of >= 16 columns with long rows
+// (the dense coarse Galerkin levels): one row per warp, split into slices.
+int slices_for(const DevCsr &M, int nv, bool fp32) {
+  if (M.n == 0) return 1;
   const double avg = (double)M.nnz / M.n;
-  return avg >= 24.0 ? 16 : 4;
+  if (nv == 1) return avg >= 24.0 ? 16 : 4;
+  if (fp32 && nv >= 16 && avg >= 64.0) return 32 / (nv / 4);
+  return 1;
 }
 
 // Algorithmic bytes of one fused row launch: the matrix once, the operand
@@ -445,9 +449,9 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
   }
   int g;
   if constexpr (sizeof(TB) == 8)
-    g = launch_rows(op, nv, slices_for(M, nv), neg, epi, st);
+    g = launch_rows(op, nv, slices_for(M, nv, false), neg, epi, st);
   else
-    g = launch_rows_f(op, nv, slices_for(M, nv), neg, epi, vt, st);
+    g = launch_rows_f(op, nv, slices_for(M, nv, true), neg, epi, vt, st);
   if (h->timing) {
     cudaEventRecord(b, st);
     const int slot = which + (sizeof(TB) == 8 ? 0 : 3);

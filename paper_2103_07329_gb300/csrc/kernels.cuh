@@ -81,6 +81,39 @@ __device__ __forceinline__ void block_colsum_store(double v, double *out) {
   }
 }
 
+// Block-level per-column reduction when lane g of each group of G = NV/VEC
+// lanes holds the partial sums of columns g*VEC .. g*VEC+VEC-1: a fixed
+// xor tree over the groups of a warp, then thread c < NV adds the warps in
+// order and writes out[blockIdx.x*NV + c].
+template <int NV, int VEC>
+__device__ __forceinline__ void block_colsum_store_vec(const double (&v)[VEC], double *out) {
+  if constexpr (VEC == 1) {
+    block_colsum_store<NV>(v[0], out);
+  } else {
+    constexpr int G = NV / VEC;
+    __shared__ double red[kWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double s[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      s[k] = v[k];
+#pragma unroll
+      for (int o = G; o < 32; o <<= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    }
+    if (lane < G) {
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) red[warp][lane * VEC + k] = s[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) t += red[w][threadIdx.x];
+      out[(size_t)blockIdx.x * NV + threadIdx.x] = t;
+    }
+  }
+}
+
 // Epilogue of a row kernel, fixed at compile time so that no floating-point
 // operation of an unused branch is executed (v is the row's product sum):
 enum Epi : int {
@@ -197,77 +230,244 @@ __device__ __forceinline__ TB tail_fma(int rem, const TB (&as)[8], const TB (&xs
   return acc;
 }
 
-// Row kernel, one lane per column (S = 1).  A group of NV lanes owns one row
-// (32/NV rows per warp).  The group reads the row's column indices and values
-// NV at a time with one coalesced load each and passes them around with
-// shuffles, so all operand-row gathers of a chunk of eight entries are issued
-// before their FMAs: the dependent chain per row is row pointer -> index/value
-// -> operand rows, independent of the row length.  Each lane adds its
-// column's products in the row's storage order (no reduction adds), and a
-// chunk's tail takes exactly as many FMAs as it has entries.  With scaled
-// (bf16) values the products are summed first and the row scale applied once:
-// v = init +/- s_i * sum_k q_ik x_k.
-template <class TB, class TV, int NV, bool NEG, int EPI>
-__device__ __forceinline__ void rows_lane_per_column(const RowOpT<TB> &op) {
+// Small vectors of VEC consecutive block columns held by one lane, loaded and
+// stored with one 8/16-byte access (VEC = 1, 2, 4).
+template <class T, int VEC>
+struct Vec {
+  T v[VEC];
+};
+template <class T, int VEC>
+__device__ __forceinline__ Vec<T, VEC> vload(const T *p) {
+  Vec<T, VEC> r;
+  if constexpr (VEC == 1) {
+    r.v[0] = *p;
+  } else if constexpr (sizeof(T) * VEC == 16) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 q = *reinterpret_cast<const float4 *>(p);
+      r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
+    } else {
+      const double2 q = *reinterpret_cast<const double2 *>(p);
+      r.v[0] = q.x; r.v[1] = q.y;
+    }
+  } else {
+    static_assert(sizeof(T) * VEC == 8, "8- or 16-byte vectors");
+    const float2 q = *reinterpret_cast<const float2 *>(p);
+    r.v[0] = q.x; r.v[1] = q.y;
+  }
+  return r;
+}
+template <class T, int VEC>
+__device__ __forceinline__ Vec<T, VEC> vldg(const T *p) {
+  Vec<T, VEC> r;
+  if constexpr (VEC == 1) {
+    r.v[0] = __ldg(p);
+  } else if constexpr (sizeof(T) * VEC == 16) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+      r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
+    } else {
+      const double2 q = __ldg(reinterpret_cast<const double2 *>(p));
+      r.v[0] = q.x; r.v[1] = q.y;
+    }
+  } else {
+    const float2 q = __ldg(reinterpret_cast<const float2 *>(p));
+    r.v[0] = q.x; r.v[1] = q.y;
+  }
+  return r;
+}
+template <class T, int VEC>
+__device__ __forceinline__ void vstore(T *p, const Vec<T, VEC> &r) {
+  if constexpr (VEC == 1) {
+    *p = r.v[0];
+  } else if constexpr (sizeof(T) * VEC == 16) {
+    if constexpr (sizeof(T) == 4)
+      *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+    else
+      *reinterpret_cast<double2 *>(p) = make_double2(r.v[0], r.v[1]);
+  } else {
+    *reinterpret_cast<float2 *>(p) = make_float2(r.v[0], r.v[1]);
+  }
+}
+
+// Row kernel, S = 1.  A group of G = NV/VEC lanes owns one row (32/G rows per
+// warp); lane g of the group holds the VEC adjacent columns g*VEC .. g*VEC+VEC-1
+// and moves them with one 8/16-byte access, so a warp keeps 32/G rows' gathers
+// in flight at once.  The group reads the row's column indices and values G
+// at a time with one coalesced load each and passes them around with
+// shuffles; all operand-row gathers of a chunk of eight entries are issued
+// before their FMAs, so the dependent chain per row is row pointer ->
+// index/value -> operand rows.  Each column's products are added in the row's
+// storage order (no reduction adds), and a chunk's tail takes exactly as many
+// FMAs as it has entries.  With scaled (bf16) values the products are summed
+// first and the row scale applied once: v = init +/- s_i * sum_k q_ik x_k.
+template <class TB, class TV, int NV, int VEC, int SL, bool NEG, int EPI>
+__device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
   using VL = ValueLoad<TV>;
-  constexpr int RPW = 32 / NV;
+  using V = Vec<TB, VEC>;
+  constexpr int G = NV / VEC;
+  constexpr int RPW = 32 / (G * SL);
+  // entries gathered per chunk: 8 for FP64 (exact-count tails keep the FP64
+  // FMA count at the algorithmic one); 4 for FP32, whose 16-byte gathers
+  // already fill the registers
+  constexpr int CH = sizeof(TB) == 4 ? 4 : 8;
+  constexpr int K = 32 / G < 4 ? 32 / G : 4;  // entries each lane fetches per round
+  constexpr bool xlast = EPI == EPI_XLAST || EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2;
   const int lane = threadIdx.x & 31;
-  const int c = lane % NV;
-  const int grp = lane / NV;
-  const int gbase = grp * NV;
+  const int gl = lane % G;
+  const int c0 = gl * VEC;
+  const int sl = (lane / G) % SL;   // slice of the row
+  const int grp = lane / (G * SL);  // row of the warp
+  const int gbase = (lane / G) * G;
   const int64_t warp0 = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t wstride = (int64_t)gridDim.x * kWarps;
   const int32_t *__restrict__ col = op.col;
   const TB *__restrict__ src = op.src;
-  double dsum = 0.0, dsum2 = 0.0;
+  double dsum[VEC], dsum2[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) dsum[v] = dsum2[v] = 0.0;
   for (int64_t base = warp0 * RPW; base < op.n; base += wstride * RPW) {
     const int64_t i = base + grp;
     const bool valid = i < op.n;
+    const int64_t e = i * NV + c0;
     int start = 0, len = 0;
-    TB acc = 0, dpv = 0, wv = 0, xv = 0;
-    double du = 0.0, du2 = 0.0;
+    V acc, dpv, xv;
+    TB wv = 0;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc.v[v] = dpv.v[v] = xv.v[v] = 0;
     if (valid) {
       start = __ldg(op.rowptr + i);
       len = __ldg(op.rowptr + i + 1) - start;
-      if (!VL::scaled && op.init) acc = op.init[i * NV + c];
-      row_operands<TB, NV, EPI>(op, i, c, dpv, wv, xv, du, du2);
+      if (!VL::scaled && op.init && sl == 0) acc = vload<TB, VEC>(op.init + e);
+      if constexpr (EPI == EPI_Y_DN || EPI == EPI_Y_XDP || EPI == EPI_MID || xlast)
+        dpv = vload<TB, VEC>(op.dp + e);
+      if constexpr (EPI == EPI_Y_D0 || EPI == EPI_Y_DN || EPI == EPI_MID || xlast) wv = op.w[i];
+      if constexpr (EPI == EPI_Y_XDP || EPI == EPI_MID || xlast) xv = vload<TB, VEC>(op.x + e);
     }
-    const int maxlen = RPW == 1 ? len : __reduce_max_sync(0xffffffffu, len);
-    for (int kb = 0; kb < maxlen; kb += NV) {
-      const bool own = kb + c < len;
-      const int cl = own ? __ldg(col + start + kb + c) : 0;
-      const TB av = own ? (TB)VL::get(op.val, start + kb + c) : (TB)0;
-      const int cnt = min(NV, maxlen - kb);
-      for (int t = 0; t < cnt; t += 8) {
-        TB xs[8], as[8];
+    const int maxlen = (RPW == 1 && SL == 1) ? len : __reduce_max_sync(0xffffffffu, len);
+    // slice sl takes rounds sl, sl + SL, ...; every slice runs the same number
+    // of rounds (entries past the row's end are zeros), so the shuffles stay
+    // warp-uniform
+    for (int kb0 = 0; kb0 < maxlen; kb0 += G * K * SL) {
+      const int kb = kb0 + sl * G * K;
+      // the group fetches G*K entries per round: slot q of lane g holds entry
+      // kb + q*G + g (coalesced across the group for every q)
+      int cl[K];
+      TB av[K];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int from = (gbase + t + u) & 31;
-          const int cc = __shfl_sync(0xffffffffu, cl, from);
-          as[u] = __shfl_sync(0xffffffffu, av, from);
-          xs[u] = (t + u < cnt && kb + t + u < len) ? __ldg(src + (int64_t)cc * NV + c) : (TB)0;
-        }
-        // entries past this row's own end carry a = x = 0 (rows of one warp
-        // may differ in length when NV < 32)
-        const int rem = min(8, cnt - t);
-        if (rem == 8) {
+      for (int q = 0; q < K; ++q) {
+        const bool own = kb + q * G + gl < len;
+        cl[q] = own ? __ldg(col + start + kb + q * G + gl) : 0;
+        av[q] = own ? (TB)VL::get(op.val, start + kb + q * G + gl) : (TB)0;
+      }
+      const int cnt = min(G * K, maxlen - kb0);  // uniform over the warp
 #pragma unroll
-          for (int u = 0; u < 8; ++u) acc = fmadd<NEG>(as[u], xs[u], acc);
-        } else {
-          acc = tail_fma<NEG>(rem, as, xs, acc);
+      for (int q = 0; q < K; ++q) {
+        if (q * G >= cnt) break;
+        const int cq = min(G, cnt - q * G);
+        const int kq = kb + q * G;
+        for (int t = 0; t < cq; t += CH) {
+          V xs[CH];
+          TB as[CH];
+#pragma unroll
+          for (int u = 0; u < CH; ++u) {
+            const int from = (gbase + t + u) & 31;
+            const int cc = __shfl_sync(0xffffffffu, cl[q], from);
+            as[u] = __shfl_sync(0xffffffffu, av[q], from);
+            if (t + u < cq && kq + t + u < len) {
+              xs[u] = vldg<TB, VEC>(src + (int64_t)cc * NV + c0);
+            } else {
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) xs[u].v[v] = 0;
+            }
+          }
+          // entries past this row's own end carry a = x = 0 (rows of one warp
+          // may differ in length)
+          const int rem = min(CH, cq - t);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            TB xv8[CH];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) xv8[u] = xs[u].v[v];
+            if (rem == CH) {
+#pragma unroll
+              for (int u = 0; u < CH; ++u) acc.v[v] = fmadd<NEG>(as[u], xv8[u], acc.v[v]);
+            } else if constexpr (CH == 8) {
+              acc.v[v] = tail_fma<NEG>(rem, as, xv8, acc.v[v]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < CH - 1; ++u)
+                if (u < rem) acc.v[v] = fmadd<NEG>(as[u], xv8[u], acc.v[v]);
+            }
+          }
         }
       }
     }
-    if constexpr (VL::scaled) {
-      if (valid) acc = fma((TB)op.rscale[i], acc, op.init ? op.init[i * NV + c] : (TB)0);
+    if constexpr (SL > 1) {
+      // add the slices (fixed xor order); the sum is valid in every slice
+#pragma unroll
+      for (int v = 0; v < VEC; ++v)
+#pragma unroll
+        for (int o = G; o < G * SL; o <<= 1) acc.v[v] += __shfl_xor_sync(0xffffffffu, acc.v[v], o);
     }
-    if (valid) row_epilogue<TB, NV, EPI>(op, i, c, acc, dpv, wv, xv, du, du2, dsum, dsum2);
+    if (valid && sl == 0) {
+      if constexpr (VL::scaled) {
+        V in;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) in.v[v] = 0;
+        if (op.init) in = vload<TB, VEC>(op.init + e);
+        const TB s = (TB)op.rscale[i];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc.v[v] = fma(s, acc.v[v], in.v[v]);
+      }
+      // epilogue (see enum Epi)
+      if constexpr (!xlast) {
+        if (op.y) vstore<TB, VEC>(op.y + e, acc);
+      }
+      if constexpr (EPI == EPI_Y_D0 || EPI == EPI_Y_DN || EPI == EPI_MID) {
+        V dn;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v)
+          dn.v[v] = EPI == EPI_Y_D0 ? wv * acc.v[v] : fma(op.c1, dpv.v[v], wv * acc.v[v]);
+        vstore<TB, VEC>(op.dnext + e, dn);
+      }
+      if constexpr (EPI == EPI_Y_XDP || EPI == EPI_MID) {
+        V xn;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) xn.v[v] = xv.v[v] + dpv.v[v];
+        vstore<TB, VEC>(op.x + e, xn);
+      }
+      if constexpr (xlast) {
+        V xn;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) xn.v[v] = (xv.v[v] + dpv.v[v]) + fma(op.c1, dpv.v[v], wv * acc.v[v]);
+        vstore<TB, VEC>(op.x + e, xn);
+        if constexpr (EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) dsum[v] = fma(op.dot_u[e + v], (double)xn.v[v], dsum[v]);
+        }
+        if constexpr (EPI == EPI_XLAST_DOT2) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) dsum2[v] = fma(op.dot_u2[e + v], (double)xn.v[v], dsum2[v]);
+        }
+      }
+      if constexpr (EPI == EPI_Y_DOT) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) dsum[v] = fma(op.dot_u[e + v], (double)acc.v[v], dsum[v]);
+      }
+      if constexpr (EPI == EPI_Y_DOT2) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          if (op.dot_u) dsum[v] = fma(op.dot_u[e + v], (double)acc.v[v], dsum[v]);
+          dsum2[v] = fma((double)acc.v[v], (double)acc.v[v], dsum2[v]);
+        }
+      }
+    }
   }
   if constexpr (epi_has_dot<EPI>()) {
-    if (EPI != EPI_Y_DOT2 || op.dot_u) block_colsum_store<NV>(dsum, op.partials);
+    if (EPI != EPI_Y_DOT2 || op.dot_u) block_colsum_store_vec<NV, VEC>(dsum, op.partials);
     if constexpr (EPI == EPI_Y_DOT2 || EPI == EPI_XLAST_DOT2) {
       __syncthreads();
-      block_colsum_store<NV>(dsum2, op.partials2);
+      block_colsum_store_vec<NV, VEC>(dsum2, op.partials2);
     }
   }
 }
@@ -333,6 +533,15 @@ __device__ __forceinline__ void rows_sliced(const RowOpT<TB> &op) {
   }
 }
 
+// Columns per lane: FP32 blocks move 4 columns (16 bytes) per lane, which
+// keeps 4x more rows' gathers in flight than one column per lane; FP64 blocks
+// keep one column per lane (their bound is the FP64 FMA rate, not latency).
+template <class TB, int NV>
+__host__ __device__ constexpr int row_vec() {
+  if constexpr (sizeof(TB) == 4) return NV >= 4 ? 4 : NV;
+  return 1;
+}
+
 // The fused row kernel.  Warps walk the rows in a grid-stride loop, so the
 // row -> block map (and with it the order of the partial dot sums) depends
 // only on n and the grid size.  At most 64 registers per thread (four
@@ -341,7 +550,9 @@ __device__ __forceinline__ void rows_sliced(const RowOpT<TB> &op) {
 template <class TB, class TV, int NV, int S, bool NEG, int EPI>
 __global__ void __launch_bounds__(kBlock, 4) k_rows(RowOpT<TB> op) {
   if constexpr (S == 1) {
-    rows_lane_per_column<TB, TV, NV, NEG, EPI>(op);
+    rows_vec<TB, TV, NV, row_vec<TB, NV>(), 1, NEG, EPI>(op);
+  } else if constexpr (NV > 1) {
+    rows_vec<TB, TV, NV, row_vec<TB, NV>(), S, NEG, EPI>(op);
   } else {
     rows_sliced<TB, TV, NV, S, NEG, EPI>(op);
   }

@@ -30,7 +30,8 @@ int rows_t(const RowOpT<TBx> &op, cudaStream_t st) {
       b = 1;
     max_grid = std::min(kMaxGrid, b * device_sm_count());
   }
-  constexpr int rows_per_block = kWarps * (32 / (NV * S));
+  constexpr int lanes_per_row = NV == 1 ? S : (NV / row_vec<TBx, NV>()) * S;
+  constexpr int rows_per_block = kWarps * (32 / lanes_per_row);
   const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
   k_rows<TBx, TV, NV, S, NEG, EPI><<<grid, kBlock, 0, st>>>(op);
@@ -69,13 +70,19 @@ int rows_e(const RowOpT<TBx> &op, bool neg, int epi, cudaStream_t st) {
   }
 }
 
-// m = 1 splits rows over 4 or 16 lanes; wider blocks use one lane per column.
+// m = 1 splits rows over 4 or 16 lanes; wider blocks give each lane VEC
+// columns, and FP32 blocks of 16 or 32 columns may split long rows over the
+// whole warp (slices).
 template <class TV>
 int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t st) {
 #if XAMG_NV == 1
   if (slices >= 16) return rows_e<TV, 1, 16>(op, neg, epi, st);
   return rows_e<TV, 1, 4>(op, neg, epi, st);
 #else
+#if XAMG_FLOAT && XAMG_NV >= 16
+  // long rows of FP32 blocks: every group of the warp takes a slice of one row
+  if (slices > 1) return rows_e<TV, XAMG_NV, 32 / (XAMG_NV / 4)>(op, neg, epi, st);
+#endif
   (void)slices;
   return rows_e<TV, XAMG_NV, 1>(op, neg, epi, st);
 #endif
