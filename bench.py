@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision forms")
+    ap.add_argument("--sweep", action="store_true",
+                    help="measurement mode: m in 1..32, PCG and BiCGStab, FP64/FP32/bf16 "
+                         "preconditioner, one JSON line each (not the benchmark line)")
     a = ap.parse_args()
     if a.grid is None:
         a.grid = 192 if a.matrix == "poisson7" else 160
@@ -398,10 +401,66 @@ def run_ours(a):
     return 0
 
 
+def run_sweep(a):
+    """One JSON line per (m, method, preconditioner precision) on the chosen
+    matrix: RHS/s over `steps` solves after one warm-up, iterations, and the
+    row kernel's achieved FP64 TFLOP/s or FP32 GB/s per level."""
+    import torch
+
+    from paper_2103_07329_gb300 import binding as B
+    from paper_2103_07329_gb300 import build as build_mod
+    from paper_2103_07329_gb300 import problems as P
+
+    build_mod.build()
+    A = make_matrix(a)
+    t0 = time.perf_counter()
+    h = B.Hierarchy(A)
+    setup = time.perf_counter() - t0
+    hbm = measured_hbm()[0]
+    for m in (1, 2, 4, 8, 16, 32):
+        Bm = P.rhs_uniform(A.n, m, 0, m_draw=32)
+        Bd = torch.from_numpy(Bm).cuda()
+        X = torch.empty_like(Bd)
+        for method_name, method in (("pcg", B.PCG), ("bicgstab", B.BICGSTAB)):
+            for form, prec in (("fp64", B.PREC_FP64), ("mixed_fp32", B.PREC_FP32),
+                               ("mixed_bf16", B.PREC_BF16)):
+                h.solve(Bd, X, a.tol, a.maxit, method, precond=prec)
+                h.timing_enable(True)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                solved = 0
+                for _ in range(a.steps):
+                    st = h.solve(Bd, X, a.tol, a.maxit, method, precond=prec)
+                    solved += int(np.sum((st.status == 0) & (st.relres <= a.tol)))
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / a.steps
+                base = 0 if prec == B.PREC_FP64 else 3
+                levels = []
+                for l in range(h.levels - 1):
+                    r = h.timing_read(l, base)
+                    if r["launches"]:
+                        levels.append({"level": l, "ms_per_launch": round(r["ms"] / r["launches"], 4),
+                                       "tflops": round(r["flops"] / r["ms"] / 1e9, 3),
+                                       "gbs": round(r["bytes"] / r["ms"] / 1e6, 1)})
+                h.timing_enable(False)
+                print(json.dumps({"matrix": a.matrix, "grid": a.grid, "n": A.n, "m": m,
+                                  "method": method_name, "form": form,
+                                  "rhs_per_s": round(solved / (ms * a.steps / 1e3), 2),
+                                  "ms_per_solve": round(ms, 3), "iters": int(st.iters.max()),
+                                  "max_relres": float(st.relres.max()), "setup_s": round(setup, 1),
+                                  "hbm_peak_gbs": hbm, "levels": levels}), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.sweep:
+        return run_sweep(a)
     return run_ours(a)
 
 

@@ -649,6 +649,9 @@ struct SolveCtx {
   int prec = XAMG_PREC_FP64;
   cudaStream_t st;
   int iterations = 0, vcycles = 0;
+  // set when the loop ended on a confirmation that restarted no column: the
+  // true residual norms in the column state are those of the final X
+  bool confirmed = false;
 };
 
 // z = M r for the FP64 Krylov loops.  FP64 preconditioner: on entry z holds
@@ -674,9 +677,11 @@ int finish(SolveCtx &c, double *Xuser, xamg_stats *stats) {
   Work &W = c.W;
   const int64_t n = h->lv[0].A.n;
   double *T = W.Q ? W.Q : W.T;
-  const int g = true_residual(h, W, T, W.part[4], c.st);
-  if (g < 0) return XAMG_ERR_CUDA;
-  launch_scalar(c.nv, SM_FINAL, W.cs, W.part[4], nullptr, g, c.tol, 0, nullptr, c.st);
+  if (!c.confirmed) {
+    const int g = true_residual(h, W, T, W.part[4], c.st);
+    if (g < 0) return XAMG_ERR_CUDA;
+    launch_scalar(c.nv, SM_FINAL, W.cs, W.part[4], nullptr, g, c.tol, 0, nullptr, c.st);
+  }
   launch_copy_out(c.nv, n, W.X, Xuser, c.m, elem_grid(n, c.nv), c.st);
   ColState cs;
   XCK(cudaMemcpyAsync(&cs, W.cs, sizeof(cs), cudaMemcpyDeviceToHost, c.st));
@@ -754,7 +759,10 @@ int solve_pcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
       if ((g = true_residual(h, W, W.Q, W.part[2], st)) < 0) return XAMG_ERR_CUDA;
       launch_scalar(nv, SM_CONFIRM, W.cs, W.part[2], nullptr, g, c.tol, k, fl, st);
       if ((rc = sync_read(st)) != XAMG_OK) return rc;
-      if (h->flags_h->reactivated == 0) break;
+      if (h->flags_h->reactivated == 0) {
+        c.confirmed = true;
+        break;
+      }
       launch_copy_cols(nv, n, W.R, W.Q, W.cs, ge, st);
       if (w0) launch_scale_rows(nv, n, w0, W.R, W.Z, ge, st);
     }
@@ -807,7 +815,10 @@ int solve_fpcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
       if ((g = true_residual(h, W, W.Q, W.part[2], st)) < 0) return XAMG_ERR_CUDA;
       launch_scalar(nv, SM_CONFIRM, W.cs, W.part[2], nullptr, g, c.tol, k, fl, st);
       if ((rc = sync_read(st)) != XAMG_OK) return rc;
-      if (h->flags_h->reactivated == 0) break;
+      if (h->flags_h->reactivated == 0) {
+        c.confirmed = true;
+        break;
+      }
       launch_copy_cols(nv, n, W.R, W.Q, W.cs, ge, st);
       launch_to_f32(nv, n, W.R, W.R32, w0f, W.Z32, ge, st);
     }
@@ -873,7 +884,10 @@ int solve_bicgstab(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stat
       if ((g = true_residual(h, W, W.T, W.part[2], st)) < 0) return XAMG_ERR_CUDA;
       launch_scalar(nv, SM_CONFIRM, W.cs, W.part[2], nullptr, g, c.tol, k, fl, st);
       if ((rc = sync_read(st)) != XAMG_OK) return rc;
-      if (h->flags_h->reactivated == 0) break;
+      if (h->flags_h->reactivated == 0) {
+        c.confirmed = true;
+        break;
+      }
       launch_copy_cols(nv, n, W.R, W.T, W.cs, ge, st);
       launch_copy_cols(nv, n, W.RH, W.T, W.cs, ge, st);
       launch_coldot(nv, n, W.RH, W.R, W.part[0], ge, st);
