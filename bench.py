@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--matrix", default="poisson7", choices=["poisson7", "poisson27"])
+    ap.add_argument("--matrix", default="poisson7", choices=["poisson7", "poisson27", "diffusion7"])
+    ap.add_argument("--sigma", type=float, default=1.0, help="diffusion7: lognormal sigma of k")
+    ap.add_argument("--kseed", type=int, default=1, help="diffusion7: seed of the cell coefficients")
     ap.add_argument("--grid", type=int, default=None)
     ap.add_argument("--m", type=int, default=32)
     ap.add_argument("--method", default="pcg", choices=["pcg", "bicgstab"])
@@ -64,18 +66,24 @@ def parse():
                          "preconditioner, one JSON line each (not the benchmark line)")
     a = ap.parse_args()
     if a.grid is None:
-        a.grid = 192 if a.matrix == "poisson7" else 160
+        a.grid = 160 if a.matrix == "poisson27" else 192
     return a
 
 
 def make_matrix(a):
     from paper_2103_07329_gb300 import problems as P
+    if a.matrix == "diffusion7":
+        return P.diffusion7(a.grid, P.lognormal_cells(a.grid, a.sigma, a.kseed))
     return P.poisson7(a.grid) if a.matrix == "poisson7" else P.poisson27(a.grid)
 
 
 def workload_name(a, A):
-    kind = "7-point" if a.matrix == "poisson7" else "27-point"
-    return (f"3-D {kind} Poisson {a.grid}^3 (n={A.n}, nnz={A.nnz}), m={a.m} RHS uniform[-1,1) "
+    if a.matrix == "diffusion7":
+        kind = (f"3-D 7-point variable-coefficient diffusion (cell k lognormal sigma={a.sigma:g}, "
+                f"seed {a.kseed})")
+    else:
+        kind = "3-D 7-point Poisson" if a.matrix == "poisson7" else "3-D 27-point Poisson"
+    return (f"{kind} {a.grid}^3 (n={A.n}, nnz={A.nnz}), m={a.m} RHS uniform[-1,1) "
             f"seed 0, {a.method.upper()} + classical RS AMG V(1,1) Chebyshev-2, tol {a.tol:g}, FP64")
 
 

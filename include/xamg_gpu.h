@@ -65,7 +65,10 @@ extern "C" {
  *                   FP32 accumulation; FP64 coarsest solve; PCG becomes
  *                   flexible PCG (FP64 outer loop, FP64 dots and residuals)
  *   XAMG_PREC_BF16  as FP32, but A's values are bf16 relative to a per-row
- *                   FP32 scale s_i = max_j |a_ij|: a_ij ~ s_i bf16(a_ij / s_i) */
+ *                   FP32 scale s_i = max_j |a_ij|: a_ij ~ s_i bf16(a_ij / s_i);
+ *                   where every row's columns lie in two consecutive windows
+ *                   of 65536 columns, A's column indices are also stored as
+ *                   uint16 (low 16 bits plus one per-row window word) */
 #define XAMG_PREC_FP64 0
 #define XAMG_PREC_FP32 1
 #define XAMG_PREC_BF16 2

@@ -33,6 +33,8 @@ struct DevLevel {
   float *a32 = nullptr, *p32 = nullptr, *r32 = nullptr;
   __nv_bfloat16 *a16 = nullptr;  // bf16(fl32(a_ij) / s_i)
   float *a16s = nullptr;         // s_i = fl32(max_j |a_ij|)
+  uint16_t *a16w = nullptr;      // low 16 bits of A's columns (if every row fits two windows)
+  uint32_t *a16meta = nullptr;   // per row: first window << 16 | entries in it
   float *w32[4] = {nullptr, nullptr, nullptr, nullptr};
   float c1f[4] = {0, 0, 0, 0};
 };
@@ -204,6 +206,31 @@ int upload_lowp(xamg_hier *h) {
     }
     if ((rc = dev_upload(h, &D.a16, q.data(), q.size())) != XAMG_OK) return rc;
     if ((rc = dev_upload(h, &D.a16s, s.data(), s.size())) != XAMG_OK) return rc;
+    // 16-bit column indices: usable when every row's columns lie in two
+    // consecutive windows of 65536 columns (and a row has < 65536 entries in
+    // its first window); otherwise the level keeps its 32-bit indices
+    {
+      std::vector<uint16_t> lw(H.A.col.size());
+      std::vector<uint32_t> meta((size_t)H.A.n);
+      bool ok = true;
+      for (int i = 0; i < H.A.n && ok; ++i) {
+        const int p0 = H.A.rowptr[i], p1 = H.A.rowptr[i + 1];
+        const uint32_t hw = p1 > p0 ? (uint32_t)H.A.col[p0] >> 16 : 0u;
+        uint32_t split = 0;
+        for (int p = p0; p < p1; ++p) {
+          const uint32_t w = (uint32_t)H.A.col[p] >> 16;
+          if (w == hw) ++split;
+          else if (w != hw + 1) ok = false;
+          lw[p] = (uint16_t)(H.A.col[p] & 0xffff);
+        }
+        if (split > 0xffffu || hw > 0xffffu) ok = false;
+        meta[i] = hw << 16 | split;
+      }
+      if (ok) {
+        if ((rc = dev_upload(h, &D.a16w, lw.data(), lw.size())) != XAMG_OK) return rc;
+        if ((rc = dev_upload(h, &D.a16meta, meta.data(), meta.size())) != XAMG_OK) return rc;
+      }
+    }
     if (l + 1 == L) continue;
     std::vector<float> pf(H.P.val.size()), rf(H.R.val.size());
     for (size_t k = 0; k < pf.size(); ++k) pf[k] = (float)H.P.val[k];
@@ -401,8 +428,10 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
 template <class TB>
 double row_bytes(const DevCsr &M, const RowOpT<TB> &op, int nv, double val_bytes) {
   const double blk = (double)M.n * nv * sizeof(TB);
-  double b = (4.0 + val_bytes) * (double)M.nnz + 4.0 * (M.n + 1) + (double)M.ncols * nv * sizeof(TB);
+  const double idx_bytes = op.colw ? 2.0 : 4.0;
+  double b = (idx_bytes + val_bytes) * (double)M.nnz + 4.0 * (M.n + 1) + (double)M.ncols * nv * sizeof(TB);
   if (op.rscale) b += 4.0 * M.n;
+  if (op.rowmeta) b += 4.0 * M.n;
   if (op.init) b += blk;
   if (op.y) b += blk;
   if (op.dp) b += blk;
@@ -436,6 +465,11 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
       op.rscale = D.a16s;
       vt = 1;
       vbytes = 2.0;
+      if (D.a16w) {
+        op.colw = D.a16w;
+        op.rowmeta = D.a16meta;
+        vt = 2;
+      }
     } else {
       op.val = which == 0 ? D.a32 : which == 1 ? D.p32 : D.r32;
       op.rscale = nullptr;

@@ -39,6 +39,8 @@ struct RowOpT {
   const int32_t *col;
   const void *val;       // matrix values (TV)
   const float *rscale;   // per-row scale of bf16 values
+  const uint16_t *colw;  // 16-bit column indices (Bf16Idx16)
+  const uint32_t *rowmeta;  // per row: first window << 16 | entries in it (Bf16Idx16)
   const TB *src;
   const TB *init;
   TB *y;
@@ -183,18 +185,34 @@ __device__ __forceinline__ void row_operands(const RowOpT<TB> &op, int64_t i, in
 template <class TV> struct ValueLoad;
 template <> struct ValueLoad<double> {
   static constexpr bool scaled = false;
+  static constexpr bool idx16 = false;
   __device__ __forceinline__ static double get(const void *v, int k) {
     return __ldg(static_cast<const double *>(v) + k);
   }
 };
 template <> struct ValueLoad<float> {
   static constexpr bool scaled = false;
+  static constexpr bool idx16 = false;
   __device__ __forceinline__ static float get(const void *v, int k) {
     return __ldg(static_cast<const float *>(v) + k);
   }
 };
 template <> struct ValueLoad<__nv_bfloat16> {
   static constexpr bool scaled = true;
+  static constexpr bool idx16 = false;
+  __device__ __forceinline__ static float get(const void *v, int k) {
+    return __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(v) + k));
+  }
+};
+// bf16 values with 16-bit column indices: entry k of row i holds the low 16
+// bits of its column; the row's entries lie in two consecutive windows of
+// 65536 columns, the first `split` entries in window `hw` and the rest in
+// hw + 1, packed as rowmeta[i] = hw << 16 | split (paper Sec. 2.3: CSR index
+// types reduced to uint16_t).
+struct Bf16Idx16 {};
+template <> struct ValueLoad<Bf16Idx16> {
+  static constexpr bool scaled = true;
+  static constexpr bool idx16 = true;
   __device__ __forceinline__ static float get(const void *v, int k) {
     return __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(v) + k));
   }
@@ -330,6 +348,7 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
     const bool valid = i < op.n;
     const int64_t e = i * NV + c0;
     int start = 0, len = 0;
+    uint32_t meta = 0;
     V acc, dpv, xv;
     TB wv = 0;
 #pragma unroll
@@ -337,6 +356,7 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
     if (valid) {
       start = __ldg(op.rowptr + i);
       len = __ldg(op.rowptr + i + 1) - start;
+      if constexpr (VL::idx16) meta = __ldg(op.rowmeta + i);
       if (!VL::scaled && op.init && sl == 0) acc = vload<TB, VEC>(op.init + e);
       if constexpr (EPI == EPI_Y_DN || EPI == EPI_Y_XDP || EPI == EPI_MID || xlast)
         dpv = vload<TB, VEC>(op.dp + e);
@@ -356,7 +376,14 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
 #pragma unroll
       for (int q = 0; q < K; ++q) {
         const bool own = kb + q * G + gl < len;
-        cl[q] = own ? __ldg(col + start + kb + q * G + gl) : 0;
+        if constexpr (VL::idx16) {
+          const int kl = kb + q * G + gl;
+          cl[q] = own ? (int)((((meta >> 16) + (kl >= (int)(meta & 0xffffu) ? 1u : 0u)) << 16) |
+                             __ldg(op.colw + start + kl))
+                      : 0;
+        } else {
+          cl[q] = own ? __ldg(col + start + kb + q * G + gl) : 0;
+        }
         av[q] = own ? (TB)VL::get(op.val, start + kb + q * G + gl) : (TB)0;
       }
       const int cnt = min(G * K, maxlen - kb0);  // uniform over the warp

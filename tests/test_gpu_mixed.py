@@ -94,3 +94,33 @@ def test_reduced_precision_edge_cases():
     assert e.value.code == B.ERR_NONFINITE and torch.all(X == 5.0)
     with pytest.raises(B.XamgError):
         g.solve(dev(Bm), X, precond=7)
+
+
+def _long_range(N, stride):
+    """7-point Poisson plus a symmetric coupling of every row to the row
+    `stride` away (diagonally dominant, so still SPD): with a stride beyond
+    two index windows of 65536 the rows cannot use 16-bit column indices."""
+    import scipy.sparse as sp
+    A0 = P.poisson7(N)
+    M = sp.csr_matrix((A0.val, A0.col, A0.rowptr), shape=(A0.n, A0.n))
+    n = A0.n
+    E = sp.diags([np.full(n - stride, -0.1), np.full(n - stride, -0.1)], [stride, -stride], shape=(n, n))
+    M = (M + E + sp.identity(n) * 0.2).tocsr()
+    M.sort_indices()
+    return P.CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data)
+
+
+@pytest.mark.parametrize("which", ["windows", "fallback"])
+def test_bf16_index_compression_paths(which):
+    # n = 262144 spans four windows; the 7-point rows cross window borders but
+    # fit two windows (16-bit indices).  The long-range variant does not fit
+    # and keeps 32-bit indices.  Both must match the oracle's bf16 V-cycle.
+    A = P.poisson7(64) if which == "windows" else _long_range(64, 140000)
+    g, o = B.Hierarchy(A), oracle.Hierarchy(A)
+    Bm = P.rhs_uniform(A.n, 8, 0, m_draw=32)
+    X = torch.empty((A.n, 8), dtype=torch.float64, device="cuda")
+    g.vcycle_precond(B.PREC_BF16, dev(Bm), X)
+    assert colrel(X.cpu().numpy(), o.vcycle_prec(B.PREC_BF16, Bm)).max() <= 2e-5
+    st = g.solve(dev(Bm), X, precond=B.PREC_BF16)
+    rr = np.linalg.norm(Bm - oracle.spmm(A, X.cpu().numpy()), axis=0) / np.linalg.norm(Bm, axis=0)
+    assert st.rc == 0 and np.all(rr <= 1e-8)
