@@ -123,6 +123,10 @@ typedef struct {
 /* Solve options (fill with xamg_solve_opts_default first).
  *   method       XAMG_PCG or XAMG_BICGSTAB
  *   precond      XAMG_PREC_FP64 (default), XAMG_PREC_FP32 or XAMG_PREC_BF16
+ *   x0_given     0 (default): start from X = 0; 1: X holds the initial guess
+ *                X0 on entry (a warm start, e.g. a learned prediction); the
+ *                stopping test stays ||b_j - A x_j|| <= tol ||b_j||, and a
+ *                zero column b_j still returns x_j = 0
  *   stream       cudaStream_t as void*, NULL = legacy default stream
  *   workspace    optional caller-owned DEVICE buffer of workspace_bytes bytes
  *                (at least xamg_workspace_bytes(); 256-byte aligned); NULL
@@ -131,6 +135,7 @@ typedef struct {
 typedef struct {
   int32_t method;
   int32_t precond;
+  int32_t x0_given;
   void *stream;
   void *workspace;
   size_t workspace_bytes;
@@ -198,7 +203,8 @@ int xamg_workspace_bytes(const xamg_hier *h, int32_t m, int32_t method, int32_t 
 /* Solves A X = B to ||b_j - A x_j|| <= tol ||b_j|| for every column
  * (paper Sec. 1 and 2.1; PCG or BiCGStab preconditioned by one V(1,1)
  * Chebyshev cycle, paper Fig. 3).  B and X are DEVICE n x m row-major
- * blocks, 1 <= m <= XAMG_MAX_RHS, caller-owned; X0 = 0.  Each column stops
+ * blocks, 1 <= m <= XAMG_MAX_RHS, caller-owned; X0 = 0 unless
+ * opts->x0_given.  Each column stops
  * on its own (status flags); X always holds the last iterate.  Returns 0 when
  * every column converged, XAMG_NOT_CONVERGED / XAMG_BREAKDOWN otherwise, or
  * a negative error (NONFINITE if B holds NaN/Inf: X is then untouched).

@@ -78,8 +78,8 @@ def lib():
         L.orc_bf16_bits.restype = C.c_uint16
         for name in ("orc_pcg_prec", "orc_bicgstab_prec"):
             f = getattr(L, name)
-            f.argtypes = [C.c_void_p, C.c_int, C.c_int, _f64p, _f64p, C.c_double, C.c_int, _i32p,
-                          _f64p, _i32p]
+            f.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, _f64p, _f64p, C.c_double, C.c_int,
+                          _i32p, _f64p, _i32p]
             f.restype = C.c_int
         for name in ("orc_pcg", "orc_bicgstab"):
             f = getattr(L, name)
@@ -221,29 +221,30 @@ class Hierarchy:
             raise RuntimeError(f"orc_spmm_f failed: {rc}")
         return Y
 
-    def _solve(self, fn, B, tol, maxit, prec=None):
+    def _solve(self, fn, B, tol, maxit, prec=None, X0=None):
         B = np.ascontiguousarray(B, dtype=np.float64)
         m = B.shape[1]
-        X = np.empty_like(B)
+        X = np.empty_like(B) if X0 is None else np.ascontiguousarray(X0, dtype=np.float64).copy()
         it = np.zeros(m, np.int32); rr = np.zeros(m, np.float64); st = np.zeros(m, np.int32)
         if prec is None:
             rc = fn(self._h, m, B, X, tol, maxit, it, rr, st)
         else:
-            rc = fn(self._h, prec, m, B, X, tol, maxit, it, rr, st)
+            rc = fn(self._h, prec, 0 if X0 is None else 1, m, B, X, tol, maxit, it, rr, st)
         if rc < 0:
             raise RuntimeError(f"oracle solve failed: {rc}")
         return SolveResult(X, it, rr, st, rc)
 
-    def pcg(self, B, tol=1e-8, maxit=200, prec=0):
+    def pcg(self, B, tol=1e-8, maxit=200, prec=0, X0=None):
         """PCG; with prec 1 (FP32) or 2 (bf16 A) the preconditioner is the
-        reduced-precision V-cycle and the iteration is flexible PCG."""
-        if prec:
-            return self._solve(lib().orc_pcg_prec, B, tol, maxit, prec)
+        reduced-precision V-cycle and the iteration is flexible PCG; X0 is an
+        optional initial guess."""
+        if prec or X0 is not None:
+            return self._solve(lib().orc_pcg_prec, B, tol, maxit, prec, X0)
         return self._solve(lib().orc_pcg, B, tol, maxit)
 
-    def bicgstab(self, B, tol=1e-8, maxit=200, prec=0):
-        if prec:
-            return self._solve(lib().orc_bicgstab_prec, B, tol, maxit, prec)
+    def bicgstab(self, B, tol=1e-8, maxit=200, prec=0, X0=None):
+        if prec or X0 is not None:
+            return self._solve(lib().orc_bicgstab_prec, B, tol, maxit, prec, X0)
         return self._solve(lib().orc_bicgstab, B, tol, maxit)
 
 

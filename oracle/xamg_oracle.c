@@ -971,8 +971,8 @@ static int confirm(const ocsr *A, int m, const double *b, const double *x, doubl
  * approximately symmetric, and the direction update takes the flexible form
  * beta = z_{k+1} . (r_{k+1} - r_k) / (z_k . r_k) (Notay 2000; Golub and
  * Ye 1999), for which the previous residual is kept. */
-int orc_pcg_prec(ohier *h, int prec, int m, const double *b, double *x, double tol, int maxit,
-                 int *iters, double *relres, int *status) {
+int orc_pcg_prec(ohier *h, int prec, int x0_given, int m, const double *b, double *x, double tol,
+                 int maxit, int *iters, double *relres, int *status) {
   const ocsr *A = &h->A[0];
   size_t N = (size_t)A->n * m, i;
   int j, k, rc = ORC_OK, any;
@@ -992,7 +992,20 @@ int orc_pcg_prec(ohier *h, int prec, int m, const double *b, double *x, double t
   if (!r || !z || !p || !q || !t || !nb || !rho || !c || !tn || !state || !restart) { rc = ORC_ERR_OOM; goto done; }
   coldot((size_t)A->n, m, b, b, nb);
   for (j = 0; j < m; ++j) { nb[j] = sqrt(nb[j]); iters[j] = 0; if (nb[j] == 0.0) state[j] = 4; }
-  for (i = 0; i < N; ++i) { x[i] = 0.0; r[i] = b[i]; }
+  if (x0_given) {
+    /* warm start: r = b - A x0; a zero right-hand side keeps x = 0 */
+    if (!all_finite(N, x)) { rc = ORC_ERR_NONFINITE; goto done; }
+    for (i = 0; i < (size_t)A->n; ++i)
+      for (j = 0; j < m; ++j) if (state[j] == 4) x[i * m + j] = 0.0;
+    spmm(A, m, x, t);
+    for (i = 0; i < N; ++i) r[i] = b[i] - t[i];
+    /* columns whose initial guess already meets the tolerance start frozen */
+    coldot((size_t)A->n, m, r, r, c);
+    for (j = 0; j < m; ++j)
+      if (state[j] == 0 && sqrt(c[j]) <= tol * nb[j]) state[j] = 1;
+  } else {
+    for (i = 0; i < N; ++i) { x[i] = 0.0; r[i] = b[i]; }
+  }
   if ((rc = apply_M(h, prec, m, r, z)) != ORC_OK) goto done;
   memcpy(p, z, N * sizeof(double));
   coldot((size_t)A->n, m, r, z, rho);
@@ -1058,13 +1071,13 @@ done:
 
 int orc_pcg(ohier *h, int m, const double *b, double *x, double tol, int maxit, int *iters,
             double *relres, int *status) {
-  return orc_pcg_prec(h, 0, m, b, x, tol, maxit, iters, relres, status);
+  return orc_pcg_prec(h, 0, 0, m, b, x, tol, maxit, iters, relres, status);
 }
 
 
 /* Right-preconditioned BiCGStab (paper Sec. 2.1, Tab. 1; van der Vorst), M = one V-cycle. */
-int orc_bicgstab_prec(ohier *h, int prec, int m, const double *b, double *x, double tol,
-                      int maxit, int *iters, double *relres, int *status) {
+int orc_bicgstab_prec(ohier *h, int prec, int x0_given, int m, const double *b, double *x,
+                      double tol, int maxit, int *iters, double *relres, int *status) {
   const ocsr *A = &h->A[0];
   size_t N = (size_t)A->n * m, i, n = (size_t)A->n;
   int j, k, rc = ORC_OK, any;
@@ -1086,7 +1099,19 @@ int orc_bicgstab_prec(ohier *h, int prec, int m, const double *b, double *x, dou
       !c2 || !tn || !state || !restart) { rc = ORC_ERR_OOM; goto done; }
   coldot(n, m, b, b, nb);
   for (j = 0; j < m; ++j) { nb[j] = sqrt(nb[j]); iters[j] = 0; if (nb[j] == 0.0) state[j] = 4; restart[j] = 1; }
-  for (i = 0; i < N; ++i) { x[i] = 0.0; r[i] = b[i]; rh[i] = b[i]; p[i] = 0.0; v[i] = 0.0; }
+  if (x0_given) {
+    /* warm start: r = rhat = b - A x0; a zero right-hand side keeps x = 0 */
+    if (!all_finite(N, x)) { rc = ORC_ERR_NONFINITE; goto done; }
+    for (i = 0; i < n; ++i)
+      for (j = 0; j < m; ++j) if (state[j] == 4) x[i * m + j] = 0.0;
+    spmm(A, m, x, t);
+    for (i = 0; i < N; ++i) { r[i] = b[i] - t[i]; rh[i] = r[i]; p[i] = 0.0; v[i] = 0.0; }
+    coldot(n, m, r, r, c);
+    for (j = 0; j < m; ++j)
+      if (state[j] == 0 && sqrt(c[j]) <= tol * nb[j]) state[j] = 1;
+  } else {
+    for (i = 0; i < N; ++i) { x[i] = 0.0; r[i] = b[i]; rh[i] = b[i]; p[i] = 0.0; v[i] = 0.0; }
+  }
   for (k = 1; k <= maxit; ++k) {
     any = 0;
     for (j = 0; j < m; ++j) any |= (state[j] == 0);
@@ -1174,5 +1199,5 @@ done:
 
 int orc_bicgstab(ohier *h, int m, const double *b, double *x, double tol, int maxit, int *iters,
                  double *relres, int *status) {
-  return orc_bicgstab_prec(h, 0, m, b, x, tol, maxit, iters, relres, status);
+  return orc_bicgstab_prec(h, 0, 0, m, b, x, tol, maxit, iters, relres, status);
 }

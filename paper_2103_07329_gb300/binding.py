@@ -64,8 +64,8 @@ class AmgParamsT(C.Structure):
 
 
 class SolveOptsT(C.Structure):
-    _fields_ = [("method", C.c_int32), ("precond", C.c_int32), ("stream", C.c_void_p),
-                ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+    _fields_ = [("method", C.c_int32), ("precond", C.c_int32), ("x0_given", C.c_int32),
+                ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
 
 
 class StatsT(C.Structure):
@@ -261,11 +261,12 @@ class Hierarchy:
                "xamg_workspace_bytes")
         return b.value
 
-    def _opts(self, method, stream, workspace, precond=PREC_FP64):
+    def _opts(self, method, stream, workspace, precond=PREC_FP64, x0_given=False):
         o = SolveOptsT()
         _load().xamg_solve_opts_default(C.byref(o))
         o.method = method
         o.precond = precond
+        o.x0_given = 1 if x0_given else 0
         o.stream = _stream(stream)
         if workspace is not None:
             o.workspace = _ptr(workspace)
@@ -273,25 +274,26 @@ class Hierarchy:
         return o
 
     def solve(self, B, X, tol=1e-8, maxit=200, method=PCG, stream=None, workspace=None,
-              precond=PREC_FP64) -> SolveStats:
-        """xamg_solve on device blocks B, X (torch float64 CUDA tensors, n x m)."""
+              precond=PREC_FP64, x0_given=False) -> SolveStats:
+        """xamg_solve on device blocks B, X (torch float64 CUDA tensors, n x m);
+        with x0_given, X holds the initial guess on entry."""
         m = B.shape[1] if B.dim() == 2 else 1
         st = SolveStats(m)
         s = st.struct()
-        o = self._opts(method, stream, workspace, precond)
+        o = self._opts(method, stream, workspace, precond, x0_given)
         rc = _load().xamg_solve(self._h, _ptr(B), _ptr(X), m, tol, maxit, C.byref(o), C.byref(s))
         _check(rc, "xamg_solve", allow_positive=True)
         st.iterations, st.vcycles, st.rc = s.iterations, s.vcycles, rc
         return st
 
     def solve_host(self, B: np.ndarray, X: np.ndarray, tol=1e-8, maxit=200, method=PCG,
-                   stream=None, precond=PREC_FP64) -> SolveStats:
+                   stream=None, precond=PREC_FP64, x0_given=False) -> SolveStats:
         """xamg_solve_host on host arrays (float64, C order, n x m)."""
         assert B.flags.c_contiguous and X.flags.c_contiguous and B.dtype == np.float64
         m = B.shape[1]
         st = SolveStats(m)
         s = st.struct()
-        o = self._opts(method, stream, None, precond)
+        o = self._opts(method, stream, None, precond, x0_given)
         rc = _load().xamg_solve_host(self._h, B.ctypes.data, X.ctypes.data, m, tol, maxit,
                                      C.byref(o), C.byref(s))
         _check(rc, "xamg_solve_host", allow_positive=True)

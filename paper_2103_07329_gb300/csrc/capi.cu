@@ -686,7 +686,33 @@ struct SolveCtx {
   // set when the loop ended on a confirmation that restarted no column: the
   // true residual norms in the column state are those of the final X
   bool confirmed = false;
+  const double *x0 = nullptr;  // user initial guess (n x m), or null for X0 = 0
 };
+
+int sync_read(cudaStream_t st);
+
+// Warm start: columns whose initial residual already meets the tolerance start
+// frozen (state 1); the host reads how many stay active.
+int initial_check(SolveCtx &c) {
+  Work &W = c.W;
+  const int64_t n = c.h->lv[0].A.n;
+  const int ge = elem_grid(n, c.nv);
+  launch_coldot(c.nv, n, W.R, W.R, W.part[3], ge, c.st);
+  launch_scalar(c.nv, SM_PCG_CONV, W.cs, W.part[3], nullptr, ge, c.tol, 0, c.h->flags_d, c.st);
+  return sync_read(c.st);
+}
+
+// Warm start: X = X0 (zero right-hand-side columns stay 0) and R = B - A X.
+int load_x0(SolveCtx &c) {
+  Work &W = c.W;
+  const int64_t n = c.h->lv[0].A.n;
+  const int ge = elem_grid(n, c.nv);
+  launch_pad_in(c.nv, n, c.x0, c.m, W.X, ge, c.st);
+  launch_zero_rhs_cols(c.nv, n, W.X, W.cs, ge, c.st);
+  RowOp o = blank<double>();
+  o.init = W.Bn; o.src = W.X; o.y = W.R;
+  return rows<double>(c.h, 0, 0, XAMG_PREC_FP64, o, c.nv, true, EPI_Y, c.st) < 0 ? XAMG_ERR_CUDA : XAMG_OK;
+}
 
 // z = M r for the FP64 Krylov loops.  FP64 preconditioner: on entry z holds
 // w0 .* r (written by the kernel that produced r).  Reduced precision: r is
@@ -773,6 +799,11 @@ int solve_pcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
   launch_scalar(nv, SM_INIT, W.cs, W.part[0], nullptr, ge, c.tol, 0, fl, st);
   int rc = check_init(c);
   if (rc != XAMG_OK) return rc;
+  if (c.x0) {
+    if ((rc = load_x0(c)) != XAMG_OK) return rc;
+    if (w0) launch_scale_rows(nv, n, w0, W.R, W.Z, ge, st);
+    if ((rc = initial_check(c)) != XAMG_OK) return rc;
+  }
   if (h->flags_h->active > 0) {
     if ((rc = vcycle<double>(h, W, XAMG_PREC_FP64, 0, W.R, W.Z, st, dot1(W.R, W.part[1], &g))) != XAMG_OK)
       return rc;
@@ -829,6 +860,11 @@ int solve_fpcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
   launch_scalar(nv, SM_INIT, W.cs, W.part[0], nullptr, ge, c.tol, 0, fl, st);
   int rc = check_init(c);
   if (rc != XAMG_OK) return rc;
+  if (c.x0) {
+    if ((rc = load_x0(c)) != XAMG_OK) return rc;
+    launch_to_f32(nv, n, W.R, W.R32, w0f, W.Z32, ge, st);
+    if ((rc = initial_check(c)) != XAMG_OK) return rc;
+  }
   if (h->flags_h->active > 0) {
     if ((rc = vcycle<float>(h, W, prec, 0, W.R32, W.Z32, st, dot1(W.R, W.part[1], &g))) != XAMG_OK)
       return rc;
@@ -887,6 +923,13 @@ int solve_bicgstab(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stat
   launch_scalar(nv, SM_INIT, W.cs, W.part[0], nullptr, ge, c.tol, 0, fl, st);
   int rc = check_init(c);
   if (rc != XAMG_OK) return rc;
+  if (c.x0) {
+    // rhat = r_0 = b - A x_0
+    if ((rc = load_x0(c)) != XAMG_OK) return rc;
+    XCK(cudaMemcpyAsync(W.RH, W.R, blk, cudaMemcpyDeviceToDevice, st));
+    if ((rc = initial_check(c)) != XAMG_OK) return rc;
+    launch_coldot(nv, n, W.RH, W.R, W.part[0], ge, st);
+  }
   double *prh = W.part[0];  // partial sums of rhat . r
   int grh = ge;
   for (int k = 1; k <= c.maxit && h->flags_h->active > 0; ++k) {
@@ -949,6 +992,7 @@ int solve_impl(xamg_hier *h, const double *B, double *X, int m, double tol, int 
   c.maxit = maxit;
   c.prec = o.precond;
   c.st = (cudaStream_t)o.stream;
+  if (o.x0_given) c.x0 = X;
   int rc = ensure_workspace(h, c.nv, o.method, c.prec, &o, c.W);
   if (rc != XAMG_OK) return rc;
   h->flags_h->active = 0;
@@ -1001,6 +1045,7 @@ void xamg_solve_opts_default(xamg_solve_opts *o) {
   if (!o) return;
   o->method = XAMG_PCG;
   o->precond = XAMG_PREC_FP64;
+  o->x0_given = 0;
   o->stream = nullptr;
   o->workspace = nullptr;
   o->workspace_bytes = 0;
@@ -1139,6 +1184,7 @@ int xamg_solve_host(xamg_hier *h, const double *B, double *X, int32_t m, double 
   double *db = h->hb, *dx = (double *)((char *)h->hb + align256(bytes));
   cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
   XCK(cudaMemcpyAsync(db, B, bytes, cudaMemcpyHostToDevice, st));
+  if (opts && opts->x0_given) XCK(cudaMemcpyAsync(dx, X, bytes, cudaMemcpyHostToDevice, st));
   int rc = solve_impl(h, db, dx, m, tol, maxit, opts, stats);
   if (rc < 0) return rc;
   XCK(cudaMemcpyAsync(X, dx, bytes, cudaMemcpyDeviceToHost, st));

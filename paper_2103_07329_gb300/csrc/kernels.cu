@@ -583,6 +583,14 @@ __global__ void __launch_bounds__(kBlock) k_coarse_f(int nc, const double *lu, c
   for (int e = tid; e < nc * NV; e += kBlock) X[e] = (float)W[e];
 }
 
+// X[:, c] = 0 for the columns with a zero right-hand side (state 4)
+template <int NV>
+__global__ void __launch_bounds__(kBlock) k_zero_rhs_cols(int64_t n, double *X, const ColState *cs) {
+  const int c = threadIdx.x % NV;
+  if (cs->state[c] != 4) return;
+  XAMG_ELEM_LOOP(NV, n) { X[e] = 0.0; }
+}
+
 // ------------------------------------------------------------------ runtime-m dots
 // Thread t of a block owns column t % m for t < (kBlock / m) * m; rows are
 // strided over the grid.  Partials: per block and column, summed over the
@@ -723,6 +731,10 @@ void launch_axpy_dot_f(int nv, int64_t n, float *X, const float *D, const double
 void launch_coarse_f(int nv, int nc, const double *lu, const int32_t *piv, const float *B, float *X,
                      double *W, cudaStream_t st) {
   XAMG_NV_SWITCH(nv, (k_coarse_f<NV><<<1, kBlock, 0, st>>>(nc, lu, piv, B, X, W)));
+}
+
+void launch_zero_rhs_cols(int nv, int64_t n, double *X, const ColState *cs, int grid, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_zero_rhs_cols<NV><<<grid, kBlock, 0, st>>>(n, X, cs)));
 }
 
 int coldot_rt_grid(int64_t n, int m) {

@@ -124,6 +124,7 @@ void launch_axpy_dot_f(int nv, int64_t n, float *X, const float *D, const double
                        const double *U2, double *part, double *part2, int grid, cudaStream_t st);
 void launch_coarse_f(int nv, int nc, const double *lu, const int32_t *piv, const float *B, float *X,
                      double *W, cudaStream_t st);
+void launch_zero_rhs_cols(int nv, int64_t n, double *X, const ColState *cs, int grid, cudaStream_t st);
 // Runtime-m column dots for the public entry point: partials then reduce.
 int coldot_rt_grid(int64_t n, int m);
 void launch_coldot_rt(int64_t n, int m, const double *U, const double *V, double *part, int grid,

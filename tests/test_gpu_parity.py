@@ -285,3 +285,26 @@ def test_coldot(m):
     out2 = torch.empty(m, dtype=torch.float64, device="cuda")
     B.coldot(dev(U), dev(V), out2)
     assert torch.equal(out, out2)
+
+
+@pytest.mark.parametrize("method", [B.PCG, B.BICGSTAB])
+@pytest.mark.parametrize("prec", [B.PREC_FP64, B.PREC_FP32])
+def test_warm_start_matches_oracle(cfg0, method, prec):
+    Bm = P.rhs_uniform(cfg0.A.n, 4, 7)
+    Bm[:, 3] = 0.0
+    ref = cfg0.o.pcg(Bm, tol=1e-12)
+    X0 = ref.X + 1e-4 * np.random.default_rng(2).standard_normal(ref.X.shape)
+    X = dev(X0)
+    st = cfg0.g.solve(dev(Bm), X, tol=1e-8, method=method, precond=prec, x0_given=True)
+    o = (cfg0.o.pcg if method == B.PCG else cfg0.o.bicgstab)(Bm, tol=1e-8, prec=prec, X0=X0)
+    Xg = X.cpu().numpy()
+    assert st.rc == 0 and np.all(st.status == 0)
+    assert np.all(true_relres(cfg0.A, Bm[:, :3], Xg[:, :3]) <= 1e-8)
+    assert np.all(Xg[:, 3] == 0.0) and st.iters[3] == 0
+    assert np.all(np.abs(st.iters - o.iters) <= 1), (st.iters, o.iters)
+    cold = cfg0.g.solve(dev(Bm), torch.empty_like(X), tol=1e-8, method=method, precond=prec)
+    assert np.all(st.iters[:3] < cold.iters[:3])
+    # the exact solution as guess: nothing to do
+    X = dev(ref.X)
+    st = cfg0.g.solve(dev(Bm), X, tol=1e-8, method=method, precond=prec, x0_given=True)
+    assert np.all(st.iters == 0) and np.all(st.status == 0)

@@ -459,3 +459,24 @@ def test_maxit_reports_not_converged():
     B = P.rhs_uniform(A.n, 2, 0)
     r = h.pcg(B, tol=1e-14, maxit=2)
     assert r.rc == 1 and np.all(r.status == 1) and np.all(r.iters == 2)
+
+
+@pytest.mark.parametrize("method", ["pcg", "bicgstab"])
+def test_warm_start(method):
+    A = P.poisson7(10)
+    h = oracle.Hierarchy(A)
+    B = P.rhs_uniform(A.n, 3, 0)
+    B[:, 2] = 0.0
+    exact = sla.lu_solve(sla.lu_factor(to_scipy(A).toarray()), B)
+    # the exact solution as initial guess: no iteration, unchanged up to rounding
+    r = getattr(h, method)(B, X0=exact)
+    assert np.all(r.iters == 0) and np.all(r.status == 0)
+    assert np.allclose(r.X, exact, rtol=0, atol=1e-14)
+    # a perturbed guess: fewer iterations than from zero, same tolerance met;
+    # the zero column returns x = 0 whatever the guess
+    cold = getattr(h, method)(B)
+    X0 = exact + 1e-5 * np.random.default_rng(1).standard_normal(exact.shape)
+    warm = getattr(h, method)(B, X0=X0)
+    assert np.all(warm.relres <= 1e-8) and np.all(warm.status == 0)
+    assert np.all(warm.iters[:2] < cold.iters[:2])
+    assert np.all(warm.X[:, 2] == 0.0) and warm.iters[2] == 0
