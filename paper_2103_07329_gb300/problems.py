@@ -17,6 +17,8 @@ Matrices (paper Sec. 3, "Example case": the 3D Poisson equation on a cube,
   * ``diffusion7(N, k)``: cell-centred finite volumes for -div(k grad u) with
     cell coefficients k (e.g. lognormal, ``lognormal_cells``), the
     variable-coefficient systems the mixed-precision and batched forms use.
+  * ``grf(N, corr_len, sigma, seed)``: Gaussian random fields (log-coefficients
+    and smooth right-hand sides of the learned warm start).
 
 Right-hand sides: entries i.i.d. uniform[-1, 1) from numpy's
 ``default_rng(seed)``, n x m row-major (C order).
@@ -129,6 +131,26 @@ def diffusion7(N: int, kcell: np.ndarray) -> CSR:
     np.cumsum(counts, out=rowptr[1:])
     return CSR(n, rowptr.astype(np.int32), np.ascontiguousarray(cols[valid], dtype=np.int32),
                np.ascontiguousarray(vals[valid], dtype=np.float64))
+
+
+def grf(N: int, corr_len: float, sigma: float, seed: int, count: int = 1) -> np.ndarray:
+    """`count` Gaussian random fields on the periodic N^3 grid of the unit cube,
+    squared-exponential covariance sigma^2 exp(-r^2 / (2 corr_len^2)).
+
+    White noise (numpy default_rng(seed)) is convolved, by FFT on the periodic
+    grid, with exp(-r^2 / corr_len^2), whose self-convolution is the
+    squared-exponential kernel; the result is scaled by the filter's L2 norm
+    so that each point has variance sigma^2.  Returns count x N^3 (lexicographic,
+    i fastest)."""
+    h = 1.0 / N
+    d = np.minimum(np.arange(N), N - np.arange(N)) * h          # periodic distance
+    r2 = d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2
+    g = np.exp(-r2 / corr_len ** 2)
+    G = np.fft.rfftn(g)
+    scale = sigma / np.sqrt((g * g).sum())
+    w = np.random.default_rng(seed).standard_normal((count, N, N, N))
+    f = np.fft.irfftn(np.fft.rfftn(w, axes=(1, 2, 3)) * G, s=(N, N, N), axes=(1, 2, 3)) * scale
+    return f.reshape(count, -1)
 
 
 def rhs_uniform(n: int, m: int, seed: int = 0, m_draw: int | None = None) -> np.ndarray:

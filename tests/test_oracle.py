@@ -480,3 +480,18 @@ def test_warm_start(method):
     assert np.all(warm.relres <= 1e-8) and np.all(warm.status == 0)
     assert np.all(warm.iters[:2] < cold.iters[:2])
     assert np.all(warm.X[:, 2] == 0.0) and warm.iters[2] == 0
+
+
+def test_grf_covariance():
+    # empirical covariance of the periodic fields against the squared-exponential
+    # kernel sigma^2 exp(-r^2 / (2 l^2)) at lags along one axis
+    N, ell, sigma = 32, 0.1, 1.5
+    f = P.grf(N, ell, sigma, seed=3, count=64).reshape(64, N, N, N)
+    f = f - f.mean()
+    for lag in (0, 1, 2, 3, 5):
+        emp = (f * np.roll(f, -lag, axis=3)).mean()
+        ref = sigma ** 2 * np.exp(-(lag / N) ** 2 / (2 * ell ** 2))
+        assert abs(emp - ref) <= 0.08 * sigma ** 2, (lag, emp, ref)
+    # reproducible and seed-dependent
+    assert np.array_equal(P.grf(8, 0.2, 1.0, 5), P.grf(8, 0.2, 1.0, 5))
+    assert not np.array_equal(P.grf(8, 0.2, 1.0, 5), P.grf(8, 0.2, 1.0, 6))
