@@ -282,6 +282,93 @@ int xamg_coldot(const double *U, const double *V, int64_t n, int32_t m, double *
 int xamg_coldot_noalloc(const double *U, const double *V, int64_t n, int32_t m, double *out,
                         void *stream);
 
+/* ---- learned initial guess ----
+ *
+ * A 3-D convolutional encoder-decoder that predicts a first iterate X0 of the
+ * solve from (B, log coefficient) on an N^3 grid, trained on the GPU on
+ * solutions this library computes; the solve then starts from X0
+ * (xamg_solve_opts.x0_given) instead of X0 = 0.  The paper has no learned
+ * component.  Architecture, four grid levels of edge N, N/2, N/4, N/8 (all
+ * convolutions 3x3x3, stride 1, zero padding, ReLU after all but the last):
+ *   e0a 2->8, e0b 8->8 | avg-pool 2, e1a 8->16, e1b 16->16 | pool, e2a, e2b
+ *   16->16 | pool, e3a, e3b 16->16 | nearest-upsample + skip(e2b), d2 16->16 |
+ *   up + skip(e1b), d1a 16->16, d1b 16->8 | up + skip(e0b), d0a 8->8, d0b 8->1.
+ * The flat FP32 parameter vector (xamg_net_param_count() floats) holds, per
+ * layer in the order above, W[cout][27][cin] (tap t = 9(dz+1) + 3(dy+1) +
+ * (dx+1), a cross-correlation) then b[cout]; e0a is stored with cin = 8 (input
+ * channels 2..7 are zero) and d0b with cout = 8 (only output channel 0 is
+ * used), so their extra weights receive zero gradient.  Activations and
+ * gradients are BF16, products accumulate in FP32 on the tensor cores,
+ * parameters and Adam moments are FP32.  One handle serves one device and
+ * one stream at a time. */
+typedef struct xamg_net xamg_net;
+
+typedef struct {
+  float lr, beta1, beta2, eps; /* Adam step size and decay rates; eps > 0 */
+} xamg_adam;
+
+int64_t xamg_net_param_count(void);
+
+/* Allocates a network for N^3 grids (N a multiple of 8, 8 <= N <= 1024) and
+ * batches of up to max_batch samples on the current device; parameters start
+ * at zero (set them with xamg_net_set_params). */
+int xamg_net_create(int32_t N, int32_t max_batch, xamg_net **out);
+void xamg_net_destroy(xamg_net *net);
+
+/* HOST flat parameter vectors (layout above); set also resets Adam. */
+int xamg_net_set_params(xamg_net *net, const float *params);
+int xamg_net_get_params(const xamg_net *net, float *params);
+
+/* out[b][v] = network output (channel 0) for the DEVICE input
+ * inp[b][v][2] (FP32 pairs: normalised right-hand side, log coefficient),
+ * v = (z N + y) N + x.  Returns after the work on `stream` has finished. */
+int xamg_net_forward(xamg_net *net, const float *inp, float *out, int32_t batch, void *stream);
+
+/* Loss L = mean over b, v of (out[b][v] - target[b][v])^2 (DEVICE target
+ * [batch][N^3] FP32) into *loss and, if grad != NULL, dL/dparams into the
+ * HOST array grad (flat layout).  XAMG_ERR_NONFINITE if L is not finite. */
+int xamg_net_loss_grad(xamg_net *net, const float *inp, const float *target, int32_t batch, float *loss,
+                       float *grad, void *stream);
+
+/* One Adam step on the loss of the samples idx[0..batch) (DEVICE int32
+ * indices into the DEVICE arrays inp[nsamples][N^3][2] and
+ * target[nsamples][N^3]); *loss (may be NULL) receives the loss before the
+ * step.  The indices are copied to the host and checked (each in
+ * [0, nsamples), else XAMG_ERR_INVALID_ARG and nothing is launched), so the
+ * call synchronizes `stream` once before its kernels. */
+int xamg_net_train_step(xamg_net *net, const float *inp, const float *target, int64_t nsamples,
+                        const int32_t *idx, int32_t batch, const xamg_adam *opt, float *loss, void *stream);
+
+/* Initial guess for the DEVICE n x m row-major block B (n = N^3, m <=
+ * min(max_batch, XAMG_MAX_RHS)) and DEVICE FP32 log coefficient logk[n]:
+ * column j is fed as B[:, j] / s_j with s_j = ||B[:, j]||_2 / sqrt(n), and
+ * X0[v][j] = out_j[v] * s_j * out_scale (a zero column gives X0 = 0).
+ * X0 is a DEVICE n x m row-major block.  Asynchronous on `stream`. */
+int xamg_net_predict_x0(xamg_net *net, const double *B, const float *logk, double out_scale, double *X0,
+                        int32_t m, void *stream);
+
+/* Single layers, for testing: BF16 tensors are uint16 bit patterns in DEVICE
+ * memory, channels-last [batch][N^3][c]; W is DEVICE FP32 [cout][27][cin],
+ * bias DEVICE FP32 [cout] or NULL; cin, cout in {8, 16}; any N >= 1.
+ * adjoint = 0: out[v][co] = relu?(b[co] + sum W[co][t][ci] in'[v + off_t][ci])
+ *              with in' = in * (mask > 0) if mask != NULL (mask shaped like in);
+ * adjoint = 1: the backward-data product: `in` has cout channels, out has
+ *              cin: out[v][ci] = sum W[co][t][ci] in'[v - off_t][co]
+ *              (bias must be NULL).
+ * Inputs outside the grid are zero.  Allocates (and frees) device
+ * temporaries; returns after the work on `stream` has finished. */
+int xamg_conv3d_bf16(const uint16_t *in, const uint16_t *mask, const float *w, const float *bias, uint16_t *out,
+                     int32_t batch, int32_t N, int32_t cin, int32_t cout, int32_t relu, int32_t adjoint,
+                     void *stream);
+
+/* Weight and bias gradients of one layer (DEVICE FP32 dw[cout][27][cin],
+ * db[cout]): dw[co][t][ci] = sum_{b,v} g[v][co] in[v + off_t][ci] and
+ * db[co] = sum g[v][co], with g = gout * (act > 0) if act != NULL else gout
+ * (gout and act: [batch][N^3][cout], in: [batch][N^3][cin]).  Sums are
+ * reduced in a fixed order. */
+int xamg_conv3d_bf16_wgrad(const uint16_t *in, const uint16_t *gout, const uint16_t *act, float *dw, float *db,
+                           int32_t batch, int32_t N, int32_t cin, int32_t cout, void *stream);
+
 /* ---- measurement ---- */
 
 /* Turns per-launch timing of the sparse row kernels on (1) or off (0).  When

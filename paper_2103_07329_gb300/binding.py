@@ -42,6 +42,9 @@ EXPORTS = [
     "xamg_coarse_solve",
     "xamg_coldot", "xamg_timing_enable", "xamg_timing_read", "xamg_kernel_launches",
     "xamg_coldot_noalloc",
+    "xamg_net_param_count", "xamg_net_create", "xamg_net_destroy", "xamg_net_set_params",
+    "xamg_net_get_params", "xamg_net_forward", "xamg_net_loss_grad", "xamg_net_train_step",
+    "xamg_net_predict_x0", "xamg_conv3d_bf16", "xamg_conv3d_bf16_wgrad",
 ]
 
 
@@ -66,6 +69,10 @@ class AmgParamsT(C.Structure):
 class SolveOptsT(C.Structure):
     _fields_ = [("method", C.c_int32), ("precond", C.c_int32), ("x0_given", C.c_int32),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+
+
+class AdamT(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
 
 
 class StatsT(C.Structure):
@@ -114,6 +121,18 @@ def _load():
         "xamg_kernel_launches": ([], C.c_int64),
         "xamg_timing_read": ([vp, i32, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl),
                               C.POINTER(dbl)], C.c_int),
+        "xamg_net_param_count": ([], C.c_int64),
+        "xamg_net_create": ([i32, i32, C.POINTER(vp)], C.c_int),
+        "xamg_net_destroy": ([vp], None),
+        "xamg_net_set_params": ([vp, vp], C.c_int),
+        "xamg_net_get_params": ([vp, vp], C.c_int),
+        "xamg_net_forward": ([vp, vp, vp, i32, vp], C.c_int),
+        "xamg_net_loss_grad": ([vp, vp, vp, i32, C.POINTER(C.c_float), vp, vp], C.c_int),
+        "xamg_net_train_step": ([vp, vp, vp, i64, vp, i32, C.POINTER(AdamT), C.POINTER(C.c_float), vp],
+                                C.c_int),
+        "xamg_net_predict_x0": ([vp, vp, vp, dbl, vp, i32, vp], C.c_int),
+        "xamg_conv3d_bf16": ([vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, vp], C.c_int),
+        "xamg_conv3d_bf16_wgrad": ([vp, vp, vp, vp, vp, i32, i32, i32, i32, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -351,3 +370,100 @@ def coldot_noalloc(U, V, out, stream=None):
     n, m = U.shape
     _check(_load().xamg_coldot_noalloc(_ptr(U), _ptr(V), n, m, _ptr(out), _stream(stream)),
            "xamg_coldot_noalloc")
+
+
+# ---- learned initial guess ----
+
+def net_param_count() -> int:
+    return int(_load().xamg_net_param_count())
+
+
+def _bits(t):
+    """Device address of a bf16 tensor passed as its uint16 bit patterns."""
+    return None if t is None else _ptr(t)
+
+
+def conv3d_bf16(x, w, bias=None, mask=None, relu=False, adjoint=False, stream=None):
+    """xamg_conv3d_bf16 on channels-last bf16 tensors x [batch, N, N, N, c];
+    w: float32 CUDA tensor [cout, 27, cin]. Returns the bf16 output tensor."""
+    import torch
+    batch, N = x.shape[0], x.shape[1]
+    cout, _, cin = w.shape
+    cres = cin if adjoint else cout
+    out = torch.empty((batch, N, N, N, cres), dtype=torch.bfloat16, device=x.device)
+    _check(_load().xamg_conv3d_bf16(_bits(x), _bits(mask), _ptr(w), _ptr(bias), _bits(out), batch, N,
+                                    cin, cout, 1 if relu else 0, 1 if adjoint else 0,
+                                    _stream(stream)), "xamg_conv3d_bf16")
+    return out
+
+
+def conv3d_bf16_wgrad(x, g, act=None, stream=None):
+    """xamg_conv3d_bf16_wgrad: (dW [cout, 27, cin], db [cout]) as float32 CUDA tensors."""
+    import torch
+    batch, N, cin, cout = x.shape[0], x.shape[1], x.shape[-1], g.shape[-1]
+    dw = torch.empty((cout, 27, cin), dtype=torch.float32, device=x.device)
+    db = torch.empty(cout, dtype=torch.float32, device=x.device)
+    _check(_load().xamg_conv3d_bf16_wgrad(_bits(x), _bits(g), _bits(act), _ptr(dw), _ptr(db), batch,
+                                          N, cin, cout, _stream(stream)), "xamg_conv3d_bf16_wgrad")
+    return dw, db
+
+
+class Net:
+    """Handle on the library's warm-start network (``xamg_net_create``)."""
+
+    def __init__(self, N: int, max_batch: int):
+        h = C.c_void_p()
+        _check(_load().xamg_net_create(N, max_batch, C.byref(h)), "xamg_net_create")
+        self._h = h
+        self.N = N
+        self.max_batch = max_batch
+        self.nparams = net_param_count()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().xamg_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.size == self.nparams
+        _check(_load().xamg_net_set_params(self._h, p.ctypes.data), "xamg_net_set_params")
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.nparams, np.float32)
+        _check(_load().xamg_net_get_params(self._h, p.ctypes.data), "xamg_net_get_params")
+        return p
+
+    def forward(self, inp, out, stream=None):
+        """inp: float32 CUDA [batch, N^3, 2]; out: float32 CUDA [batch, N^3]."""
+        _check(_load().xamg_net_forward(self._h, _ptr(inp), _ptr(out), inp.shape[0], _stream(stream)),
+               "xamg_net_forward")
+
+    def loss_grad(self, inp, target, stream=None):
+        """(loss, flat float32 gradient) of the mean squared error on one batch."""
+        g = np.empty(self.nparams, np.float32)
+        loss = C.c_float()
+        _check(_load().xamg_net_loss_grad(self._h, _ptr(inp), _ptr(target), inp.shape[0], C.byref(loss),
+                                          g.ctypes.data, _stream(stream)), "xamg_net_loss_grad")
+        return float(loss.value), g
+
+    def train_step(self, inp, target, idx, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None,
+                   want_loss=True):
+        opt = AdamT(lr, beta1, beta2, eps)
+        loss = C.c_float()
+        _check(_load().xamg_net_train_step(self._h, _ptr(inp), _ptr(target), inp.shape[0], _ptr(idx),
+                                           idx.shape[0],
+                                           C.byref(opt), C.byref(loss) if want_loss else None,
+                                           _stream(stream)), "xamg_net_train_step")
+        return float(loss.value) if want_loss else None
+
+    def predict_x0(self, B, logk, X0, out_scale: float, stream=None):
+        """X0 (float64 CUDA n x m) from B (float64 CUDA n x m) and logk (float32 CUDA n)."""
+        _check(_load().xamg_net_predict_x0(self._h, _ptr(B), _ptr(logk), out_scale, _ptr(X0), B.shape[1],
+                                           _stream(stream)), "xamg_net_predict_x0")

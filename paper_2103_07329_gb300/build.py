@@ -34,7 +34,8 @@ def sources():
                                             "rows_nv1.cu", "rows_nv2.cu", "rows_nv4.cu",
                                             "rows_nv8.cu", "rows_nv16.cu", "rows_nv32.cu",
                                             "rowsf_nv1.cu", "rowsf_nv2.cu", "rowsf_nv4.cu",
-                                            "rowsf_nv8.cu", "rowsf_nv16.cu", "rowsf_nv32.cu")]
+                                            "rowsf_nv8.cu", "rowsf_nv16.cu", "rowsf_nv32.cu",
+                                            "net.cu")]
 
 
 def _deps():

@@ -133,24 +133,59 @@ def diffusion7(N: int, kcell: np.ndarray) -> CSR:
                np.ascontiguousarray(vals[valid], dtype=np.float64))
 
 
-def grf(N: int, corr_len: float, sigma: float, seed: int, count: int = 1) -> np.ndarray:
-    """`count` Gaussian random fields on the periodic N^3 grid of the unit cube,
+def grf(N: int, corr_len: float, sigma: float, seed: int, count: int = 1, pad: int = 1,
+        dtype=np.float64) -> np.ndarray:
+    """`count` Gaussian random fields on the N^3 cell grid of the unit cube,
     squared-exponential covariance sigma^2 exp(-r^2 / (2 corr_len^2)).
 
-    White noise (numpy default_rng(seed)) is convolved, by FFT on the periodic
-    grid, with exp(-r^2 / corr_len^2), whose self-convolution is the
-    squared-exponential kernel; the result is scaled by the filter's L2 norm
-    so that each point has variance sigma^2.  Returns count x N^3 (lexicographic,
-    i fastest)."""
+    White noise (numpy default_rng(seed), drawn on the periodic grid of edge
+    pad * N and spacing 1/N) is convolved by FFT with exp(-r^2 / corr_len^2),
+    whose self-convolution is the squared-exponential kernel, and scaled by
+    the filter's L2 norm so that each point has variance sigma^2; the first
+    N^3 points are returned.  pad = 1 gives a periodic field; pad = 2 removes
+    the wrap-around (for lags up to N cells the periodic distance on the
+    padded grid is the true distance).  Returns count x N^3 (lexicographic, i
+    fastest) in `dtype` (float32 halves the work of large batches)."""
+    import scipy.fft as sfft
+    M = N * pad
     h = 1.0 / N
-    d = np.minimum(np.arange(N), N - np.arange(N)) * h          # periodic distance
+    d = np.minimum(np.arange(M), M - np.arange(M)) * h          # periodic distance
     r2 = d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2
-    g = np.exp(-r2 / corr_len ** 2)
-    G = np.fft.rfftn(g)
-    scale = sigma / np.sqrt((g * g).sum())
-    w = np.random.default_rng(seed).standard_normal((count, N, N, N))
-    f = np.fft.irfftn(np.fft.rfftn(w, axes=(1, 2, 3)) * G, s=(N, N, N), axes=(1, 2, 3)) * scale
-    return f.reshape(count, -1)
+    g = np.exp(-r2 / corr_len ** 2).astype(dtype)
+    G = sfft.rfftn(g, workers=-1)
+    scale = sigma / np.sqrt((g.astype(np.float64) ** 2).sum())
+    w = np.random.default_rng(seed).standard_normal((count, M, M, M), dtype=dtype)
+    f = sfft.irfftn(sfft.rfftn(w, axes=(1, 2, 3), workers=-1) * G, s=(M, M, M), axes=(1, 2, 3),
+                    workers=-1)
+    f = f[:, :N, :N, :N] * dtype(scale)
+    return np.ascontiguousarray(f.reshape(count, -1), dtype=dtype)
+
+
+# (cin, cout) of the warm-start network's 13 convolutions, in the order of its
+# flat parameter vector (per layer W[cout][27][cin], then b[cout]).
+NET_LAYERS = [(8, 8), (8, 8), (8, 16), (16, 16), (16, 16), (16, 16), (16, 16), (16, 16), (16, 16),
+              (16, 16), (16, 8), (8, 8), (8, 8)]
+
+
+def net_init(seed: int) -> np.ndarray:
+    """He-normal initial weights of the warm-start network (std sqrt(2 / fan_in),
+    fan_in = 27 x used input channels; the last, linear layer sqrt(1 / fan_in)),
+    zero biases.  The first layer uses 2 of its 8 input channels and the last
+    1 of its 8 outputs; the other weights there start (and stay) zero."""
+    rng = np.random.default_rng(seed)
+    out = []
+    last = len(NET_LAYERS) - 1
+    for l, (ci, co) in enumerate(NET_LAYERS):
+        ci_used = 2 if l == 0 else ci
+        std = np.sqrt((1.0 if l == last else 2.0) / (27 * ci_used))
+        W = rng.standard_normal((co, 27, ci)) * std
+        if l == 0:
+            W[:, :, 2:] = 0.0
+        if l == last:
+            W[1:] = 0.0
+        out.append(W.reshape(-1))
+        out.append(np.zeros(co))
+    return np.concatenate(out).astype(np.float32)
 
 
 def rhs_uniform(n: int, m: int, seed: int = 0, m_draw: int | None = None) -> np.ndarray:

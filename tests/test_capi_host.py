@@ -23,7 +23,7 @@ def built():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "xamg_gpu.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(xamg_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(xamg_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_every_declared_symbol_is_exported():
