@@ -319,25 +319,45 @@ void xamg_net_destroy(xamg_net *net);
 int xamg_net_set_params(xamg_net *net, const float *params);
 int xamg_net_get_params(const xamg_net *net, float *params);
 
-/* out[b][v] = network output (channel 0) for the DEVICE input
- * inp[b][v][2] (FP32 pairs: normalised right-hand side, log coefficient),
- * v = (z N + y) N + x.  Returns after the work on `stream` has finished. */
+/* out[b][v] = network output (FP32 channel 0 of the last layer) for the
+ * DEVICE input inp[b][v][2] (FP32 pairs: normalised right-hand side, log
+ * coefficient), v = (z N + y) N + x; out is a DEVICE [batch][N^3] array.
+ * Returns after the work on `stream` has finished. */
 int xamg_net_forward(xamg_net *net, const float *inp, float *out, int32_t batch, void *stream);
 
-/* Loss L = mean over b, v of (out[b][v] - target[b][v])^2 (DEVICE target
- * [batch][N^3] FP32) into *loss and, if grad != NULL, dL/dparams into the
- * HOST array grad (flat layout).  XAMG_ERR_NONFINITE if L is not finite. */
-int xamg_net_loss_grad(xamg_net *net, const float *inp, const float *target, int32_t batch, float *loss,
-                       float *grad, void *stream);
+/* Training loss.  With e_b = out_b - target_b for sample b of a batch and
+ * w_b = sample_weight[row of b] (1 if sample_weight is NULL):
+ *   XAMG_NET_LOSS_MSE:    L = sum_b w_b |e_b|^2 / (batch N^3)
+ *   XAMG_NET_LOSS_ENERGY: L = sum_b w_b e_b^T A_b e_b / batch, with A_b the
+ *     cell-centred diffusion operator on the N^3 grid of unit cells whose log
+ *     coefficient is the sample's input channel 1 (face transmissibility
+ *     2 k_a k_c / (k_a + k_c) between cells, 2 k_c on a boundary face).
+ * The energy norm is the norm in which PCG's error decreases, so it weighs
+ * the parts of e that the solve would otherwise have to remove. */
+#define XAMG_NET_LOSS_MSE 0
+#define XAMG_NET_LOSS_ENERGY 1
+typedef struct {
+  int32_t kind;                /* XAMG_NET_LOSS_MSE or XAMG_NET_LOSS_ENERGY */
+  const float *sample_weight;  /* DEVICE, one per sample row, or NULL */
+} xamg_net_loss;
+
+/* Loss L (lo NULL: unweighted MSE) of the DEVICE batch inp[batch][N^3][2],
+ * target[batch][N^3] (FP32) into *loss and, if grad != NULL, dL/dparams into
+ * the HOST array grad (flat layout); sample_weight is indexed by b.
+ * XAMG_ERR_NONFINITE if L is not finite. */
+int xamg_net_loss_grad(xamg_net *net, const float *inp, const float *target, int32_t batch,
+                       const xamg_net_loss *lo, float *loss, float *grad, void *stream);
 
 /* One Adam step on the loss of the samples idx[0..batch) (DEVICE int32
  * indices into the DEVICE arrays inp[nsamples][N^3][2] and
- * target[nsamples][N^3]); *loss (may be NULL) receives the loss before the
- * step.  The indices are copied to the host and checked (each in
- * [0, nsamples), else XAMG_ERR_INVALID_ARG and nothing is launched), so the
- * call synchronizes `stream` once before its kernels. */
+ * target[nsamples][N^3]; sample_weight is indexed by idx[b]); *loss (may be
+ * NULL) receives the loss before the step.  The indices are copied to the
+ * host and checked (each in [0, nsamples), else XAMG_ERR_INVALID_ARG and
+ * nothing is launched), so the call synchronizes `stream` once before its
+ * kernels. */
 int xamg_net_train_step(xamg_net *net, const float *inp, const float *target, int64_t nsamples,
-                        const int32_t *idx, int32_t batch, const xamg_adam *opt, float *loss, void *stream);
+                        const int32_t *idx, int32_t batch, const xamg_net_loss *lo, const xamg_adam *opt,
+                        float *loss, void *stream);
 
 /* Initial guess for the DEVICE n x m row-major block B (n = N^3, m <=
  * min(max_batch, XAMG_MAX_RHS)) and DEVICE FP32 log coefficient logk[n]:

@@ -26,9 +26,18 @@ the gradient routines torch.nn.grad.conv3d_input / conv3d_weight) or a plain
 tensor expression, evaluated in FP64.  With ``emulate=True`` the values the
 CUDA kernels store in BF16 (activations, activation gradients, weights as
 tensor-core operands, the packed input) are rounded to BF16 at the same
-points; everything else stays FP64.  The backward pass is written out layer
-by layer in reverse order (no autograd), so tests can pin it against finite
-differences of the FP64 forward pass.
+points; everything else stays FP64.  The network output (channel 0 of the
+last layer) is kept unrounded, as the kernels store it in FP32.  The backward
+pass is written out layer by layer in reverse order (no autograd), so tests
+can pin it against finite differences of the FP64 forward pass.
+
+Two losses, for e_b = y_b - t_b and sample weights w_b:
+  "mse":    sum_b w_b |e_b|^2 / (batch N^3)
+  "energy": sum_b w_b e_b^T A_b e_b / batch, A_b the cell-centred diffusion
+            operator of unit cells with log coefficient = input channel 1:
+            (A e)_c = sum over the six faces of T_f (e_c - e_nb), T_f =
+            2 k_c k_nb / (k_c + k_nb), and T_f e_c with T_f = 2 k_c on a
+            boundary face.
 """
 from __future__ import annotations
 
@@ -127,6 +136,31 @@ def pack_input(inp, N):
     return x
 
 
+def energy_apply(e, logk, N):
+    """(A e) for one sample: e, logk flat [N^3] (x fastest), A as above."""
+    e = e.reshape(N, N, N)
+    k = torch.exp(logk.reshape(N, N, N))
+    out = torch.zeros_like(e)
+    for ax in range(3):
+        # interior faces between cells i and i+1 along axis ax
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax] = slice(0, N - 1)
+        hi[ax] = slice(1, N)
+        lo, hi = tuple(lo), tuple(hi)
+        T = 2.0 * k[lo] * k[hi] / (k[lo] + k[hi])
+        flux = T * (e[lo] - e[hi])
+        out[lo] += flux
+        out[hi] -= flux
+        # the two boundary faces
+        for end in (0, N - 1):
+            sl = [slice(None)] * 3
+            sl[ax] = slice(end, end + 1)
+            sl = tuple(sl)
+            out[sl] += 2.0 * k[sl] * e[sl]
+    return out.reshape(-1)
+
+
 class Net:
     """Forward and backward passes of the network for one parameter vector."""
 
@@ -137,12 +171,12 @@ class Net:
         self.R = R
         self.Wq = [R(W) for W, _ in self.layers]  # tensor-core operands
 
-    def _conv(self, l, x):
+    def _conv(self, l, x, store=True):
         _, b = self.layers[l]
         y = conv(x, self.Wq[l], b)
         if LAYERS[l][2]:
             y = torch.clamp_min(y, 0.0)
-        return self.R(y)
+        return self.R(y) if store else y
 
     def forward(self, inp, N):
         R = self.R
@@ -166,23 +200,34 @@ class Net:
         a["d1b"] = self._conv(10, a["d1a"])
         a["u0"] = R(up(a["d1b"]) + a["s0"])
         a["d0a"] = self._conv(11, a["u0"])
-        a["y"] = self._conv(12, a["d0a"])
+        a["y"] = self._conv(12, a["d0a"], store=False)
         self.a = a
         return a["y"][..., 0].reshape(a["y"].shape[0], -1)
 
-    def loss(self, inp, target, N):
-        """Mean over samples and voxels of (output - target)^2."""
+    def loss(self, inp, target, N, kind="mse", weight=None):
+        """(L, y, t, dL/dy) for the batch."""
         y = self.forward(inp, N)
         t = torch.as_tensor(np.asarray(target, dtype=np.float64)).reshape(y.shape)
-        return float(((y - t) ** 2).mean()), y, t
+        Bn = y.shape[0]
+        w = torch.ones(Bn, dtype=f64) if weight is None else torch.as_tensor(np.asarray(weight, np.float64))
+        e = y - t
+        if kind == "mse":
+            L = float((w[:, None] * e * e).sum() / e.numel())
+            gy = 2.0 * w[:, None] * e / e.numel()
+        else:
+            logk = torch.as_tensor(np.asarray(inp, dtype=np.float64))[..., 1]
+            Ae = torch.stack([energy_apply(e[b], logk[b], N) for b in range(Bn)])
+            L = float((w[:, None] * e * Ae).sum() / Bn)
+            gy = 2.0 * w[:, None] * Ae / Bn
+        return L, y, t, gy
 
-    def grads(self, inp, target, N):
+    def grads(self, inp, target, N, kind="mse", weight=None):
         """(loss, [(dW, db)] per layer) by the backward pass in reverse layer order."""
         R = self.R
-        L, y, t = self.loss(inp, target, N)
+        L, y, t, g0 = self.loss(inp, target, N, kind, weight)
         a = self.a
         gy = torch.zeros_like(a["y"])
-        gy[..., 0] = R((2.0 / y.numel()) * (y - t)).reshape(a["y"].shape[:-1])
+        gy[..., 0] = R(g0).reshape(a["y"].shape[:-1])
         g = {"y": gy}
         dW = [None] * len(LAYERS)
         ins = ["x", "e0a", "p0", "e1a", "p1", "e2a", "p2", "e3a", "u2", "u1", "d1a", "u0", "d0a"]

@@ -75,6 +75,14 @@ class AdamT(C.Structure):
     _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
 
 
+class NetLossT(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("sample_weight", C.c_void_p)]
+
+
+LOSS_MSE = 0
+LOSS_ENERGY = 1
+
+
 class StatsT(C.Structure):
     _fields_ = [("iters", C.c_void_p), ("relres", C.c_void_p), ("status", C.c_void_p),
                 ("iterations", C.c_int32), ("vcycles", C.c_int32)]
@@ -127,9 +135,10 @@ def _load():
         "xamg_net_set_params": ([vp, vp], C.c_int),
         "xamg_net_get_params": ([vp, vp], C.c_int),
         "xamg_net_forward": ([vp, vp, vp, i32, vp], C.c_int),
-        "xamg_net_loss_grad": ([vp, vp, vp, i32, C.POINTER(C.c_float), vp, vp], C.c_int),
-        "xamg_net_train_step": ([vp, vp, vp, i64, vp, i32, C.POINTER(AdamT), C.POINTER(C.c_float), vp],
-                                C.c_int),
+        "xamg_net_loss_grad": ([vp, vp, vp, i32, C.POINTER(NetLossT), C.POINTER(C.c_float), vp, vp],
+                               C.c_int),
+        "xamg_net_train_step": ([vp, vp, vp, i64, vp, i32, C.POINTER(NetLossT), C.POINTER(AdamT),
+                                 C.POINTER(C.c_float), vp], C.c_int),
         "xamg_net_predict_x0": ([vp, vp, vp, dbl, vp, i32, vp], C.c_int),
         "xamg_conv3d_bf16": ([vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, vp], C.c_int),
         "xamg_conv3d_bf16_wgrad": ([vp, vp, vp, vp, vp, i32, i32, i32, i32, vp], C.c_int),
@@ -445,23 +454,28 @@ class Net:
         _check(_load().xamg_net_forward(self._h, _ptr(inp), _ptr(out), inp.shape[0], _stream(stream)),
                "xamg_net_forward")
 
-    def loss_grad(self, inp, target, stream=None):
-        """(loss, flat float32 gradient) of the mean squared error on one batch."""
+    def loss_grad(self, inp, target, loss=LOSS_MSE, weight=None, stream=None):
+        """(loss, flat float32 gradient) on one batch; weight: float32 CUDA [batch] or None."""
         g = np.empty(self.nparams, np.float32)
-        loss = C.c_float()
-        _check(_load().xamg_net_loss_grad(self._h, _ptr(inp), _ptr(target), inp.shape[0], C.byref(loss),
-                                          g.ctypes.data, _stream(stream)), "xamg_net_loss_grad")
-        return float(loss.value), g
+        lv = C.c_float()
+        lo = NetLossT(loss, _ptr(weight))
+        _check(_load().xamg_net_loss_grad(self._h, _ptr(inp), _ptr(target), inp.shape[0], C.byref(lo),
+                                          C.byref(lv), g.ctypes.data, _stream(stream)),
+               "xamg_net_loss_grad")
+        return float(lv.value), g
 
-    def train_step(self, inp, target, idx, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None,
-                   want_loss=True):
+    def train_step(self, inp, target, idx, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, loss=LOSS_MSE,
+                   weight=None, stream=None, want_loss=True):
+        """One Adam step on samples idx (int32 CUDA) of inp/target; weight:
+        float32 CUDA [nsamples] or None."""
         opt = AdamT(lr, beta1, beta2, eps)
-        loss = C.c_float()
+        lo = NetLossT(loss, _ptr(weight))
+        lv = C.c_float()
         _check(_load().xamg_net_train_step(self._h, _ptr(inp), _ptr(target), inp.shape[0], _ptr(idx),
-                                           idx.shape[0],
-                                           C.byref(opt), C.byref(loss) if want_loss else None,
-                                           _stream(stream)), "xamg_net_train_step")
-        return float(loss.value) if want_loss else None
+                                           idx.shape[0], C.byref(lo), C.byref(opt),
+                                           C.byref(lv) if want_loss else None, _stream(stream)),
+               "xamg_net_train_step")
+        return float(lv.value) if want_loss else None
 
     def predict_x0(self, B, logk, X0, out_scale: float, stream=None):
         """X0 (float64 CUDA n x m) from B (float64 CUDA n x m) and logk (float32 CUDA n)."""

@@ -146,14 +146,16 @@ __device__ __forceinline__ void stage_brick(bf16 *dst, const bf16 *__restrict__ 
 }
 
 // out = [relu](conv(in [* (mask > 0)]) + bias); wt: BF16 [COUT][kpad(CIN)]
-// with k = t CIN + ci and zeros for k >= 27 CIN.  Blocks loop over the
-// `total` bricks (samples x nb^3).
+// with k = t CIN + ci and zeros for k >= 27 CIN.  With out0 != NULL only
+// output channel 0 is stored, in FP32, to out0[sample][voxel] (out unused).
+// Blocks loop over the `total` bricks (samples x nb^3).
 template <int CIN, int COUT, bool RELU>
 __global__ void __launch_bounds__(kThreads) k_conv3(const bf16 *__restrict__ in,
                                                     const bf16 *__restrict__ mask,
                                                     const bf16 *__restrict__ wt,
                                                     const float *__restrict__ bias,
-                                                    bf16 *__restrict__ out, int N, int nb, int total) {
+                                                    bf16 *__restrict__ out, float *__restrict__ out0,
+                                                    int N, int nb, int total) {
   constexpr int VS = vstride(CIN), KP = kpad(CIN), KS = kstride(CIN), NT = COUT / 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   bf16 *in_s = reinterpret_cast<bf16 *>(smem_raw);
@@ -229,7 +231,15 @@ __global__ void __launch_bounds__(kThreads) k_conv3(const bf16 *__restrict__ in,
         for (int h = 0; h < 2; ++h) {
           const int gy = bk.y0 + 2 * mt + h;
           if (gy >= N) continue;
-          const int64_t o = (bk.sbase + ((int64_t)gz * N + gy) * N + gx) * COUT + 2 * tq;
+          const int64_t vox = bk.sbase + ((int64_t)gz * N + gy) * N + gx;
+          if (out0) {
+            if (tq == 0) {
+              const float v0 = acc[mt][0][2 * h] + bv[0][0];
+              out0[vox] = RELU ? fmaxf(v0, 0.0f) : v0;
+            }
+            continue;
+          }
+          const int64_t o = vox * COUT + 2 * tq;
 #pragma unroll
           for (int nt = 0; nt < NT; ++nt) {
             float v0 = acc[mt][nt][2 * h] + bv[nt][0], v1 = acc[mt][nt][2 * h + 1] + bv[nt][1];
@@ -481,44 +491,99 @@ __global__ void k_pack_rhs(const double *__restrict__ B, int m, const double *__
   *reinterpret_cast<uint4 *>(out + ((int64_t)j * n + v) * 8) = make_uint4(pack2(c0, __ldg(logk + v)), 0u, 0u, 0u);
 }
 
-// X0[v][j] = y_j[v] * s_j * scale
-__global__ void k_unpack_x0(const bf16 *__restrict__ y, int m, const double *__restrict__ ss, int64_t n,
+// X0[v][j] = y[j][v] * s_j * scale
+__global__ void k_unpack_x0(const float *__restrict__ y, int m, const double *__restrict__ ss, int64_t n,
                             double scale, double *__restrict__ X0) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * m) return;
   const int j = (int)(i % m);
   const int64_t v = i / m;
   const double s = sqrt(ss[j] / (double)n);
-  X0[i] = (double)__bfloat162float(y[((int64_t)j * n + v) * 8]) * s * scale;
+  X0[i] = (double)y[(int64_t)j * n + v] * s * scale;
 }
 
-__global__ void k_unpack_output(const bf16 *__restrict__ y, float *__restrict__ out, int64_t total) {
-  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < total) out[v] = __bfloat162float(y[8 * v]);
+__device__ __forceinline__ int64_t sample_row(const int32_t *idx, int b) {
+  return idx ? (int64_t)idx[b] : (int64_t)b;
 }
 
-// loss partials: lpart[block] = inv * sum over its voxels of (y - t)^2, and
-// the output gradient gy = (2 inv (y - t), 0 x 7); target row src = idx[b] or b
-__global__ void __launch_bounds__(kThreads) k_mse(const bf16 *__restrict__ y, const float *__restrict__ target,
-                                                  const int32_t *__restrict__ idx, int64_t V, int batch,
-                                                  float inv, bf16 *__restrict__ gy, float *__restrict__ lpart) {
-  __shared__ float red[kThreads];
-  float s = 0.0f;
-  const int64_t total = V * batch;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int b = (int)(i / V);
-    const int64_t src = (idx ? (int64_t)idx[b] : (int64_t)b) * V + i % V;
-    const float d = __bfloat162float(y[8 * i]) - __ldg(target + src);
-    s = fmaf(d, d, s);
-    *reinterpret_cast<uint4 *>(gy + 8 * i) = make_uint4(pack2(2.0f * inv * d, 0.0f), 0u, 0u, 0u);
-  }
+__device__ __forceinline__ float block_sum(float s, float *red) {
   red[threadIdx.x] = s;
   __syncthreads();
   for (int o = kThreads / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) lpart[blockIdx.x] = red[0] * inv;
+  return red[0];
+}
+
+// Mean squared error: lpart[block] = inv * sum over its voxels of
+// w_b (y - t)^2 and the output gradient gy = (2 inv w_b (y - t), 0 x 7), with
+// inv = 1 / (batch N^3), w_b = wsample[src] (1 if NULL), src = idx[b] or b.
+__global__ void __launch_bounds__(kThreads) k_mse(const float *__restrict__ y, const float *__restrict__ target,
+                                                  const int32_t *__restrict__ idx,
+                                                  const float *__restrict__ wsample, int64_t V, int batch,
+                                                  float inv, bf16 *__restrict__ gy, float *__restrict__ lpart) {
+  __shared__ float red[kThreads];
+  float s = 0.0f;
+  const int64_t total = V * batch;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / V);
+    const int64_t src = sample_row(idx, b);
+    const float w = wsample ? __ldg(wsample + src) : 1.0f;
+    const float d = y[i] - __ldg(target + src * V + i % V);
+    s = fmaf(w * d, d, s);
+    *reinterpret_cast<uint4 *>(gy + 8 * i) = make_uint4(pack2(2.0f * inv * w * d, 0.0f), 0u, 0u, 0u);
+  }
+  const float t = block_sum(s, red);
+  if (threadIdx.x == 0) lpart[blockIdx.x] = t * inv;
+}
+
+// Energy-norm loss of the cell-centred diffusion operator A_b whose log
+// coefficient is channel 1 of the sample's input (inp[src][v][1]), the
+// operator of problems.diffusion7 (face transmissibility 2 k_a k_c / (k_a +
+// k_c) between cells, 2 k_c on a boundary face):
+//   L = (1 / batch) sum_b w_b e_b^T A_b e_b,  e_b = y_b - t_b,
+//   dL/dy_b = (2 / batch) w_b A_b e_b.
+// lpart[block] = the block's share of L; gy = (dL/dy, 0 x 7).
+__global__ void __launch_bounds__(kThreads) k_energy(const float *__restrict__ y, const float *__restrict__ target,
+                                                     const float *__restrict__ inp, const int32_t *__restrict__ idx,
+                                                     const float *__restrict__ wsample, int N, int batch,
+                                                     float invb, bf16 *__restrict__ gy, float *__restrict__ lpart) {
+  __shared__ float red[kThreads];
+  const int64_t V = (int64_t)N * N * N;
+  float s = 0.0f;
+  const int64_t total = V * batch;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / V);
+    const int64_t v = i % V;
+    const int64_t src = sample_row(idx, b);
+    const float w = wsample ? __ldg(wsample + src) : 1.0f;
+    const float *lk = inp + src * V * 2 + 1;  // log k, stride 2
+    const float *tg = target + src * V;
+    const float *yb = y + (int64_t)b * V;
+    const int x = (int)(v % N), yy = (int)((v / N) % N), z = (int)(v / ((int64_t)N * N));
+    const float kc = expf(__ldg(lk + 2 * v));
+    const float ec = yb[v] - __ldg(tg + v);
+    float ae = 0.0f;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int d = (f & 1) ? 1 : -1;
+      const int ax = f >> 1;  // 0: x, 1: y, 2: z
+      const int c = ax == 0 ? x : (ax == 1 ? yy : z);
+      if (c + d < 0 || c + d >= N) {
+        ae = fmaf(2.0f * kc, ec, ae);
+        continue;
+      }
+      const int64_t nb = v + (int64_t)d * (ax == 0 ? 1 : (ax == 1 ? (int64_t)N : (int64_t)N * N));
+      const float kn = expf(__ldg(lk + 2 * nb));
+      const float T = 2.0f * kc * kn / (kc + kn);
+      ae = fmaf(T, ec - (yb[nb] - __ldg(tg + nb)), ae);
+    }
+    s = fmaf(w * ec, ae, s);
+    *reinterpret_cast<uint4 *>(gy + 8 * i) = make_uint4(pack2(2.0f * invb * w * ae, 0.0f), 0u, 0u, 0u);
+  }
+  const float t = block_sum(s, red);
+  if (threadIdx.x == 0) lpart[blockIdx.x] = t * invb;
 }
 
 // Adam (Kingma & Ba 2015) on the FP32 parameters; c1 = 1 - b1^t, c2 = 1 - b2^t
@@ -557,8 +622,8 @@ __global__ void k_prep_weights(const float *__restrict__ W, bf16 *__restrict__ w
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 template <int CIN, int COUT, bool RELU>
-cudaError_t conv_t(const bf16 *in, const bf16 *mask, const bf16 *wt, const float *bias, bf16 *out, int batch,
-                   int N, cudaStream_t st) {
+cudaError_t conv_t(const bf16 *in, const bf16 *mask, const bf16 *wt, const float *bias, bf16 *out, float *out0,
+                   int batch, int N, cudaStream_t st) {
   constexpr size_t sm = fwd_smem<CIN, COUT>();
   static bool attr = false;
   if (!attr) {
@@ -569,17 +634,17 @@ cudaError_t conv_t(const bf16 *in, const bf16 *mask, const bf16 *wt, const float
   const int nb = (N + 7) / 8;
   const int total = nb * nb * nb * batch;
   const int grid = (int)std::min<int64_t>(total, (int64_t)device_sm_count() * 3);
-  k_conv3<CIN, COUT, RELU><<<grid, kThreads, sm, st>>>(in, mask, wt, bias, out, N, nb, total);
+  k_conv3<CIN, COUT, RELU><<<grid, kThreads, sm, st>>>(in, mask, wt, bias, out, out0, N, nb, total);
   ++g_launches;
   return cudaGetLastError();
 }
 
 cudaError_t conv(int cin, int cout, bool relu, const bf16 *in, const bf16 *mask, const bf16 *wt,
-                 const float *bias, bf16 *out, int batch, int N, cudaStream_t st) {
+                 const float *bias, bf16 *out, int batch, int N, cudaStream_t st, float *out0 = nullptr) {
 #define XAMG_CONV_CASE(CI, CO)                                                \
   if (cin == CI && cout == CO)                                                \
-    return relu ? conv_t<CI, CO, true>(in, mask, wt, bias, out, batch, N, st) \
-                : conv_t<CI, CO, false>(in, mask, wt, bias, out, batch, N, st);
+    return relu ? conv_t<CI, CO, true>(in, mask, wt, bias, out, out0, batch, N, st) \
+                : conv_t<CI, CO, false>(in, mask, wt, bias, out, out0, batch, N, st);
   XAMG_CONV_CASE(8, 8)
   XAMG_CONV_CASE(8, 16)
   XAMG_CONV_CASE(16, 8)
@@ -705,6 +770,7 @@ struct xamg_net {
   bf16 *wt[kLayers] = {}, *wb[kLayers] = {};
   bf16 *act[T_COUNT] = {}, *grad[T_COUNT] = {};
   float *part = nullptr, *bpart = nullptr, *lpart = nullptr, *loss_d = nullptr;
+  float *y32 = nullptr;       // FP32 network output [max_batch][N^3]
   double *ss = nullptr;       // column sums of squares of the last predicted block
   double *ss_part = nullptr;
   int steps = 0;
@@ -751,13 +817,15 @@ int refresh_weights(xamg_net *net, cudaStream_t st) {
   return XAMG_OK;
 }
 
-int forward(xamg_net *net, int batch, cudaStream_t st) {
+// Forward pass of `batch` packed samples in act[T_X]; the output (channel 0
+// of the last layer, FP32) goes to y[batch][N^3].
+int forward(xamg_net *net, int batch, float *y, cudaStream_t st) {
   const int N = net->N;
   auto edge = [&](int t) { return N >> kTensors[t].level; };
   auto L = [&](int l) -> cudaError_t {
     const LayerDef &d = kLayerDefs[l];
     return conv(d.cin, d.cout, d.relu != 0, net->act[d.in], nullptr, net->wt[l], net->W + net->boff[l],
-                net->act[d.out], batch, edge(d.out), st);
+                net->act[d.out], batch, edge(d.out), st, l == kLayers - 1 ? y : nullptr);
   };
   NCK(L(0));
   NCK(L(1));
@@ -832,11 +900,16 @@ int backward(xamg_net *net, int batch, cudaStream_t st) {
   return XAMG_OK;
 }
 
-int loss_and_output_grad(xamg_net *net, const float *target, const int32_t *idx, int batch, cudaStream_t st) {
+int loss_and_output_grad(xamg_net *net, const float *inp, const float *target, const int32_t *idx,
+                         const float *wsample, int kind, int batch, cudaStream_t st) {
   const int64_t V = level_vox(net, 0);
-  const float inv = (float)(1.0 / ((double)V * batch));
   const int grid = (int)std::min<int64_t>(kLossGrid, cdiv(V * batch, kThreads));
-  k_mse<<<grid, kThreads, 0, st>>>(net->act[T_Y], target, idx, V, batch, inv, net->grad[T_Y], net->lpart);
+  if (kind == XAMG_NET_LOSS_ENERGY)
+    k_energy<<<grid, kThreads, 0, st>>>(net->y32, target, inp, idx, wsample, net->N, batch, 1.0f / batch,
+                                        net->grad[T_Y], net->lpart);
+  else
+    k_mse<<<grid, kThreads, 0, st>>>(net->y32, target, idx, wsample, V, batch, (float)(1.0 / ((double)V * batch)),
+                                     net->grad[T_Y], net->lpart);
   k_reduce_parts<<<1, 32, 0, st>>>(net->lpart, grid, 1, net->loss_d);
   g_launches += 2;
   NCK(cudaGetLastError());
@@ -910,6 +983,7 @@ int xamg_net_create(int32_t N, int32_t max_batch, xamg_net **out) {
   A(&net->part, (size_t)kWgradGrid * 16 * kpad(16));
   A(&net->bpart, (size_t)kWgradGrid * 16);
   A(&net->lpart, (size_t)kLossGrid);
+  A(&net->y32, (size_t)level_vox(net, 0) * max_batch);
   A(&net->loss_d, 1);
   A(&net->ss, XAMG_MAX_RHS);
   A(&net->ss_part, (size_t)kMaxGrid * XAMG_MAX_RHS);
@@ -955,33 +1029,39 @@ int xamg_net_forward(xamg_net *net, const float *inp, float *out, int32_t batch,
   NCK(cudaSetDevice(net->device));
   NRET(refresh_weights(net, st));
   NRET(pack_input(net, inp, nullptr, batch, st));
-  NRET(forward(net, batch, st));
-  const int64_t total = level_vox(net, 0) * batch;
-  k_unpack_output<<<(int)cdiv(total, 256), 256, 0, st>>>(net->act[T_Y], out, total);
-  ++g_launches;
-  NCK(cudaGetLastError());
+  NRET(forward(net, batch, out, st));
   NCK(cudaStreamSynchronize(st));
   return XAMG_OK;
 }
 
-int xamg_net_loss_grad(xamg_net *net, const float *inp, const float *target, int32_t batch, float *loss,
-                       float *grad, void *stream) {
+namespace {
+int check_loss(const xamg_net_loss *lo) {
+  if (lo && lo->kind != XAMG_NET_LOSS_MSE && lo->kind != XAMG_NET_LOSS_ENERGY) return XAMG_ERR_INVALID_ARG;
+  return XAMG_OK;
+}
+}  // namespace
+
+int xamg_net_loss_grad(xamg_net *net, const float *inp, const float *target, int32_t batch,
+                       const xamg_net_loss *lo, float *loss, float *grad, void *stream) {
   NRET(check_net(net, batch));
+  NRET(check_loss(lo));
   if (!inp || !target) return XAMG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   NCK(cudaSetDevice(net->device));
   NRET(refresh_weights(net, st));
   NRET(pack_input(net, inp, nullptr, batch, st));
-  NRET(forward(net, batch, st));
-  NRET(loss_and_output_grad(net, target, nullptr, batch, st));
+  NRET(forward(net, batch, net->y32, st));
+  NRET(loss_and_output_grad(net, inp, target, nullptr, lo ? lo->sample_weight : nullptr,
+                            lo ? lo->kind : XAMG_NET_LOSS_MSE, batch, st));
   NRET(backward(net, batch, st));
   if (grad) NCK(cudaMemcpyAsync(grad, net->G, net->np * sizeof(float), cudaMemcpyDeviceToHost, st));
   return read_loss(net, loss, st);
 }
 
 int xamg_net_train_step(xamg_net *net, const float *inp, const float *target, int64_t nsamples, const int32_t *idx,
-                        int32_t batch, const xamg_adam *opt, float *loss, void *stream) {
+                        int32_t batch, const xamg_net_loss *lo, const xamg_adam *opt, float *loss, void *stream) {
   NRET(check_net(net, batch));
+  NRET(check_loss(lo));
   if (!inp || !target || !idx || !opt || nsamples < 1 || !(opt->lr > 0.0f) ||
       !(opt->beta1 >= 0.0f && opt->beta1 < 1.0f) || !(opt->beta2 >= 0.0f && opt->beta2 < 1.0f) ||
       !(opt->eps > 0.0f))
@@ -997,8 +1077,9 @@ int xamg_net_train_step(xamg_net *net, const float *inp, const float *target, in
   }
   NRET(refresh_weights(net, st));
   NRET(pack_input(net, inp, idx, batch, st));
-  NRET(forward(net, batch, st));
-  NRET(loss_and_output_grad(net, target, idx, batch, st));
+  NRET(forward(net, batch, net->y32, st));
+  NRET(loss_and_output_grad(net, inp, target, idx, lo ? lo->sample_weight : nullptr,
+                            lo ? lo->kind : XAMG_NET_LOSS_MSE, batch, st));
   NRET(backward(net, batch, st));
   const int t = net->steps + 1;
   const float c1 = 1.0f - std::pow(opt->beta1, (float)t), c2 = 1.0f - std::pow(opt->beta2, (float)t);
@@ -1026,8 +1107,8 @@ int xamg_net_predict_x0(xamg_net *net, const double *B, const float *logk, doubl
   k_pack_rhs<<<(int)cdiv(n * m, 256), 256, 0, st>>>(B, m, net->ss, n, logk, net->act[T_X]);
   ++g_launches;
   NCK(cudaGetLastError());
-  NRET(forward(net, m, st));
-  k_unpack_x0<<<(int)cdiv(n * m, 256), 256, 0, st>>>(net->act[T_Y], m, net->ss, n, out_scale, X0);
+  NRET(forward(net, m, net->y32, st));
+  k_unpack_x0<<<(int)cdiv(n * m, 256), 256, 0, st>>>(net->y32, m, net->ss, n, out_scale, X0);
   ++g_launches;
   NCK(cudaGetLastError());
   return XAMG_OK;

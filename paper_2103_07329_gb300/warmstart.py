@@ -13,8 +13,11 @@ are synthesised on the padded periodic grid (``problems.grf``, pad = 2).
   column's root mean square; target X_j / s_j times a global constant c that
   gives the targets unit mean square.
 * Held-out pairs: fields 20000 + f, right-hand sides 120000 + f.
-* Training: Adam on the mean squared error, mini-batches of 32 samples drawn
-  from a seeded permutation each epoch, step size decayed by a cosine.
+* Training: Adam on the relative energy-norm error ||X0_j - X_j||_A^2 /
+  ||X_j||_A^2 (the norm in which PCG's error decreases; ||X_j||_A^2 =
+  X_j^T B_j from the label solve), or on the mean squared error, with
+  mini-batches of 32 samples drawn from a seeded permutation each epoch and
+  the step size decayed by a cosine.
 * Use: ``Net.predict_x0(B, log k, X0, 1 / c)`` then ``Hierarchy.solve(...,
   x0_given=True)``; the plain solve from X0 = 0 is the fallback and the
   judge of accuracy (both run to 1e-8).
@@ -88,12 +91,14 @@ def _col_rms(Bm: np.ndarray) -> np.ndarray:
 
 def make_pairs(N: int, nfields: int, seed0: int, rhs_seed0: int, m: int = M, tol: float = 1e-8,
                log=print):
-    """Inputs [nfields m, N^3, 2] and unscaled targets X_j / s_j [nfields m, N^3]
-    (float32 CUDA tensors) from solves of the library."""
+    """Inputs [nfields m, N^3, 2], unscaled targets X_j / s_j [nfields m, N^3]
+    (float32 CUDA tensors) and the targets' energies X_j^T B_j / s_j^2
+    (float64 CUDA [nfields m]) from solves of the library."""
     import torch
     n = N ** 3
     inp = torch.empty((nfields * m, n, 2), dtype=torch.float32, device="cuda")
     tgt = torch.empty((nfields * m, n), dtype=torch.float32, device="cuda")
+    energy = torch.empty(nfields * m, dtype=torch.float64, device="cuda")
     t0 = time.time()
     iters = []
     seeds = [seed0 + f for f in range(nfields)]
@@ -110,21 +115,25 @@ def make_pairs(N: int, nfields: int, seed0: int, rhs_seed0: int, m: int = M, tol
         inp[sl, :, 0] = (Bd / s).T.float()
         inp[sl, :, 1] = torch.as_tensor(sysf.logk, dtype=torch.float32, device="cuda")[None, :]
         tgt[sl] = (X / s).T.float()
+        energy[sl] = (X * Bd).sum(dim=0) / (s * s)
         sysf.hier.close()
         if log and (f + 1) % 16 == 0:
             log(f"  pairs: {f + 1}/{nfields} fields, {time.time() - t0:.1f} s")
-    return inp, tgt, iters
+    return inp, tgt, energy, iters
 
 
 def train(N: int = GRID, nfields: int = 128, epochs: int = 30, batch: int = 32, lr: float = 2e-3,
-          seed: int = 0, log=print):
+          seed: int = 0, loss: str = "energy", log=print):
     """Trains the network on solver-generated pairs; returns (params, c, info)."""
     import torch
     t0 = time.time()
-    inp, tgt, iters = make_pairs(N, nfields, TRAIN_SEED, TRAIN_RHS_SEED, log=log)
+    inp, tgt, energy, iters = make_pairs(N, nfields, TRAIN_SEED, TRAIN_RHS_SEED, log=log)
     t_data = time.time() - t0
     c = float(1.0 / torch.sqrt((tgt.double() ** 2).mean()))
     tgt.mul_(c)
+    kind = B.LOSS_ENERGY if loss == "energy" else B.LOSS_MSE
+    # relative energy error: weight 1 / ||t_b||_A^2 with t = c X / s
+    weight = (1.0 / (c * c * energy)).float() if kind == B.LOSS_ENERGY else None
     S = inp.shape[0]
     net = B.Net(N, batch)
     net.set_params(P.net_init(seed))
@@ -139,14 +148,14 @@ def train(N: int = GRID, nfields: int = 128, epochs: int = 30, batch: int = 32, 
         for b0 in range(0, S - batch + 1, batch):
             idx = torch.as_tensor(perm[b0:b0 + batch], device="cuda")
             step_lr = 0.5 * lr * (1.0 + np.cos(np.pi * k / steps))
-            el.append(net.train_step(inp, tgt, idx, lr=float(step_lr)))
+            el.append(net.train_step(inp, tgt, idx, lr=float(step_lr), loss=kind, weight=weight))
             k += 1
         hist.append(float(np.mean(el)))
         if log:
             log(f"  epoch {ep + 1}/{epochs}: loss {hist[-1]:.5f} ({time.time() - t1:.1f} s)")
     torch.cuda.synchronize()
     t_train = time.time() - t1
-    info = dict(N=N, fields=nfields, pairs=S, epochs=epochs, batch=batch, lr=lr, seed=seed,
+    info = dict(N=N, fields=nfields, pairs=S, epochs=epochs, batch=batch, lr=lr, seed=seed, loss=loss,
                 steps=steps, loss_history=hist, data_seconds=t_data, train_seconds=t_train,
                 label_iters_max=int(max(iters)))
     return net.get_params(), c, info
@@ -207,13 +216,20 @@ def evaluate(params: np.ndarray, c: float, N: int = GRID, nfields: int = 8, m: i
         t_plain, st_p = _timed(plain, reps)
         t_warm, st_w = _timed(warm, reps)
         t_pred, _ = _timed(lambda: net.predict_x0(Bd, logk, X, 1.0 / c), reps)
-        # accuracy of X0 itself: relative error against the converged solution
+        # accuracy of X0 itself against the converged solution X*: relative
+        # L2 and A-norm errors and the initial relative residual (max over columns)
         plain()
         Xs = X.clone()
         net.predict_x0(Bd, logk, X, 1.0 / c)
+        E, AE, AX = X - Xs, torch.empty_like(X), torch.empty_like(X)
+        sysf.hier.spmm(0, 0, E, AE)
+        sysf.hier.spmm(0, 0, X, AX)
         torch.cuda.synchronize()
-        e0 = float(torch.linalg.norm(X - Xs) / torch.linalg.norm(Xs))
+        e0 = float(torch.linalg.norm(E) / torch.linalg.norm(Xs))
+        ea = float(torch.sqrt((E * AE).sum(0) / (Xs * Bd).sum(0)).max())
+        r0 = float((torch.linalg.norm(Bd - AX, dim=0) / torch.linalg.norm(Bd, dim=0)).max())
         rec = dict(iters_plain=int(st_p.iters.max()), iters_warm=int(st_w.iters.max()),
+                   x0_anorm_error=ea, x0_relres=r0,
                    mean_iters_plain=float(st_p.iters.mean()), mean_iters_warm=float(st_w.iters.mean()),
                    ms_plain=t_plain, ms_warm=t_warm, ms_predict=t_pred, x0_rel_error=e0,
                    relres_max_plain=float(st_p.relres.max()), relres_max_warm=float(st_w.relres.max()),
@@ -222,7 +238,8 @@ def evaluate(params: np.ndarray, c: float, N: int = GRID, nfields: int = 8, m: i
         sysf.hier.close()
         if log:
             log(f"  field: iters {rec['iters_plain']} -> {rec['iters_warm']}, "
-                f"ms {t_plain:.2f} -> {t_warm:.2f} (predict {t_pred:.2f}), X0 error {e0:.3f}")
+                f"ms {t_plain:.2f} -> {t_warm:.2f} (predict {t_pred:.2f}), X0 error {e0:.3f}, "
+                f"A-norm {ea:.3f}, residual {r0:.3f}")
     tp = sum(r["ms_plain"] for r in recs)
     tw = sum(r["ms_warm"] for r in recs)
     return dict(fields=nfields, m=m, tol=tol, records=recs,
@@ -239,13 +256,14 @@ def main(argv=None):
     t.add_argument("--fields", type=int, default=128)
     t.add_argument("--epochs", type=int, default=30)
     t.add_argument("--lr", type=float, default=2e-3)
+    t.add_argument("--loss", choices=["energy", "mse"], default="energy")
     t.add_argument("--eval-fields", type=int, default=8)
     e = sub.add_parser("eval")
     e.add_argument("--params", default=PARAMS_FILE)
     e.add_argument("--fields", type=int, default=8)
     a = ap.parse_args(argv)
     if a.cmd == "train":
-        params, c, info = train(a.grid, a.fields, a.epochs, lr=a.lr)
+        params, c, info = train(a.grid, a.fields, a.epochs, lr=a.lr, loss=a.loss)
         save(a.out, params, c, info)
         print(json.dumps({k: v for k, v in info.items() if k != "loss_history"}))
         if a.eval_fields:

@@ -185,3 +185,29 @@ def test_predict_x0_normalises_columns():
     net.predict_x0(torch.as_tensor(Bh * 8.0).to(dev), torch.as_tensor(logk).to(dev), X1, scale)
     torch.cuda.synchronize()
     assert np.array_equal(X1.cpu().numpy(), 8.0 * X0)
+
+
+@pytest.mark.parametrize("kind", ["mse", "energy"])
+def test_weighted_losses(kind):
+    N, batch = 16, 2
+    inp, tgt, p = _net_problem(N, batch, seed=3)
+    w = np.array([0.5, 2.0], np.float32)
+    net = B.Net(N, batch)
+    net.set_params(p)
+    di, dt = torch.as_tensor(inp).to(dev), torch.as_tensor(tgt).to(dev)
+    code = B.LOSS_ENERGY if kind == "energy" else B.LOSS_MSE
+    L, g = net.loss_grad(di, dt, loss=code, weight=torch.as_tensor(w).to(dev))
+    L_ref, dW_ref = O.Net(p.astype(np.float64), emulate=True).grads(inp, tgt, N, kind, w)
+    assert abs(L - L_ref) <= 2e-2 * L_ref
+    for l, ((dW, db), (rW, rb)) in enumerate(zip(O.unflatten(g), dW_ref)):
+        assert rel(dW.numpy(), rW.numpy()) < 2e-2, (l, rel(dW.numpy(), rW.numpy()))
+        assert rel(db.numpy(), rb.numpy()) < 2e-2, (l, rel(db.numpy(), rb.numpy()))
+    # a training step uses the weight of each selected sample row
+    idx = torch.tensor([1, 0], dtype=torch.int32, device=dev)
+    wt = torch.as_tensor(w).to(dev)
+    la = net.train_step(di, dt, idx, lr=1e-3, loss=code, weight=wt)
+    net2 = B.Net(N, batch)
+    net2.set_params(p)
+    lb, _ = net2.loss_grad(di[[1, 0]].contiguous(), dt[[1, 0]].contiguous(), loss=code,
+                           weight=wt[[1, 0]].contiguous())
+    assert la == lb

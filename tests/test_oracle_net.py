@@ -106,11 +106,12 @@ def _problem(N=8, batch=2, seed=11):
     return inp, tgt, p
 
 
-def test_network_gradient_matches_finite_differences():
+@pytest.mark.parametrize("kind", ["mse", "energy"])
+def test_network_gradient_matches_finite_differences(kind):
     N = 8
     inp, tgt, p = _problem(N)
     net = O.Net(p, emulate=False)
-    L0, dW = net.grads(inp, tgt, N)
+    L0, dW = net.grads(inp, tgt, N, kind)
     g = O.flatten(dW)
     rng = np.random.default_rng(3)
     # entries from every layer's weights (used channels) and biases
@@ -129,8 +130,8 @@ def test_network_gradient_matches_finite_differences():
         pp, pm = p.copy(), p.copy()
         pp[i] += h
         pm[i] -= h
-        Lp = O.Net(pp, emulate=False).loss(inp, tgt, N)[0]
-        Lm = O.Net(pm, emulate=False).loss(inp, tgt, N)[0]
+        Lp = O.Net(pp, emulate=False).loss(inp, tgt, N, kind)[0]
+        Lm = O.Net(pm, emulate=False).loss(inp, tgt, N, kind)[0]
         fd = (Lp - Lm) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(g).max()), (i, fd, g[i])
     # unused weights receive exactly zero gradient
@@ -145,9 +146,42 @@ def test_emulated_values_are_bf16():
     inp, tgt, p = _problem(N, batch=1)
     net = O.Net(p, emulate=True)
     L, dW = net.grads(inp, tgt, N)
-    for k in ("x", "s0", "p1", "u2", "y"):
+    for k in ("x", "s0", "p1", "u2", "d0a"):
         a = net.a[k]
         assert torch.equal(a, O.bf16(a))
     # emulation changes values by BF16 rounding only: the FP64 loss is close
     L64 = O.Net(p, emulate=False).loss(inp, tgt, N)[0]
+    assert not torch.equal(net.a["y"], O.bf16(net.a["y"]))   # the output is not rounded
     assert abs(L - L64) <= 2e-2 * L64
+
+
+def test_energy_operator_is_the_diffusion_matrix():
+    # the loss's stencil equals the matrix problems.diffusion7 assembles
+    N = 8
+    rng = np.random.default_rng(4)
+    logk = rng.standard_normal(N ** 3)
+    e = rng.standard_normal(N ** 3)
+    A = P.diffusion7(N, np.exp(logk))
+    import scipy.sparse as sp
+    Ae = sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n)) @ e
+    got = O.energy_apply(torch.as_tensor(e), torch.as_tensor(logk), N).numpy()
+    assert np.allclose(got, Ae, rtol=1e-13, atol=1e-12)
+    # e^T A e > 0 and the loss of the exact target is zero
+    inp = np.stack([rng.standard_normal(N ** 3), logk], axis=1)[None]
+    net = O.Net(np.zeros(O.param_count()), emulate=False)
+    L, y, t, gy = net.loss(inp, np.zeros((1, N ** 3)), N, "energy")
+    assert L == 0.0 and float(gy.abs().max()) == 0.0
+    assert float(e @ Ae) > 0
+
+
+def test_sample_weights_scale_each_sample():
+    N = 8
+    inp, tgt, p = _problem(N)
+    net = O.Net(p, emulate=False)
+    for kind in ("mse", "energy"):
+        L1 = net.loss(inp, tgt, N, kind, weight=[1.0, 0.0])[0]
+        L2 = net.loss(inp, tgt, N, kind, weight=[0.0, 1.0])[0]
+        L = net.loss(inp, tgt, N, kind)[0]
+        assert abs(L1 + L2 - L) <= 1e-12 * L
+        L3 = net.loss(inp, tgt, N, kind, weight=[2.0, 0.5])[0]
+        assert abs(L3 - (2 * L1 + 0.5 * L2)) <= 1e-12 * L3
