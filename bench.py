@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--cpu-cols", type=int, default=1, help="columns in the oracle's sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision forms")
+    ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision and warm forms")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned-initial-guess form")
     ap.add_argument("--sweep", action="store_true",
                     help="measurement mode: m in 1..32, PCG and BiCGStab, FP64/FP32/bf16 "
                          "preconditioner, one JSON line each (not the benchmark line)")
@@ -356,6 +357,29 @@ def run_ours(a):
                                                   "frac": round(gbs / measured_hbm()[0], 4),
                                                   "launches": f32["launches"],
                                                   "share_of_step": round(f32["ms"] / (1e3 * ft), 4)}}
+
+    # learned initial guess: held-out 64^3 GRF-coefficient diffusion systems,
+    # 32 smooth right-hand sides each, solved from X0 = 0 and from the trained
+    # network's X0 (prediction time included), all to the same tolerance
+    if not a.no_forms and not a.no_warm:
+        from paper_2103_07329_gb300 import warmstart as W
+        params, c, info = W.load()
+        r = W.evaluate(params, c, info["N"], nfields=2, tol=a.tol, sweeps=3, log=None)
+        recs = r["records"]
+        forms["warm_start_64"] = {
+            "workload": (f"3-D 7-point diffusion {info['N']}^3, log k Gaussian random field "
+                         f"(corr. 0.1, sigma 1), 32 smooth GRF right-hand sides (corr. 0.2), held-out "
+                         f"fields {W.TEST_SEED}..{W.TEST_SEED + 1}, PCG + AMG FP64, tol {a.tol:g}"),
+            "rhs_per_s_plain": r["rhs_per_s_plain"], "rhs_per_s_warm": r["rhs_per_s_warm"],
+            "rhs_per_s_warm_smoothed": r["rhs_per_s_warm_smooth"],
+            "speedup_vs_plain": r["speedup"], "speedup_smoothed_vs_plain": r["speedup_smooth"],
+            "iters_plain": [x["iters_plain"] for x in recs], "iters_warm": [x["iters_warm"] for x in recs],
+            "iters_warm_smoothed": [x["iters_warm_smooth"] for x in recs],
+            "x0_anorm_error": [round(x["x0_anorm_error"], 4) for x in recs],
+            "x0_relres": [round(x["x0_relres"], 4) for x in recs],
+            "ms_predict": [round(x["ms_predict"], 3) for x in recs],
+            "max_relres": max(max(x["relres_max_warm"], x["relres_max_warm_smooth"]) for x in recs),
+            "training": {k: info[k] for k in ("fields", "pairs", "epochs", "finetune_epochs", "train_seconds")}}
 
     # end to end through the host-buffer entry point: H2D of B and D2H of X inside
     e2e = None

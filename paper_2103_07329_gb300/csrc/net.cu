@@ -478,28 +478,50 @@ __global__ void k_pack_input(const float *__restrict__ inp, const int32_t *__res
   *reinterpret_cast<uint4 *>(out + i * 8) = make_uint4(pack2(q.x, q.y), 0u, 0u, 0u);
 }
 
-// from the solver's blocks: channel 0 = B[v][j] / s_j (s_j the column's root
-// mean square; 0 for a zero column), channel 1 = logk[v]
-__global__ void k_pack_rhs(const double *__restrict__ B, int m, const double *__restrict__ ss, int64_t n,
-                           const float *__restrict__ logk, bf16 *__restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * m) return;
-  const int j = (int)(i % m);
-  const int64_t v = i / m;
-  const double s = sqrt(ss[j] / (double)n);
-  const float c0 = s > 0.0 ? (float)(B[i] / s) : 0.0f;
-  *reinterpret_cast<uint4 *>(out + ((int64_t)j * n + v) * 8) = make_uint4(pack2(c0, __ldg(logk + v)), 0u, 0u, 0u);
+// Transposes between the solver's n x m row-major blocks and the network's
+// sample-major tensors, through a 32-voxel x 32-column tile in shared memory
+// so that both sides are read and written in whole rows.  Block (32, 8).
+//
+// Network input from B: channel 0 of sample j = B[v][j] / s_j (s_j the
+// column's root mean square; 0 for a zero column), channel 1 = logk[v].
+__global__ void __launch_bounds__(256) k_pack_rhs(const double *__restrict__ B, int m,
+                                                  const double *__restrict__ ss, int64_t n,
+                                                  const float *__restrict__ logk, bf16 *__restrict__ out) {
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t v0 = (int64_t)blockIdx.x * 32;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t v = v0 + r;
+    float val = 0.0f;
+    if (tx < m && v < n) {
+      const double s = sqrt(ss[tx] / (double)n);
+      val = s > 0.0 ? (float)(B[v * m + tx] / s) : 0.0f;
+    }
+    tile[r][tx] = val;
+  }
+  __syncthreads();
+  const int64_t v = v0 + tx;
+  if (v >= n) return;
+  const float lk = __ldg(logk + v);
+  for (int j = ty; j < m; j += 8)
+    *reinterpret_cast<uint4 *>(out + ((int64_t)j * n + v) * 8) = make_uint4(pack2(tile[tx][j], lk), 0u, 0u, 0u);
 }
 
 // X0[v][j] = y[j][v] * s_j * scale
-__global__ void k_unpack_x0(const float *__restrict__ y, int m, const double *__restrict__ ss, int64_t n,
-                            double scale, double *__restrict__ X0) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * m) return;
-  const int j = (int)(i % m);
-  const int64_t v = i / m;
-  const double s = sqrt(ss[j] / (double)n);
-  X0[i] = (double)y[(int64_t)j * n + v] * s * scale;
+__global__ void __launch_bounds__(256) k_unpack_x0(const float *__restrict__ y, int m,
+                                                   const double *__restrict__ ss, int64_t n, double scale,
+                                                   double *__restrict__ X0) {
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t v0 = (int64_t)blockIdx.x * 32;
+  for (int j = ty; j < m; j += 8) tile[j][tx] = v0 + tx < n ? y[(int64_t)j * n + v0 + tx] : 0.0f;
+  __syncthreads();
+  if (tx >= m) return;
+  const double f = sqrt(ss[tx] / (double)n) * scale;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t v = v0 + r;
+    if (v < n) X0[v * m + tx] = (double)tile[tx][r] * f;
+  }
 }
 
 __device__ __forceinline__ int64_t sample_row(const int32_t *idx, int b) {
@@ -625,15 +647,17 @@ template <int CIN, int COUT, bool RELU>
 cudaError_t conv_t(const bf16 *in, const bf16 *mask, const bf16 *wt, const float *bias, bf16 *out, float *out0,
                    int batch, int N, cudaStream_t st) {
   constexpr size_t sm = fwd_smem<CIN, COUT>();
-  static bool attr = false;
-  if (!attr) {
+  static int per_sm = 0;  // resident blocks per SM
+  if (!per_sm) {
     cudaError_t e = cudaFuncSetAttribute(k_conv3<CIN, COUT, RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    attr = true;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3<CIN, COUT, RELU>, kThreads, sm);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(per_sm, 1);
   }
   const int nb = (N + 7) / 8;
   const int total = nb * nb * nb * batch;
-  const int grid = (int)std::min<int64_t>(total, (int64_t)device_sm_count() * 3);
+  const int grid = (int)std::min<int64_t>(total, (int64_t)device_sm_count() * per_sm);
   k_conv3<CIN, COUT, RELU><<<grid, kThreads, sm, st>>>(in, mask, wt, bias, out, out0, N, nb, total);
   ++g_launches;
   return cudaGetLastError();
@@ -1104,11 +1128,11 @@ int xamg_net_predict_x0(xamg_net *net, const double *B, const float *logk, doubl
   launch_coldot_rt(n, m, B, B, net->ss_part, grid, st);
   launch_reduce_rt(m, net->ss_part, grid, net->ss, st);
   NRET(refresh_weights(net, st));
-  k_pack_rhs<<<(int)cdiv(n * m, 256), 256, 0, st>>>(B, m, net->ss, n, logk, net->act[T_X]);
+  k_pack_rhs<<<(int)cdiv(n, 32), dim3(32, 8), 0, st>>>(B, m, net->ss, n, logk, net->act[T_X]);
   ++g_launches;
   NCK(cudaGetLastError());
   NRET(forward(net, m, net->y32, st));
-  k_unpack_x0<<<(int)cdiv(n * m, 256), 256, 0, st>>>(net->y32, m, net->ss, n, out_scale, X0);
+  k_unpack_x0<<<(int)cdiv(n, 32), dim3(32, 8), 0, st>>>(net->y32, m, net->ss, n, out_scale, X0);
   ++g_launches;
   NCK(cudaGetLastError());
   return XAMG_OK;

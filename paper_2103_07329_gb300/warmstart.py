@@ -13,14 +13,20 @@ are synthesised on the padded periodic grid (``problems.grf``, pad = 2).
   column's root mean square; target X_j / s_j times a global constant c that
   gives the targets unit mean square.
 * Held-out pairs: fields 20000 + f, right-hand sides 120000 + f.
-* Training: Adam on the relative energy-norm error ||X0_j - X_j||_A^2 /
-  ||X_j||_A^2 (the norm in which PCG's error decreases; ||X_j||_A^2 =
-  X_j^T B_j from the label solve), or on the mean squared error, with
-  mini-batches of 32 samples drawn from a seeded permutation each epoch and
-  the step size decayed by a cosine.
-* Use: ``Net.predict_x0(B, log k, X0, 1 / c)`` then ``Hierarchy.solve(...,
-  x0_given=True)``; the plain solve from X0 = 0 is the fallback and the
-  judge of accuracy (both run to 1e-8).
+* Training: Adam on the mean squared error, then (fine-tuning) on the
+  relative energy-norm error ||X0_j - X_j||_A^2 / ||X_j||_A^2
+  (||X_j||_A^2 = X_j^T B_j from the label solve), the norm in which PCG's
+  error decreases.  The energy norm alone is badly conditioned (its Hessian
+  in the output is A): started from scratch it settles at X0 = 0, so it only
+  refines a network whose smooth part the mean squared error has fitted.
+  Mini-batches of 32 samples come from a seeded permutation each epoch; each
+  phase decays its step size by a cosine.
+* Use: ``Net.predict_x0(B, log k, X0, 1 / c)``, optionally one Chebyshev
+  smoothing of X0 on the finest level (``Hierarchy.smooth(0, B, X0,
+  x_zero=False)``: it removes the high-frequency part of the network's
+  error, which dominates the initial residual), then ``Hierarchy.solve(...,
+  x0_given=True)``.  The plain solve from X0 = 0 is the fallback and the
+  judge of accuracy (all forms run to 1e-8).
 
 Run ``python -m paper_2103_07329_gb300.warmstart train --out PATH`` to train
 and store the parameters, ``... eval --params PATH`` to compare held-out
@@ -123,7 +129,8 @@ def make_pairs(N: int, nfields: int, seed0: int, rhs_seed0: int, m: int = M, tol
 
 
 def train(N: int = GRID, nfields: int = 128, epochs: int = 30, batch: int = 32, lr: float = 2e-3,
-          seed: int = 0, loss: str = "energy", log=print):
+          seed: int = 0, loss: str = "mse", finetune_epochs: int = 0, finetune_lr: float = 5e-4,
+          log=print):
     """Trains the network on solver-generated pairs; returns (params, c, info)."""
     import torch
     t0 = time.time()
@@ -131,33 +138,40 @@ def train(N: int = GRID, nfields: int = 128, epochs: int = 30, batch: int = 32, 
     t_data = time.time() - t0
     c = float(1.0 / torch.sqrt((tgt.double() ** 2).mean()))
     tgt.mul_(c)
-    kind = B.LOSS_ENERGY if loss == "energy" else B.LOSS_MSE
     # relative energy error: weight 1 / ||t_b||_A^2 with t = c X / s
-    weight = (1.0 / (c * c * energy)).float() if kind == B.LOSS_ENERGY else None
+    weight = (1.0 / (c * c * energy)).float()
     S = inp.shape[0]
     net = B.Net(N, batch)
     net.set_params(P.net_init(seed))
     rng = np.random.default_rng(seed)
-    steps = epochs * (S // batch)
+    phases = [(B.LOSS_ENERGY if loss == "energy" else B.LOSS_MSE, epochs, lr)]
+    if finetune_epochs:
+        phases.append((B.LOSS_ENERGY, finetune_epochs, finetune_lr))
     hist = []
-    k = 0
     t1 = time.time()
-    for ep in range(epochs):
-        perm = rng.permutation(S).astype(np.int32)
-        el = []
-        for b0 in range(0, S - batch + 1, batch):
-            idx = torch.as_tensor(perm[b0:b0 + batch], device="cuda")
-            step_lr = 0.5 * lr * (1.0 + np.cos(np.pi * k / steps))
-            el.append(net.train_step(inp, tgt, idx, lr=float(step_lr), loss=kind, weight=weight))
-            k += 1
-        hist.append(float(np.mean(el)))
-        if log:
-            log(f"  epoch {ep + 1}/{epochs}: loss {hist[-1]:.5f} ({time.time() - t1:.1f} s)")
+    for ph, (kind, ne, plr) in enumerate(phases):
+        if ph:
+            net.set_params(net.get_params())  # fresh Adam moments for the new loss
+        steps = ne * (S // batch)
+        k = 0
+        w = weight if kind == B.LOSS_ENERGY else None
+        for ep in range(ne):
+            perm = rng.permutation(S).astype(np.int32)
+            el = []
+            for b0 in range(0, S - batch + 1, batch):
+                idx = torch.as_tensor(perm[b0:b0 + batch], device="cuda")
+                step_lr = 0.5 * plr * (1.0 + np.cos(np.pi * k / steps))
+                el.append(net.train_step(inp, tgt, idx, lr=float(step_lr), loss=kind, weight=w))
+                k += 1
+            hist.append(float(np.mean(el)))
+            if log and ((ep + 1) % 10 == 0 or ep == 0):
+                name = "energy" if kind == B.LOSS_ENERGY else "mse"
+                log(f"  {name} epoch {ep + 1}/{ne}: loss {hist[-1]:.5f} ({time.time() - t1:.1f} s)")
     torch.cuda.synchronize()
     t_train = time.time() - t1
     info = dict(N=N, fields=nfields, pairs=S, epochs=epochs, batch=batch, lr=lr, seed=seed, loss=loss,
-                steps=steps, loss_history=hist, data_seconds=t_data, train_seconds=t_train,
-                label_iters_max=int(max(iters)))
+                finetune_epochs=finetune_epochs, finetune_lr=finetune_lr, loss_history=hist,
+                data_seconds=t_data, train_seconds=t_train, label_iters_max=int(max(iters)))
     return net.get_params(), c, info
 
 
@@ -188,7 +202,7 @@ def _timed(fn, reps: int = 3):
 
 
 def evaluate(params: np.ndarray, c: float, N: int = GRID, nfields: int = 8, m: int = M,
-             tol: float = 1e-8, precond: int = B.PREC_FP64, reps: int = 3, log=print):
+             tol: float = 1e-8, precond: int = B.PREC_FP64, reps: int = 3, sweeps: int = 1, log=print):
     """Held-out comparison of the solve from X0 = 0 and from the network's X0.
 
     Per field: iterations (max over columns), device time of the solve (and of
@@ -209,42 +223,57 @@ def evaluate(params: np.ndarray, c: float, N: int = GRID, nfields: int = 8, m: i
             X.zero_()
             return sysf.hier.solve(Bd, X, tol=tol, maxit=200, precond=precond)
 
-        def warm():
+        def warm(smooth=False):
             net.predict_x0(Bd, logk, X, 1.0 / c)
+            for _ in range(sweeps if smooth else 0):
+                sysf.hier.smooth(0, Bd, X, x_zero=False)
             return sysf.hier.solve(Bd, X, tol=tol, maxit=200, precond=precond, x0_given=True)
 
         t_plain, st_p = _timed(plain, reps)
         t_warm, st_w = _timed(warm, reps)
+        t_warms, st_s = _timed(lambda: warm(True), reps)
         t_pred, _ = _timed(lambda: net.predict_x0(Bd, logk, X, 1.0 / c), reps)
-        # accuracy of X0 itself against the converged solution X*: relative
-        # L2 and A-norm errors and the initial relative residual (max over columns)
+        # quality of X0 (and of X0 after the smoothing) against the converged
+        # solution X*: relative L2 and A-norm errors and the initial relative
+        # residual (max over columns)
         plain()
         Xs = X.clone()
-        net.predict_x0(Bd, logk, X, 1.0 / c)
-        E, AE, AX = X - Xs, torch.empty_like(X), torch.empty_like(X)
-        sysf.hier.spmm(0, 0, E, AE)
-        sysf.hier.spmm(0, 0, X, AX)
-        torch.cuda.synchronize()
-        e0 = float(torch.linalg.norm(E) / torch.linalg.norm(Xs))
-        ea = float(torch.sqrt((E * AE).sum(0) / (Xs * Bd).sum(0)).max())
-        r0 = float((torch.linalg.norm(Bd - AX, dim=0) / torch.linalg.norm(Bd, dim=0)).max())
+
+        def quality(smooth):
+            net.predict_x0(Bd, logk, X, 1.0 / c)
+            for _ in range(sweeps if smooth else 0):
+                sysf.hier.smooth(0, Bd, X, x_zero=False)
+            E, AE, AX = X - Xs, torch.empty_like(X), torch.empty_like(X)
+            sysf.hier.spmm(0, 0, E, AE)
+            sysf.hier.spmm(0, 0, X, AX)
+            torch.cuda.synchronize()
+            return (float(torch.linalg.norm(E) / torch.linalg.norm(Xs)),
+                    float(torch.sqrt((E * AE).sum(0) / (Xs * Bd).sum(0)).max()),
+                    float((torch.linalg.norm(Bd - AX, dim=0) / torch.linalg.norm(Bd, dim=0)).max()))
+
+        e0, ea, r0 = quality(False)
+        _, eas, r0s = quality(True)
         rec = dict(iters_plain=int(st_p.iters.max()), iters_warm=int(st_w.iters.max()),
-                   x0_anorm_error=ea, x0_relres=r0,
+                   iters_warm_smooth=int(st_s.iters.max()), x0_l2_error=e0, x0_anorm_error=ea,
+                   x0_relres=r0, x0s_anorm_error=eas, x0s_relres=r0s,
                    mean_iters_plain=float(st_p.iters.mean()), mean_iters_warm=float(st_w.iters.mean()),
-                   ms_plain=t_plain, ms_warm=t_warm, ms_predict=t_pred, x0_rel_error=e0,
+                   mean_iters_warm_smooth=float(st_s.iters.mean()),
+                   ms_plain=t_plain, ms_warm=t_warm, ms_warm_smooth=t_warms, ms_predict=t_pred,
                    relres_max_plain=float(st_p.relres.max()), relres_max_warm=float(st_w.relres.max()),
-                   rc_plain=st_p.rc, rc_warm=st_w.rc)
+                   relres_max_warm_smooth=float(st_s.relres.max()),
+                   rc_plain=st_p.rc, rc_warm=st_w.rc, rc_warm_smooth=st_s.rc)
         recs.append(rec)
         sysf.hier.close()
         if log:
-            log(f"  field: iters {rec['iters_plain']} -> {rec['iters_warm']}, "
-                f"ms {t_plain:.2f} -> {t_warm:.2f} (predict {t_pred:.2f}), X0 error {e0:.3f}, "
-                f"A-norm {ea:.3f}, residual {r0:.3f}")
+            log(f"  field: iters {rec['iters_plain']} -> {rec['iters_warm']} / {rec['iters_warm_smooth']} "
+                f"(smoothed), ms {t_plain:.2f} -> {t_warm:.2f} / {t_warms:.2f} (predict {t_pred:.2f}); "
+                f"X0 L2 error {e0:.3f}, A-norm {ea:.3f} / {eas:.3f}, residual {r0:.3f} / {r0s:.3f}")
     tp = sum(r["ms_plain"] for r in recs)
     tw = sum(r["ms_warm"] for r in recs)
-    return dict(fields=nfields, m=m, tol=tol, records=recs,
+    ts = sum(r["ms_warm_smooth"] for r in recs)
+    return dict(fields=nfields, m=m, tol=tol, sweeps=sweeps, records=recs,
                 rhs_per_s_plain=nfields * m / (tp * 1e-3), rhs_per_s_warm=nfields * m / (tw * 1e-3),
-                speedup=tp / tw)
+                rhs_per_s_warm_smooth=nfields * m / (ts * 1e-3), speedup=tp / tw, speedup_smooth=tp / ts)
 
 
 def main(argv=None):
@@ -256,22 +285,27 @@ def main(argv=None):
     t.add_argument("--fields", type=int, default=128)
     t.add_argument("--epochs", type=int, default=30)
     t.add_argument("--lr", type=float, default=2e-3)
-    t.add_argument("--loss", choices=["energy", "mse"], default="energy")
+    t.add_argument("--loss", choices=["energy", "mse"], default="mse")
     t.add_argument("--eval-fields", type=int, default=8)
+    t.add_argument("--finetune-epochs", type=int, default=0)
+    t.add_argument("--finetune-lr", type=float, default=5e-4)
+    t.add_argument("--sweeps", type=int, default=1)
     e = sub.add_parser("eval")
     e.add_argument("--params", default=PARAMS_FILE)
     e.add_argument("--fields", type=int, default=8)
+    e.add_argument("--sweeps", type=int, default=1)
     a = ap.parse_args(argv)
     if a.cmd == "train":
-        params, c, info = train(a.grid, a.fields, a.epochs, lr=a.lr, loss=a.loss)
+        params, c, info = train(a.grid, a.fields, a.epochs, lr=a.lr, loss=a.loss,
+                                finetune_epochs=a.finetune_epochs, finetune_lr=a.finetune_lr)
         save(a.out, params, c, info)
         print(json.dumps({k: v for k, v in info.items() if k != "loss_history"}))
         if a.eval_fields:
-            r = evaluate(params, c, a.grid, a.eval_fields)
+            r = evaluate(params, c, a.grid, a.eval_fields, sweeps=a.sweeps)
             print(json.dumps({k: v for k, v in r.items() if k != "records"}))
     else:
         params, c, info = load(a.params)
-        r = evaluate(params, c, info["N"], a.fields)
+        r = evaluate(params, c, info["N"], a.fields, sweeps=a.sweeps)
         print(json.dumps(r))
 
 
