@@ -282,6 +282,55 @@ int xamg_coldot(const double *U, const double *V, int64_t n, int32_t m, double *
 int xamg_coldot_noalloc(const double *U, const double *V, int64_t n, int32_t m, double *out,
                         void *stream);
 
+/* ---- batched solve of many independent systems ----
+ *
+ * Solves count independent systems A_s X_s = B_s (A_s n_s x n_s with its own
+ * frozen hierarchy h[s], B_s and X_s n_s x m[s] row-major DEVICE blocks) to
+ * the relative residual tol per column.  Each system runs exactly the steps
+ * of xamg_solve with method XAMG_PCG and precond XAMG_PREC_FP32 (flexible PCG
+ * in FP64 around the FP32 V(1,1) Chebyshev preconditioner, FP64 coarsest
+ * solve), and all systems advance in lockstep: every stage of the V-cycle
+ * and of the Krylov loop is one launch for all of them, whatever their sizes,
+ * column counts and hierarchy depths.  A system leaves the lockstep when all
+ * its columns are confirmed converged.  The paper solves one system at a
+ * time; this form serves many small systems, whose single-system launches are
+ * latency-bound.
+ *
+ * Requirements: every hierarchy on the same device with at least two levels
+ * and cheb_steps = 2 (the default); 1 <= m[s] <= XAMG_MAX_RHS.  Otherwise
+ * XAMG_ERR_INVALID_ARG. */
+typedef struct xamg_batch xamg_batch;
+
+typedef struct {
+  int32_t autotune;  /* 1 (default): at creation, time both row splits (rows per warp: the
+                        single-system default, or one row per warp with its entries split over
+                        the lanes) of every FP32 operator of every level and keep the faster */
+  int32_t use_graph; /* 1 (default): replay the steady iteration as one CUDA graph */
+} xamg_batch_opts;
+
+void xamg_batch_opts_default(xamg_batch_opts *o);
+
+/* Plans the batch: device tables of the systems, one workspace for all of
+ * them (allocated here and owned by the batch), launch grids, autotuning.
+ * The hierarchies must outlive the batch. */
+int xamg_batch_create(xamg_hier *const *h, const int32_t *m, int32_t count, const xamg_batch_opts *opts,
+                      xamg_batch **out);
+int xamg_batch_destroy(xamg_batch *b);
+
+/* Launches per steady iteration (for every system together), operators
+ * autotuned and how many of them chose the one-row-per-warp split, bytes of
+ * the batch's workspace.  Output pointers may be NULL. */
+int xamg_batch_info(const xamg_batch *b, int32_t *launches_per_iteration, int32_t *ops_tuned, int32_t *ops_wide,
+                    int64_t *workspace_bytes);
+
+/* B, X: HOST arrays of count DEVICE pointers.  stats: NULL or a HOST array of
+ * count xamg_stats (their per-column arrays sized m[s]).  Work runs on the
+ * batch's own stream, ordered after earlier work on `stream` and before later
+ * work on it; returns when the solutions are written.  Return code as
+ * xamg_solve's, over all systems. */
+int xamg_batch_solve(xamg_batch *b, const double *const *B, double *const *X, double tol, int32_t maxit,
+                     void *stream, xamg_stats *stats);
+
 /* ---- learned initial guess ----
  *
  * A 3-D convolutional encoder-decoder that predicts a first iterate X0 of the

@@ -45,6 +45,8 @@ EXPORTS = [
     "xamg_net_param_count", "xamg_net_create", "xamg_net_destroy", "xamg_net_set_params",
     "xamg_net_get_params", "xamg_net_forward", "xamg_net_loss_grad", "xamg_net_train_step",
     "xamg_net_predict_x0", "xamg_conv3d_bf16", "xamg_conv3d_bf16_wgrad",
+    "xamg_batch_opts_default", "xamg_batch_create", "xamg_batch_destroy", "xamg_batch_info",
+    "xamg_batch_solve",
 ]
 
 
@@ -73,6 +75,10 @@ class SolveOptsT(C.Structure):
 
 class AdamT(C.Structure):
     _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
+class BatchOptsT(C.Structure):
+    _fields_ = [("autotune", C.c_int32), ("use_graph", C.c_int32)]
 
 
 class NetLossT(C.Structure):
@@ -142,6 +148,11 @@ def _load():
         "xamg_net_predict_x0": ([vp, vp, vp, dbl, vp, i32, vp], C.c_int),
         "xamg_conv3d_bf16": ([vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, vp], C.c_int),
         "xamg_conv3d_bf16_wgrad": ([vp, vp, vp, vp, vp, i32, i32, i32, i32, vp], C.c_int),
+        "xamg_batch_opts_default": ([C.POINTER(BatchOptsT)], None),
+        "xamg_batch_create": ([vp, vp, i32, C.POINTER(BatchOptsT), C.POINTER(vp)], C.c_int),
+        "xamg_batch_destroy": ([vp], C.c_int),
+        "xamg_batch_info": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)], C.c_int),
+        "xamg_batch_solve": ([vp, vp, vp, dbl, i32, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -481,3 +492,59 @@ class Net:
         """X0 (float64 CUDA n x m) from B (float64 CUDA n x m) and logk (float32 CUDA n)."""
         _check(_load().xamg_net_predict_x0(self._h, _ptr(B), _ptr(logk), out_scale, _ptr(X0), B.shape[1],
                                            _stream(stream)), "xamg_net_predict_x0")
+
+
+# ---- batched solve of many independent systems ----
+
+class Batch:
+    """Handle on ``xamg_batch_create``: the hierarchies (``Hierarchy``, on the
+    device) of independent systems and their column counts; solves them
+    together with ``solve``."""
+
+    def __init__(self, hiers, ms, autotune: bool = True, use_graph: bool = True):
+        L = _load()
+        n = len(hiers)
+        hs = (C.c_void_p * n)(*[h.handle.value for h in hiers])
+        marr = (C.c_int32 * n)(*[int(m) for m in ms])
+        o = BatchOptsT()
+        L.xamg_batch_opts_default(C.byref(o))
+        o.autotune = 1 if autotune else 0
+        o.use_graph = 1 if use_graph else 0
+        b = C.c_void_p()
+        _check(L.xamg_batch_create(hs, marr, n, C.byref(o), C.byref(b)), "xamg_batch_create")
+        self._h = b
+        self._hiers = list(hiers)   # the hierarchies must outlive the batch
+        self.ms = [int(m) for m in ms]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().xamg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        a = C.c_int32(); t = C.c_int32(); w = C.c_int32(); by = C.c_int64()
+        _check(_load().xamg_batch_info(self._h, C.byref(a), C.byref(t), C.byref(w), C.byref(by)),
+               "xamg_batch_info")
+        return dict(launches_per_iteration=a.value, ops_tuned=t.value, ops_wide=w.value,
+                    workspace_bytes=by.value)
+
+    def solve(self, Bs, Xs, tol=1e-8, maxit=200, stream=None):
+        """xamg_batch_solve on lists of device blocks (torch float64 CUDA,
+        n_s x m_s); returns one SolveStats per system (rc: the batch's code)."""
+        n = len(self.ms)
+        assert len(Bs) == n and len(Xs) == n
+        bp = (C.c_void_p * n)(*[_ptr(B) for B in Bs])
+        xp = (C.c_void_p * n)(*[_ptr(X) for X in Xs])
+        stats = [SolveStats(m) for m in self.ms]
+        arr = (StatsT * n)(*[st.struct() for st in stats])
+        rc = _load().xamg_batch_solve(self._h, bp, xp, tol, maxit, _stream(stream), arr)
+        _check(rc, "xamg_batch_solve", allow_positive=True)
+        for st, a in zip(stats, arr):
+            st.iterations, st.vcycles, st.rc = a.iterations, a.vcycles, rc
+        return stats

@@ -35,12 +35,14 @@ def sources():
                                             "rows_nv8.cu", "rows_nv16.cu", "rows_nv32.cu",
                                             "rowsf_nv1.cu", "rowsf_nv2.cu", "rowsf_nv4.cu",
                                             "rowsf_nv8.cu", "rowsf_nv16.cu", "rowsf_nv32.cu",
-                                            "net.cu")]
+                                            "net.cu", "batch.cu", "batch_stage1.cu",
+                                            "batch_stage2.cu", "batch_stage3.cu")]
 
 
 def _deps():
     return sources() + [os.path.join(CSRC, f) for f in ("hier_host.h", "launch.h", "kernels.cuh",
-                                                              "rows_inst.cuh")] + [
+                                                              "rows_inst.cuh", "elem.cuh", "batch.h",
+                                                              "batch_stage.cuh")] + [
         os.path.join(ROOT, "include", "xamg_gpu.h")]
 
 

@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 
+#include "batch.h"
 #include "hier_host.h"
 #include "launch.h"
 
@@ -972,6 +973,56 @@ int solve_bicgstab(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stat
   }
   return finish(c, Xuser, stats);
 }
+
+}  // namespace
+
+namespace xamg {
+
+int hier_view(xamg_hier *h, HierView *v) {
+  if (!h || !h->on_device || !v) return XAMG_ERR_INVALID_ARG;
+  const int L = (int)h->lv.size();
+  if (L > kBatchMaxLevels) return XAMG_ERR_INVALID_ARG;
+  XCK(cudaSetDevice(h->device));
+  const int rc = upload_lowp(h);
+  if (rc != XAMG_OK) return rc;
+  *v = HierView();
+  v->L = L;
+  v->nc = h->host.nc;
+  v->cheb_steps = h->host.cheb_steps;
+  v->device = h->device;
+  v->lu = h->lu;
+  v->piv = h->piv;
+  for (int l = 0; l < L; ++l) {
+    const DevLevel &D = h->lv[l];
+    HierLevelView &o = v->lv[l];
+    o.n = D.A.n;
+    o.nnzA = D.A.nnz;
+    o.Arp = D.A.rowptr;
+    o.Aci = D.A.col;
+    o.Av = D.a32;
+    o.A64 = D.A.val;
+    if (l + 1 < L) {
+      o.nc = D.R.n;
+      o.nnzP = D.P.nnz;
+      o.nnzR = D.R.nnz;
+      o.Prp = D.P.rowptr;
+      o.Pci = D.P.col;
+      o.Pv = D.p32;
+      o.Rrp = D.R.rowptr;
+      o.Rci = D.R.col;
+      o.Rv = D.r32;
+      for (int k = 0; k < 4; ++k) {
+        o.w32[k] = D.w32[k];
+        o.c1f[k] = D.c1f[k];
+      }
+    }
+  }
+  return XAMG_OK;
+}
+
+}  // namespace xamg
+
+namespace {
 
 int solve_impl(xamg_hier *h, const double *B, double *X, int m, double tol, int maxit,
                const xamg_solve_opts *opts, xamg_stats *stats) {

@@ -188,6 +188,24 @@ def net_init(seed: int) -> np.ndarray:
     return np.concatenate(out).astype(np.float32)
 
 
+def batch_spec(count: int = 64, seed: int = 2, edge_lo: int = 16, edge_hi: int = 96, m_max: int = 32):
+    """Sizes of a batch of independent systems: per system s a grid edge
+    drawn uniformly from edge_lo..edge_hi and a column count from 1..m_max
+    (numpy default_rng(seed)).  Returns a list of (edge, m)."""
+    rng = np.random.default_rng(seed)
+    edges = rng.integers(edge_lo, edge_hi + 1, size=count)
+    ms = rng.integers(1, m_max + 1, size=count)
+    return [(int(e), int(m)) for e, m in zip(edges, ms)]
+
+
+def batch_system(edge: int, m: int, s: int, sigma: float = 0.5):
+    """System s of a batch: 7-point finite-volume diffusion on an edge^3 grid
+    with i.i.d. lognormal cell coefficients (sigma, seed 100 + s) and an
+    n x m block of uniform[-1, 1) right-hand sides (seed 1000 + s)."""
+    A = diffusion7(edge, lognormal_cells(edge, sigma, 100 + s))
+    return A, rhs_uniform(A.n, m, 1000 + s)
+
+
 def rhs_uniform(n: int, m: int, seed: int = 0, m_draw: int | None = None) -> np.ndarray:
     """n x m row-major block with entries i.i.d. uniform[-1, 1).
 
