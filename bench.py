@@ -62,6 +62,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision and warm forms")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned-initial-guess form")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched form")
+    ap.add_argument("--batch-count", type=int, default=64, help="systems of the batched form")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="measurement mode: only the batched form, as one JSON line")
+    ap.add_argument("--batch-no-seq", action="store_true",
+                    help="with --batch-only: skip the one-system-at-a-time solves (profiling)")
     ap.add_argument("--sweep", action="store_true",
                     help="measurement mode: m in 1..32, PCG and BiCGStab, FP64/FP32/bf16 "
                          "preconditioner, one JSON line each (not the benchmark line)")
@@ -196,6 +202,113 @@ def cpu_baseline(a, A, seconds_note=True):
     t = time.perf_counter() - t0
     ok = int(np.sum((r.status == 0) & (r.relres <= a.tol)))
     return ok / t, dict(t_solve=t, t_setup=t_setup, iters=r.iters.tolist(), h=h)
+
+
+def batch_form(a, seq=True):
+    """The batched form: `batch_count` independent 7-point diffusion systems
+    (grid edge uniform in 16..96, m uniform in 1..32, lognormal sigma 0.5
+    coefficients; problems.batch_spec / batch_system) solved to a.tol, timed
+    over a.steps rounds after one warm-up: one system after another with the
+    plain FP64 solve and with the FP32 preconditioner, and all systems at once
+    (xamg_batch_solve: one launch per stage for all systems, CUDA graph,
+    autotuned row splits).  RHS/s count the columns that reached the
+    tolerance."""
+    import concurrent.futures as cf
+
+    import torch
+
+    from paper_2103_07329_gb300 import binding as B
+    from paper_2103_07329_gb300 import problems as P
+    spec = P.batch_spec(a.batch_count)
+    t0 = time.perf_counter()
+    nth = max(1, (os.cpu_count() or 4) // 4)
+
+    def mk(s):
+        e, m = spec[s]
+        A, Bm = P.batch_system(e, m, s)
+        return A, Bm, B.Hierarchy(A, nthreads=nth)
+
+    with cf.ThreadPoolExecutor(4) as ex:
+        systems = list(ex.map(mk, range(len(spec))))
+    t_setup = time.perf_counter() - t0
+    hs = [h for _, _, h in systems]
+    ms = [Bm.shape[1] for _, Bm, _ in systems]
+    Bd = [torch.from_numpy(Bm).cuda() for _, Bm, _ in systems]
+    Xs = [torch.empty_like(b) for b in Bd]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        solved = 0
+        e0.record(stream)
+        for _ in range(a.steps):
+            solved += fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), solved
+
+    def seq_fn(prec):
+        def f():
+            ok = 0
+            for h, b, x in zip(hs, Bd, Xs):
+                st = h.solve(b, x, a.tol, a.maxit, precond=prec)
+                ok += int(np.sum((st.status == 0) & (st.relres <= a.tol)))
+            return ok
+        return f
+
+    out = {"workload": (f"{len(spec)} independent 3-D 7-point diffusion systems, grid edge uniform "
+                        f"16..96 and m uniform 1..32 (seed 2), cell k lognormal sigma 0.5 (seed 100+s), "
+                        f"B uniform[-1,1) (seed 1000+s), tol {a.tol:g}"),
+           "systems": len(spec), "rhs": int(sum(ms)), "unknowns": int(sum(e ** 3 for e, _ in spec)),
+           "setup_s": round(t_setup, 2), "max_levels": max(h.levels for h in hs)}
+    if seq:
+        ms64, ok64 = timed(seq_fn(B.PREC_FP64))
+        ms32, ok32 = timed(seq_fn(B.PREC_FP32))
+        out["rhs_per_s_plain_fp64_one_by_one"] = ok64 / (ms64 * 1e-3)
+        out["rhs_per_s_fp32_one_by_one"] = ok32 / (ms32 * 1e-3)
+    t0 = time.perf_counter()
+    batch = B.Batch(hs, ms)
+    out["create_s"] = round(time.perf_counter() - t0, 3)
+    last = []
+
+    def bf():
+        st = batch.solve(Bd, Xs, a.tol, a.maxit)
+        last[:] = st
+        return sum(int(np.sum((s.status == 0) & (s.relres <= a.tol))) for s in st)
+
+    l0 = B.kernel_launches()
+    msb, okb = timed(bf)
+    out["gpu_launches_per_solve"] = (B.kernel_launches() - l0) // (a.steps + 1)
+    out["value"] = okb / (msb * 1e-3)
+    out["ms_per_step"] = msb / a.steps
+    if seq:
+        out["speedup_vs_plain_fp64"] = out["value"] / out["rhs_per_s_plain_fp64_one_by_one"]
+        out["speedup_vs_fp32_one_by_one"] = out["value"] / out["rhs_per_s_fp32_one_by_one"]
+    out["iterations_max"] = max(s.iterations for s in last)
+    out["max_relres"] = max(float(s.relres.max()) for s in last)
+    out.update(batch.info())
+    batch.close()
+    for h in hs:
+        h.close()
+    return out
+
+
+def run_batch_only(a):
+    import torch
+
+    from paper_2103_07329_gb300 import build as build_mod
+    build_mod.build()
+    torch.cuda.set_device(0)
+    r = batch_form(a, seq=not a.batch_no_seq)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": a.steps,
+            "warmup": 1, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": r["workload"], "form": "batched"}, "batched": r}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_reference(a):
@@ -381,6 +494,9 @@ def run_ours(a):
             "max_relres": max(max(x["relres_max_warm"], x["relres_max_warm_smooth"]) for x in recs),
             "training": {k: info[k] for k in ("fields", "pairs", "epochs", "finetune_epochs", "train_seconds")}}
 
+    if not a.no_forms and not a.no_batch:
+        forms["batched_64"] = batch_form(a)
+
     # end to end through the host-buffer entry point: H2D of B and D2H of X inside
     e2e = None
     if not a.no_e2e:
@@ -493,6 +609,8 @@ def main():
         return run_reference(a)
     if a.sweep:
         return run_sweep(a)
+    if a.batch_only:
+        return run_batch_only(a)
     return run_ours(a)
 
 

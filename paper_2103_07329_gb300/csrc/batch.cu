@@ -22,24 +22,39 @@
 
 namespace xamg {
 
-int launch_bstage_g1(int st, const BSys *sys, int ns, const int *sel, int level, int grid, cudaStream_t s);
-int launch_bstage_g2(int st, const BSys *sys, int ns, const int *sel, int level, int grid, cudaStream_t s);
-int launch_bstage_g3(int st, const BSys *sys, int ns, const int *sel, int level, int grid, cudaStream_t s);
+int launch_bk_g1(int kind, const void *params, const int *sel, int grid, cudaStream_t st);
+int launch_bk_g2(int kind, const void *params, const int *sel, int grid, cudaStream_t st);
+int launch_bk_g3(int kind, const void *params, const int *sel, int grid, cudaStream_t st);
 
-int launch_bstage(int st, const BSys *sys, int ns, const int *sel, int level, int grid, cudaStream_t s) {
-  int r = launch_bstage_g1(st, sys, ns, sel, level, grid, s);
+int launch_bk(int kind, const void *params, const int *sel, int grid, cudaStream_t st) {
+  int r = launch_bk_g1(kind, params, sel, grid, st);
   if (r != -2) return r;
-  r = launch_bstage_g2(st, sys, ns, sel, level, grid, s);
+  r = launch_bk_g2(kind, params, sel, grid, st);
   if (r != -2) return r;
-  return launch_bstage_g3(st, sys, ns, sel, level, grid, s);
+  return launch_bk_g3(kind, params, sel, grid, st);
 }
 
-int bstage_max_grid(int st) { return launch_bstage(st, nullptr, 0, nullptr, 0, 0, nullptr); }
+// kernel of each stage
+int stage_kind(int st) {
+  switch (st) {
+    case BS_PRE1: return BK_F_YDN;
+    case BS_PRE2: return BK_F_YXDP;
+    case BS_RESTRICT: return BK_F_D0_POS;
+    case BS_RESTRICT_C: case BS_PROLONG: case BS_TUNE_A: case BS_TUNE_P: case BS_TUNE_R: return BK_F_Y_POS;
+    case BS_POST1: return BK_F_D0_NEG;
+    case BS_POST2: return BK_F_XLAST;
+    case BS_POST2_DOT2: return BK_F_XLAST_DOT2;
+    case BS_AP: return BK_D_YDOT;
+    default: return BK_D_YDOT2;
+  }
+}
+
+int bstage_max_grid(int st) { return launch_bk(stage_kind(st), nullptr, nullptr, 0, nullptr); }
 
 int bstage_rows_per_block(int st, int nv, int opt) {
-  const bool fp64 = st == BS_AP || st == BS_TRUERES;
-  const bool wide_ok = !(fp64 || st == BS_POST2_DOT2);
-  if (!wide_ok) opt = 0;
+  const int kind = stage_kind(st);
+  const bool fp64 = kind == BK_D_YDOT || kind == BK_D_YDOT2;
+  if (kind == BK_F_XLAST_DOT2 || fp64) opt = 0;
 #define XAMG_RPB(V) \
   case V: return fp64 ? rows_per_block<double, V>(opt) : rows_per_block<float, V>(opt);
   switch (nv) {
@@ -200,6 +215,9 @@ struct xamg_batch {
   int g_ap = 0, g_tr = 0, g_post0 = 0, g_elem = 0;
   int launches_per_iter = 0;
   int ops_tuned = 0, ops_wide = 0;
+  // host staging of one launch's parameter block (the larger of the FP32 and
+  // FP64 forms)
+  std::vector<char> params = std::vector<char>(std::max(sizeof(StageParams<float>), sizeof(StageParams<double>)));
 };
 
 namespace {
@@ -291,8 +309,116 @@ void compute_grids(xamg_batch *b) {
   b->g_elem = (int)std::max<int64_t>(1, std::min<int64_t>((emax + kBlock - 1) / kBlock, (int64_t)device_sm_count() * 8));
 }
 
-int stage(xamg_batch *b, int st, int sel, int l, int grid) {
-  return launch_bstage(st, b->sys_d, b->ns, sel_dev(b, sel), l, grid, b->st) < 0 ? XAMG_ERR_CUDA : XAMG_OK;
+template <class TB>
+RowOpT<TB> blank_row() {
+  RowOpT<TB> o;
+  std::memset(&o, 0, sizeof(o));
+  return o;
+}
+
+// The row operation of stage st on level l of system s, or false if the
+// stage does not apply to it (mirrors presmooth / postsmooth / vcycle and the
+// Krylov steps of the single-system solve with the FP32 preconditioner).
+bool stage_op_f(xamg_batch *b, int st, int s, int l, RowOpF &o, int &opt) {
+  const BSys &S = b->sys_h[s];
+  if (l >= S.L - 1) return false;
+  const BLevel &V = blev(b, s, l);
+  const BLevel *C = l + 1 < S.L ? &blev(b, s, l + 1) : nullptr;
+  o = blank_row<float>();
+  auto A = [&]() { o.n = V.n; o.rowptr = V.Arp; o.col = V.Aci; o.val = V.Av; opt = V.optA; };
+  auto P = [&]() { o.n = V.n; o.rowptr = V.Prp; o.col = V.Pci; o.val = V.Pv; opt = V.optP; };
+  auto R = [&]() { o.n = V.nc; o.rowptr = V.Rrp; o.col = V.Rci; o.val = V.Rv; opt = V.optR; };
+  switch (st) {
+    case BS_PRE1:
+      A(); o.init = V.b; o.src = V.x; o.y = V.r; o.dp = V.x; o.w = V.w[1]; o.c1 = V.c1[1]; o.dnext = V.d;
+      return true;
+    case BS_PRE2:
+      A(); o.init = V.r; o.src = V.d; o.y = V.r; o.dp = V.d; o.x = V.x;
+      return true;
+    case BS_RESTRICT:
+      if (l + 2 >= S.L) return false;
+      R(); o.src = V.r; o.y = C->b; o.w = C->w[0]; o.dnext = C->x;
+      return true;
+    case BS_RESTRICT_C:
+      if (l + 2 != S.L) return false;
+      R(); o.src = V.r; o.y = C->b;
+      return true;
+    case BS_PROLONG:
+      P(); o.init = V.x; o.src = C->x; o.y = V.x;
+      return true;
+    case BS_POST1:
+      A(); o.init = V.b; o.src = V.x; o.y = V.r; o.w = V.w[0]; o.dnext = V.d;
+      return true;
+    case BS_POST2:
+    case BS_POST2_DOT2:
+      A(); o.init = V.r; o.src = V.d; o.dp = V.d; o.w = V.w[1]; o.c1 = V.c1[1]; o.x = V.x;
+      if (st == BS_POST2_DOT2) {
+        o.dot_u = S.R; o.partials = S.part[1]; o.dot_u2 = S.Q; o.partials2 = S.part[2];
+        opt = 0;
+      }
+      return true;
+    case BS_TUNE_A:
+      A(); o.src = V.x; o.y = V.r;
+      return true;
+    case BS_TUNE_P:
+      P(); o.src = C->x; o.y = V.r;
+      return true;
+    case BS_TUNE_R:
+      R(); o.src = V.r; o.y = C->b;
+      return true;
+    default:
+      return false;
+  }
+}
+
+bool stage_op_d(xamg_batch *b, int st, int s, RowOp &o, int &opt) {
+  const BSys &S = b->sys_h[s];
+  o = blank_row<double>();
+  o.n = (int)S.n0; o.rowptr = S.A0rp; o.col = S.A0ci; o.val = S.A0v;
+  opt = 0;
+  if (st == BS_AP) {
+    o.src = S.P; o.y = S.Q; o.dot_u = S.P; o.partials = S.part[0];
+  } else {
+    o.init = S.Bn; o.src = S.X; o.y = S.Q; o.partials2 = S.part[2];
+  }
+  return true;
+}
+
+// One launch (per kStageOps systems) of stage st on level l for the systems
+// of selection mask `sel` to which the stage applies; `only` >= 0 restricts
+// the list to that system (autotuner).
+template <class TB>
+int stage_t(xamg_batch *b, int st, int sel, int l, int grid, int only) {
+  StageParams<TB> &P = *reinterpret_cast<StageParams<TB> *>(b->params.data());
+  const int kind = stage_kind(st);
+  P.count = 0;
+  auto flush = [&]() -> int {
+    if (!P.count) return XAMG_OK;
+    const int r = launch_bk(kind, &P, sel_dev(b, sel), grid, b->st);
+    P.count = 0;
+    return r < 0 ? XAMG_ERR_CUDA : XAMG_OK;
+  };
+  for (int s = 0; s < b->ns; ++s) {
+    if (only >= 0 && s != only) continue;
+    RowOpT<TB> o;
+    int opt = 0;
+    bool on;
+    if constexpr (sizeof(TB) == 8) on = stage_op_d(b, st, s, o, opt);
+    else on = stage_op_f(b, st, s, l, o, opt);
+    if (!on) continue;
+    const int i = P.count++;
+    P.sys[i] = s;
+    P.nv[i] = (unsigned char)b->sys_h[s].nv;
+    P.opt[i] = (unsigned char)opt;
+    P.op[i] = o;
+    if (P.count == kStageOps) BRET(flush());
+  }
+  return flush();
+}
+
+int stage(xamg_batch *b, int st, int sel, int l, int grid, int only = -1) {
+  if (st == BS_AP || st == BS_TRUERES) return stage_t<double>(b, st, sel, l, grid, only);
+  return stage_t<float>(b, st, sel, l, grid, only);
 }
 
 // the FP32 V(1,1) cycle of every system selected by mask `sel`: on entry each
@@ -405,17 +531,13 @@ int autotune(xamg_batch *b) {
         int best_opt = 0;
         for (int o = 0; o < 2; ++o) {
           opt = o;
-          if ((rc = upload_tables(b)) != XAMG_OK) break;
           // the grid this system alone needs under this split
           const int64_t rows = op == 2 ? V.nc : V.n;
           const int rpb = bstage_rows_per_block(st, b->sys_h[s].nv, o);
           const int grid = (int)std::min<int64_t>((rows + rpb - 1) / rpb, bstage_max_grid(st));
-          if (launch_bstage(st, b->sys_d, b->ns, sel_dev(b, 4), l, grid, b->st) < 0) {
-            rc = XAMG_ERR_CUDA;
-            break;
-          }
+          if ((rc = stage(b, st, 4, l, grid, s)) != XAMG_OK) break;
           cudaEventRecord(e0, b->st);
-          for (int r = 0; r < 3; ++r) launch_bstage(st, b->sys_d, b->ns, sel_dev(b, 4), l, grid, b->st);
+          for (int r = 0; r < 3; ++r) stage(b, st, 4, l, grid, s);
           cudaEventRecord(e1, b->st);
           if (cudaEventSynchronize(e1) != cudaSuccess) {
             rc = XAMG_ERR_CUDA;

@@ -96,10 +96,8 @@ enum BStage : int {
   BS_COUNT
 };
 
-// Launches stage `st` on level `level` for the systems with sel[s] != 0;
-// returns the grid used (-1 on error).  `grid` 0 lets the launcher choose.
-int launch_bstage(int st, const BSys *sys, int ns, const int *sel, int level, int grid, cudaStream_t s);
-// Rows per block of the stage's product for a system of nv columns and split opt.
+// Rows per block of stage st's product for a system of nv columns and row
+// split opt, and the stage kernel's persistent grid bound.
 int bstage_rows_per_block(int st, int nv, int opt);
 int bstage_max_grid(int st);
 

@@ -1,13 +1,18 @@
 // batch_stage.cuh -- the batched row stages: one persistent launch applies
-// one step of the V-cycle (or of the Krylov loop) to every selected system.
-// Blocks walk the systems in order; within a system the warps take the rows
-// in the same grid-stride order as the single-system row kernel (rows_vec /
-// rows_sliced of kernels.cuh), so each system's products and partial dot
-// sums are computed exactly as a single-system launch with the same grid
-// would compute them.  The column count NV and the row split of every
-// system's operator are runtime values: a switch selects the compile-time
-// body.  Included by batch_stage*.cu (one group of stages per unit).
+// one step of the V-cycle (or of the Krylov loop) to a list of systems.  The
+// host builds each system's row operation (as for a single-system launch) and
+// passes the whole list as one kernel parameter block, so every field is read
+// from the constant bank where it is used, as in the single-system kernel.
+// Blocks walk the list in order; within a system the warps take the rows in
+// the single-system grid-stride order (rows_vec / rows_sliced of
+// kernels.cuh), so each system's products and partial dot sums are computed
+// exactly as a single-system launch with the same grid computes them.  The
+// column count NV and the row split of each entry are runtime values: a
+// switch selects the compile-time body.  Included by batch.cu and
+// batch_stage*.cu (one group of kernels per unit).
 #pragma once
+#include <algorithm>
+
 #include "batch.h"
 #include "kernels.cuh"
 
@@ -37,7 +42,7 @@ __host__ __device__ constexpr int rows_per_block(int opt) {
   return kWarps * (32 / ((NV == 1 ? 1 : NV / row_vec<TB, NV>()) * (opt ? wide_s<TB, NV>() : narrow_s<TB, NV>())));
 }
 
-// WIDE: whether the wide split is compiled for this stage (the stages that
+// WIDE: whether the wide split is compiled for this kernel (the kernels that
 // only act on the fine level, a short-row stencil, keep the narrow one).
 template <class TB, class TV, bool NEG, int EPI, bool WIDE>
 __device__ __forceinline__ void row_dispatch(int nv, int opt, const RowOpT<TB> &op) {
@@ -60,280 +65,71 @@ __device__ __forceinline__ void row_dispatch(int nv, int opt, const RowOpT<TB> &
 #undef XAMG_RD
 }
 
+// Entries per launch: the parameter block stays below the 32 KB limit of
+// kernel parameters.
+constexpr int kStageOps = 96;
+
 template <class TB>
-__device__ __forceinline__ RowOpT<TB> blank_op() {
-  RowOpT<TB> o;
-  o.n = 0;
-  o.rowptr = nullptr;
-  o.col = nullptr;
-  o.val = nullptr;
-  o.rscale = nullptr;
-  o.colw = nullptr;
-  o.rowmeta = nullptr;
-  o.src = nullptr;
-  o.init = nullptr;
-  o.y = nullptr;
-  o.dp = nullptr;
-  o.w = nullptr;
-  o.c1 = 0;
-  o.dnext = nullptr;
-  o.x = nullptr;
-  o.dot_u = nullptr;
-  o.dot_u2 = nullptr;
-  o.partials = nullptr;
-  o.partials2 = nullptr;
-  return o;
-}
-
-// Stage definitions: block scalar, sign, epilogue; whether it applies to
-// system S at level l; the operation; the operator's row split.
-template <int ST>
-struct SD;
-
-__device__ __forceinline__ void op_A(RowOpT<float> &o, const BLevel &V) {
-  o.n = V.n;
-  o.rowptr = V.Arp;
-  o.col = V.Aci;
-  o.val = V.Av;
-}
-
-template <>
-struct SD<BS_PRE1> {
-  using TB = float;
-  static constexpr bool WIDE = true;
-  static constexpr bool NEG = true;
-  static constexpr int EPI = EPI_Y_DN;
-  __device__ static bool on(const BSys &S, int l) { return l < S.L - 1; }
-  __device__ static int opt(const BSys &, const BLevel &V) { return V.optA; }
-  __device__ static RowOpT<float> make(const BSys &S, int l) {
-    const BLevel &V = S.lv[l];
-    RowOpT<float> o = blank_op<float>();
-    op_A(o, V);
-    o.init = V.b; o.src = V.x; o.y = V.r; o.dp = V.x; o.w = V.w[1]; o.c1 = V.c1[1]; o.dnext = V.d;
-    return o;
-  }
-};
-template <>
-struct SD<BS_PRE2> {
-  using TB = float;
-  static constexpr bool WIDE = true;
-  static constexpr bool NEG = true;
-  static constexpr int EPI = EPI_Y_XDP;
-  __device__ static bool on(const BSys &S, int l) { return l < S.L - 1; }
-  __device__ static int opt(const BSys &, const BLevel &V) { return V.optA; }
-  __device__ static RowOpT<float> make(const BSys &S, int l) {
-    const BLevel &V = S.lv[l];
-    RowOpT<float> o = blank_op<float>();
-    op_A(o, V);
-    o.init = V.r; o.src = V.d; o.y = V.r; o.dp = V.d; o.x = V.x;
-    return o;
-  }
-};
-template <>
-struct SD<BS_RESTRICT> {
-  using TB = float;
-  static constexpr bool WIDE = true;
-  static constexpr bool NEG = false;
-  static constexpr int EPI = EPI_Y_D0;
-  __device__ static bool on(const BSys &S, int l) { return l + 2 < S.L; }
-  __device__ static int opt(const BSys &, const BLevel &V) { return V.optR; }
-  __device__ static RowOpT<float> make(const BSys &S, int l) {
-    const BLevel &V = S.lv[l], &C = S.lv[l + 1];
-    RowOpT<float> o = blank_op<float>();
-    o.n = V.nc; o.rowptr = V.Rrp; o.col = V.Rci; o.val = V.Rv;
-    o.src = V.r; o.y = C.b; o.w = C.w[0]; o.dnext = C.x;
-    return o;
-  }
-};
-template <>
-struct SD<BS_RESTRICT_C> {
-  using TB = float;
-  static constexpr bool WIDE = true;
-  static constexpr bool NEG = false;
-  static constexpr int EPI = EPI_Y;
-  __device__ static bool on(const BSys &S, int l) { return l + 2 == S.L; }
-  __device__ static int opt(const BSys &, const BLevel &V) { return V.optR; }
-  __device__ static RowOpT<float> make(const BSys &S, int l) {
-    const BLevel &V = S.lv[l], &C = S.lv[l + 1];
-    RowOpT<float> o = blank_op<float>();
-    o.n = V.nc; o.rowptr = V.Rrp; o.col = V.Rci; o.val = V.Rv;
-    o.src = V.r; o.y = C.b;
-    return o;
-  }
-};
-template <>
-struct SD<BS_PROLONG> {
-  using TB = float;
-  static constexpr bool WIDE = true;
-  static constexpr bool NEG = false;
-  static constexpr int EPI = EPI_Y;
-  __device__ static bool on(const BSys &S, int l) { return l < S.L - 1; }
-  __device__ static int opt(const BSys &, const BLevel &V) { return V.optP; }
-  __device__ static RowOpT<float> make(const BSys &S, int l) {
-    const BLevel &V = S.lv[l], &C = S.lv[l + 1];
-    RowOpT<float> o = blank_op<float>();
-    o.n = V.n; o.rowptr = V.Prp; o.col = V.Pci; o.val = V.Pv;
-    o.init = V.x; o.src = C.x; o.y = V.x;
-    return o;
-  }
-};
-template <>
-struct SD<BS_POST1> {
-  using TB = float;
-  static constexpr bool WIDE = true;
-  static constexpr bool NEG = true;
-  static constexpr int EPI = EPI_Y_D0;
-  __device__ static bool on(const BSys &S, int l) { return l < S.L - 1; }
-  __device__ static int opt(const BSys &, const BLevel &V) { return V.optA; }
-  __device__ static RowOpT<float> make(const BSys &S, int l) {
-    const BLevel &V = S.lv[l];
-    RowOpT<float> o = blank_op<float>();
-    op_A(o, V);
-    o.init = V.b; o.src = V.x; o.y = V.r; o.w = V.w[0]; o.dnext = V.d;
-    return o;
-  }
-};
-template <>
-struct SD<BS_POST2> {
-  using TB = float;
-  static constexpr bool WIDE = true;
-  static constexpr bool NEG = true;
-  static constexpr int EPI = EPI_XLAST;
-  __device__ static bool on(const BSys &S, int l) { return l < S.L - 1; }
-  __device__ static int opt(const BSys &, const BLevel &V) { return V.optA; }
-  __device__ static RowOpT<float> make(const BSys &S, int l) {
-    const BLevel &V = S.lv[l];
-    RowOpT<float> o = blank_op<float>();
-    op_A(o, V);
-    o.init = V.r; o.src = V.d; o.dp = V.d; o.w = V.w[1]; o.c1 = V.c1[1]; o.x = V.x;
-    return o;
-  }
-};
-template <>
-struct SD<BS_POST2_DOT2> {
-  using TB = float;
-  static constexpr bool WIDE = false;
-  static constexpr bool NEG = true;
-  static constexpr int EPI = EPI_XLAST_DOT2;
-  __device__ static bool on(const BSys &S, int l) { return l < S.L - 1; }
-  __device__ static int opt(const BSys &, const BLevel &V) { return V.optA; }
-  __device__ static RowOpT<float> make(const BSys &S, int l) {
-    RowOpT<float> o = SD<BS_POST2>::make(S, l);
-    o.dot_u = S.R; o.partials = S.part[1];
-    o.dot_u2 = S.Q; o.partials2 = S.part[2];
-    return o;
-  }
-};
-template <>
-struct SD<BS_AP> {
-  using TB = double;
-  static constexpr bool WIDE = false;
-  static constexpr bool NEG = false;
-  static constexpr int EPI = EPI_Y_DOT;
-  __device__ static bool on(const BSys &, int) { return true; }
-  __device__ static int opt(const BSys &S, const BLevel &) { return S.optA0; }
-  __device__ static RowOpT<double> make(const BSys &S, int) {
-    RowOpT<double> o = blank_op<double>();
-    o.n = (int)S.n0; o.rowptr = S.A0rp; o.col = S.A0ci; o.val = S.A0v;
-    o.src = S.P; o.y = S.Q; o.dot_u = S.P; o.partials = S.part[0];
-    return o;
-  }
-};
-template <>
-struct SD<BS_TRUERES> {
-  using TB = double;
-  static constexpr bool WIDE = false;
-  static constexpr bool NEG = true;
-  static constexpr int EPI = EPI_Y_DOT2;
-  __device__ static bool on(const BSys &, int) { return true; }
-  __device__ static int opt(const BSys &S, const BLevel &) { return S.optA0; }
-  __device__ static RowOpT<double> make(const BSys &S, int) {
-    RowOpT<double> o = blank_op<double>();
-    o.n = (int)S.n0; o.rowptr = S.A0rp; o.col = S.A0ci; o.val = S.A0v;
-    o.init = S.Bn; o.src = S.X; o.y = S.Q; o.partials2 = S.part[2];
-    return o;
-  }
-};
-template <>
-struct SD<BS_TUNE_A> {
-  using TB = float;
-  static constexpr bool WIDE = true;
-  static constexpr bool NEG = false;
-  static constexpr int EPI = EPI_Y;
-  __device__ static bool on(const BSys &S, int l) { return l < S.L - 1; }
-  __device__ static int opt(const BSys &, const BLevel &V) { return V.optA; }
-  __device__ static RowOpT<float> make(const BSys &S, int l) {
-    const BLevel &V = S.lv[l];
-    RowOpT<float> o = blank_op<float>();
-    op_A(o, V);
-    o.src = V.x; o.y = V.r;
-    return o;
-  }
-};
-template <>
-struct SD<BS_TUNE_P> {
-  using TB = float;
-  static constexpr bool WIDE = true;
-  static constexpr bool NEG = false;
-  static constexpr int EPI = EPI_Y;
-  __device__ static bool on(const BSys &S, int l) { return l < S.L - 1; }
-  __device__ static int opt(const BSys &, const BLevel &V) { return V.optP; }
-  __device__ static RowOpT<float> make(const BSys &S, int l) {
-    const BLevel &V = S.lv[l], &C = S.lv[l + 1];
-    RowOpT<float> o = blank_op<float>();
-    o.n = V.n; o.rowptr = V.Prp; o.col = V.Pci; o.val = V.Pv;
-    o.src = C.x; o.y = V.r;
-    return o;
-  }
-};
-template <>
-struct SD<BS_TUNE_R> {
-  using TB = float;
-  static constexpr bool WIDE = true;
-  static constexpr bool NEG = false;
-  static constexpr int EPI = EPI_Y;
-  __device__ static bool on(const BSys &S, int l) { return l < S.L - 1; }
-  __device__ static int opt(const BSys &, const BLevel &V) { return V.optR; }
-  __device__ static RowOpT<float> make(const BSys &S, int l) {
-    const BLevel &V = S.lv[l], &C = S.lv[l + 1];
-    RowOpT<float> o = blank_op<float>();
-    o.n = V.nc; o.rowptr = V.Rrp; o.col = V.Rci; o.val = V.Rv;
-    o.src = V.r; o.y = C.b;
-    return o;
-  }
+struct StageParams {
+  int count;
+  int sys[kStageOps];              // system index (selection mask)
+  unsigned char nv[kStageOps];     // block width
+  unsigned char opt[kStageOps];    // row split
+  RowOpT<TB> op[kStageOps];
 };
 
-// One launch of stage ST on level `level` for every system s with sel[s]:
-// blocks take the systems in order and, inside one, the rows in the
-// single-system grid-stride order.
-template <int ST>
-__global__ void __launch_bounds__(kBlock, 3) k_bstage(const BSys *__restrict__ sys, int ns,
-                                                      const int *__restrict__ sel, int level) {
-  using D = SD<ST>;
+// The (block scalar, sign, epilogue, wide split) combinations the batched
+// solve uses.
+enum BKind : int {
+  BK_F_YDN = 0,     // FP32 first pre-smoothing step
+  BK_F_YXDP,        // FP32 last pre-smoothing step
+  BK_F_D0_POS,      // FP32 restriction writing the next level's first iterate
+  BK_F_Y_POS,       // FP32 plain product (restriction to the coarsest, prolongation, tuning)
+  BK_F_D0_NEG,      // FP32 first post-smoothing step
+  BK_F_XLAST,       // FP32 last post-smoothing step
+  BK_F_XLAST_DOT2,  // the same on level 0 with two FP64 partial dots
+  BK_D_YDOT,        // FP64 A p with p.q
+  BK_D_YDOT2,       // FP64 true residual with |r|^2
+  BK_COUNT
+};
+
+template <int K> struct KD;
+template <> struct KD<BK_F_YDN> { using TB = float; static constexpr bool NEG = true, WIDE = true; static constexpr int EPI = EPI_Y_DN; };
+template <> struct KD<BK_F_YXDP> { using TB = float; static constexpr bool NEG = true, WIDE = true; static constexpr int EPI = EPI_Y_XDP; };
+template <> struct KD<BK_F_D0_POS> { using TB = float; static constexpr bool NEG = false, WIDE = true; static constexpr int EPI = EPI_Y_D0; };
+template <> struct KD<BK_F_Y_POS> { using TB = float; static constexpr bool NEG = false, WIDE = true; static constexpr int EPI = EPI_Y; };
+template <> struct KD<BK_F_D0_NEG> { using TB = float; static constexpr bool NEG = true, WIDE = true; static constexpr int EPI = EPI_Y_D0; };
+template <> struct KD<BK_F_XLAST> { using TB = float; static constexpr bool NEG = true, WIDE = true; static constexpr int EPI = EPI_XLAST; };
+template <> struct KD<BK_F_XLAST_DOT2> { using TB = float; static constexpr bool NEG = true, WIDE = false; static constexpr int EPI = EPI_XLAST_DOT2; };
+template <> struct KD<BK_D_YDOT> { using TB = double; static constexpr bool NEG = false, WIDE = false; static constexpr int EPI = EPI_Y_DOT; };
+template <> struct KD<BK_D_YDOT2> { using TB = double; static constexpr bool NEG = true, WIDE = false; static constexpr int EPI = EPI_Y_DOT2; };
+
+template <int K>
+__global__ void __launch_bounds__(kBlock, 4) k_bstage(const __grid_constant__ StageParams<typename KD<K>::TB> P,
+                                                      const int *__restrict__ sel) {
+  using D = KD<K>;
   using TB = typename D::TB;
-  for (int s = 0; s < ns; ++s) {
-    if (!sel[s]) continue;
-    const BSys &S = sys[s];
-    if (!D::on(S, level)) continue;
-    const RowOpT<TB> op = D::make(S, level);
-    const int opt = D::opt(S, S.lv[level]);
-    row_dispatch<TB, TB, D::NEG, D::EPI, D::WIDE>(S.nv, opt, op);
+  for (int i = 0; i < P.count; ++i) {
+    if (!sel[P.sys[i]]) continue;
+    row_dispatch<TB, TB, D::NEG, D::EPI, D::WIDE>(P.nv[i], P.opt[i], P.op[i]);
     // the dot epilogues reuse the block's shared reduction buffers
     if constexpr (epi_has_dot<D::EPI>()) __syncthreads();
   }
 }
 
-template <int ST>
-int bstage_launch_t(const BSys *sys, int ns, const int *sel, int level, int grid, cudaStream_t st) {
+// Launches kernel K with the parameter block `params` (a StageParams of the
+// kernel's block scalar); grid <= 0 returns the persistent grid bound.
+template <int K>
+int bk_launch_t(const void *params, const int *sel, int grid, cudaStream_t st) {
   static int max_grid = 0;
   if (!max_grid) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bstage<ST>, kBlock, 0) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bstage<K>, kBlock, 0) != cudaSuccess || b < 1) b = 1;
     max_grid = std::min(kMaxGrid, b * device_sm_count());
   }
-  if (grid <= 0) return max_grid;  // query
+  if (grid <= 0) return max_grid;
   grid = std::min(grid, max_grid);
-  k_bstage<ST><<<grid, kBlock, 0, st>>>(sys, ns, sel, level);
+  k_bstage<K><<<grid, kBlock, 0, st>>>(*static_cast<const StageParams<typename KD<K>::TB> *>(params), sel);
   g_launches++;
   return cudaPeekAtLastError() == cudaSuccess ? grid : -1;
 }
