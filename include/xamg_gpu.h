@@ -282,6 +282,19 @@ int xamg_coldot(const double *U, const double *V, int64_t n, int32_t m, double *
 int xamg_coldot_noalloc(const double *U, const double *V, int64_t n, int32_t m, double *out,
                         void *stream);
 
+/* Autotuner of the reduced-precision preconditioner's sparse products: for
+ * every level's A, P and R, times y = M x on FP32 blocks of pad(m) columns
+ * (m in [1, XAMG_MAX_RHS]; precond XAMG_PREC_FP32 or XAMG_PREC_BF16) under
+ * both row splits -- the default (a group of lanes per row, several rows per
+ * warp) and one row per warp with its entries split over the lanes -- and
+ * keeps the faster in the hierarchy; later solves and V-cycles of that block
+ * width and precision use it.  Results do not depend on the split beyond the
+ * order of each row's FP32 sums.  ops_tuned / ops_wide (may be NULL): products
+ * tuned and how many chose one row per warp.  Uses the hierarchy's cached
+ * workspace; synchronizes `stream`.  No counterpart in the paper. */
+int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_t *ops_tuned,
+                  int32_t *ops_wide);
+
 /* ---- batched solve of many independent systems ----
  *
  * Solves count independent systems A_s X_s = B_s (A_s n_s x n_s with its own

@@ -38,6 +38,11 @@ struct DevLevel {
   uint32_t *a16meta = nullptr;   // per row: first window << 16 | entries in it
   float *w32[4] = {nullptr, nullptr, nullptr, nullptr};
   float c1f[4] = {0, 0, 0, 0};
+  // row split of the FP32-block products chosen by xamg_autotune, per values
+  // (0: FP32, 1: bf16 A), operator (A, P, R) and block width (log2 nv):
+  // -1 untuned (the default rule), 0 narrow, 1 one row per warp
+  signed char split[2][3][6];
+  DevLevel() { std::memset(split, -1, sizeof(split)); }
 };
 
 struct TimerRec {
@@ -483,10 +488,16 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
     cudaEventRecord(a, st);
   }
   int g;
-  if constexpr (sizeof(TB) == 8)
+  if constexpr (sizeof(TB) == 8) {
     g = launch_rows(op, nv, slices_for(M, nv, false), neg, epi, st);
-  else
-    g = launch_rows_f(op, nv, slices_for(M, nv, true), neg, epi, vt, st);
+  } else {
+    int sl = slices_for(M, nv, true);
+    int lg = 0;
+    while ((1 << lg) < nv) ++lg;
+    const int t = D.split[vt ? 1 : 0][which][lg];
+    if (t >= 0) sl = t ? (nv == 1 ? 16 : 2) : (nv == 1 ? 4 : 1);
+    g = launch_rows_f(op, nv, sl, neg, epi, vt, st);
+  }
   if (h->timing) {
     cudaEventRecord(b, st);
     const int slot = which + (sizeof(TB) == 8 ? 0 : 3);
@@ -1382,6 +1393,75 @@ int xamg_coldot(const double *U, const double *V, int64_t n, int32_t m, double *
   cudaError_t e2 = cudaFreeAsync(part, st);
   cudaError_t e3 = cudaStreamSynchronize(st);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return XAMG_ERR_CUDA;
+  return XAMG_OK;
+}
+
+int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_t *ops_tuned,
+                  int32_t *ops_wide) {
+  if (!h || !h->on_device || m < 1 || m > XAMG_MAX_RHS ||
+      (precond != XAMG_PREC_FP32 && precond != XAMG_PREC_BF16))
+    return XAMG_ERR_INVALID_ARG;
+  XCK(cudaSetDevice(h->device));
+  const int nv = pad_nv(m);
+  Work W;
+  int rc = ensure_workspace(h, nv, XAMG_PCG, precond, nullptr, W);
+  if (rc != XAMG_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int lg = 0;
+  while ((1 << lg) < nv) ++lg;
+  const int pc = precond == XAMG_PREC_BF16 ? 1 : 0;
+  const bool timing = h->timing;
+  h->timing = false;
+  cudaEvent_t e0, e1;
+  XCK(cudaEventCreate(&e0));
+  XCK(cudaEventCreate(&e1));
+  int tuned = 0, wide = 0;
+  const int L = (int)h->lv.size();
+  for (int l = 0; l + 1 < L && rc == XAMG_OK; ++l) {
+    for (int which = 0; which < 3 && rc == XAMG_OK; ++which) {
+      // y = M x on this level's FP32 work blocks
+      RowOpT<float> o = blank<float>();
+      if (which == 0) {
+        o.src = W.fx[l]; o.y = W.fr[l];
+      } else if (which == 1) {
+        o.src = W.fx[l + 1]; o.y = W.fr[l];
+      } else {
+        o.src = W.fr[l]; o.y = W.fb[l + 1];
+      }
+      signed char &slot = h->lv[l].split[pc][which][lg];
+      float best = 1e30f;
+      int best_opt = 0;
+      for (int opt = 0; opt < 2; ++opt) {
+        slot = (signed char)opt;
+        if (rows<float>(h, l, which, precond, o, nv, false, EPI_Y, st) < 0) {
+          rc = XAMG_ERR_CUDA;
+          break;
+        }
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) rows<float>(h, l, which, precond, o, nv, false, EPI_Y, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = XAMG_ERR_CUDA;
+          break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          best_opt = opt;
+        }
+      }
+      slot = (signed char)best_opt;
+      ++tuned;
+      wide += best_opt;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->timing = timing;
+  if (rc != XAMG_OK) return rc;
+  if (ops_tuned) *ops_tuned = tuned;
+  if (ops_wide) *ops_wide = wide;
   return XAMG_OK;
 }
 

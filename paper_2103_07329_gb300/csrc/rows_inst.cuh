@@ -71,17 +71,17 @@ int rows_e(const RowOpT<TBx> &op, bool neg, int epi, cudaStream_t st) {
 }
 
 // m = 1 splits rows over 4 or 16 lanes; wider blocks give each lane VEC
-// columns, and FP32 blocks of 16 or 32 columns may split long rows over the
-// whole warp (slices).
+// columns, and FP32 blocks may split long rows over the whole warp (slices:
+// one row per warp).
 template <class TV>
 int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t st) {
 #if XAMG_NV == 1
   if (slices >= 16) return rows_e<TV, 1, 16>(op, neg, epi, st);
   return rows_e<TV, 1, 4>(op, neg, epi, st);
 #else
-#if XAMG_FLOAT && XAMG_NV >= 16
+#if XAMG_FLOAT
   // long rows of FP32 blocks: every group of the warp takes a slice of one row
-  if (slices > 1) return rows_e<TV, XAMG_NV, 32 / (XAMG_NV / 4)>(op, neg, epi, st);
+  if (slices > 1) return rows_e<TV, XAMG_NV, 32 / (XAMG_NV / row_vec<float, XAMG_NV>())>(op, neg, epi, st);
 #endif
   (void)slices;
   return rows_e<TV, XAMG_NV, 1>(op, neg, epi, st);
