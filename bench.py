@@ -43,6 +43,18 @@ UNIT = "RHS/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+METHODS = {"pcg": 0, "bicgstab": 1, "bicgstab_reordered": 2, "bicgstab_pipelined": 3}
+
+
+def oracle_solve(h, a, Bm):
+    """The oracle's solve of the benchmark's method."""
+    if a.method == "pcg":
+        return h.pcg(Bm, a.tol, a.maxit)
+    variant = {"bicgstab": "classical", "bicgstab_reordered": "reordered",
+               "bicgstab_pipelined": "pipelined"}[a.method]
+    return h.bicgstab(Bm, a.tol, a.maxit, variant=variant)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -54,7 +66,10 @@ def parse():
     ap.add_argument("--kseed", type=int, default=1, help="diffusion7: seed of the cell coefficients")
     ap.add_argument("--grid", type=int, default=None)
     ap.add_argument("--m", type=int, default=32)
-    ap.add_argument("--method", default="pcg", choices=["pcg", "bicgstab"])
+    ap.add_argument("--method", default="pcg",
+                    choices=["pcg", "bicgstab", "bicgstab_reordered", "bicgstab_pipelined"])
+    ap.add_argument("--sweep-methods", default="pcg,bicgstab",
+                    help="--sweep: comma-separated methods (also bicgstab_reordered, bicgstab_pipelined)")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=100)
     ap.add_argument("--cpu-cols", type=int, default=1, help="columns in the oracle's sample")
@@ -198,7 +213,7 @@ def cpu_baseline(a, A, seconds_note=True):
     t_setup = time.perf_counter() - t0
     Bm = P.rhs_uniform(A.n, a.cpu_cols, 0, m_draw=max(a.m, a.cpu_cols))
     t0 = time.perf_counter()
-    r = h.pcg(Bm, a.tol, a.maxit) if a.method == "pcg" else h.bicgstab(Bm, a.tol, a.maxit)
+    r = oracle_solve(h, a, Bm)
     t = time.perf_counter() - t0
     ok = int(np.sum((r.status == 0) & (r.relres <= a.tol)))
     return ok / t, dict(t_solve=t, t_setup=t_setup, iters=r.iters.tolist(), h=h)
@@ -322,7 +337,9 @@ def run_reference(a):
     A = make_matrix(a)
     h = oracle.Hierarchy(A)
     Bm = P.rhs_uniform(A.n, a.cpu_cols, 0, m_draw=max(a.m, a.cpu_cols))
-    solve = h.pcg if a.method == "pcg" else h.bicgstab
+
+    def solve(Bm, tol, maxit):
+        return oracle_solve(h, a, Bm)
     for _ in range(a.warmup):
         solve(Bm, a.tol, a.maxit)
     times, solved = [], 0
@@ -369,7 +386,7 @@ def run_ours(a):
     t0 = time.perf_counter()
     h = B.Hierarchy(A)
     t_setup = time.perf_counter() - t0
-    method = B.PCG if a.method == "pcg" else B.BICGSTAB
+    method = METHODS[a.method]
     Bm = P.rhs_uniform(A.n, a.m, MR.rhs_seed(rank), m_draw=max(a.m, 32))
     Bd = torch.from_numpy(Bm).cuda()
     X = torch.empty_like(Bd)
@@ -588,9 +605,12 @@ def run_sweep(a):
         Bm = P.rhs_uniform(A.n, m, 0, m_draw=32)
         Bd = torch.from_numpy(Bm).cuda()
         X = torch.empty_like(Bd)
-        for method_name, method in (("pcg", B.PCG), ("bicgstab", B.BICGSTAB)):
+        for method_name in a.sweep_methods.split(","):
+            method = METHODS[method_name]
             for form, prec in (("fp64", B.PREC_FP64), ("mixed_fp32", B.PREC_FP32),
                                ("mixed_bf16", B.PREC_BF16)):
+                if method == B.BICGSTAB_PIPELINED and prec != B.PREC_FP64:
+                    continue  # its recurrences need a linear preconditioner
                 h.solve(Bd, X, a.tol, a.maxit, method, precond=prec)
                 h.timing_enable(True)
                 torch.cuda.synchronize()

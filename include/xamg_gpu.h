@@ -57,6 +57,21 @@ extern "C" {
  * level) */
 #define XAMG_PCG 0
 #define XAMG_BICGSTAB 1
+/* BiCGStab variants (paper Sec. 2.1: "Reordered BiCGStab", "Pipelined
+ * BiCGStab" and their merged formulations), the same right-preconditioned
+ * method in exact arithmetic:
+ *   REORDERED: the dot products of an iteration in two groups, (rhat, v) and
+ *     (t, s), (t, t), (rhat, s), (rhat, t), (s, s), with rho and ||r|| of the
+ *     next iteration from recurrences (Krasnopolsky 2010): one host read per
+ *     iteration instead of two (no test between the two halves).
+ *   PIPELINED: auxiliary products w = B r, s = B p, z = B s, t = B w, v = B z
+ *     of B = A M, so that each group of dot products can run beside one
+ *     application of B (Cools and Vanroose 2017); the solution is formed as
+ *     x = x0 + M u when the columns stop.  Its recurrences assume a linear
+ *     M: XAMG_PREC_FP64 only (XAMG_ERR_INVALID_ARG otherwise).
+ * Vector updates carry their dot products in both (merged formulation). */
+#define XAMG_BICGSTAB_REORDERED 2
+#define XAMG_BICGSTAB_PIPELINED 3
 
 /* preconditioner precision (paper Sec. 2.3, "mixed-precision": reduced
  * precision in the multigrid hierarchy only, basic precision for the result)
@@ -121,7 +136,8 @@ typedef struct {
 } xamg_amg_params;
 
 /* Solve options (fill with xamg_solve_opts_default first).
- *   method       XAMG_PCG or XAMG_BICGSTAB
+ *   method       XAMG_PCG, XAMG_BICGSTAB, XAMG_BICGSTAB_REORDERED or
+ *                XAMG_BICGSTAB_PIPELINED
  *   precond      XAMG_PREC_FP64 (default), XAMG_PREC_FP32 or XAMG_PREC_BF16
  *   x0_given     0 (default): start from X = 0; 1: X holds the initial guess
  *                X0 on entry (a warm start, e.g. a learned prediction); the

@@ -76,7 +76,7 @@ def lib():
         L.orc_spmm_f.restype = C.c_int
         L.orc_bf16_bits.argtypes = [C.c_float]
         L.orc_bf16_bits.restype = C.c_uint16
-        for name in ("orc_pcg_prec", "orc_bicgstab_prec"):
+        for name in ("orc_pcg_prec", "orc_bicgstab_prec", "orc_rbicgstab_prec", "orc_pbicgstab_prec"):
             f = getattr(L, name)
             f.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, _f64p, _f64p, C.c_double, C.c_int,
                           _i32p, _f64p, _i32p]
@@ -242,7 +242,14 @@ class Hierarchy:
             return self._solve(lib().orc_pcg_prec, B, tol, maxit, prec, X0)
         return self._solve(lib().orc_pcg, B, tol, maxit)
 
-    def bicgstab(self, B, tol=1e-8, maxit=200, prec=0, X0=None):
+    def bicgstab(self, B, tol=1e-8, maxit=200, prec=0, X0=None, variant="classical"):
+        """BiCGStab; variant "reordered" (two dot-product groups per iteration,
+        recurrences for rho and |r|) or "pipelined" (auxiliary products so that
+        each dot-product group overlaps one operator application)."""
+        if variant == "reordered":
+            return self._solve(lib().orc_rbicgstab_prec, B, tol, maxit, prec, X0)
+        if variant == "pipelined":
+            return self._solve(lib().orc_pbicgstab_prec, B, tol, maxit, prec, X0)
         if prec or X0 is not None:
             return self._solve(lib().orc_bicgstab_prec, B, tol, maxit, prec, X0)
         return self._solve(lib().orc_bicgstab, B, tol, maxit)

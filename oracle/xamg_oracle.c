@@ -1201,3 +1201,321 @@ int orc_bicgstab(ohier *h, int m, const double *b, double *x, double tol, int ma
                  double *relres, int *status) {
   return orc_bicgstab_prec(h, 0, 0, m, b, x, tol, maxit, iters, relres, status);
 }
+
+/* Reordered BiCGStab (paper Sec. 2.1: "Reordered BiCGStab"; Krasnopolsky
+ * 2010): the operations of the right-preconditioned BiCGStab regrouped so
+ * that an iteration has two groups of dot products instead of three:
+ *   group 1, after v = A M p:  (rhat, v)
+ *   group 2, after t = A M s:  (t, s), (t, t), (rhat, s), (rhat, t), (s, s)
+ * and the next rho and residual norm come from the recurrences
+ *   rho' = (rhat, r') = (rhat, s) - omega (rhat, t)
+ *   |r'|^2 = (s, s) - 2 omega (t, s) + omega^2 (t, t).
+ * There is no convergence test between the two halves: a column whose s
+ * already meets the tolerance (read from group 2) takes x += alpha M p,
+ * r = s.  Same freezing, confirmation and restart rules as orc_bicgstab_prec
+ * (a restarted column takes rhat = r and rho = |r|^2). */
+int orc_rbicgstab_prec(ohier *h, int prec, int x0_given, int m, const double *b, double *x,
+                       double tol, int maxit, int *iters, double *relres, int *status) {
+  const ocsr *A = &h->A[0];
+  size_t N = (size_t)A->n * m, i, n = (size_t)A->n;
+  int j, k, rc = ORC_OK, any;
+  double *r = NULL, *rh = NULL, *p = NULL, *v = NULL, *s = NULL, *t = NULL, *ph = NULL, *sh = NULL;
+  double *nb = NULL, *rho = NULL, *rho_old = NULL, *alpha = NULL, *omega = NULL, *c = NULL;
+  double *ts = NULL, *tt = NULL, *rs = NULL, *rt = NULL, *ss = NULL, *tn = NULL;
+  int *state = NULL, *restart = NULL;
+  if (!h || m < 1 || maxit < 0 || !(tol > 0.0) || prec < 0 || prec > 2) return ORC_ERR_ARG;
+  if (!all_finite(N, b)) return ORC_ERR_NONFINITE;
+  r = (double *)malloc(N * sizeof(double)); rh = (double *)malloc(N * sizeof(double));
+  p = (double *)malloc(N * sizeof(double)); v = (double *)malloc(N * sizeof(double));
+  s = (double *)malloc(N * sizeof(double)); t = (double *)malloc(N * sizeof(double));
+  ph = (double *)malloc(N * sizeof(double)); sh = (double *)malloc(N * sizeof(double));
+  nb = (double *)malloc((size_t)m * sizeof(double)); rho = (double *)malloc((size_t)m * sizeof(double));
+  rho_old = (double *)malloc((size_t)m * sizeof(double)); alpha = (double *)malloc((size_t)m * sizeof(double));
+  omega = (double *)malloc((size_t)m * sizeof(double)); c = (double *)malloc((size_t)m * sizeof(double));
+  ts = (double *)malloc((size_t)m * sizeof(double)); tt = (double *)malloc((size_t)m * sizeof(double));
+  rs = (double *)malloc((size_t)m * sizeof(double)); rt = (double *)malloc((size_t)m * sizeof(double));
+  ss = (double *)malloc((size_t)m * sizeof(double)); tn = (double *)malloc((size_t)m * sizeof(double));
+  state = (int *)calloc((size_t)m, sizeof(int)); restart = (int *)calloc((size_t)m, sizeof(int));
+  if (!r || !rh || !p || !v || !s || !t || !ph || !sh || !nb || !rho || !rho_old || !alpha ||
+      !omega || !c || !ts || !tt || !rs || !rt || !ss || !tn || !state || !restart) {
+    rc = ORC_ERR_OOM;
+    goto done;
+  }
+  coldot(n, m, b, b, nb);
+  for (j = 0; j < m; ++j) { nb[j] = sqrt(nb[j]); iters[j] = 0; if (nb[j] == 0.0) state[j] = 4; restart[j] = 1; }
+  if (x0_given) {
+    if (!all_finite(N, x)) { rc = ORC_ERR_NONFINITE; goto done; }
+    for (i = 0; i < n; ++i)
+      for (j = 0; j < m; ++j) if (state[j] == 4) x[i * m + j] = 0.0;
+    spmm(A, m, x, t);
+    for (i = 0; i < N; ++i) { r[i] = b[i] - t[i]; rh[i] = r[i]; p[i] = 0.0; v[i] = 0.0; }
+    coldot(n, m, r, r, c);
+    for (j = 0; j < m; ++j)
+      if (state[j] == 0 && sqrt(c[j]) <= tol * nb[j]) state[j] = 1;
+  } else {
+    for (i = 0; i < N; ++i) { x[i] = 0.0; r[i] = b[i]; rh[i] = b[i]; p[i] = 0.0; v[i] = 0.0; }
+  }
+  coldot(n, m, rh, r, rho);                     /* rho_1 = rhat . r_0, the only direct one */
+  for (k = 1; k <= maxit; ++k) {
+    any = 0;
+    for (j = 0; j < m; ++j) any |= (state[j] == 0);
+    if (!any) break;
+    for (j = 0; j < m; ++j) {
+      double beta;
+      if (state[j] != 0) continue;
+      if (rho[j] == 0.0 || !isfinite(rho[j])) { state[j] = 3; continue; }
+      if (restart[j]) {
+        for (i = 0; i < n; ++i) p[i * m + j] = r[i * m + j];
+        restart[j] = 0;
+      } else {
+        beta = (rho[j] / rho_old[j]) * (alpha[j] / omega[j]);
+        for (i = 0; i < n; ++i)
+          p[i * m + j] = r[i * m + j] + beta * (p[i * m + j] - omega[j] * v[i * m + j]);
+      }
+    }
+    if ((rc = apply_M(h, prec, m, p, ph)) != ORC_OK) goto done;
+    spmm(A, m, ph, v);
+    coldot(n, m, rh, v, c);                       /* group 1 */
+    for (j = 0; j < m; ++j) {
+      if (state[j] != 0) continue;
+      if (c[j] == 0.0 || !isfinite(c[j])) { state[j] = 3; continue; }
+      alpha[j] = rho[j] / c[j];
+      for (i = 0; i < n; ++i) s[i * m + j] = r[i * m + j] - alpha[j] * v[i * m + j];
+    }
+    if ((rc = apply_M(h, prec, m, s, sh)) != ORC_OK) goto done;
+    spmm(A, m, sh, t);
+    coldot(n, m, t, s, ts);                       /* group 2 */
+    coldot(n, m, t, t, tt);
+    coldot(n, m, rh, s, rs);
+    coldot(n, m, rh, t, rt);
+    coldot(n, m, s, s, ss);
+    for (j = 0; j < m; ++j) {
+      double rr;
+      if (state[j] != 0) continue;
+      iters[j] = k;
+      if (sqrt(ss[j]) <= tol * nb[j]) {           /* s already meets the tolerance */
+        for (i = 0; i < n; ++i) {
+          x[i * m + j] = x[i * m + j] + alpha[j] * ph[i * m + j];
+          r[i * m + j] = s[i * m + j];
+        }
+        state[j] = 1;
+        continue;
+      }
+      if (tt[j] == 0.0 || ts[j] == 0.0 || !isfinite(ts[j] / tt[j])) { state[j] = 3; continue; }
+      omega[j] = ts[j] / tt[j];
+      for (i = 0; i < n; ++i) {
+        x[i * m + j] = x[i * m + j] + alpha[j] * ph[i * m + j] + omega[j] * sh[i * m + j];
+        r[i * m + j] = s[i * m + j] - omega[j] * t[i * m + j];
+      }
+      rho_old[j] = rho[j];
+      rho[j] = rs[j] - omega[j] * rt[j];
+      rr = ss[j] - 2.0 * omega[j] * ts[j] + omega[j] * omega[j] * tt[j];
+      if (rr <= (tol * nb[j]) * (tol * nb[j])) state[j] = 1;
+    }
+    any = 0;
+    for (j = 0; j < m; ++j) any |= (state[j] == 0);
+    if (!any) {
+      if (confirm(A, m, b, x, r, t, tn, nb, tol, state, restart) == 0) break;
+      for (j = 0; j < m; ++j)          /* restarted columns take rhat = r, rho = |r|^2 */
+        if (state[j] == 0 && restart[j]) {
+          double d = 0.0;
+          for (i = 0; i < n; ++i) { rh[i * m + j] = r[i * m + j]; d = d + r[i * m + j] * r[i * m + j]; }
+          rho[j] = d;
+        }
+    }
+  }
+  true_resnorm(A, m, b, x, t, tn);
+  rc = ORC_OK;
+  for (j = 0; j < m; ++j) {
+    relres[j] = nb[j] > 0.0 ? tn[j] / nb[j] : 0.0;
+    if (state[j] == 4) status[j] = COL_CONVERGED;
+    else if (state[j] == 3) status[j] = COL_BREAKDOWN;
+    else status[j] = relres[j] <= tol ? COL_CONVERGED : COL_NOT_CONVERGED;
+    if (status[j] == COL_BREAKDOWN) rc = ORC_BREAKDOWN;
+    else if (status[j] == COL_NOT_CONVERGED && rc == ORC_OK) rc = ORC_NOT_CONVERGED;
+  }
+done:
+  free(r); free(rh); free(p); free(v); free(s); free(t); free(ph); free(sh);
+  free(nb); free(rho); free(rho_old); free(alpha); free(omega); free(c);
+  free(ts); free(tt); free(rs); free(rt); free(ss); free(tn);
+  free(state); free(restart);
+  return rc;
+}
+
+/* u_out = A (M u) for all m columns (the right-preconditioned operator B). */
+static int apply_B(ohier *h, int prec, int m, const double *u, double *tmp, double *out) {
+  int rc = apply_M(h, prec, m, u, tmp);
+  if (rc != ORC_OK) return rc;
+  spmm(&h->A[0], m, tmp, out);
+  return ORC_OK;
+}
+
+/* Pipelined BiCGStab (paper Sec. 2.1: "Pipelined BiCGStab"; Cools and
+ * Vanroose 2017), for the right-preconditioned operator B = A M.  Auxiliary
+ * vectors carry the products of the classical recurrences, w = B r, s = B p,
+ * z = B s, t = B w, v = B z, so that each dot-product group of an iteration
+ * can overlap one application of B:
+ *   p = r + beta (p - omega s)        s = w + beta (s - omega z)
+ *   z = t + beta (z - omega v)        q = r - alpha s       y = w - alpha z
+ *   [ (q, y), (y, y) ]  ||  v = B z
+ *   omega = (q, y) / (y, y)
+ *   u += alpha p + omega q            (correction in the preconditioned variable)
+ *   r = q - omega y                   w = y - omega (t - alpha v)
+ *   [ (rhat, r), (rhat, w), (rhat, s), (rhat, z), (r, r) ]  ||  t = B w
+ *   beta = (alpha / omega) (rhat, r) / rho     rho = (rhat, r)
+ *   alpha = rho / ((rhat, w) + beta (rhat, s) - beta omega (rhat, z))
+ * The solution is x = x0 + M u (M applied once, when the columns stop).  A
+ * column freezes when its recursive ||r|| meets the tolerance; when all have
+ * stopped, x is formed and the true residuals confirm them; a restarted column
+ * starts again from x with r = rhat = b - A x and u = 0. */
+int orc_pbicgstab_prec(ohier *h, int prec, int x0_given, int m, const double *b, double *x,
+                       double tol, int maxit, int *iters, double *relres, int *status) {
+  const ocsr *A = &h->A[0];
+  size_t N = (size_t)A->n * m, i, n = (size_t)A->n;
+  int j, k, rc = ORC_OK, any;
+  double *r = NULL, *rh = NULL, *w = NULL, *t = NULL, *p = NULL, *s = NULL, *z = NULL, *q = NULL;
+  double *y = NULL, *v = NULL, *u = NULL, *x0 = NULL, *tmp = NULL;
+  double *nb = NULL, *rho = NULL, *alpha = NULL, *beta = NULL, *omega = NULL, *d1 = NULL, *d2 = NULL;
+  double *rr = NULL, *rhr = NULL, *rhw = NULL, *rhs = NULL, *rhz = NULL, *tn = NULL;
+  int *state = NULL, *restart = NULL, first = 1;
+  if (!h || m < 1 || maxit < 0 || !(tol > 0.0) || prec < 0 || prec > 2) return ORC_ERR_ARG;
+  if (!all_finite(N, b)) return ORC_ERR_NONFINITE;
+#define ORC_V(ptr) ptr = (double *)malloc(N * sizeof(double))
+#define ORC_S(ptr) ptr = (double *)malloc((size_t)m * sizeof(double))
+  ORC_V(r); ORC_V(rh); ORC_V(w); ORC_V(t); ORC_V(p); ORC_V(s); ORC_V(z); ORC_V(q);
+  ORC_V(y); ORC_V(v); ORC_V(u); ORC_V(x0); ORC_V(tmp);
+  ORC_S(nb); ORC_S(rho); ORC_S(alpha); ORC_S(beta); ORC_S(omega); ORC_S(d1); ORC_S(d2);
+  ORC_S(rr); ORC_S(rhr); ORC_S(rhw); ORC_S(rhs); ORC_S(rhz); ORC_S(tn);
+#undef ORC_V
+#undef ORC_S
+  state = (int *)calloc((size_t)m, sizeof(int)); restart = (int *)calloc((size_t)m, sizeof(int));
+  if (!r || !rh || !w || !t || !p || !s || !z || !q || !y || !v || !u || !x0 || !tmp || !nb || !rho ||
+      !alpha || !beta || !omega || !d1 || !d2 || !rr || !rhr || !rhw || !rhs || !rhz || !tn ||
+      !state || !restart) {
+    rc = ORC_ERR_OOM;
+    goto done;
+  }
+  coldot(n, m, b, b, nb);
+  for (j = 0; j < m; ++j) { nb[j] = sqrt(nb[j]); iters[j] = 0; if (nb[j] == 0.0) state[j] = 4; restart[j] = 1; }
+  if (x0_given) {
+    if (!all_finite(N, x)) { rc = ORC_ERR_NONFINITE; goto done; }
+    for (i = 0; i < n; ++i)
+      for (j = 0; j < m; ++j) if (state[j] == 4) x[i * m + j] = 0.0;
+  } else {
+    for (i = 0; i < N; ++i) x[i] = 0.0;
+  }
+  spmm(A, m, x, t);
+  for (i = 0; i < N; ++i) { x0[i] = x[i]; r[i] = b[i] - t[i]; rh[i] = r[i]; u[i] = 0.0; }
+  coldot(n, m, r, r, rr);
+  for (j = 0; j < m; ++j)
+    if (state[j] == 0 && sqrt(rr[j]) <= tol * nb[j]) state[j] = 1;
+  for (k = 1; k <= maxit; ++k) {
+    any = 0;
+    for (j = 0; j < m; ++j) any |= (state[j] == 0);
+    if (!any) {
+      if (first) break;
+      /* x = x0 + M u, then confirm with the true residuals */
+      if ((rc = apply_M(h, prec, m, u, tmp)) != ORC_OK) goto done;
+      for (i = 0; i < N; ++i) x[i] = x0[i] + tmp[i];
+      if (confirm(A, m, b, x, r, t, tn, nb, tol, state, restart) == 0) break;
+      for (j = 0; j < m; ++j)
+        if (state[j] == 0 && restart[j])
+          for (i = 0; i < n; ++i) {
+            x0[i * m + j] = x[i * m + j];
+            u[i * m + j] = 0.0;
+            rh[i * m + j] = r[i * m + j];
+          }
+    }
+    /* (re)start: w = B r, t = B w, rho = (rhat, r), alpha = rho / (rhat, w) */
+    any = 0;
+    for (j = 0; j < m; ++j) any |= (state[j] == 0 && restart[j]);
+    if (any) {
+      if ((rc = apply_B(h, prec, m, r, tmp, q)) != ORC_OK) goto done;
+      if ((rc = apply_B(h, prec, m, q, tmp, y)) != ORC_OK) goto done;
+      coldot(n, m, rh, r, rhr);
+      coldot(n, m, rh, q, rhw);
+      for (j = 0; j < m; ++j) {
+        if (!(state[j] == 0 && restart[j])) continue;
+        for (i = 0; i < n; ++i) { w[i * m + j] = q[i * m + j]; t[i * m + j] = y[i * m + j]; }
+        if (rhr[j] == 0.0 || rhw[j] == 0.0 || !isfinite(rhr[j] / rhw[j])) { state[j] = 3; continue; }
+        rho[j] = rhr[j];
+        alpha[j] = rhr[j] / rhw[j];
+      }
+    }
+    first = 0;
+    for (j = 0; j < m; ++j) {
+      if (state[j] != 0) continue;
+      if (restart[j]) {
+        for (i = 0; i < n; ++i) {
+          p[i * m + j] = r[i * m + j];
+          s[i * m + j] = w[i * m + j];
+          z[i * m + j] = t[i * m + j];
+        }
+        restart[j] = 0;
+      } else {
+        for (i = 0; i < n; ++i) {
+          const size_t e = i * m + j;
+          p[e] = r[e] + beta[j] * (p[e] - omega[j] * s[e]);
+          s[e] = w[e] + beta[j] * (s[e] - omega[j] * z[e]);
+          z[e] = t[e] + beta[j] * (z[e] - omega[j] * v[e]);
+        }
+      }
+      for (i = 0; i < n; ++i) {
+        const size_t e = i * m + j;
+        q[e] = r[e] - alpha[j] * s[e];
+        y[e] = w[e] - alpha[j] * z[e];
+      }
+    }
+    coldot(n, m, q, y, d1);
+    coldot(n, m, y, y, d2);
+    if ((rc = apply_B(h, prec, m, z, tmp, v)) != ORC_OK) goto done;
+    for (j = 0; j < m; ++j) {
+      if (state[j] != 0) continue;
+      iters[j] = k;
+      if (d2[j] == 0.0 || d1[j] == 0.0 || !isfinite(d1[j] / d2[j])) { state[j] = 3; continue; }
+      omega[j] = d1[j] / d2[j];
+      for (i = 0; i < n; ++i) {
+        const size_t e = i * m + j;
+        u[e] = u[e] + alpha[j] * p[e] + omega[j] * q[e];
+        r[e] = q[e] - omega[j] * y[e];
+        w[e] = y[e] - omega[j] * (t[e] - alpha[j] * v[e]);
+      }
+    }
+    coldot(n, m, rh, r, rhr);
+    coldot(n, m, rh, w, rhw);
+    coldot(n, m, rh, s, rhs);
+    coldot(n, m, rh, z, rhz);
+    coldot(n, m, r, r, rr);
+    if ((rc = apply_B(h, prec, m, w, tmp, t)) != ORC_OK) goto done;
+    for (j = 0; j < m; ++j) {
+      double den;
+      if (state[j] != 0) continue;
+      if (sqrt(rr[j]) <= tol * nb[j]) { state[j] = 1; continue; }
+      beta[j] = (alpha[j] / omega[j]) * (rhr[j] / rho[j]);
+      rho[j] = rhr[j];
+      den = rhw[j] + beta[j] * rhs[j] - beta[j] * omega[j] * rhz[j];
+      if (rho[j] == 0.0 || den == 0.0 || !isfinite(rho[j] / den)) { state[j] = 3; continue; }
+      alpha[j] = rho[j] / den;
+    }
+  }
+  /* columns still active after maxit: form x as well */
+  if ((rc = apply_M(h, prec, m, u, tmp)) != ORC_OK) goto done;
+  for (i = 0; i < N; ++i) x[i] = x0[i] + tmp[i];
+  true_resnorm(A, m, b, x, t, tn);
+  rc = ORC_OK;
+  for (j = 0; j < m; ++j) {
+    relres[j] = nb[j] > 0.0 ? tn[j] / nb[j] : 0.0;
+    if (state[j] == 4) status[j] = COL_CONVERGED;
+    else if (state[j] == 3) status[j] = COL_BREAKDOWN;
+    else status[j] = relres[j] <= tol ? COL_CONVERGED : COL_NOT_CONVERGED;
+    if (status[j] == COL_BREAKDOWN) rc = ORC_BREAKDOWN;
+    else if (status[j] == COL_NOT_CONVERGED && rc == ORC_OK) rc = ORC_NOT_CONVERGED;
+  }
+done:
+  free(r); free(rh); free(w); free(t); free(p); free(s); free(z); free(q); free(y); free(v);
+  free(u); free(x0); free(tmp);
+  free(nb); free(rho); free(alpha); free(beta); free(omega); free(d1); free(d2);
+  free(rr); free(rhr); free(rhw); free(rhs); free(rhz); free(tn);
+  free(state); free(restart);
+  return rc;
+}

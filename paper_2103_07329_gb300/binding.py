@@ -28,6 +28,8 @@ NOT_CONVERGED = 1
 BREAKDOWN = 2
 PCG = 0
 BICGSTAB = 1
+BICGSTAB_REORDERED = 2
+BICGSTAB_PIPELINED = 3
 PREC_FP64 = 0
 PREC_FP32 = 1
 PREC_BF16 = 2

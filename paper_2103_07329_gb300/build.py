@@ -36,7 +36,8 @@ def sources():
                                             "rowsf_nv1.cu", "rowsf_nv2.cu", "rowsf_nv4.cu",
                                             "rowsf_nv8.cu", "rowsf_nv16.cu", "rowsf_nv32.cu",
                                             "net.cu", "batch.cu", "batch_stage1.cu",
-                                            "batch_stage2.cu", "batch_stage3.cu")]
+                                            "batch_stage2.cu", "batch_stage3.cu",
+                                            "bicg_variants.cu")]
 
 
 def _deps():

@@ -66,6 +66,7 @@ struct Work {
   float *R32 = nullptr, *Z32 = nullptr;
   std::vector<float *> fb, fx, fr, fd, fd2;
   double *cw = nullptr;  // FP64 working copy of the coarsest block
+  double *E[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // pipelined BiCGStab: Z, Q, Y, U, X0
   double *part[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   ColState *cs = nullptr;
 };
@@ -313,6 +314,8 @@ size_t plan(const xamg_hier *h, int nv, int method, int prec, Work *w, char *bas
     W.T = (double *)take(blk);
     W.PH = (double *)take(blk);
     W.SH = (double *)take(blk);
+    if (method == XAMG_BICGSTAB_PIPELINED)
+      for (int i = 0; i < 5; ++i) W.E[i] = (double *)take(blk);
   }
   const int L = (int)h->host.lv.size();
   const bool dd = h->host.cheb_steps >= 3;
@@ -1035,6 +1038,176 @@ int hier_view(xamg_hier *h, HierView *v) {
 
 namespace {
 
+VParts vparts(const double *p0, int n0, const double *p1 = nullptr, int n1 = 0, const double *p2 = nullptr,
+              int n2 = 0, const double *p3 = nullptr, int n3 = 0, const double *p4 = nullptr, int n4 = 0) {
+  VParts v;
+  v.p[0] = p0; v.nblk[0] = n0;
+  v.p[1] = p1; v.nblk[1] = n1;
+  v.p[2] = p2; v.nblk[2] = n2;
+  v.p[3] = p3; v.nblk[3] = n3;
+  v.p[4] = p4; v.nblk[4] = n4;
+  return v;
+}
+
+// Reordered BiCGStab (Krasnopolsky 2010), right-preconditioned: dot
+// products in two groups per iteration, rho and ||r|| of the next iteration
+// from recurrences, one host read per iteration (the test between the two
+// halves is folded into the omega step: a column whose s meets the tolerance
+// takes omega = 0, i.e. x += alpha M p, r = s).
+int solve_rbicgstab(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
+  xamg_hier *h = c.h;
+  Work &W = c.W;
+  const int nv = c.nv;
+  const int64_t n = h->lv[0].A.n;
+  const int ge = elem_grid(n, nv);
+  const bool single = h->lv.size() == 1;
+  const double *w0 = (single || c.prec != XAMG_PREC_FP64) ? nullptr : h->lv[0].w[0];
+  Flags *fl = h->flags_d;
+  cudaStream_t st = c.st;
+  const size_t blk = (size_t)n * nv * sizeof(double);
+  XCK(cudaMemsetAsync(W.T, 0, blk, st));
+  XCK(cudaMemsetAsync(W.SH, 0, blk, st));
+  launch_init_bicg(nv, n, B, c.m, W.Bn, W.R, W.RH, W.X, W.P, W.V, W.part[0], ge, st);
+  launch_scalar(nv, SM_INIT, W.cs, W.part[0], nullptr, ge, c.tol, 0, fl, st);
+  int rc = check_init(c);
+  if (rc != XAMG_OK) return rc;
+  if (c.x0) {
+    if ((rc = load_x0(c)) != XAMG_OK) return rc;
+    XCK(cudaMemcpyAsync(W.RH, W.R, blk, cudaMemcpyDeviceToDevice, st));
+    if ((rc = initial_check(c)) != XAMG_OK) return rc;
+  }
+  // rho = rhat . r, the only direct one
+  launch_coldot(nv, n, W.RH, W.R, W.part[0], ge, st);
+  launch_vscalar(nv, VS_RHO0, W.cs, vparts(W.part[0], ge), c.tol, 0, nullptr, st);
+  int g;
+  for (int k = 1; k <= c.maxit && h->flags_h->active > 0; ++k) {
+    c.iterations = k;
+    launch_vscalar(nv, VS_RB_BETA, W.cs, vparts(nullptr, 0), c.tol, k, nullptr, st);
+    launch_bicg_p(nv, n, W.P, W.R, W.V, W.cs, w0, W.PH, ge, st);
+    if ((rc = apply_precond(c, W.P, W.PH)) != XAMG_OK) return rc;
+    RowOp o = blank<double>();
+    o.src = W.PH; o.y = W.V; o.dot_u = W.RH; o.partials = W.part[0];
+    if ((g = rows<double>(h, 0, 0, XAMG_PREC_FP64, o, nv, false, EPI_Y_DOT, st)) < 0) return XAMG_ERR_CUDA;
+    launch_scalar(nv, SM_BI_ALPHA, W.cs, W.part[0], nullptr, g, c.tol, k, nullptr, st);
+    launch_rb_s(nv, n, W.S, W.R, W.V, W.RH, W.cs, w0, W.SH, W.part[1], W.part[2], ge, st);
+    if ((rc = apply_precond(c, W.S, W.SH)) != XAMG_OK) return rc;
+    RowOp t = blank<double>();
+    t.src = W.SH; t.y = W.T; t.dot_u = W.S; t.partials = W.part[3]; t.partials2 = W.part[4];
+    if ((g = rows<double>(h, 0, 0, XAMG_PREC_FP64, t, nv, false, EPI_Y_DOT2, st)) < 0) return XAMG_ERR_CUDA;
+    launch_vscalar(nv, VS_RB_OMEGA, W.cs, vparts(W.part[3], g, W.part[4], g, W.part[1], ge), c.tol, k, fl, st);
+    launch_rb_xr(nv, n, W.X, W.R, W.S, W.T, W.PH, W.SH, W.RH, W.cs, W.part[0], ge, st);
+    launch_vscalar(nv, VS_RB_RHO, W.cs, vparts(W.part[2], ge, W.part[0], ge), c.tol, k, nullptr, st);
+    if ((rc = sync_read(st)) != XAMG_OK) return rc;
+    if (h->flags_h->active == 0) {
+      if ((g = true_residual(h, W, W.T, W.part[2], st)) < 0) return XAMG_ERR_CUDA;
+      launch_scalar(nv, SM_CONFIRM, W.cs, W.part[2], nullptr, g, c.tol, k, fl, st);
+      if ((rc = sync_read(st)) != XAMG_OK) return rc;
+      if (h->flags_h->reactivated == 0) {
+        c.confirmed = true;
+        break;
+      }
+      // restarted columns: r = rhat = the true residual, rho = |r|^2
+      launch_copy_cols(nv, n, W.R, W.T, W.cs, ge, st);
+      launch_copy_cols(nv, n, W.RH, W.T, W.cs, ge, st);
+      launch_coldot(nv, n, W.RH, W.R, W.part[0], ge, st);
+      launch_vscalar(nv, VS_RHO0, W.cs, vparts(W.part[0], ge), c.tol, k, nullptr, st);
+    }
+  }
+  return finish(c, Xuser, stats);
+}
+
+// out = A (M u) for the FP64 preconditioner; tmp receives M u.
+int apply_B(SolveCtx &c, const double *u, double *tmp, double *out) {
+  xamg_hier *h = c.h;
+  Work &W = c.W;
+  const int64_t n = h->lv[0].A.n;
+  if (h->lv.size() > 1) launch_scale_rows(c.nv, n, h->lv[0].w[0], u, tmp, elem_grid(n, c.nv), c.st);
+  int rc = apply_precond(c, u, tmp);
+  if (rc != XAMG_OK) return rc;
+  RowOp o = blank<double>();
+  o.src = tmp; o.y = out;
+  return rows<double>(h, 0, 0, XAMG_PREC_FP64, o, c.nv, false, EPI_Y, c.st) < 0 ? XAMG_ERR_CUDA : XAMG_OK;
+}
+
+// Pipelined BiCGStab (Cools and Vanroose 2017) for B = A M.  Blocks: R, RH,
+// W (in PH), T, P, S, Z, Q, Y, V, U (the correction in the preconditioned
+// variable), X0; SH is the scratch that receives M applications.
+int solve_pbicgstab(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
+  xamg_hier *h = c.h;
+  Work &W = c.W;
+  const int nv = c.nv;
+  const int64_t n = h->lv[0].A.n;
+  const int ge = elem_grid(n, nv);
+  Flags *fl = h->flags_d;
+  cudaStream_t st = c.st;
+  const size_t blk = (size_t)n * nv * sizeof(double);
+  double *Wv = W.PH, *TMP = W.SH, *Z = W.E[0], *Q = W.E[1], *Y = W.E[2], *U = W.E[3], *X0 = W.E[4];
+  launch_init_bicg(nv, n, B, c.m, W.Bn, W.R, W.RH, W.X, W.P, W.V, W.part[0], ge, st);
+  launch_scalar(nv, SM_INIT, W.cs, W.part[0], nullptr, ge, c.tol, 0, fl, st);
+  int rc = check_init(c);
+  if (rc != XAMG_OK) return rc;
+  if (c.x0) {
+    if ((rc = load_x0(c)) != XAMG_OK) return rc;
+    XCK(cudaMemcpyAsync(W.RH, W.R, blk, cudaMemcpyDeviceToDevice, st));
+    if ((rc = initial_check(c)) != XAMG_OK) return rc;
+  }
+  XCK(cudaMemcpyAsync(X0, W.X, blk, cudaMemcpyDeviceToDevice, st));
+  XCK(cudaMemsetAsync(U, 0, blk, st));
+  XCK(cudaMemsetAsync(Z, 0, blk, st));
+  // (re)start of the fresh columns: w = B r, t = B w, rho = rhat.r, alpha = rho / rhat.w
+  auto start = [&](int k) -> int {
+    int r;
+    if ((r = apply_B(c, W.R, TMP, Wv)) != XAMG_OK) return r;
+    if ((r = apply_B(c, Wv, TMP, W.T)) != XAMG_OK) return r;
+    launch_coldot(nv, n, W.RH, W.R, W.part[0], ge, st);
+    launch_coldot(nv, n, W.RH, Wv, W.part[1], ge, st);
+    launch_vscalar(nv, VS_PB_INIT, W.cs, vparts(W.part[0], ge, W.part[1], ge), c.tol, k, nullptr, st);
+    return XAMG_OK;
+  };
+  // x = x0 + M u
+  auto form_x = [&]() -> int {
+    if (h->lv.size() > 1) launch_scale_rows(nv, n, h->lv[0].w[0], U, TMP, ge, st);
+    const int r = apply_precond(c, U, TMP);
+    if (r != XAMG_OK) return r;
+    launch_pb_form_x(nv, n, W.X, X0, TMP, ge, st);
+    return XAMG_OK;
+  };
+  if (h->flags_h->active > 0 && (rc = start(0)) != XAMG_OK) return rc;
+  double *const parts[5] = {W.part[0], W.part[1], W.part[2], W.part[3], W.part[4]};
+  bool formed = true;  // X holds x0 + M u
+  for (int k = 1; k <= c.maxit && h->flags_h->active > 0; ++k) {
+    c.iterations = k;
+    formed = false;
+    launch_pb_psz(nv, n, W.P, W.S, Z, W.R, Wv, W.T, W.V, W.cs, ge, st);
+    launch_pb_qy(nv, n, Q, Y, W.R, W.S, Wv, Z, W.cs, W.part[0], W.part[1], ge, st);
+    if ((rc = apply_B(c, Z, TMP, W.V)) != XAMG_OK) return rc;
+    launch_vscalar(nv, VS_PB_OMEGA, W.cs, vparts(W.part[0], ge, W.part[1], ge), c.tol, k, nullptr, st);
+    launch_pb_urw(nv, n, U, W.R, Wv, W.P, Q, Y, W.T, W.V, W.S, Z, W.RH, W.cs, parts, ge, st);
+    if ((rc = apply_B(c, Wv, TMP, W.T)) != XAMG_OK) return rc;
+    launch_vscalar(nv, VS_PB_ALPHA, W.cs,
+                   vparts(W.part[0], ge, W.part[1], ge, W.part[2], ge, W.part[3], ge, W.part[4], ge), c.tol, k,
+                   fl, st);
+    if ((rc = sync_read(st)) != XAMG_OK) return rc;
+    if (h->flags_h->active == 0) {
+      if ((rc = form_x()) != XAMG_OK) return rc;
+      formed = true;
+      int g;
+      if ((g = true_residual(h, W, TMP, W.part[2], st)) < 0) return XAMG_ERR_CUDA;
+      launch_scalar(nv, SM_CONFIRM, W.cs, W.part[2], nullptr, g, c.tol, k, fl, st);
+      if ((rc = sync_read(st)) != XAMG_OK) return rc;
+      if (h->flags_h->reactivated == 0) {
+        c.confirmed = true;
+        break;
+      }
+      launch_copy_cols(nv, n, W.R, TMP, W.cs, ge, st);
+      launch_pb_restart(nv, n, W.X, X0, U, W.RH, W.R, W.cs, ge, st);
+      if ((rc = start(k)) != XAMG_OK) return rc;
+    }
+  }
+  if (!formed && (rc = form_x()) != XAMG_OK) return rc;
+  return finish(c, Xuser, stats);
+}
+
 int solve_impl(xamg_hier *h, const double *B, double *X, int m, double tol, int maxit,
                const xamg_solve_opts *opts, xamg_stats *stats) {
   if (!h || !h->on_device || !B || !X || m < 1 || m > XAMG_MAX_RHS || !(tol > 0.0) || maxit < 0)
@@ -1042,7 +1215,10 @@ int solve_impl(xamg_hier *h, const double *B, double *X, int m, double tol, int 
   xamg_solve_opts o;
   xamg_solve_opts_default(&o);
   if (opts) o = *opts;
-  if (o.method != XAMG_PCG && o.method != XAMG_BICGSTAB) return XAMG_ERR_INVALID_ARG;
+  if (o.method != XAMG_PCG && o.method != XAMG_BICGSTAB && o.method != XAMG_BICGSTAB_REORDERED &&
+      o.method != XAMG_BICGSTAB_PIPELINED)
+    return XAMG_ERR_INVALID_ARG;
+  if (o.method == XAMG_BICGSTAB_PIPELINED && o.precond != XAMG_PREC_FP64) return XAMG_ERR_INVALID_ARG;
   if (o.precond != XAMG_PREC_FP64 && o.precond != XAMG_PREC_FP32 && o.precond != XAMG_PREC_BF16)
     return XAMG_ERR_INVALID_ARG;
   XCK(cudaSetDevice(h->device));
@@ -1060,6 +1236,10 @@ int solve_impl(xamg_hier *h, const double *B, double *X, int m, double tol, int 
   h->flags_h->active = 0;
   if (o.method == XAMG_PCG)
     rc = c.prec == XAMG_PREC_FP64 ? solve_pcg(c, B, X, stats) : solve_fpcg(c, B, X, stats);
+  else if (o.method == XAMG_BICGSTAB_REORDERED)
+    rc = solve_rbicgstab(c, B, X, stats);
+  else if (o.method == XAMG_BICGSTAB_PIPELINED)
+    rc = solve_pbicgstab(c, B, X, stats);
   else
     rc = solve_bicgstab(c, B, X, stats);
   if (h->timing && rc < 0) {
@@ -1219,7 +1399,7 @@ int xamg_coarse_export(const xamg_hier *h, int32_t *nc, double *lu, int32_t *piv
 
 int xamg_workspace_bytes(const xamg_hier *h, int32_t m, int32_t method, int32_t precond,
                          size_t *bytes) {
-  if (!h || !bytes || m < 1 || m > XAMG_MAX_RHS || (method != XAMG_PCG && method != XAMG_BICGSTAB) ||
+  if (!h || !bytes || m < 1 || m > XAMG_MAX_RHS || (method < XAMG_PCG || method > XAMG_BICGSTAB_PIPELINED) ||
       precond < XAMG_PREC_FP64 || precond > XAMG_PREC_BF16)
     return XAMG_ERR_INVALID_ARG;
   *bytes = plan(h, pad_nv(m), method, precond, nullptr, nullptr);

@@ -20,6 +20,7 @@ struct ColState {
   double beta[32];
   double omega[32];
   double tn[32];       // true residual norms
+  double rho_old[32];  // reordered BiCGStab: rho of the previous iteration
   int32_t state[32];   // 0 active, 1 frozen by the residual test, 2 confirmed,
                        // 3 breakdown, 4 zero right-hand side
   int32_t restart[32]; // next direction update starts afresh
@@ -50,6 +51,22 @@ enum ScalarMode : int {
   SM_FPCG_BETA = 11, // p0: r.z, p1: q.z -> flexible beta, rho
 };
 
+// Scalar steps of the BiCGStab variants (k_vscalar): the partial-sum arrays
+// and their block counts.
+enum VScalarMode : int {
+  VS_RHO0 = 0,     // p0: rhat.r -> rho of every column that starts afresh
+  VS_RB_BETA = 1,  // reordered: beta of the direction update
+  VS_RB_OMEGA = 2, // reordered: p0 t.s, p1 t.t, p2 s.s -> omega, iters, freeze
+  VS_RB_RHO = 3,   // reordered: p0 rhat.s, p1 rhat.t -> rho' = rhat.s - omega rhat.t
+  VS_PB_INIT = 4,  // pipelined: p0 rhat.r, p1 rhat.w -> rho, alpha (fresh columns)
+  VS_PB_OMEGA = 5, // pipelined: p0 q.y, p1 y.y -> omega, iters
+  VS_PB_ALPHA = 6, // pipelined: p0..p4 rhat.r, rhat.w, rhat.s, rhat.z, r.r -> freeze, beta, rho, alpha
+};
+struct VParts {
+  const double *p[5];
+  int nblk[5];
+};
+
 int device_sm_count();
 extern std::atomic<int64_t> g_launches;  // kernels launched by the library
 
@@ -71,6 +88,26 @@ int launch_rowsf_nv4(const RowOpF &op, int slices, bool neg, int epi, int vt, cu
 int launch_rowsf_nv8(const RowOpF &op, int slices, bool neg, int epi, int vt, cudaStream_t st);
 int launch_rowsf_nv16(const RowOpF &op, int slices, bool neg, int epi, int vt, cudaStream_t st);
 int launch_rowsf_nv32(const RowOpF &op, int slices, bool neg, int epi, int vt, cudaStream_t st);
+
+void launch_rb_s(int nv, int64_t n, double *S, const double *R, const double *V, const double *RH,
+                 const ColState *cs, const double *w0, double *SH, double *part_ss, double *part_rs, int grid,
+                 cudaStream_t st);
+void launch_rb_xr(int nv, int64_t n, double *X, double *R, const double *S, const double *T, const double *PH,
+                  const double *SH, const double *RH, const ColState *cs, double *part_rt, int grid,
+                  cudaStream_t st);
+void launch_pb_psz(int nv, int64_t n, double *P, double *S, double *Z, const double *R, const double *W,
+                   const double *T, const double *V, const ColState *cs, int grid, cudaStream_t st);
+void launch_pb_qy(int nv, int64_t n, double *Q, double *Y, const double *R, const double *S, const double *W,
+                  const double *Z, const ColState *cs, double *part_qy, double *part_yy, int grid,
+                  cudaStream_t st);
+void launch_pb_urw(int nv, int64_t n, double *U, double *R, double *W, const double *P, const double *Q,
+                   const double *Y, const double *T, const double *V, const double *S, const double *Z,
+                   const double *RH, const ColState *cs, double *const part[5], int grid, cudaStream_t st);
+void launch_pb_form_x(int nv, int64_t n, double *X, const double *X0, const double *D, int grid, cudaStream_t st);
+void launch_pb_restart(int nv, int64_t n, const double *X, double *X0, double *U, double *RH, const double *R,
+                       const ColState *cs, int grid, cudaStream_t st);
+void launch_vscalar(int nv, int mode, ColState *cs, const VParts &P, double tol, int k, Flags *flags,
+                    cudaStream_t st);
 
 // Elementwise grid size for n rows of nv columns.
 int elem_grid(int64_t n, int nv);
