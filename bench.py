@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--m", type=int, default=32)
     ap.add_argument("--method", default="pcg",
                     choices=["pcg", "bicgstab", "bicgstab_reordered", "bicgstab_pipelined"])
+    ap.add_argument("--sweep-ms", default="1,2,4,8,16,32", help="--sweep: comma-separated m values")
     ap.add_argument("--sweep-methods", default="pcg,bicgstab",
                     help="--sweep: comma-separated methods (also bicgstab_reordered, bicgstab_pipelined)")
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -601,7 +602,7 @@ def run_sweep(a):
     h = B.Hierarchy(A)
     setup = time.perf_counter() - t0
     hbm = measured_hbm()[0]
-    for m in (1, 2, 4, 8, 16, 32):
+    for m in [int(v) for v in a.sweep_ms.split(",")]:
         Bm = P.rhs_uniform(A.n, m, 0, m_draw=32)
         Bd = torch.from_numpy(Bm).cuda()
         X = torch.empty_like(Bd)

@@ -298,13 +298,14 @@ int xamg_coldot(const double *U, const double *V, int64_t n, int32_t m, double *
 int xamg_coldot_noalloc(const double *U, const double *V, int64_t n, int32_t m, double *out,
                         void *stream);
 
-/* Autotuner of the reduced-precision preconditioner's sparse products: for
- * every level's A, P and R, times y = M x on FP32 blocks of pad(m) columns
- * (m in [1, XAMG_MAX_RHS]; precond XAMG_PREC_FP32 or XAMG_PREC_BF16) under
- * both row splits -- the default (a group of lanes per row, several rows per
- * warp) and one row per warp with its entries split over the lanes -- and
- * keeps the faster in the hierarchy; later solves and V-cycles of that block
- * width and precision use it.  Results do not depend on the split beyond the
+/* Autotuner of the preconditioner's sparse products: for every level's A, P
+ * and R, times y = M x on blocks of pad(m) columns (m in [1, XAMG_MAX_RHS])
+ * of the precision `precond` selects (XAMG_PREC_FP64: FP64 blocks;
+ * XAMG_PREC_FP32 / XAMG_PREC_BF16: FP32 blocks with FP32 / bf16 values of A)
+ * under both row splits -- the default (a group of lanes per row, several
+ * rows per warp) and one row per warp with its entries split over the lanes
+ * -- and keeps the faster in the hierarchy; later solves and V-cycles of that
+ * block width and precision use it.  Results do not depend on the split beyond the
  * order of each row's FP32 sums.  ops_tuned / ops_wide (may be NULL): products
  * tuned and how many chose one row per warp.  Uses the hierarchy's cached
  * workspace; synchronizes `stream`.  No counterpart in the paper. */

@@ -38,10 +38,11 @@ struct DevLevel {
   uint32_t *a16meta = nullptr;   // per row: first window << 16 | entries in it
   float *w32[4] = {nullptr, nullptr, nullptr, nullptr};
   float c1f[4] = {0, 0, 0, 0};
-  // row split of the FP32-block products chosen by xamg_autotune, per values
-  // (0: FP32, 1: bf16 A), operator (A, P, R) and block width (log2 nv):
-  // -1 untuned (the default rule), 0 narrow, 1 one row per warp
-  signed char split[2][3][6];
+  // row split of the sparse products chosen by xamg_autotune, per values
+  // (0: FP32 blocks, 1: FP32 blocks with bf16 A, 2: FP64), operator (A, P, R)
+  // and block width (log2 nv): -1 untuned (the default rule), 0 narrow, 1 one
+  // row per warp
+  signed char split[3][3][6];
   DevLevel() { std::memset(split, -1, sizeof(split)); }
 };
 
@@ -429,6 +430,12 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
   const double avg = (double)M.nnz / M.n;
   if (nv == 1) return avg >= 24.0 ? 16 : 4;
   if (fp32 && nv >= 16 && avg >= 64.0) return 32 / (nv / 4);
+  // a dense Galerkin level with fewer row groups than resident warps under the
+  // default split (rows per warp = 32 / lanes per row): one row per warp, the
+  // row's entries split over the warp
+  const int vec = fp32 ? (nv >= 4 ? 4 : nv) : 1;
+  const double warps = (double)M.n / (32 / (nv / vec));
+  if (avg >= 32.0 && warps < 32.0 * device_sm_count()) return 2;
   return 1;
 }
 
@@ -492,7 +499,12 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
   }
   int g;
   if constexpr (sizeof(TB) == 8) {
-    g = launch_rows(op, nv, slices_for(M, nv, false), neg, epi, st);
+    int sl = slices_for(M, nv, false);
+    int lg = 0;
+    while ((1 << lg) < nv) ++lg;
+    const int t = D.split[2][which][lg];
+    if (t >= 0 && nv < 32) sl = t ? (nv == 1 ? 16 : 2) : (nv == 1 ? 4 : 1);
+    g = launch_rows(op, nv, sl, neg, epi, st);
   } else {
     int sl = slices_for(M, nv, true);
     int lg = 0;
@@ -1252,6 +1264,36 @@ int solve_impl(xamg_hier *h, const double *B, double *X, int m, double tol, int 
 }  // namespace
 
 // ===================================================================== C ABI
+namespace {
+
+// Times y = M x for operator `which` of level l under both row splits and
+// keeps the faster in `slot`.
+template <class TB>
+int tune_product(xamg_hier *h, int l, int which, int precond, RowOpT<TB> o, int nv, signed char &slot,
+                 cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int *wide) {
+  float best = 1e30f;
+  int best_opt = 0;
+  for (int opt = 0; opt < 2; ++opt) {
+    slot = (signed char)opt;
+    if (rows<TB>(h, l, which, precond, o, nv, false, EPI_Y, st) < 0) return XAMG_ERR_CUDA;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) rows<TB>(h, l, which, precond, o, nv, false, EPI_Y, st);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return XAMG_ERR_CUDA;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_opt = opt;
+    }
+  }
+  slot = (signed char)best_opt;
+  *wide += best_opt;
+  return XAMG_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *xamg_strerror(int code) {
@@ -1579,7 +1621,7 @@ int xamg_coldot(const double *U, const double *V, int64_t n, int32_t m, double *
 int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_t *ops_tuned,
                   int32_t *ops_wide) {
   if (!h || !h->on_device || m < 1 || m > XAMG_MAX_RHS ||
-      (precond != XAMG_PREC_FP32 && precond != XAMG_PREC_BF16))
+      (precond != XAMG_PREC_FP64 && precond != XAMG_PREC_FP32 && precond != XAMG_PREC_BF16))
     return XAMG_ERR_INVALID_ARG;
   XCK(cudaSetDevice(h->device));
   const int nv = pad_nv(m);
@@ -1589,7 +1631,7 @@ int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_
   cudaStream_t st = (cudaStream_t)stream;
   int lg = 0;
   while ((1 << lg) < nv) ++lg;
-  const int pc = precond == XAMG_PREC_BF16 ? 1 : 0;
+  const int pc = precond == XAMG_PREC_BF16 ? 1 : precond == XAMG_PREC_FP32 ? 0 : 2;
   const bool timing = h->timing;
   h->timing = false;
   cudaEvent_t e0, e1;
@@ -1599,41 +1641,31 @@ int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_
   const int L = (int)h->lv.size();
   for (int l = 0; l + 1 < L && rc == XAMG_OK; ++l) {
     for (int which = 0; which < 3 && rc == XAMG_OK; ++which) {
-      // y = M x on this level's FP32 work blocks
-      RowOpT<float> o = blank<float>();
-      if (which == 0) {
-        o.src = W.fx[l]; o.y = W.fr[l];
-      } else if (which == 1) {
-        o.src = W.fx[l + 1]; o.y = W.fr[l];
-      } else {
-        o.src = W.fr[l]; o.y = W.fb[l + 1];
-      }
       signed char &slot = h->lv[l].split[pc][which][lg];
-      float best = 1e30f;
-      int best_opt = 0;
-      for (int opt = 0; opt < 2; ++opt) {
-        slot = (signed char)opt;
-        if (rows<float>(h, l, which, precond, o, nv, false, EPI_Y, st) < 0) {
-          rc = XAMG_ERR_CUDA;
-          break;
+      if (precond == XAMG_PREC_FP64) {
+        // y = M x on this level's FP64 work blocks
+        RowOpT<double> o = blank<double>();
+        double *x_l = l == 0 ? W.R : W.vx[l];
+        if (which == 0) {
+          o.src = x_l; o.y = W.vr[l];
+        } else if (which == 1) {
+          o.src = W.vx[l + 1]; o.y = W.vr[l];
+        } else {
+          o.src = W.vr[l]; o.y = W.vb[l + 1];
         }
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < 3; ++r) rows<float>(h, l, which, precond, o, nv, false, EPI_Y, st);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-          rc = XAMG_ERR_CUDA;
-          break;
+        rc = tune_product<double>(h, l, which, precond, o, nv, slot, st, e0, e1, &wide);
+      } else {
+        RowOpT<float> o = blank<float>();
+        if (which == 0) {
+          o.src = W.fx[l]; o.y = W.fr[l];
+        } else if (which == 1) {
+          o.src = W.fx[l + 1]; o.y = W.fr[l];
+        } else {
+          o.src = W.fr[l]; o.y = W.fb[l + 1];
         }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-          best = ms;
-          best_opt = opt;
-        }
+        rc = tune_product<float>(h, l, which, precond, o, nv, slot, st, e0, e1, &wide);
       }
-      slot = (signed char)best_opt;
       ++tuned;
-      wide += best_opt;
     }
   }
   cudaEventDestroy(e0);

@@ -326,8 +326,11 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
   constexpr int RPW = 32 / (G * SL);
   // entries gathered per chunk: 8 for FP64 (exact-count tails keep the FP64
   // FMA count at the algorithmic one); 4 for FP32, whose 16-byte gathers
-  // already fill the registers
-  constexpr int CH = sizeof(TB) == 4 ? 4 : 8;
+  // already fill the registers; never more than the G lanes of a row group
+  // hold, since a chunk's shuffles broadcast the group's own entries (narrow
+  // blocks, m = 2..8, would otherwise spend most shuffles on empty slots)
+  constexpr int CH0 = sizeof(TB) == 4 ? 4 : 8;
+  constexpr int CH = CH0 < G ? CH0 : G;
   constexpr int K = 32 / G < 4 ? 32 / G : 4;  // entries each lane fetches per round
   constexpr bool xlast = EPI == EPI_XLAST || EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2;
   const int lane = threadIdx.x & 31;

@@ -71,18 +71,20 @@ int rows_e(const RowOpT<TBx> &op, bool neg, int epi, cudaStream_t st) {
 }
 
 // m = 1 splits rows over 4 or 16 lanes; wider blocks give each lane VEC
-// columns, and FP32 blocks may split long rows over the whole warp (slices:
-// one row per warp).
+// columns and may split long rows over the whole warp (slices: one row per
+// warp).
 template <class TV>
 int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t st) {
 #if XAMG_NV == 1
   if (slices >= 16) return rows_e<TV, 1, 16>(op, neg, epi, st);
   return rows_e<TV, 1, 4>(op, neg, epi, st);
 #else
-#if XAMG_FLOAT
-  // long rows of FP32 blocks: every group of the warp takes a slice of one row
-  if (slices > 1) return rows_e<TV, XAMG_NV, 32 / (XAMG_NV / row_vec<float, XAMG_NV>())>(op, neg, epi, st);
-#endif
+  // long rows: every group of the warp takes a slice of one row (one row per
+  // warp; with 32 FP64 columns a row already fills the warp)
+  constexpr int WS = 32 / (XAMG_NV / row_vec<TBx, XAMG_NV>());
+  if constexpr (WS > 1) {
+    if (slices > 1) return rows_e<TV, XAMG_NV, WS>(op, neg, epi, st);
+  }
   (void)slices;
   return rows_e<TV, XAMG_NV, 1>(op, neg, epi, st);
 #endif
