@@ -26,7 +26,7 @@ are synthesised on the padded periodic grid (``problems.grf``, pad = 2).
   x_zero=False)``: it removes the high-frequency part of the network's
   error, which dominates the initial residual), then ``Hierarchy.solve(...,
   x0_given=True)``.  The plain solve from X0 = 0 is the fallback and the
-  judge of accuracy (all forms run to 1e-8).
+  measure of accuracy (all forms run to 1e-8).
 
 Run ``python -m paper_2103_07329_gb300.warmstart train --out PATH`` to train
 and store the parameters, ``... eval --params PATH`` to compare held-out

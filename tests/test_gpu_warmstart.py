@@ -2,7 +2,7 @@
 held-out 64^3 diffusion system (log k Gaussian random field, 32 smooth
 right-hand sides), with the parameters trained on the GPU by
 ``python -m paper_2103_07329_gb300.warmstart train`` and stored in the
-package.  The plain solve to 1e-8 judges the initial guess: every form must
+package.  The plain solve to 1e-8 is the measure of the initial guess: every form must
 reach the tolerance; the network's X0 must be much closer to the solution in
 the energy norm (the norm PCG reduces) than X0 = 0 or an untrained network's
 output, and must not cost iterations."""
