@@ -263,8 +263,10 @@ int xamg_vcycle(xamg_hier *h, const double *B, double *X, int32_t m, void *strea
 int xamg_vcycle_precond(xamg_hier *h, int32_t precond, const double *B, double *X, int32_t m,
                         void *stream);
 
-/* Coarsest-level direct solve X = A_L^-1 B with the LU factors of the setup
- * (paper Tab. 1, Direct).  DEVICE row-major blocks n_L x m. */
+/* Coarsest-level direct solve X = A_L^-1 B (paper Tab. 1, Direct): the
+ * setup's LU factors (partial pivoting) give the explicit inverse once, at
+ * upload, and every solve is the dense FP64 product A_L^-1 B on the tensor
+ * cores (mma.sync m8n8k4 .f64).  DEVICE row-major blocks n_L x m. */
 int xamg_coarse_solve(xamg_hier *h, const double *B, double *X, int32_t m, void *stream);
 
 /* Column dot products out[j] = sum_i U[i*m + j] * V[i*m + j] of two DEVICE

@@ -129,13 +129,14 @@ __global__ void __launch_bounds__(kBlock) k_b_copy_out(const BSys *__restrict__ 
   }
 }
 
-// one block per system: the coarsest-level FP64 LU solve of the FP32 block
+// one block per system: the coarsest-level solve of the FP32 block (FP64
+// product with the inverse on the tensor cores)
 __global__ void __launch_bounds__(kBlock) k_b_coarse(const BSys *__restrict__ sys, int ns, const int *__restrict__ sel) {
   const int s = blockIdx.x;
   if (s >= ns || !sel[s]) return;
   const BSys &S = sys[s];
   const BLevel &C = S.lv[S.L - 1];
-  XAMG_BNV(S.nv, (d_coarse_f<NV>(S.nc, S.lu, S.piv, C.b, C.x, S.cw)));
+  XAMG_BNV(S.nv, (d_coarse_mma<NV, float, float>(S.nc, S.ainv, C.b, C.x)));
 }
 
 // one 1024-thread block per system: the per-column scalar step of the
@@ -497,7 +498,6 @@ int plan_workspace(xamg_batch *b, bool alloc) {
         V.d = (float *)take(fb);
       }
     }
-    S.cw = (double *)take((size_t)H.nc * nv * sizeof(double));
     for (int i = 0; i < 3; ++i) S.part[i] = (double *)take((size_t)part_rows * nv * sizeof(double));
     S.cs = (ColState *)take(sizeof(ColState));
     S.kiter = (int *)take(sizeof(int));
@@ -627,8 +627,7 @@ int xamg_batch_create(xamg_hier *const *h, const int32_t *m, int32_t count, cons
     S.L = H.L;
     S.nc = H.nc;
     S.n0 = H.lv[0].n;
-    S.lu = H.lu;
-    S.piv = H.piv;
+    S.ainv = H.ainv;
     S.A0rp = H.lv[0].Arp;
     S.A0ci = H.lv[0].Aci;
     S.A0v = H.lv[0].A64;

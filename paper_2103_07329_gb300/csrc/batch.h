@@ -32,6 +32,7 @@ struct HierView {
   int L = 0, nc = 0, cheb_steps = 0, device = 0;
   const double *lu = nullptr;
   const int32_t *piv = nullptr;
+  const double *ainv = nullptr;  // inverse of the coarsest operator (nc x nc)
   HierLevelView lv[kBatchMaxLevels];
 };
 
@@ -59,8 +60,7 @@ struct BLevel {
 struct BSys {
   int nv = 0, m = 0, L = 0, nc = 0;
   int64_t n0 = 0;
-  const double *lu = nullptr;
-  const int32_t *piv = nullptr;
+  const double *ainv = nullptr;  // inverse of the coarsest operator (nc x nc)
   const int32_t *A0rp = nullptr, *A0ci = nullptr;
   const double *A0v = nullptr;  // FP64 fine operator
   int optA0 = 0;                // row split of the FP64 fine products
@@ -68,7 +68,6 @@ struct BSys {
   double *Xu = nullptr;         // caller's solution block (n0 x m)
   double *Bn = nullptr, *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr;
   float *R32 = nullptr, *Z32 = nullptr;
-  double *cw = nullptr;         // FP64 working copy of the coarsest block
   const float *w0 = nullptr;    // level-0 first Chebyshev weights (FP32)
   ColState *cs = nullptr;
   Flags *flags = nullptr;       // device address of the mapped host counters

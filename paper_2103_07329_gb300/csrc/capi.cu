@@ -103,6 +103,7 @@ struct xamg_hier {
   std::vector<DevLevel> lv;
   double *lu = nullptr;
   int32_t *piv = nullptr;
+  double *ainv = nullptr;     // inverse of the coarsest operator (nc x nc, row-major)
   std::vector<void *> owned;  // device allocations of the hierarchy
   void *ws = nullptr;         // cached solve workspace
   size_t ws_bytes = 0;
@@ -161,6 +162,27 @@ int upload_csr(xamg_hier *h, const HostCsr &a, DevCsr &d) {
 //   theta = (hi+lo)/2, delta = (hi-lo)/2, sigma = theta/delta, rho_0 = 1/sigma
 //   step 0: d_0 = (D^-1 / theta) r_0
 //   step k: rho_k = 1/(2 sigma - rho_{k-1}), d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k/delta) D^-1 r_k
+// Inverse of the coarsest operator from its LU factors (partial pivoting,
+// unit lower L): column j solves A x = e_j by the row interchanges, then
+// forward and back substitution.  Row-major nc x nc.
+std::vector<double> lu_inverse(int nc, const std::vector<double> &lu, const std::vector<int32_t> &piv) {
+  std::vector<double> inv((size_t)nc * nc), x(nc);
+  for (int j = 0; j < nc; ++j) {
+    std::fill(x.begin(), x.end(), 0.0);
+    x[j] = 1.0;
+    for (int k = 0; k < nc; ++k)
+      if (piv[k] != k) std::swap(x[k], x[piv[k]]);
+    for (int i = 1; i < nc; ++i)
+      for (int k = 0; k < i; ++k) x[i] -= lu[(size_t)i * nc + k] * x[k];
+    for (int i = nc - 1; i >= 0; --i) {
+      for (int k = i + 1; k < nc; ++k) x[i] -= lu[(size_t)i * nc + k] * x[k];
+      x[i] /= lu[(size_t)i * nc + i];
+    }
+    for (int i = 0; i < nc; ++i) inv[(size_t)i * nc + j] = x[i];
+  }
+  return inv;
+}
+
 int upload_level(xamg_hier *h, int l) {
   const HostLevel &H = h->host.lv[l];
   DevLevel &D = h->lv[l];
@@ -638,10 +660,10 @@ int vcycle(xamg_hier *h, Work &W, int prec, int l, const TB *b, TB *x, cudaStrea
     const int nc = h->host.nc;
     const double *xd;
     if constexpr (sizeof(TB) == 8) {
-      launch_coarse(nv, nc, h->lu, h->piv, b, x, st);
+      launch_coarse(nv, nc, h->ainv, b, x, st);
       xd = x;
     } else {
-      launch_coarse_f(nv, nc, h->lu, h->piv, b, x, W.cw, st);
+      launch_coarse_f(nv, nc, h->ainv, b, x, st);
       launch_to_f64(nv, nc, x, W.cw, elem_grid(nc, nv), st);  // the dots read the FP32 result
       xd = W.cw;
     }
@@ -1017,6 +1039,7 @@ int hier_view(xamg_hier *h, HierView *v) {
   v->cheb_steps = h->host.cheb_steps;
   v->device = h->device;
   v->lu = h->lu;
+  v->ainv = h->ainv;
   v->piv = h->piv;
   for (int l = 0; l < L; ++l) {
     const DevLevel &D = h->lv[l];
@@ -1360,6 +1383,12 @@ int xamg_setup_hierarchy(const xamg_csr *A, const xamg_amg_params *p, xamg_hier 
     if (rc == XAMG_OK) rc = dev_upload(h, &h->lu, h->host.lu.data(), h->host.lu.size());
     if (rc == XAMG_OK) rc = dev_upload(h, &h->piv, h->host.piv.data(), h->host.piv.size());
     if (rc == XAMG_OK) {
+      // the coarsest solve runs as a dense product with the explicit inverse
+      // (its columns: the LU solves of the unit vectors)
+      const std::vector<double> inv = lu_inverse(h->host.nc, h->host.lu, h->host.piv);
+      rc = dev_upload(h, &h->ainv, inv.data(), inv.size());
+    }
+    if (rc == XAMG_OK) {
       if (cudaHostAlloc((void **)&h->flags_h, sizeof(Flags), cudaHostAllocMapped) != cudaSuccess ||
           cudaHostGetDevicePointer((void **)&h->flags_d, h->flags_h, 0) != cudaSuccess)
         rc = XAMG_ERR_CUDA;
@@ -1596,7 +1625,7 @@ int xamg_coarse_solve(xamg_hier *h, const double *B, double *X, int32_t m, void 
   const int nc = h->host.nc;
   const int ge = elem_grid(nc, nv);
   launch_pad_in(nv, nc, B, m, W.Bn, ge, st);
-  launch_coarse(nv, nc, h->lu, h->piv, W.Bn, W.X, st);
+  launch_coarse(nv, nc, h->ainv, W.Bn, W.X, st);
   launch_copy_out(nv, nc, W.X, X, m, ge, st);
   XCK(cudaStreamSynchronize(st));
   XCK(cudaGetLastError());

@@ -268,41 +268,44 @@ __device__ __forceinline__ void d_scalar(int mode, ColState *cs, const double *p
     }
   }
 }
-// Coarsest level with FP32 blocks: the FP64 LU solve of k_coarse on an FP64
-// working copy W (nc x NV), rounded back to FP32.
-template <int NV>
-__device__ __forceinline__ void d_coarse_f(int nc, const double *lu, const int32_t *piv,
-                                                     const float *B, float *X, double *W) {
-  const int tid = threadIdx.x;
-  for (int e = tid; e < nc * NV; e += kBlock) W[e] = (double)B[e];
-  __syncthreads();
-  if (tid < NV)
-    for (int k = 0; k < nc; ++k) {
-      const int p = piv[k];
-      if (p != k) {
-        const double t = W[k * NV + tid];
-        W[k * NV + tid] = W[p * NV + tid];
-        W[p * NV + tid] = t;
-      }
+// FP64 tensor-core product D += A B of one 8x8x4 step (mma.sync m8n8k4):
+// lane (g = lane / 4, q = lane % 4) holds a = A[g][q], b = B[q][g] and
+// d = D[g][2q], D[g][2q + 1].
+__device__ __forceinline__ void dmma884(double (&d)[2], double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d[0]), "+d"(d[1])
+               : "d"(a), "d"(b));
+}
+
+// Coarsest-level direct solve (paper Tab. 1, "Direct") as the dense product
+// X = Ainv B on the FP64 tensor cores: Ainv (nc x nc, row-major) is the
+// inverse of the coarsest operator, formed at upload from its LU factors;
+// B, X are nc x NV blocks (TI / TO: double, or float widened and rounded).
+// One block; warp w takes the 8 x 8 output tiles w, w + warps, ...; rows and
+// columns past nc and NV read as zero.  FP64 products and sums throughout.
+template <int NV, class TI, class TO>
+__device__ __forceinline__ void d_coarse_mma(int nc, const double *Ainv, const TI *B, TO *X) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, q = lane & 3;
+  const int mt_n = (nc + 7) / 8;
+  constexpr int nt_n = (NV + 7) / 8;
+  for (int tile = warp; tile < mt_n * nt_n; tile += (int)(blockDim.x >> 5)) {
+    const int mt = tile / nt_n, nt = tile % nt_n;
+    const int row = mt * 8 + g;   // row of the A fragment and of the output
+    const int colb = nt * 8 + g;  // column of the B fragment
+    double acc[2] = {0.0, 0.0};
+    for (int k = 0; k < nc; k += 4) {
+      const int kk = k + q;
+      const double a = (row < nc && kk < nc) ? Ainv[(size_t)row * nc + kk] : 0.0;
+      const double b = (kk < nc && colb < NV) ? (double)B[(size_t)kk * NV + colb] : 0.0;
+      dmma884(acc, a, b);
     }
-  __syncthreads();
-  for (int k = 0; k + 1 < nc; ++k) {
-    for (int e = tid; e < (nc - k - 1) * NV; e += kBlock) {
-      const int i = k + 1 + e / NV, c = e % NV;
-      W[i * NV + c] = __dsub_rn(W[i * NV + c], __dmul_rn(lu[(size_t)i * nc + k], W[k * NV + c]));
+    const int c0 = nt * 8 + 2 * q;
+    if (row < nc) {
+      if (c0 < NV) X[(size_t)row * NV + c0] = (TO)acc[0];
+      if (c0 + 1 < NV) X[(size_t)row * NV + c0 + 1] = (TO)acc[1];
     }
-    __syncthreads();
   }
-  for (int i = nc - 1; i >= 0; --i) {
-    if (tid < NV) W[i * NV + tid] = W[i * NV + tid] / lu[(size_t)i * nc + i];
-    __syncthreads();
-    for (int e = tid; e < i * NV; e += kBlock) {
-      const int r = e / NV, c = e % NV;
-      W[r * NV + c] = __dsub_rn(W[r * NV + c], __dmul_rn(lu[(size_t)r * nc + i], W[i * NV + c]));
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < nc * NV; e += kBlock) X[e] = (float)W[e];
 }
 template <int NV>
 __device__ __forceinline__ void d_to_f64(int64_t n, const float *X32, double *Y) {

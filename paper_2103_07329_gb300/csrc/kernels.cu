@@ -236,41 +236,10 @@ __global__ void __launch_bounds__(1024) k_scalar(int mode, ColState *cs, const d
 
 
 // ------------------------------------------------------------------ coarsest
-// X = A_c^-1 B with the LU factors (unit lower L, partial pivoting): one block
-// works through the rows in order; the forward sweep subtracts in the same
-// order as the row form of forward substitution.
+// X = A_c^-1 B as a dense product on the FP64 tensor cores (elem.cuh).
 template <int NV>
-__global__ void __launch_bounds__(kBlock) k_coarse(int nc, const double *lu, const int32_t *piv,
-                                                   const double *B, double *X) {
-  const int tid = threadIdx.x;
-  for (int e = tid; e < nc * NV; e += kBlock) X[e] = B[e];
-  __syncthreads();
-  if (tid < NV)
-    for (int k = 0; k < nc; ++k) {
-      const int p = piv[k];
-      if (p != k) {
-        const double t = X[k * NV + tid];
-        X[k * NV + tid] = X[p * NV + tid];
-        X[p * NV + tid] = t;
-      }
-    }
-  __syncthreads();
-  for (int k = 0; k + 1 < nc; ++k) {
-    for (int e = tid; e < (nc - k - 1) * NV; e += kBlock) {
-      const int i = k + 1 + e / NV, c = e % NV;
-      X[i * NV + c] = __dsub_rn(X[i * NV + c], __dmul_rn(lu[(size_t)i * nc + k], X[k * NV + c]));
-    }
-    __syncthreads();
-  }
-  for (int i = nc - 1; i >= 0; --i) {
-    if (tid < NV) X[i * NV + tid] = X[i * NV + tid] / lu[(size_t)i * nc + i];
-    __syncthreads();
-    for (int e = tid; e < i * NV; e += kBlock) {
-      const int r = e / NV, c = e % NV;
-      X[r * NV + c] = __dsub_rn(X[r * NV + c], __dmul_rn(lu[(size_t)r * nc + i], X[i * NV + c]));
-    }
-    __syncthreads();
-  }
+__global__ void __launch_bounds__(kBlock) k_coarse(int nc, const double *Ainv, const double *B, double *X) {
+  d_coarse_mma<NV, double, double>(nc, Ainv, B, X);
 }
 
 // ------------------------------------------------------------------ mixed precision
@@ -335,9 +304,8 @@ __global__ void __launch_bounds__(kBlock) k_axpy_dot_f(int64_t n, float *X, cons
 }
 
 template <int NV>
-__global__ void __launch_bounds__(kBlock) k_coarse_f(int nc, const double *lu, const int32_t *piv,
-                                                     const float *B, float *X, double *W) {
-  d_coarse_f<NV>(nc, lu, piv, B, X, W);
+__global__ void __launch_bounds__(kBlock) k_coarse_f(int nc, const double *Ainv, const float *B, float *X) {
+  d_coarse_mma<NV, float, float>(nc, Ainv, B, X);
 }
 
 
@@ -456,9 +424,8 @@ void launch_scalar(int nv, int mode, ColState *cs, const double *p0, const doubl
                    double tol, int k, Flags *flags, cudaStream_t st) {
   XAMG_NV_SWITCH(nv, (k_scalar<NV><<<1, 1024, 0, st>>>(mode, cs, p0, p1, nblk, tol, k, flags)));
 }
-void launch_coarse(int nv, int nc, const double *lu, const int32_t *piv, const double *B, double *X,
-                   cudaStream_t st) {
-  XAMG_NV_SWITCH(nv, (k_coarse<NV><<<1, kBlock, 0, st>>>(nc, lu, piv, B, X)));
+void launch_coarse(int nv, int nc, const double *Ainv, const double *B, double *X, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_coarse<NV><<<1, kBlock, 0, st>>>(nc, Ainv, B, X)));
 }
 
 void launch_init_fpcg(int nv, int64_t n, const double *B, int m, double *Bn, double *R, double *X,
@@ -486,9 +453,8 @@ void launch_axpy_dot_f(int nv, int64_t n, float *X, const float *D, const double
                        const double *U2, double *part, double *part2, int grid, cudaStream_t st) {
   XAMG_NV_SWITCH(nv, (k_axpy_dot_f<NV><<<grid, kBlock, 0, st>>>(n, X, D, U, U2, part, part2)));
 }
-void launch_coarse_f(int nv, int nc, const double *lu, const int32_t *piv, const float *B, float *X,
-                     double *W, cudaStream_t st) {
-  XAMG_NV_SWITCH(nv, (k_coarse_f<NV><<<1, kBlock, 0, st>>>(nc, lu, piv, B, X, W)));
+void launch_coarse_f(int nv, int nc, const double *Ainv, const float *B, float *X, cudaStream_t st) {
+  XAMG_NV_SWITCH(nv, (k_coarse_f<NV><<<1, kBlock, 0, st>>>(nc, Ainv, B, X)));
 }
 
 void launch_zero_rhs_cols(int nv, int64_t n, double *X, const ColState *cs, int grid, cudaStream_t st) {

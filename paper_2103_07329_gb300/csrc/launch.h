@@ -143,8 +143,8 @@ void launch_coldot(int nv, int64_t n, const double *U, const double *V, double *
                    cudaStream_t st);
 void launch_scalar(int nv, int mode, ColState *cs, const double *p0, const double *p1, int nblk,
                    double tol, int k, Flags *flags, cudaStream_t st);
-void launch_coarse(int nv, int nc, const double *lu, const int32_t *piv, const double *B, double *X,
-                   cudaStream_t st);
+// Coarsest solve X = Ainv B (Ainv: nc x nc inverse of the coarsest operator).
+void launch_coarse(int nv, int nc, const double *Ainv, const double *B, double *X, cudaStream_t st);
 // Outer FP64 loop around an FP32-block preconditioner.
 void launch_init_fpcg(int nv, int64_t n, const double *B, int m, double *Bn, double *R, double *X,
                       float *R32, float *Z32, const float *w0, double *part, int grid,
@@ -159,8 +159,7 @@ void launch_to_f32(int nv, int64_t n, const double *X, float *Y32, const float *
 void launch_to_f64(int nv, int64_t n, const float *X32, double *Y, int grid, cudaStream_t st);
 void launch_axpy_dot_f(int nv, int64_t n, float *X, const float *D, const double *U,
                        const double *U2, double *part, double *part2, int grid, cudaStream_t st);
-void launch_coarse_f(int nv, int nc, const double *lu, const int32_t *piv, const float *B, float *X,
-                     double *W, cudaStream_t st);
+void launch_coarse_f(int nv, int nc, const double *Ainv, const float *B, float *X, cudaStream_t st);
 void launch_zero_rhs_cols(int nv, int64_t n, double *X, const ColState *cs, int grid, cudaStream_t st);
 // Runtime-m column dots for the public entry point: partials then reduce.
 int coldot_rt_grid(int64_t n, int m);
