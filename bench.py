@@ -87,6 +87,12 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="measurement mode: m in 1..32, PCG and BiCGStab, FP64/FP32/bf16 "
                          "preconditioner, one JSON line each (not the benchmark line)")
+    ap.add_argument("--split-table", action="store_true",
+                    help="measurement mode: every row split of every level's FP64 product y = M x "
+                         "on --m columns, microseconds per product, one JSON line per operator")
+    ap.add_argument("--spmm-only", action="store_true",
+                    help="profiling mode: four level-0 products y = A x on --m columns with the "
+                         "default row split, nothing else (the case for kernel captures)")
     a = ap.parse_args()
     if a.grid is None:
         a.grid = 160 if a.matrix == "poisson27" else 192
@@ -643,12 +649,85 @@ def run_sweep(a):
     return 0
 
 
+SPLIT_NAMES = {1: ["stream1x256", "lanes16", "stream1x1024", "stream4x1024", "stream32x1024",
+                    "stream1x512", "stream2x512"],
+               0: ["narrow", "row_per_warp"]}
+
+
+def run_split_table(a):
+    """Microseconds per FP64 product y = M x of every level and operator under
+    every row split (xamg_set_split), 20 timed products after 3 warm-ups."""
+    import torch
+
+    from paper_2103_07329_gb300 import binding as B
+    from paper_2103_07329_gb300 import build as build_mod
+
+    build_mod.build()
+    A = make_matrix(a)
+    h = B.Hierarchy(A)
+    L = h.levels
+    info = [h.level_info(l) for l in range(L)]
+    names = SPLIT_NAMES[1] if a.m == 1 else SPLIT_NAMES[0]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for l in range(L):
+        for which in (0, 1, 2):
+            if which > 0 and l + 1 >= L:
+                continue
+            n_out = info[l][0] if which in (0, 1) else info[l + 1][0]
+            n_src = info[l][0] if which in (0, 2) else info[l + 1][0]
+            X = torch.rand(n_src, a.m, dtype=torch.float64, device="cuda")
+            Y = torch.empty(n_out, a.m, dtype=torch.float64, device="cuda")
+            us = {}
+            for c, name in enumerate(names):
+                h.set_split(a.m, B.PREC_FP64, l, which, c)
+                for _ in range(3):
+                    h.spmm(l, which, X, Y)
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(20):
+                    h.spmm(l, which, X, Y)
+                e1.record()
+                torch.cuda.synchronize()
+                us[name] = round(e0.elapsed_time(e1) / 20 * 1e3, 1)
+            h.set_split(a.m, B.PREC_FP64, l, which, -1)
+            nnz = info[l][1] if which == 0 else info[l][2]
+            print(json.dumps({"matrix": a.matrix, "grid": a.grid, "m": a.m, "level": l,
+                              "op": "APR"[which], "rows": n_out, "nnz": nnz,
+                              "avg_row": round(nnz / max(n_out, 1), 1), "us": us}), flush=True)
+    return 0
+
+
+def run_spmm_only(a):
+    """Four level-0 products y = A x with the default split, for kernel captures."""
+    import torch
+
+    from paper_2103_07329_gb300 import binding as B
+    from paper_2103_07329_gb300 import build as build_mod
+
+    build_mod.build()
+    A = make_matrix(a)
+    h = B.Hierarchy(A)
+    X = torch.rand(A.n, a.m, dtype=torch.float64, device="cuda")
+    Y = torch.empty(A.n, a.m, dtype=torch.float64, device="cuda")
+    for _ in range(4):
+        h.spmm(0, 0, X, Y)
+    torch.cuda.synchronize()
+    print(json.dumps({"matrix": a.matrix, "grid": a.grid, "n": A.n, "nnz": A.nnz, "m": a.m,
+                      "products": 4}))
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
     if a.sweep:
         return run_sweep(a)
+    if a.split_table:
+        return run_split_table(a)
+    if a.spmm_only:
+        return run_spmm_only(a)
     if a.batch_only:
         return run_batch_only(a)
     return run_ours(a)

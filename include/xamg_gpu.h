@@ -304,15 +304,34 @@ int xamg_coldot_noalloc(const double *U, const double *V, int64_t n, int32_t m, 
  * and R, times y = M x on blocks of pad(m) columns (m in [1, XAMG_MAX_RHS])
  * of the precision `precond` selects (XAMG_PREC_FP64: FP64 blocks;
  * XAMG_PREC_FP32 / XAMG_PREC_BF16: FP32 blocks with FP32 / bf16 values of A)
- * under both row splits -- the default (a group of lanes per row, several
- * rows per warp) and one row per warp with its entries split over the lanes
- * -- and keeps the faster in the hierarchy; later solves and V-cycles of that
- * block width and precision use it.  Results do not depend on the split beyond the
- * order of each row's FP32 sums.  ops_tuned / ops_wide (may be NULL): products
- * tuned and how many chose one row per warp.  Uses the hierarchy's cached
+ * under every row split -- for m > 1 the default (a group of lanes per row,
+ * several rows per warp) and one row per warp with its entries split over the
+ * lanes; for m = 1 the stream kernel (the warp's entries staged in shared
+ * memory) with one lane per row and a 256-, 512- or 1024-entry window, 2, 4
+ * or 32 lanes per row, and 16 lanes per row without staging -- and keeps
+ * the fastest in the hierarchy; later solves and V-cycles of
+ * that block width and precision use it.  Results do not depend on the split
+ * beyond the order of each row's sums.  ops_tuned / ops_wide (may be NULL):
+ * products tuned and how many chose a split other than the first candidate
+ * (m > 1: one row per warp).  Uses the hierarchy's cached
  * workspace; synchronizes `stream`.  No counterpart in the paper. */
 int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_t *ops_tuned,
                   int32_t *ops_wide);
+
+/* Sets the row split of one sparse product by hand (what xamg_autotune sets
+ * by timing): operator `which` (0 = A, 1 = P, 2 = R; P and R exist below the
+ * coarsest level) of level `level`, blocks of pad(m) columns of precision
+ * `precond`.  candidate: -1 = the default rule; otherwise the index of a
+ * tuning candidate -- m = 1: 0 = stream kernel, one lane per row, 256-entry
+ * window; 1 = 16 lanes per row; 2, 3, 4 = stream kernel with a 1024-entry
+ * window and 1 lane, 4 lanes or a warp per row; 5, 6 = stream kernel with a
+ * 512-entry window and 1 or 2 lanes per row; m > 1: 0 = a
+ * group of lanes per row, 1 = one row per warp (ignored for FP64 blocks of 32
+ * columns, where a row fills the warp).  Results do not depend on the split
+ * beyond the order of each row's sums.  XAMG_ERR_INVALID_ARG for any other
+ * value.  Host only.  No counterpart in the paper. */
+int xamg_set_split(xamg_hier *h, int32_t m, int32_t precond, int32_t level, int32_t which,
+                   int32_t candidate);
 
 /* ---- batched solve of many independent systems ----
  *

@@ -47,7 +47,7 @@ EXPORTS = [
     "xamg_net_param_count", "xamg_net_create", "xamg_net_destroy", "xamg_net_set_params",
     "xamg_net_get_params", "xamg_net_forward", "xamg_net_loss_grad", "xamg_net_train_step",
     "xamg_net_predict_x0", "xamg_conv3d_bf16", "xamg_conv3d_bf16_wgrad",
-    "xamg_autotune", "xamg_batch_opts_default", "xamg_batch_create", "xamg_batch_destroy", "xamg_batch_info",
+    "xamg_autotune", "xamg_set_split", "xamg_batch_opts_default", "xamg_batch_create", "xamg_batch_destroy", "xamg_batch_info",
     "xamg_batch_solve",
 ]
 
@@ -151,6 +151,7 @@ def _load():
         "xamg_conv3d_bf16": ([vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, vp], C.c_int),
         "xamg_conv3d_bf16_wgrad": ([vp, vp, vp, vp, vp, i32, i32, i32, i32, vp], C.c_int),
         "xamg_autotune": ([vp, i32, i32, vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
+        "xamg_set_split": ([vp, i32, i32, i32, i32, i32], C.c_int),
         "xamg_batch_opts_default": ([C.POINTER(BatchOptsT)], None),
         "xamg_batch_create": ([vp, vp, i32, C.POINTER(BatchOptsT), C.POINTER(vp)], C.c_int),
         "xamg_batch_destroy": ([vp], C.c_int),
@@ -365,13 +366,19 @@ class Hierarchy:
                "xamg_coarse_solve")
 
     def autotune(self, m: int, precond: int = PREC_FP32, stream=None):
-        """xamg_autotune: time both row splits of every level's FP32-block
-        products for pad(m) columns and keep the faster; returns
-        (products tuned, products that chose one row per warp)."""
+        """xamg_autotune: time every row split of each level's products on
+        blocks of pad(m) columns of precision `precond` and keep the fastest;
+        returns (products tuned, products that chose a split other than the
+        first candidate)."""
         t = C.c_int32(); w = C.c_int32()
         _check(_load().xamg_autotune(self._h, m, precond, _stream(stream), C.byref(t), C.byref(w)),
                "xamg_autotune")
         return t.value, w.value
+
+    def set_split(self, m: int, precond: int, level: int, which: int, candidate: int):
+        """xamg_set_split: force tuning candidate `candidate` (-1: the default
+        rule) for operator `which` of `level` on pad(m)-column blocks."""
+        _check(_load().xamg_set_split(self._h, m, precond, level, which, candidate), "xamg_set_split")
 
     def timing_enable(self, on: bool = True):
         _check(_load().xamg_timing_enable(self._h, 1 if on else 0), "xamg_timing_enable")

@@ -40,8 +40,8 @@ struct DevLevel {
   float c1f[4] = {0, 0, 0, 0};
   // row split of the sparse products chosen by xamg_autotune, per values
   // (0: FP32 blocks, 1: FP32 blocks with bf16 A, 2: FP64), operator (A, P, R)
-  // and block width (log2 nv): -1 untuned (the default rule), 0 narrow, 1 one
-  // row per warp
+  // and block width (log2 nv): -1 untuned (the default rule), else the
+  // tuning candidate that won (split_slices)
   signed char split[3][3][6];
   DevLevel() { std::memset(split, -1, sizeof(split)); }
 };
@@ -234,6 +234,8 @@ int upload_lowp(xamg_hier *h) {
       s[i] = mx > 0.0 ? (float)mx : 1.0f;
       for (int p = H.A.rowptr[i]; p < H.A.rowptr[i + 1]; ++p) q[p] = __float2bfloat16_rn(f[p] / s[i]);
     }
+    // an even number of values: the m = 1 stream kernel copies aligned pairs
+    if (q.size() & 1) q.push_back(__float2bfloat16_rn(0.0f));
     if ((rc = dev_upload(h, &D.a16, q.data(), q.size())) != XAMG_OK) return rc;
     if ((rc = dev_upload(h, &D.a16s, s.data(), s.size())) != XAMG_OK) return rc;
     // 16-bit column indices: usable when every row's columns lie in two
@@ -450,7 +452,12 @@ void flush_timing(xamg_hier *h) {
 int slices_for(const DevCsr &M, int nv, bool fp32) {
   if (M.n == 0) return 1;
   const double avg = (double)M.nnz / M.n;
-  if (nv == 1) return avg >= 24.0 ? 16 : 4;
+  // m = 1: the stream kernel with as many lanes per row as keep a chunk's
+  // rows inside one window (32 x 7.5 = 240 of 256 entries, 32 x 30 = 960 of
+  // 1024; 4 lanes per row up to 64 entries), 16 lanes per row beyond, which
+  // measured fastest on the dense Galerkin levels
+  if (nv == 1)
+    return avg <= 7.5 ? kStreamShort : avg <= 30.0 ? kStreamLong : avg <= 64.0 ? kStreamQuad : kSliced16;
   if (fp32 && nv >= 16 && avg >= 64.0) return 32 / (nv / 4);
   // a dense Galerkin level with fewer row groups than resident warps under the
   // default split (rows per warp = 32 / lanes per row): one row per warp, the
@@ -459,6 +466,19 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
   const double warps = (double)M.n / (32 / (nv / vec));
   if (avg >= 32.0 && warps < 32.0 * device_sm_count()) return 2;
   return 1;
+}
+
+// Row split of tuning candidate t: m = 1 has seven (the stream-kernel
+// variants and 16 lanes per row, launch.h), wider blocks two (narrow, one row
+// per warp).
+int split_candidates(int nv) { return nv == 1 ? 7 : 2; }
+int split_slices(int nv, int t) {
+  if (nv == 1) {
+    static const int c[7] = {kStreamShort, kSliced16, kStreamLong, kStreamQuad, kStreamWarp, kStreamMid,
+                             kStreamPair};
+    return c[t];
+  }
+  return t ? 2 : 1;
 }
 
 // Algorithmic bytes of one fused row launch: the matrix once, the operand
@@ -503,7 +523,7 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
       op.rscale = D.a16s;
       vt = 1;
       vbytes = 2.0;
-      if (D.a16w) {
+      if (D.a16w && nv > 1) {
         op.colw = D.a16w;
         op.rowmeta = D.a16meta;
         vt = 2;
@@ -525,14 +545,14 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
     int lg = 0;
     while ((1 << lg) < nv) ++lg;
     const int t = D.split[2][which][lg];
-    if (t >= 0 && nv < 32) sl = t ? (nv == 1 ? 16 : 2) : (nv == 1 ? 4 : 1);
+    if (t >= 0 && nv < 32) sl = split_slices(nv, t);
     g = launch_rows(op, nv, sl, neg, epi, st);
   } else {
     int sl = slices_for(M, nv, true);
     int lg = 0;
     while ((1 << lg) < nv) ++lg;
     const int t = D.split[vt ? 1 : 0][which][lg];
-    if (t >= 0) sl = t ? (nv == 1 ? 16 : 2) : (nv == 1 ? 4 : 1);
+    if (t >= 0) sl = split_slices(nv, t);
     g = launch_rows_f(op, nv, sl, neg, epi, vt, st);
   }
   if (h->timing) {
@@ -1296,7 +1316,7 @@ int tune_product(xamg_hier *h, int l, int which, int precond, RowOpT<TB> o, int 
                  cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int *wide) {
   float best = 1e30f;
   int best_opt = 0;
-  for (int opt = 0; opt < 2; ++opt) {
+  for (int opt = 0; opt < split_candidates(nv); ++opt) {
     slot = (signed char)opt;
     if (rows<TB>(h, l, which, precond, o, nv, false, EPI_Y, st) < 0) return XAMG_ERR_CUDA;
     cudaEventRecord(e0, st);
@@ -1311,7 +1331,7 @@ int tune_product(xamg_hier *h, int l, int which, int precond, RowOpT<TB> o, int 
     }
   }
   slot = (signed char)best_opt;
-  *wide += best_opt;
+  *wide += best_opt != 0;
   return XAMG_OK;
 }
 
@@ -1703,6 +1723,23 @@ int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_
   if (rc != XAMG_OK) return rc;
   if (ops_tuned) *ops_tuned = tuned;
   if (ops_wide) *ops_wide = wide;
+  return XAMG_OK;
+}
+
+int xamg_set_split(xamg_hier *h, int32_t m, int32_t precond, int32_t level, int32_t which,
+                   int32_t candidate) {
+  if (!h || !h->on_device || m < 1 || m > XAMG_MAX_RHS ||
+      (precond != XAMG_PREC_FP64 && precond != XAMG_PREC_FP32 && precond != XAMG_PREC_BF16))
+    return XAMG_ERR_INVALID_ARG;
+  const int L = (int)h->lv.size();
+  if (level < 0 || level >= L || which < 0 || which > 2 || (which > 0 && level + 1 >= L))
+    return XAMG_ERR_INVALID_ARG;
+  const int nv = pad_nv(m);
+  if (candidate < -1 || candidate >= split_candidates(nv)) return XAMG_ERR_INVALID_ARG;
+  int lg = 0;
+  while ((1 << lg) < nv) ++lg;
+  const int pc = precond == XAMG_PREC_BF16 ? 1 : precond == XAMG_PREC_FP32 ? 0 : 2;
+  h->lv[level].split[pc][which][lg] = (signed char)candidate;
   return XAMG_OK;
 }
 

@@ -184,6 +184,7 @@ __device__ __forceinline__ void row_operands(const RowOpT<TB> &op, int64_t i, in
 // relative to the row's FP32 scale, applied once per row).
 template <class TV> struct ValueLoad;
 template <> struct ValueLoad<double> {
+  using T = double;  // storage type
   static constexpr bool scaled = false;
   static constexpr bool idx16 = false;
   __device__ __forceinline__ static double get(const void *v, int k) {
@@ -191,6 +192,7 @@ template <> struct ValueLoad<double> {
   }
 };
 template <> struct ValueLoad<float> {
+  using T = float;
   static constexpr bool scaled = false;
   static constexpr bool idx16 = false;
   __device__ __forceinline__ static float get(const void *v, int k) {
@@ -198,6 +200,7 @@ template <> struct ValueLoad<float> {
   }
 };
 template <> struct ValueLoad<__nv_bfloat16> {
+  using T = __nv_bfloat16;
   static constexpr bool scaled = true;
   static constexpr bool idx16 = false;
   __device__ __forceinline__ static float get(const void *v, int k) {
@@ -211,6 +214,7 @@ template <> struct ValueLoad<__nv_bfloat16> {
 // types reduced to uint16_t).
 struct Bf16Idx16 {};
 template <> struct ValueLoad<Bf16Idx16> {
+  using T = __nv_bfloat16;
   static constexpr bool scaled = true;
   static constexpr bool idx16 = true;
   __device__ __forceinline__ static float get(const void *v, int k) {
@@ -563,6 +567,155 @@ __device__ __forceinline__ void rows_sliced(const RowOpT<TB> &op) {
   }
 }
 
+// ---- m = 1 stream kernel ----
+// Asynchronous 4- and 8-byte global -> shared copies (no registers held while
+// they are in flight).
+__device__ __forceinline__ void cp_async_4(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Shared-memory bytes of one warp's window of R entries: R column indices,
+// then R + 2 values (bf16 values are copied in aligned pairs, so a window may
+// start one entry early and end one entry late).
+template <class TV, int R>
+__host__ __device__ constexpr int stream_warp_bytes() {
+  return ((R * 4 + (R + 2) * (int)sizeof(typename ValueLoad<TV>::T)) + 15) / 16 * 16;
+}
+
+// Row kernel for m = 1 (CSR-stream).  A warp owns 32 / LPR consecutive rows
+// (lanes g*LPR .. g*LPR + LPR - 1 share row r0 + g); the rows' entries are one
+// contiguous range of the CSR arrays, which the warp copies into its
+// shared-memory window (R entries at a time) with per-lane asynchronous copies
+// -- 32 consecutive entries per instruction -- and then the LPR lanes of each
+// row walk the row's entries in the window with stride LPR, gathering the
+// operands eight at a time (consecutive rows of a stencil-like matrix gather
+// consecutive operands) and adding the products in order; the LPR partial
+// sums are added in a fixed xor tree.  With LPR = 1 every FMA instruction of
+// the walk carries one entry per lane and the epilogue runs on every lane,
+// which matters at m = 1: the FP64 issue rate (about two FMAs per SM per
+// clock) is as tight a bound as the HBM stream.  Wider LPR serve longer rows
+// (the dense Galerkin levels), whose range per row would not fit a window.  A
+// range longer than the window is walked window by window.  The next chunk's
+// row pointers are read ahead.
+template <class TB, class TV, int LPR, int R, bool NEG, int EPI>
+__device__ __forceinline__ void rows_stream(const RowOpT<TB> &op, unsigned char *smem) {
+  using VL = ValueLoad<TV>;
+  using TS = typename VL::T;
+  static_assert(!VL::idx16, "the stream kernel reads 32-bit column indices");
+  constexpr bool pairs = sizeof(TS) == 2;
+  constexpr int RPC = 32 / LPR;  // rows per chunk
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / LPR, p = lane % LPR;
+  int32_t *s_col = reinterpret_cast<int32_t *>(smem + warp * stream_warp_bytes<TV, R>());
+  TS *s_val = reinterpret_cast<TS *>(s_col + R);
+  const int64_t n = op.n;
+  const int64_t step = (int64_t)gridDim.x * kWarps * RPC;
+  const TS *gval = static_cast<const TS *>(op.val);
+  double dsum = 0.0, dsum2 = 0.0;
+  int64_t r0 = ((int64_t)blockIdx.x * kWarps + warp) * RPC;
+  int rs = 0, re = 0;
+  if (r0 < n) {
+    rs = __ldg(op.rowptr + min(r0 + g, n));
+    re = __ldg(op.rowptr + min(r0 + g + 1, n));
+  }
+  for (; r0 < n; r0 += step) {
+    const int64_t i = r0 + g;
+    const bool valid = i < n;
+    const bool owner = valid && p == 0;  // the lane that runs the row's epilogue
+    TB dpv = 0, wv = 0, xv = 0, iv = 0;
+    double du = 0.0, du2 = 0.0;
+    float rsc = 1.0f;
+    if (owner) {
+      row_operands<TB, 1, EPI>(op, i, 0, dpv, wv, xv, du, du2);
+      if (op.init) iv = op.init[i];
+      if constexpr (VL::scaled) rsc = __ldg(op.rscale + i);
+    }
+    int nrs = 0, nre = 0;
+    if (r0 + step < n) {
+      nrs = __ldg(op.rowptr + min(r0 + step + g, n));
+      nre = __ldg(op.rowptr + min(r0 + step + g + 1, n));
+    }
+    const int e0 = __shfl_sync(0xffffffffu, rs, 0), e1 = __shfl_sync(0xffffffffu, re, 31);
+    // the owner lane starts from the init value (unscaled values), so that
+    // no FP64 add is spent on it
+    TB acc = VL::scaled ? (TB)0 : iv;
+    for (int wb = e0; wb < e1; wb += R) {
+      const int we = min(e1, wb + R);
+      const int vb = pairs ? (wb & ~1) : wb;  // first value in the window's buffer
+      __syncwarp();  // every lane is done with the previous window
+      for (int k = wb + lane; k < we; k += 32) cp_async_4(s_col + (k - wb), op.col + k);
+      if constexpr (pairs) {
+        // aligned pairs (vb, vb+1), ..., covering [wb, we); the value array
+        // holds an even number of entries
+        for (int k = vb + 2 * lane; k < we; k += 64) cp_async_4(s_val + (k - vb), gval + k);
+      } else if constexpr (sizeof(TS) == 8) {
+        for (int k = wb + lane; k < we; k += 32) cp_async_8(s_val + (k - vb), gval + k);
+      } else {
+        for (int k = wb + lane; k < we; k += 32) cp_async_4(s_val + (k - vb), gval + k);
+      }
+      cp_async_wait_all();
+      __syncwarp();
+      // this lane's entries of the window: lo, lo + LPR, ... < hi
+      const int lo = max(rs, wb) + p, hi = min(re, we);
+      const int cnt = hi > lo ? (hi - lo + LPR - 1) / LPR : 0;
+      const int wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
+      // blocks of eight entries, then a warp-uniform tail of exactly
+      // wmax % 8 FMAs (the FP64 issue rate is the bound; a masked lane adds
+      // 0 * 0)
+      for (int q = 0; q < wmax; q += 8) {
+        TB a[8], xg[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          a[u] = (TB)0;
+          xg[u] = (TB)0;
+          const int k = lo + (q + u) * LPR;
+          if (k < hi) {
+            const int c = s_col[k - wb];
+            if constexpr (pairs) a[u] = __bfloat162float(s_val[k - vb]);
+            else a[u] = (TB)s_val[k - vb];
+            xg[u] = __ldg(op.src + c);
+          }
+        }
+        if (q + 8 <= wmax) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc = fmadd<NEG>(a[u], xg[u], acc);
+        } else {
+          acc = tail_fma<NEG>(wmax - q, a, xg, acc);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < LPR; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if constexpr (VL::scaled) acc = fma((TB)rsc, acc, iv);
+    if (owner) row_epilogue<TB, 1, EPI>(op, i, 0, acc, dpv, wv, xv, du, du2, dsum, dsum2);
+    rs = nrs;
+    re = nre;
+  }
+  if constexpr (epi_has_dot<EPI>()) {
+    if (EPI != EPI_Y_DOT2 || op.dot_u) block_colsum_store<1>(dsum, op.partials);
+    if constexpr (EPI == EPI_Y_DOT2 || EPI == EPI_XLAST_DOT2) {
+      __syncthreads();
+      block_colsum_store<1>(dsum2, op.partials2);
+    }
+  }
+}
+
+// Stream-kernel variants of the m = 1 split (the S < 0 codes of the row
+// launchers): lanes per row and window entries.
+template <int S> struct StreamCfg;
+template <> struct StreamCfg<-1> { static constexpr int LPR = 1, R = 256; };
+template <> struct StreamCfg<-2> { static constexpr int LPR = 1, R = 1024; };
+template <> struct StreamCfg<-3> { static constexpr int LPR = 4, R = 1024; };
+template <> struct StreamCfg<-4> { static constexpr int LPR = 32, R = 1024; };
+template <> struct StreamCfg<-5> { static constexpr int LPR = 1, R = 512; };
+template <> struct StreamCfg<-6> { static constexpr int LPR = 2, R = 512; };
+
 // Columns per lane: FP32 blocks move 4 columns (16 bytes) per lane, which
 // keeps 4x more rows' gathers in flight than one column per lane; FP64 blocks
 // keep one column per lane (their bound is the FP64 FMA rate, not latency).
@@ -586,6 +739,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_rows(RowOpT<TB> op) {
   } else {
     rows_sliced<TB, TV, NV, S, NEG, EPI>(op);
   }
+}
+
+// The m = 1 stream kernel: window of R entries per warp in dynamic shared
+// memory (kWarps * stream_warp_bytes<TV, R>() bytes).  The 1024-entry window
+// takes 96 KB per block in FP64, so two blocks share an SM; the 512-entry
+// window 48 KB, four blocks.
+template <class TB, class TV, int LPR, int R, bool NEG, int EPI>
+__global__ void __launch_bounds__(kBlock, R <= 512 ? 4 : 2) k_rows_stream(RowOpT<TB> op) {
+  extern __shared__ __align__(16) unsigned char xamg_stream_smem[];
+  rows_stream<TB, TV, LPR, R, NEG, EPI>(op, xamg_stream_smem);
 }
 
 }  // namespace xamg

@@ -67,6 +67,14 @@ struct VParts {
   int nblk[5];
 };
 
+// Row splits at m = 1 (the `slices` argument of the row launchers at nv = 1):
+// the stream kernel with lanes per row / window entries per warp of 1 / 256
+// (kStreamShort), 1 / 512 (kStreamMid), 2 / 512 (kStreamPair), 1 / 1024
+// (kStreamLong), 4 / 1024 (kStreamQuad) or 32 / 1024 (kStreamWarp), or 16
+// lanes per row with the row's entries dealt round-robin (kSliced16).
+constexpr int kStreamShort = -1, kStreamLong = -2, kStreamQuad = -3, kStreamWarp = -4, kStreamMid = -5,
+              kStreamPair = -6, kSliced16 = 16;
+
 int device_sm_count();
 extern std::atomic<int64_t> g_launches;  // kernels launched by the library
 

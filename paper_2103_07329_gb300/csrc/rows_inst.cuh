@@ -19,24 +19,46 @@ using TBx = float;
 using TBx = double;
 #endif
 
+// S < 0: an m = 1 stream-kernel variant (StreamCfg<S>).
 template <class TV, int NV, int S, bool NEG, int EPI>
 int rows_t(const RowOpT<TBx> &op, cudaStream_t st) {
-  static int max_grid = 0;
-  if (!max_grid) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rows<TBx, TV, NV, S, NEG, EPI>, kBlock,
-                                                      0) != cudaSuccess ||
-        b < 1)
-      b = 1;
-    max_grid = std::min(kMaxGrid, b * device_sm_count());
+  if constexpr (S < 0) {
+    static_assert(NV == 1, "the stream kernel is the m = 1 split");
+    constexpr int LPR = StreamCfg<S>::LPR, R = StreamCfg<S>::R;
+    constexpr int smem = kWarps * stream_warp_bytes<TV, R>();
+    auto kern = k_rows_stream<TBx, TV, LPR, R, NEG, EPI>;
+    static int max_grid = 0;
+    if (!max_grid) {
+      int b = 0;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kBlock, smem) != cudaSuccess || b < 1)
+        b = 1;
+      max_grid = std::min(kMaxGrid, b * device_sm_count());
+    }
+    constexpr int rows_per_block = kWarps * (32 / LPR);
+    const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
+    kern<<<grid, kBlock, smem, st>>>(op);
+    g_launches++;
+    return cudaPeekAtLastError() == cudaSuccess ? grid : -1;
+  } else {
+    static int max_grid = 0;
+    if (!max_grid) {
+      int b = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_rows<TBx, TV, NV, S, NEG, EPI>, kBlock,
+                                                        0) != cudaSuccess ||
+          b < 1)
+        b = 1;
+      max_grid = std::min(kMaxGrid, b * device_sm_count());
+    }
+    constexpr int lanes_per_row = NV == 1 ? (S > 0 ? S : 1) : (NV / row_vec<TBx, NV>()) * S;
+    constexpr int rows_per_block = kWarps * (32 / lanes_per_row);
+    const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
+    k_rows<TBx, TV, NV, S, NEG, EPI><<<grid, kBlock, 0, st>>>(op);
+    g_launches++;
+    return cudaPeekAtLastError() == cudaSuccess ? grid : -1;
   }
-  constexpr int lanes_per_row = NV == 1 ? S : (NV / row_vec<TBx, NV>()) * S;
-  constexpr int rows_per_block = kWarps * (32 / lanes_per_row);
-  const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
-  k_rows<TBx, TV, NV, S, NEG, EPI><<<grid, kBlock, 0, st>>>(op);
-  g_launches++;
-  return cudaPeekAtLastError() == cudaSuccess ? grid : -1;
 }
 
 // The (sign, epilogue) pairs the solver uses.
@@ -70,14 +92,27 @@ int rows_e(const RowOpT<TBx> &op, bool neg, int epi, cudaStream_t st) {
   }
 }
 
-// m = 1 splits rows over 4 or 16 lanes; wider blocks give each lane VEC
-// columns and may split long rows over the whole warp (slices: one row per
-// warp).
+// m = 1 takes the stream kernel (short or long window) or 16 lanes per row;
+// wider blocks give each lane VEC columns and may split long rows over the
+// whole warp (slices: one row per warp).
 template <class TV>
 int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t st) {
 #if XAMG_NV == 1
-  if (slices >= 16) return rows_e<TV, 1, 16>(op, neg, epi, st);
-  return rows_e<TV, 1, 4>(op, neg, epi, st);
+  if constexpr (ValueLoad<TV>::idx16) {
+    // 16-bit indices are a wide-block format; m = 1 reads the 32-bit ones
+    (void)op; (void)slices; (void)neg; (void)epi; (void)st;
+    return -1;
+  } else {
+    switch (slices) {
+      case kStreamShort: return rows_e<TV, 1, kStreamShort>(op, neg, epi, st);
+      case kStreamLong: return rows_e<TV, 1, kStreamLong>(op, neg, epi, st);
+      case kStreamQuad: return rows_e<TV, 1, kStreamQuad>(op, neg, epi, st);
+      case kStreamWarp: return rows_e<TV, 1, kStreamWarp>(op, neg, epi, st);
+      case kStreamMid: return rows_e<TV, 1, kStreamMid>(op, neg, epi, st);
+      case kStreamPair: return rows_e<TV, 1, kStreamPair>(op, neg, epi, st);
+      default: return rows_e<TV, 1, kSliced16>(op, neg, epi, st);
+    }
+  }
 #else
   // long rows: every group of the warp takes a slice of one row (one row per
   // warp; with 32 FP64 columns a row already fills the warp)

@@ -127,7 +127,7 @@ def test_bf16_index_compression_paths(which):
 
 
 @pytest.mark.parametrize("prec", [B.PREC_FP64, B.PREC_FP32, B.PREC_BF16])
-@pytest.mark.parametrize("m", [2, 16])
+@pytest.mark.parametrize("m", [1, 2, 16])
 def test_autotuned_splits_keep_the_results(prec, m):
     # a fresh hierarchy: tuning stores its choices in the hierarchy
     A = P.diffusion7(24, P.lognormal_cells(24, 1.0, 1))
@@ -150,3 +150,26 @@ def test_autotuned_splits_keep_the_results(prec, m):
     assert np.all(rr <= 1e-8)
     with pytest.raises(B.XamgError):
         g.autotune(m, 7)
+
+
+@pytest.mark.parametrize("prec", [B.PREC_FP32, B.PREC_BF16])
+@pytest.mark.parametrize("cand", [0, 1, 2, 3, 4, 5, 6])
+def test_m1_splits_of_the_reduced_precision_vcycle(prec, cand):
+    # every product of the FP32 / bf16 V-cycle at m = 1 forced onto one split:
+    # the result moves only by the order of each row's FP32 sums
+    A = P.diffusion7(25, P.lognormal_cells(25, 1.0, 1))
+    g = B.Hierarchy(A)
+    Bm = P.rhs_uniform(A.n, 1, 0, m_draw=32)
+    z0 = torch.empty_like(dev(Bm))
+    g.vcycle_precond(prec, dev(Bm), z0)
+    for l in range(g.levels):
+        for which in (0, 1, 2):
+            if which == 0 or l + 1 < g.levels:
+                g.set_split(1, prec, l, which, cand)
+    z1 = torch.empty_like(z0)
+    g.vcycle_precond(prec, dev(Bm), z1)
+    assert colrel(z1.cpu().numpy(), z0.cpu().numpy()).max() <= 2e-5
+    X = torch.empty_like(z0)
+    s = g.solve(dev(Bm), X, tol=1e-8, maxit=100, precond=prec)
+    rr = np.linalg.norm(Bm - oracle.spmm(A, X.cpu().numpy()), axis=0) / np.linalg.norm(Bm, axis=0)
+    assert s.rc == 0 and np.all(rr <= 1e-8)

@@ -117,6 +117,45 @@ def test_spmm_27pt_long_rows():
         assert np.array_equal(Y.cpu().numpy(), oracle.spmm(pr.A, X))
 
 
+@pytest.mark.parametrize("cand", [0, 1, 2, 3, 4, 5, 6])
+def test_spmm_m1_every_split(cand):
+    # m = 1 under each row split (stream kernel with the short / long window,
+    # 16 lanes per row) on every level and operator: short rows, 27-point
+    # rows, the dense Galerkin levels, and a ragged last chunk (33^3 rows)
+    for name, N in (("p7", 33), ("p27", 20)):
+        pr = pair(name, N)
+        rng = np.random.default_rng(cand)
+        for l in range(pr.o.nlev):
+            lv = pr.o.level(l)
+            ops = [(0, csr_of(lv.A, lv.n), lv.n)]
+            if lv.P is not None:
+                nc = pr.o.level(l + 1).n
+                ops += [(1, P.CSR(lv.n, *lv.P), nc), (2, P.CSR(nc, *lv.R), lv.n)]
+            for which, M, ncols in ops:
+                pr.g.set_split(1, B.PREC_FP64, l, which, cand)
+                try:
+                    X = rng.integers(-50, 51, size=(ncols, 1)).astype(np.float64)
+                    Y = torch.empty((M.n, 1), dtype=torch.float64, device="cuda")
+                    pr.g.spmm(l, which, dev(X), Y)
+                    ref = oracle.spmm(M, X, ncols=ncols)
+                    if l == 0 and which == 0:
+                        assert np.array_equal(Y.cpu().numpy(), ref), (name, l, which)
+                    else:
+                        assert colrel(Y.cpu().numpy(), ref).max() <= RTOL, (name, l, which)
+                finally:
+                    pr.g.set_split(1, B.PREC_FP64, l, which, -1)
+
+
+def test_set_split_rejects_bad_arguments(cfg0):
+    g = cfg0.g
+    L = cfg0.o.nlev
+    for args in [(1, B.PREC_FP64, 0, 0, 7), (2, B.PREC_FP64, 0, 0, 2), (1, 9, 0, 0, 0),
+                 (1, B.PREC_FP64, L, 0, 0), (1, B.PREC_FP64, L - 1, 1, 0), (1, B.PREC_FP64, 0, 3, 0),
+                 (0, B.PREC_FP64, 0, 0, 0), (33, B.PREC_FP64, 0, 0, 0), (1, B.PREC_FP64, 0, 0, -2)]:
+        with pytest.raises(B.XamgError):
+            g.set_split(*args)
+
+
 # ---------------------------------------------------------------- smoother / coarse / V-cycle
 @pytest.mark.parametrize("m", [1, 4, 7])
 def test_chebyshev_pre_and_post(cfg0, m):
