@@ -46,6 +46,15 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 METHODS = {"pcg": 0, "bicgstab": 1, "bicgstab_reordered": 2, "bicgstab_pipelined": 3}
 
 
+def oracle_threads() -> int:
+    """Threads the oracle's OpenMP loops use: OMP_NUM_THREADS if set, else
+    every host core."""
+    try:
+        return max(1, int(os.environ["OMP_NUM_THREADS"]))
+    except (KeyError, ValueError):
+        return os.cpu_count()
+
+
 def oracle_solve(h, a, Bm):
     """The oracle's solve of the benchmark's method."""
     if a.method == "pcg":
@@ -357,7 +366,7 @@ def run_reference(a):
         solved += int(np.sum((r.status == 0) & (r.relres <= a.tol)))
     total = sum(times)
     value = solved / total
-    cores = os.cpu_count()
+    cores = oracle_threads()
     sample = f"{a.cpu_cols} of the {a.m} columns per step, full matrix, oracle setup untimed"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
@@ -562,7 +571,7 @@ def run_ours(a):
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         del Bd, X
         v, info = cpu_baseline(a, A)
-        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": v, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                "sample": f"{a.cpu_cols} of the {a.m} columns of the same workload solved to "
                          f"{a.tol:g} (oracle setup {info['t_setup']:.1f} s untimed, solve "
                          f"{info['t_solve']:.1f} s, iterations {info['iters']}); OpenMP over "
