@@ -341,8 +341,9 @@ int xamg_set_split(xamg_hier *h, int32_t m, int32_t precond, int32_t level, int3
  * of xamg_solve with method XAMG_PCG and precond XAMG_PREC_FP32 (flexible PCG
  * in FP64 around the FP32 V(1,1) Chebyshev preconditioner, FP64 coarsest
  * solve), and all systems advance in lockstep: every stage of the V-cycle
- * and of the Krylov loop is one launch for all of them, whatever their sizes,
- * column counts and hierarchy depths.  A system leaves the lockstep when all
+ * and of the Krylov loop is one launch for all of them (one per block width
+ * and row split present, for the row stages), whatever their sizes and
+ * hierarchy depths.  A system leaves the lockstep when all
  * its columns are confirmed converged.  The paper solves one system at a
  * time; this form serves many small systems, whose single-system launches are
  * latency-bound.

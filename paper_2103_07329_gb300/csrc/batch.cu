@@ -22,16 +22,16 @@
 
 namespace xamg {
 
-int launch_bk_g1(int kind, const void *params, const int *sel, int grid, cudaStream_t st);
-int launch_bk_g2(int kind, const void *params, const int *sel, int grid, cudaStream_t st);
-int launch_bk_g3(int kind, const void *params, const int *sel, int grid, cudaStream_t st);
+int launch_bk_g1(int kind, int nv, int opt, const void *params, const int *sel, int grid, cudaStream_t st);
+int launch_bk_g2(int kind, int nv, int opt, const void *params, const int *sel, int grid, cudaStream_t st);
+int launch_bk_g3(int kind, int nv, int opt, const void *params, const int *sel, int grid, cudaStream_t st);
 
-int launch_bk(int kind, const void *params, const int *sel, int grid, cudaStream_t st) {
-  int r = launch_bk_g1(kind, params, sel, grid, st);
+int launch_bk(int kind, int nv, int opt, const void *params, const int *sel, int grid, cudaStream_t st) {
+  int r = launch_bk_g1(kind, nv, opt, params, sel, grid, st);
   if (r != -2) return r;
-  r = launch_bk_g2(kind, params, sel, grid, st);
+  r = launch_bk_g2(kind, nv, opt, params, sel, grid, st);
   if (r != -2) return r;
-  return launch_bk_g3(kind, params, sel, grid, st);
+  return launch_bk_g3(kind, nv, opt, params, sel, grid, st);
 }
 
 // kernel of each stage
@@ -49,7 +49,7 @@ int stage_kind(int st) {
   }
 }
 
-int bstage_max_grid(int st) { return launch_bk(stage_kind(st), nullptr, nullptr, 0, nullptr); }
+int bstage_max_grid(int st) { return launch_bk(stage_kind(st), 0, 0, nullptr, nullptr, 0, nullptr); }
 
 int bstage_rows_per_block(int st, int nv, int opt) {
   const int kind = stage_kind(st);
@@ -385,41 +385,75 @@ bool stage_op_d(xamg_batch *b, int st, int s, RowOp &o, int &opt) {
   return true;
 }
 
-// One launch (per kStageOps systems) of stage st on level l for the systems
-// of selection mask `sel` to which the stage applies; `only` >= 0 restricts
-// the list to that system (autotuner).
+// Stage st on level l for the systems of selection mask `sel` to which the
+// stage applies: one launch per (block width, row split) present, and per
+// kStageOps systems of that pair; `only` >= 0 restricts the list to that
+// system (autotuner).  With `count` set, nothing is launched and *count
+// receives the number of launches.
 template <class TB>
-int stage_t(xamg_batch *b, int st, int sel, int l, int grid, int only) {
+int stage_t(xamg_batch *b, int st, int sel, int l, int grid, int only, int *count) {
   StageParams<TB> &P = *reinterpret_cast<StageParams<TB> *>(b->params.data());
   const int kind = stage_kind(st);
-  P.count = 0;
-  auto flush = [&]() -> int {
-    if (!P.count) return XAMG_OK;
-    const int r = launch_bk(kind, &P, sel_dev(b, sel), grid, b->st);
-    P.count = 0;
-    return r < 0 ? XAMG_ERR_CUDA : XAMG_OK;
-  };
-  for (int s = 0; s < b->ns; ++s) {
-    if (only >= 0 && s != only) continue;
-    RowOpT<TB> o;
-    int opt = 0;
-    bool on;
-    if constexpr (sizeof(TB) == 8) on = stage_op_d(b, st, s, o, opt);
-    else on = stage_op_f(b, st, s, l, o, opt);
-    if (!on) continue;
-    const int i = P.count++;
-    P.sys[i] = s;
-    P.nv[i] = (unsigned char)b->sys_h[s].nv;
-    P.opt[i] = (unsigned char)opt;
-    P.op[i] = o;
-    if (P.count == kStageOps) BRET(flush());
+  // the kernels without a wide split run every entry narrow
+  const bool has_wide = kind != BK_F_XLAST_DOT2 && kind != BK_D_YDOT && kind != BK_D_YDOT2;
+  if (count) *count = 0;
+  for (int nv = 1; nv <= XAMG_MAX_RHS; nv <<= 1) {
+    for (int split = 0; split < (has_wide ? 2 : 1); ++split) {
+      P.count = 0;
+      auto flush = [&]() -> int {
+        if (!P.count) return XAMG_OK;
+        if (count) {
+          ++*count;
+          P.count = 0;
+          return XAMG_OK;
+        }
+        const int r = launch_bk(kind, nv, split, &P, sel_dev(b, sel), grid, b->st);
+        P.count = 0;
+        return r < 0 ? XAMG_ERR_CUDA : XAMG_OK;
+      };
+      for (int s = 0; s < b->ns; ++s) {
+        if ((only >= 0 && s != only) || b->sys_h[s].nv != nv) continue;
+        RowOpT<TB> o;
+        int opt = 0;
+        bool on;
+        if constexpr (sizeof(TB) == 8) on = stage_op_d(b, st, s, o, opt);
+        else on = stage_op_f(b, st, s, l, o, opt);
+        if (!on || (has_wide && (opt != 0) != (split != 0))) continue;
+        const int i = P.count++;
+        P.sys[i] = s;
+        P.op[i] = o;
+        if (P.count == kStageOps) BRET(flush());
+      }
+      BRET(flush());
+    }
   }
-  return flush();
+  return XAMG_OK;
 }
 
-int stage(xamg_batch *b, int st, int sel, int l, int grid, int only = -1) {
-  if (st == BS_AP || st == BS_TRUERES) return stage_t<double>(b, st, sel, l, grid, only);
-  return stage_t<float>(b, st, sel, l, grid, only);
+int stage(xamg_batch *b, int st, int sel, int l, int grid, int only = -1, int *count = nullptr) {
+  if (st == BS_AP || st == BS_TRUERES) return stage_t<double>(b, st, sel, l, grid, only, count);
+  return stage_t<float>(b, st, sel, l, grid, only, count);
+}
+
+// Launches of one steady iteration (iteration_b) for every system together.
+int count_iteration_launches(xamg_batch *b) {
+  int total = 0, c = 0;
+  auto add = [&](int st, int l) {
+    stage(b, st, 0, l, 1, -1, &c);
+    total += c;
+  };
+  for (int l = 0; l + 1 < b->Lmax; ++l) {
+    add(BS_PRE1, l);
+    add(BS_PRE2, l);
+    add(BS_RESTRICT, l);
+    add(BS_RESTRICT_C, l);
+    add(BS_PROLONG, l);
+    add(BS_POST1, l);
+    add(l == 0 ? BS_POST2_DOT2 : BS_POST2, l);
+  }
+  add(BS_AP, 0);
+  // coarsest solve, flexible beta, p update, alpha, x/r update, convergence test
+  return total + 6;
 }
 
 // the FP32 V(1,1) cycle of every system selected by mask `sel`: on entry each
@@ -681,7 +715,7 @@ int xamg_batch_create(xamg_hier *const *h, const int32_t *m, int32_t count, cons
     const int pr1 = std::max(std::max(b->g_elem, b->g_ap), std::max(b->g_post0, b->g_tr));
     if (pr1 > pr0) return fail(XAMG_ERR_CUDA);
   }
-  b->launches_per_iter = 7 * (b->Lmax - 1) + 1 + 6;
+  b->launches_per_iter = count_iteration_launches(b);
   *out = b;
   return XAMG_OK;
 }

@@ -1,6 +1,7 @@
 // batch.h -- internal interface of the batched solve (many independent
 // systems of uneven size and column count advanced in lockstep, one launch per
-// V-cycle stage for all of them).  Internal to the library.
+// V-cycle stage for all of them of a block width and row split).  Internal to
+// the library.
 #pragma once
 #include <cuda_runtime.h>
 

@@ -6,9 +6,9 @@
 // Blocks walk the list in order; within a system the warps take the rows in
 // the single-system grid-stride order (rows_vec / rows_sliced of
 // kernels.cuh), so each system's products and partial dot sums are computed
-// exactly as a single-system launch with the same grid computes them.  The
-// column count NV and the row split of each entry are runtime values: a
-// switch selects the compile-time body.  Included by batch.cu and
+// exactly as a single-system launch with the same grid computes them.  A
+// launch serves the systems of one block width NV and one row split, both
+// compile-time parameters of the kernel.  Included by batch.cu and
 // batch_stage*.cu (one group of kernels per unit).
 #pragma once
 #include <algorithm>
@@ -42,29 +42,6 @@ __host__ __device__ constexpr int rows_per_block(int opt) {
   return kWarps * (32 / ((NV == 1 ? 1 : NV / row_vec<TB, NV>()) * (opt ? wide_s<TB, NV>() : narrow_s<TB, NV>())));
 }
 
-// WIDE: whether the wide split is compiled for this kernel (the kernels that
-// only act on the fine level, a short-row stencil, keep the narrow one).
-template <class TB, class TV, bool NEG, int EPI, bool WIDE>
-__device__ __forceinline__ void row_dispatch(int nv, int opt, const RowOpT<TB> &op) {
-#define XAMG_RD(V)                                                       \
-  case V:                                                                \
-    if (WIDE && opt)                                                     \
-      row_body<TB, TV, V, wide_s<TB, V>(), NEG, EPI>(op);                \
-    else                                                                 \
-      row_body<TB, TV, V, narrow_s<TB, V>(), NEG, EPI>(op);              \
-    break;
-  switch (nv) {
-    XAMG_RD(1)
-    XAMG_RD(2)
-    XAMG_RD(4)
-    XAMG_RD(8)
-    XAMG_RD(16)
-    XAMG_RD(32)
-    default: break;
-  }
-#undef XAMG_RD
-}
-
 // Entries per launch: the parameter block stays below the 32 KB limit of
 // kernel parameters.
 constexpr int kStageOps = 96;
@@ -73,8 +50,6 @@ template <class TB>
 struct StageParams {
   int count;
   int sys[kStageOps];              // system index (selection mask)
-  unsigned char nv[kStageOps];     // block width
-  unsigned char opt[kStageOps];    // row split
   RowOpT<TB> op[kStageOps];
 };
 
@@ -104,34 +79,81 @@ template <> struct KD<BK_F_XLAST_DOT2> { using TB = float; static constexpr bool
 template <> struct KD<BK_D_YDOT> { using TB = double; static constexpr bool NEG = false, WIDE = false; static constexpr int EPI = EPI_Y_DOT; };
 template <> struct KD<BK_D_YDOT2> { using TB = double; static constexpr bool NEG = true, WIDE = false; static constexpr int EPI = EPI_Y_DOT2; };
 
-template <int K>
+// One launch: every listed system of block width NV under row split WIDE
+// (both compile-time, so that each kernel holds one body and its registers).
+template <int K, int NV, bool WIDE>
 __global__ void __launch_bounds__(kBlock, 4) k_bstage(const __grid_constant__ StageParams<typename KD<K>::TB> P,
                                                       const int *__restrict__ sel) {
   using D = KD<K>;
   using TB = typename D::TB;
+  constexpr int S = WIDE ? wide_s<TB, NV>() : narrow_s<TB, NV>();
   for (int i = 0; i < P.count; ++i) {
     if (!sel[P.sys[i]]) continue;
-    row_dispatch<TB, TB, D::NEG, D::EPI, D::WIDE>(P.nv[i], P.opt[i], P.op[i]);
+    row_body<TB, TB, NV, S, D::NEG, D::EPI>(P.op[i]);
     // the dot epilogues reuse the block's shared reduction buffers
     if constexpr (epi_has_dot<D::EPI>()) __syncthreads();
   }
 }
 
-// Launches kernel K with the parameter block `params` (a StageParams of the
-// kernel's block scalar); grid <= 0 returns the persistent grid bound.
-template <int K>
-int bk_launch_t(const void *params, const int *sel, int grid, cudaStream_t st) {
+template <int K, int NV, bool WIDE>
+int bk_launch_nv(const void *params, const int *sel, int grid, cudaStream_t st) {
   static int max_grid = 0;
   if (!max_grid) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bstage<K>, kBlock, 0) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bstage<K, NV, WIDE>, kBlock, 0) != cudaSuccess ||
+        b < 1)
+      b = 1;
     max_grid = std::min(kMaxGrid, b * device_sm_count());
   }
   if (grid <= 0) return max_grid;
   grid = std::min(grid, max_grid);
-  k_bstage<K><<<grid, kBlock, 0, st>>>(*static_cast<const StageParams<typename KD<K>::TB> *>(params), sel);
+  k_bstage<K, NV, WIDE><<<grid, kBlock, 0, st>>>(*static_cast<const StageParams<typename KD<K>::TB> *>(params),
+                                                  sel);
   g_launches++;
   return cudaPeekAtLastError() == cudaSuccess ? grid : -1;
+}
+
+template <int K, int NV>
+int bk_launch_split(int opt, const void *params, const int *sel, int grid, cudaStream_t st) {
+  if constexpr (KD<K>::WIDE) {
+    if (opt) return bk_launch_nv<K, NV, true>(params, sel, grid, st);
+  }
+  return bk_launch_nv<K, NV, false>(params, sel, grid, st);
+}
+
+template <int K, int NV>
+int bk_bound(int g) {
+  g = std::min(g, bk_launch_nv<K, NV, false>(nullptr, nullptr, 0, nullptr));
+  if constexpr (KD<K>::WIDE) g = std::min(g, bk_launch_nv<K, NV, true>(nullptr, nullptr, 0, nullptr));
+  return g;
+}
+
+// Launches kernel K for block width nv and row split opt (0 narrow, 1 wide;
+// kernels without the wide split take the narrow one) with the parameter
+// block `params` (a StageParams of the kernel's block scalar).  grid <= 0
+// returns the persistent grid bound of that kernel; nv = 0 returns the
+// smallest bound over every width and split (the dot stages' partial arrays
+// have that many rows whatever the width).
+template <int K>
+int bk_launch_t(int nv, int opt, const void *params, const int *sel, int grid, cudaStream_t st) {
+  switch (nv) {
+    case 1: return bk_launch_split<K, 1>(opt, params, sel, grid, st);
+    case 2: return bk_launch_split<K, 2>(opt, params, sel, grid, st);
+    case 4: return bk_launch_split<K, 4>(opt, params, sel, grid, st);
+    case 8: return bk_launch_split<K, 8>(opt, params, sel, grid, st);
+    case 16: return bk_launch_split<K, 16>(opt, params, sel, grid, st);
+    case 32: return bk_launch_split<K, 32>(opt, params, sel, grid, st);
+    case 0: {
+      int g = kMaxGrid;
+      g = bk_bound<K, 1>(g);
+      g = bk_bound<K, 2>(g);
+      g = bk_bound<K, 4>(g);
+      g = bk_bound<K, 8>(g);
+      g = bk_bound<K, 16>(g);
+      return bk_bound<K, 32>(g);
+    }
+    default: return -1;
+  }
 }
 
 }  // namespace xamg

@@ -4,11 +4,12 @@
 
 namespace xamg {
 
-int launch_bk_g2(int kind, const void *params, const int *sel, int grid, cudaStream_t st) {
+int launch_bk_g2(int kind, int nv, int opt, const void *params, const int *sel, int grid,
+                 cudaStream_t st) {
   switch (kind) {
-    case BK_F_Y_POS: return bk_launch_t<BK_F_Y_POS>(params, sel, grid, st);
-    case BK_F_D0_NEG: return bk_launch_t<BK_F_D0_NEG>(params, sel, grid, st);
-    case BK_F_XLAST: return bk_launch_t<BK_F_XLAST>(params, sel, grid, st);
+    case BK_F_Y_POS: return bk_launch_t<BK_F_Y_POS>(nv, opt, params, sel, grid, st);
+    case BK_F_D0_NEG: return bk_launch_t<BK_F_D0_NEG>(nv, opt, params, sel, grid, st);
+    case BK_F_XLAST: return bk_launch_t<BK_F_XLAST>(nv, opt, params, sel, grid, st);
     default: return -2;
   }
 }
