@@ -228,8 +228,11 @@ int xamg_workspace_bytes(const xamg_hier *h, int32_t m, int32_t method, int32_t 
 int xamg_solve(xamg_hier *h, const double *B, double *X, int32_t m, double tol, int32_t maxit,
                const xamg_solve_opts *opts, xamg_stats *stats);
 
-/* As xamg_solve with B and X in HOST memory: the call copies B to the device,
- * solves, and copies X back, all on opts->stream. */
+/* As xamg_solve with B and X in HOST memory, all on opts->stream.  When both
+ * are page-locked memory registered with CUDA (cudaHostAlloc,
+ * cudaHostRegister, a pinned torch tensor), the solve's first pass reads B
+ * and its last pass writes X directly over the host link; otherwise the call
+ * copies B to a device buffer, solves, and copies X back. */
 int xamg_solve_host(xamg_hier *h, const double *B, double *X, int32_t m, double tol,
                     int32_t maxit, const xamg_solve_opts *opts, xamg_stats *stats);
 

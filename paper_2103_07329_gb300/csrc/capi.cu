@@ -1502,10 +1502,27 @@ int xamg_solve(xamg_hier *h, const double *B, double *X, int32_t m, double tol, 
   return solve_impl(h, B, X, m, tol, maxit, opts, stats);
 }
 
+// The device address of host memory that the GPU can reach directly
+// (page-locked memory registered with CUDA), else nullptr.
+static const void *device_view(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the query's error
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int xamg_solve_host(xamg_hier *h, const double *B, double *X, int32_t m, double tol, int32_t maxit,
                     const xamg_solve_opts *opts, xamg_stats *stats) {
   if (!h || !h->on_device || !B || !X || m < 1 || m > XAMG_MAX_RHS) return XAMG_ERR_INVALID_ARG;
   XCK(cudaSetDevice(h->device));
+  // page-locked buffers: the solve's first pass reads B, and its last pass
+  // writes X, over the host link, with no staging copies (the solve reads B
+  // once and writes X once; it synchronizes the stream before returning)
+  const double *dB = static_cast<const double *>(device_view(B));
+  double *dX = static_cast<double *>(const_cast<void *>(device_view(X)));
+  if (dB && dX) return solve_impl(h, dB, dX, m, tol, maxit, opts, stats);
   const size_t bytes = (size_t)h->host.lv[0].A.n * m * sizeof(double);
   if (h->hb_bytes < 2 * align256(bytes)) {
     if (h->hb) cudaFree(h->hb);

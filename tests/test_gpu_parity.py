@@ -301,6 +301,30 @@ def test_host_buffers_match_device(cfg0):
     assert np.array_equal(sh.iters, sd.iters)
 
 
+@pytest.mark.parametrize("method", [B.PCG, B.BICGSTAB])
+def test_pinned_host_buffers_match_device(cfg0, method):
+    # page-locked B and X: the solve reads and writes them directly (no
+    # staging copies); the kernels are the same, so the bits are too, with
+    # and without a starting guess; mixing a pinned and a pageable buffer
+    # takes the staged path with the same result
+    Bm = P.rhs_uniform(cfg0.A.n, 4, 7)
+    Xd = torch.empty_like(dev(Bm))
+    sd = cfg0.g.solve(dev(Bm), Xd, method=method)
+    Bp = torch.from_numpy(Bm).pin_memory()
+    Xp = torch.empty_like(Bp).pin_memory()
+    sp = cfg0.g.solve_host(Bp.numpy(), Xp.numpy(), method=method)
+    assert np.array_equal(Xp.numpy(), Xd.cpu().numpy()) and np.array_equal(sp.iters, sd.iters)
+    X0 = 0.5 * Xd.cpu().numpy()
+    Xd0 = dev(X0)
+    sd0 = cfg0.g.solve(dev(Bm), Xd0, method=method, x0_given=True)
+    Xp.copy_(torch.from_numpy(X0))
+    sp0 = cfg0.g.solve_host(Bp.numpy(), Xp.numpy(), method=method, x0_given=True)
+    assert np.array_equal(Xp.numpy(), Xd0.cpu().numpy()) and np.array_equal(sp0.iters, sd0.iters)
+    Xh = np.empty_like(Bm)
+    cfg0.g.solve_host(Bp.numpy(), Xh, method=method)
+    assert np.array_equal(Xh, Xd.cpu().numpy())
+
+
 def test_caller_workspace(cfg0):
     Bm = dev(P.rhs_uniform(cfg0.A.n, 4, 6))
     nb = cfg0.g.workspace_bytes(4, B.PCG)
