@@ -336,6 +336,18 @@ int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_
 int xamg_set_split(xamg_hier *h, int32_t m, int32_t precond, int32_t level, int32_t which,
                    int32_t candidate);
 
+/* CUDA graphs of the steady PCG iteration (on by default).  With graphs on,
+ * the PCG solves (XAMG_PCG, every precond) replay the fixed launch sequence
+ * between two host reads of an iteration -- preconditioner, beta, direction
+ * update, A p, alpha, x/r update, convergence test -- as one captured graph,
+ * cached per (block width, precond, workspace, tol) on the hierarchy and
+ * dropped when the workspace or a row split changes.  Results are bitwise
+ * those of the uncaptured launches; small systems, whose solves are bound by
+ * launch latency, gain the most.  Timing (xamg_timing_enable) bypasses them.
+ * enable = 0 turns them off and frees the cache.  No counterpart in the
+ * paper. */
+int xamg_set_graphs(xamg_hier *h, int32_t enable);
+
 /* ---- batched solve of many independent systems ----
  *
  * Solves count independent systems A_s X_s = B_s (A_s n_s x n_s with its own

@@ -47,7 +47,7 @@ EXPORTS = [
     "xamg_net_param_count", "xamg_net_create", "xamg_net_destroy", "xamg_net_set_params",
     "xamg_net_get_params", "xamg_net_forward", "xamg_net_loss_grad", "xamg_net_train_step",
     "xamg_net_predict_x0", "xamg_conv3d_bf16", "xamg_conv3d_bf16_wgrad",
-    "xamg_autotune", "xamg_set_split", "xamg_batch_opts_default", "xamg_batch_create", "xamg_batch_destroy", "xamg_batch_info",
+    "xamg_autotune", "xamg_set_split", "xamg_set_graphs", "xamg_batch_opts_default", "xamg_batch_create", "xamg_batch_destroy", "xamg_batch_info",
     "xamg_batch_solve",
 ]
 
@@ -152,6 +152,7 @@ def _load():
         "xamg_conv3d_bf16_wgrad": ([vp, vp, vp, vp, vp, i32, i32, i32, i32, vp], C.c_int),
         "xamg_autotune": ([vp, i32, i32, vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "xamg_set_split": ([vp, i32, i32, i32, i32, i32], C.c_int),
+        "xamg_set_graphs": ([vp, i32], C.c_int),
         "xamg_batch_opts_default": ([C.POINTER(BatchOptsT)], None),
         "xamg_batch_create": ([vp, vp, i32, C.POINTER(BatchOptsT), C.POINTER(vp)], C.c_int),
         "xamg_batch_destroy": ([vp], C.c_int),
@@ -379,6 +380,10 @@ class Hierarchy:
         """xamg_set_split: force tuning candidate `candidate` (-1: the default
         rule) for operator `which` of `level` on pad(m)-column blocks."""
         _check(_load().xamg_set_split(self._h, m, precond, level, which, candidate), "xamg_set_split")
+
+    def set_graphs(self, on: bool = True):
+        """xamg_set_graphs: CUDA graphs of the steady PCG iteration on or off."""
+        _check(_load().xamg_set_graphs(self._h, 1 if on else 0), "xamg_set_graphs")
 
     def timing_enable(self, on: bool = True):
         _check(_load().xamg_timing_enable(self._h, 1 if on else 0), "xamg_timing_enable")

@@ -95,6 +95,17 @@ template <> struct Blocks<float> {
 
 }  // namespace
 
+// One captured steady iteration: the kernels of V-cycle, beta, direction
+// update, A p, alpha, x/r update and convergence test, with the arguments of
+// this key (block width, preconditioner precision, workspace, tolerance).
+struct GraphRec {
+  int nv = 0, prec = 0;
+  const void *ws = nullptr;
+  double tol = 0.0;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;  // kernels per replay
+};
+
 struct xamg_hier {
   HostHier host;
   xamg_amg_params prm{};
@@ -116,6 +127,11 @@ struct xamg_hier {
   std::vector<TimerRec> pending;
   std::vector<cudaEvent_t> event_pool;
   std::vector<TimeAcc> tacc;  // [level * 3 + which]
+  // CUDA graphs of the steady PCG iteration (capture stream, cache); cleared
+  // whenever what they captured may change (workspace, row splits)
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<GraphRec> graphs;
 };
 
 namespace {
@@ -291,7 +307,16 @@ int upload_lowp(xamg_hier *h) {
   return XAMG_OK;
 }
 
+void clear_graphs(xamg_hier *h) {
+  for (auto &g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
+
 void free_device(xamg_hier *h) {
+  clear_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  h->cap_stream = nullptr;
   for (void *p : h->owned) cudaFree(p);
   h->owned.clear();
   if (h->ws) cudaFree(h->ws);
@@ -406,6 +431,7 @@ int ensure_workspace(xamg_hier *h, int nv, int method, int prec, const xamg_solv
     base = (char *)o->workspace;
   } else {
     if (h->ws_bytes < need) {
+      clear_graphs(h);  // they captured addresses in the old workspace
       if (h->ws) cudaFree(h->ws);
       h->ws = nullptr;
       h->ws_bytes = 0;
@@ -760,6 +786,55 @@ struct SolveCtx {
 
 int sync_read(cudaStream_t st);
 
+// The steady part of one PCG iteration: `body(stream)` issues the previous
+// iteration's preconditioner, beta and direction update, then this
+// iteration's A p, alpha, x/r update and convergence test, with the scalar
+// steps reading the iteration number from the device counter.  With graphs
+// on (and timing off) the body is captured once per key on a private stream
+// and replayed on the solve's stream, one launch for the whole sequence.
+template <class F>
+int steady(SolveCtx &c, F &&body) {
+  xamg_hier *h = c.h;
+  if (!h->use_graphs || h->timing) return body(c.st);
+  GraphRec *g = nullptr;
+  for (auto &r : h->graphs)
+    if (r.nv == c.nv && r.prec == c.prec && r.ws == (const void *)c.W.cs && r.tol == c.tol) g = &r;
+  if (!g) {
+    if (!h->cap_stream) XCK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const int64_t before = g_launches.load();
+    XCK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = body(h->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+    const int64_t launched = g_launches.load() - before;
+    g_launches -= launched;  // counted per replay below
+    if (rc != XAMG_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc != XAMG_OK ? rc : XAMG_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return XAMG_ERR_CUDA;
+    if (h->graphs.size() >= 16) {  // bounded cache: drop the oldest
+      cudaGraphExecDestroy(h->graphs.front().exec);
+      h->graphs.erase(h->graphs.begin());
+    }
+    GraphRec r;
+    r.nv = c.nv;
+    r.prec = c.prec;
+    r.ws = c.W.cs;
+    r.tol = c.tol;
+    r.exec = exec;
+    r.launches = launched;
+    h->graphs.push_back(r);
+    g = &h->graphs.back();
+  }
+  XCK(cudaGraphLaunch(g->exec, c.st));
+  g_launches += g->launches;
+  return XAMG_OK;
+}
+
 // Warm start: columns whose initial residual already meets the tolerance start
 // frozen (state 1); the host reads how many stay active.
 int initial_check(SolveCtx &c) {
@@ -880,14 +955,39 @@ int solve_pcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
     launch_scalar(nv, SM_PCG_BETA, W.cs, W.part[1], nullptr, g, c.tol, 0, fl, st);
     launch_pcg_p(nv, n, W.P, W.Z, W.cs, ge, st);
   }
-  for (int k = 1; k <= c.maxit && h->flags_h->active > 0; ++k) {
-    c.iterations = k;
+  // A p (with p.q), alpha, x/r update (with |r|^2), convergence test; kk < 0:
+  // the iteration number comes from the device counter
+  auto head = [&](cudaStream_t s, int kk) -> int {
     RowOp o = blank<double>();
     o.src = W.P; o.y = W.Q; o.dot_u = W.P; o.partials = W.part[0];
-    if ((g = rows<double>(h, 0, 0, XAMG_PREC_FP64, o, nv, false, EPI_Y_DOT, st)) < 0) return XAMG_ERR_CUDA;
-    launch_scalar(nv, SM_PCG_ALPHA, W.cs, W.part[0], nullptr, g, c.tol, k, fl, st);
-    launch_pcg_xr(nv, n, W.X, W.R, W.P, W.Q, W.cs, w0, W.Z, W.part[1], ge, st);
-    launch_scalar(nv, SM_PCG_CONV, W.cs, W.part[1], nullptr, ge, c.tol, k, fl, st);
+    int gg;
+    if ((gg = rows<double>(h, 0, 0, XAMG_PREC_FP64, o, nv, false, EPI_Y_DOT, s)) < 0) return XAMG_ERR_CUDA;
+    launch_scalar(nv, SM_PCG_ALPHA, W.cs, W.part[0], nullptr, gg, c.tol, kk, fl, s);
+    launch_pcg_xr(nv, n, W.X, W.R, W.P, W.Q, W.cs, w0, W.Z, W.part[1], ge, s);
+    launch_scalar(nv, SM_PCG_CONV, W.cs, W.part[1], nullptr, ge, c.tol, kk, fl, s);
+    return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
+  };
+  // preconditioner with r.z, beta, direction update
+  auto tail = [&](cudaStream_t s) -> int {
+    int gg;
+    const int r = vcycle<double>(h, W, XAMG_PREC_FP64, 0, W.R, W.Z, s, dot1(W.R, W.part[1], &gg));
+    if (r != XAMG_OK) return r;
+    launch_scalar(nv, SM_PCG_BETA, W.cs, W.part[1], nullptr, gg, c.tol, -1, fl, s);
+    launch_pcg_p(nv, n, W.P, W.Z, W.cs, ge, s);
+    return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
+  };
+  for (int k = 1; k <= c.maxit && h->flags_h->active > 0; ++k) {
+    c.iterations = k;
+    if (k == 1) {
+      rc = head(st, k);
+    } else {
+      c.vcycles++;
+      rc = steady(c, [&](cudaStream_t s) {
+        const int r = tail(s);
+        return r != XAMG_OK ? r : head(s, -1);
+      });
+    }
+    if (rc != XAMG_OK) return rc;
     if ((rc = sync_read(st)) != XAMG_OK) return rc;
     if (h->flags_h->active == 0) {
       if ((g = true_residual(h, W, W.Q, W.part[2], st)) < 0) return XAMG_ERR_CUDA;
@@ -900,11 +1000,6 @@ int solve_pcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
       launch_copy_cols(nv, n, W.R, W.Q, W.cs, ge, st);
       if (w0) launch_scale_rows(nv, n, w0, W.R, W.Z, ge, st);
     }
-    if ((rc = vcycle<double>(h, W, XAMG_PREC_FP64, 0, W.R, W.Z, st, dot1(W.R, W.part[1], &g))) != XAMG_OK)
-      return rc;
-    c.vcycles++;
-    launch_scalar(nv, SM_PCG_BETA, W.cs, W.part[1], nullptr, g, c.tol, k, fl, st);
-    launch_pcg_p(nv, n, W.P, W.Z, W.cs, ge, st);
   }
   return finish(c, Xuser, stats);
 }
@@ -941,14 +1036,44 @@ int solve_fpcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
     launch_scalar(nv, SM_PCG_BETA, W.cs, W.part[1], nullptr, g, c.tol, 0, fl, st);
     launch_fpcg_p(nv, n, W.P, W.Z32, W.cs, ge, st);
   }
-  for (int k = 1; k <= c.maxit && h->flags_h->active > 0; ++k) {
-    c.iterations = k;
+  // A p (with p.q), alpha, x/r update (with |r|^2 and the FP32 copy of r),
+  // convergence test; kk < 0: the iteration number comes from the device
+  // counter
+  auto head = [&](cudaStream_t s, int kk) -> int {
     RowOp o = blank<double>();
     o.src = W.P; o.y = W.Q; o.dot_u = W.P; o.partials = W.part[0];
-    if ((g = rows<double>(h, 0, 0, XAMG_PREC_FP64, o, nv, false, EPI_Y_DOT, st)) < 0) return XAMG_ERR_CUDA;
-    launch_scalar(nv, SM_PCG_ALPHA, W.cs, W.part[0], nullptr, g, c.tol, k, fl, st);
-    launch_fpcg_xr(nv, n, W.X, W.R, W.P, W.Q, W.cs, w0f, W.R32, W.Z32, W.part[1], ge, st);
-    launch_scalar(nv, SM_PCG_CONV, W.cs, W.part[1], nullptr, ge, c.tol, k, fl, st);
+    int gg;
+    if ((gg = rows<double>(h, 0, 0, XAMG_PREC_FP64, o, nv, false, EPI_Y_DOT, s)) < 0) return XAMG_ERR_CUDA;
+    launch_scalar(nv, SM_PCG_ALPHA, W.cs, W.part[0], nullptr, gg, c.tol, kk, fl, s);
+    launch_fpcg_xr(nv, n, W.X, W.R, W.P, W.Q, W.cs, w0f, W.R32, W.Z32, W.part[1], ge, s);
+    launch_scalar(nv, SM_PCG_CONV, W.cs, W.part[1], nullptr, ge, c.tol, kk, fl, s);
+    return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
+  };
+  // reduced-precision preconditioner with z.r and z.q, flexible beta,
+  // direction update
+  auto tail = [&](cudaStream_t s) -> int {
+    int gg;
+    Dots d = dot1(W.R, W.part[1], &gg);
+    d.u2 = W.Q;
+    d.part2 = W.part[2];
+    const int r = vcycle<float>(h, W, prec, 0, W.R32, W.Z32, s, d);
+    if (r != XAMG_OK) return r;
+    launch_scalar(nv, SM_FPCG_BETA, W.cs, W.part[1], W.part[2], gg, c.tol, -1, fl, s);
+    launch_fpcg_p(nv, n, W.P, W.Z32, W.cs, ge, s);
+    return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
+  };
+  for (int k = 1; k <= c.maxit && h->flags_h->active > 0; ++k) {
+    c.iterations = k;
+    if (k == 1) {
+      rc = head(st, k);
+    } else {
+      c.vcycles++;
+      rc = steady(c, [&](cudaStream_t s) {
+        const int r = tail(s);
+        return r != XAMG_OK ? r : head(s, -1);
+      });
+    }
+    if (rc != XAMG_OK) return rc;
     if ((rc = sync_read(st)) != XAMG_OK) return rc;
     if (h->flags_h->active == 0) {
       if ((g = true_residual(h, W, W.Q, W.part[2], st)) < 0) return XAMG_ERR_CUDA;
@@ -961,13 +1086,6 @@ int solve_fpcg(SolveCtx &c, const double *B, double *Xuser, xamg_stats *stats) {
       launch_copy_cols(nv, n, W.R, W.Q, W.cs, ge, st);
       launch_to_f32(nv, n, W.R, W.R32, w0f, W.Z32, ge, st);
     }
-    Dots d = dot1(W.R, W.part[1], &g);
-    d.u2 = W.Q;
-    d.part2 = W.part[2];
-    if ((rc = vcycle<float>(h, W, prec, 0, W.R32, W.Z32, st, d)) != XAMG_OK) return rc;
-    c.vcycles++;
-    launch_scalar(nv, SM_FPCG_BETA, W.cs, W.part[1], W.part[2], g, c.tol, k, fl, st);
-    launch_fpcg_p(nv, n, W.P, W.Z32, W.cs, ge, st);
   }
   return finish(c, Xuser, stats);
 }
@@ -1700,6 +1818,7 @@ int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_
   const int pc = precond == XAMG_PREC_BF16 ? 1 : precond == XAMG_PREC_FP32 ? 0 : 2;
   const bool timing = h->timing;
   h->timing = false;
+  clear_graphs(h);  // captured iterations use the splits about to change
   cudaEvent_t e0, e1;
   XCK(cudaEventCreate(&e0));
   XCK(cudaEventCreate(&e1));
@@ -1757,6 +1876,15 @@ int xamg_set_split(xamg_hier *h, int32_t m, int32_t precond, int32_t level, int3
   while ((1 << lg) < nv) ++lg;
   const int pc = precond == XAMG_PREC_BF16 ? 1 : precond == XAMG_PREC_FP32 ? 0 : 2;
   h->lv[level].split[pc][which][lg] = (signed char)candidate;
+  clear_graphs(h);  // captured iterations used the previous split
+  return XAMG_OK;
+}
+
+int xamg_set_graphs(xamg_hier *h, int32_t enable) {
+  if (!h || !h->on_device) return XAMG_ERR_INVALID_ARG;
+  XCK(cudaSetDevice(h->device));
+  h->use_graphs = enable != 0;
+  if (!h->use_graphs) clear_graphs(h);
   return XAMG_OK;
 }
 

@@ -116,6 +116,9 @@ __device__ __forceinline__ void d_scalar(int mode, ColState *cs, const double *p
     }
   }
   __syncthreads();
+  // k < 0: the iteration number is the device counter's next value (a
+  // captured iteration replays with the same arguments)
+  const int kk = k >= 0 ? k : cs->kdev + 1;
   if (threadIdx.x < NV) {
     const int c = threadIdx.x;
     const double d0 = s0[c], d1 = s1[c];
@@ -138,7 +141,7 @@ __device__ __forceinline__ void d_scalar(int mode, ColState *cs, const double *p
             cs->alpha[c] = 0.0;
           } else {
             cs->alpha[c] = cs->rho[c] / d0;
-            cs->iters[c] = k;
+            cs->iters[c] = kk;
           }
         } else {
           cs->alpha[c] = 0.0;
@@ -226,7 +229,7 @@ __device__ __forceinline__ void d_scalar(int mode, ColState *cs, const double *p
         break;
       case SM_BI_HALF:
         if (st == 0) {
-          cs->iters[c] = k;
+          cs->iters[c] = kk;
           if (sqrt(d0) <= tol * cs->nb[c]) {
             cs->state[c] = 1;
             cs->omega[c] = 0.0;
@@ -248,6 +251,10 @@ __device__ __forceinline__ void d_scalar(int mode, ColState *cs, const double *p
     }
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    if (mode == SM_INIT) cs->kdev = 0;
+    if (mode == SM_PCG_ALPHA || mode == SM_BI_HALF) cs->kdev = kk;
+  }
   if (threadIdx.x == 0 && fl) {
     int act = 0, fr = 0, re = 0, br = 0;
     for (int c = 0; c < NV; ++c) {

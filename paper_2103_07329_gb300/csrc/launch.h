@@ -26,6 +26,7 @@ struct ColState {
   int32_t restart[32]; // next direction update starts afresh
   int32_t iters[32];
   int32_t reac[32];    // 1: column restarted by the last confirmation
+  int32_t kdev;        // iteration number of the last alpha step (graph replays read it)
 };
 
 // Host-visible counters written by the scalar kernels (mapped pinned memory).

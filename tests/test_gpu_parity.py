@@ -325,6 +325,39 @@ def test_pinned_host_buffers_match_device(cfg0, method):
     assert np.array_equal(Xh, Xd.cpu().numpy())
 
 
+@pytest.mark.parametrize("prec", [B.PREC_FP64, B.PREC_FP32, B.PREC_BF16])
+def test_graph_replay_is_bitwise(prec):
+    # the captured steady PCG iteration replays the same kernels with the
+    # same arguments: X, iteration counts and residuals equal the uncaptured
+    # solve bit for bit (first solve captures, second replays the cache); a
+    # second tolerance keys its own graph; a maxit stop and a row-split
+    # change (which drops the cache) keep the equality
+    A = P.poisson7(20)
+    g = B.Hierarchy(A)
+    Bm = dev(P.rhs_uniform(A.n, 3, 11))
+
+    def run(tol=1e-8, maxit=100, m=3):
+        X = torch.empty_like(Bm[:, :m].contiguous())
+        st = g.solve(Bm[:, :m].contiguous(), X, tol=tol, maxit=maxit, precond=prec)
+        return X.cpu().numpy(), st
+
+    for kw in ({}, {"tol": 1e-10}, {"maxit": 2}, {"m": 1}):
+        g.set_graphs(False)
+        x0, s0 = run(**kw)
+        g.set_graphs(True)
+        for _ in range(2):
+            x1, s1 = run(**kw)
+            assert np.array_equal(x1, x0), kw
+            assert np.array_equal(s1.iters, s0.iters) and np.array_equal(s1.relres, s0.relres), kw
+            assert s1.rc == s0.rc
+    g.set_split(1, prec, 0, 0, 2)
+    x1, s1 = run(m=1)
+    g.set_graphs(False)
+    x0, s0 = run(m=1)
+    assert np.array_equal(x1, x0) and np.array_equal(s1.iters, s0.iters)
+    assert s0.rc == 0
+
+
 def test_caller_workspace(cfg0):
     Bm = dev(P.rhs_uniform(cfg0.A.n, 4, 6))
     nb = cfg0.g.workspace_bytes(4, B.PCG)
