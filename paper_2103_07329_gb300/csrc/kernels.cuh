@@ -124,7 +124,7 @@ enum Epi : int {
   EPI_Y_DN,        // y = v ; dnext = c1 dp + w v                 (Chebyshev step, x untouched)
   EPI_Y_XDP,       // y = v ; x += dp                             (last pre-smoothing step)
   EPI_MID,         // y = v ; dnext = c1 dp + w v ; x += dp       (middle Chebyshev step)
-  EPI_XLAST,       // x += dp + (c1 dp + w v)                     (last post-smoothing step)
+  EPI_XLAST,       // x += dp + (c1 dp + w v), as (x + (1+c1) dp) + w v  (last post-smoothing step)
   EPI_XLAST_DOT,   // EPI_XLAST and partial dot_u . x_new
   EPI_Y_DOT,       // y = v ; partial dot_u . v
   EPI_Y_DOT2,      // y = v ; partial dot_u . v (if dot_u) and v . v
@@ -149,7 +149,9 @@ __device__ __forceinline__ void row_epilogue(const RowOpT<TB> &op, int64_t i, in
     op.x[e] = xv + dpv;
   }
   if constexpr (EPI == EPI_XLAST || EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2) {
-    const TB xn = (xv + dpv) + fma(op.c1, dpv, wv * acc);
+    // x + d + (c1 d + w v) = (x + (1 + c1) d) + w v: two FMAs per element
+    // (1 + c1 is the same for every element)
+    const TB xn = fma(wv, acc, fma(op.c1 + (TB)1, dpv, xv));
     op.x[e] = xn;
     if constexpr (EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2) dsum = fma(du, (double)xn, dsum);
     if constexpr (EPI == EPI_XLAST_DOT2) dsum2 = fma(du2, (double)xn, dsum2);
