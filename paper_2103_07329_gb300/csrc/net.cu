@@ -49,9 +49,11 @@ __host__ __device__ constexpr int vstride(int c) { return c == 16 ? 24 : c; }
 __host__ __device__ constexpr int kstride(int cin) { return kpad(cin) + 8; }
 constexpr int kGStride = 24;  // voxel stride of the staged output gradient
 
+// Two input bricks (the one being multiplied and the next one in flight),
+// the weights and a zero row.
 template <int CIN, int COUT>
 constexpr size_t fwd_smem() {
-  return (size_t)(1000 * vstride(CIN) + COUT * kstride(CIN) + 8) * sizeof(bf16);
+  return (size_t)(2 * 1000 * vstride(CIN) + COUT * kstride(CIN) + 8) * sizeof(bf16);
 }
 template <int CIN>
 constexpr size_t wgrad_smem() {
@@ -145,6 +147,26 @@ __device__ __forceinline__ void stage_brick(bf16 *dst, const bf16 *__restrict__ 
   }
 }
 
+// The same staging without a mask, as asynchronous 16-byte copies (zero
+// filled outside the grid) that complete while the previous brick is
+// multiplied; the caller commits and waits.
+template <int C, int VS>
+__device__ __forceinline__ void stage_brick_async(bf16 *dst, const bf16 *__restrict__ src, int N,
+                                                  const Brick &bk) {
+  constexpr int CH = C / 8;  // 16-byte chunks per voxel
+  for (int idx = threadIdx.x; idx < 1000 * CH; idx += kThreads) {
+    const int vox = idx / CH, part = idx % CH;
+    const int hx = vox % 10, hy = (vox / 10) % 10, hz = vox / 100;
+    const int gz = bk.z0 + hz - 1, gy = bk.y0 + hy - 1, gx = bk.x0 + hx - 1;
+    const bool in = gz >= 0 && gz < N && gy >= 0 && gy < N && gx >= 0 && gx < N;
+    // outside the grid: no bytes read (src-size 0), the 16 bytes are zeroed
+    const int64_t off = in ? (bk.sbase + ((int64_t)gz * N + gy) * N + gx) * C + part * 8 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst + vox * VS + part * 8)),
+                 "l"(src + off), "r"(in ? 16 : 0)
+                 : "memory");
+  }
+}
+
 // out = [relu](conv(in [* (mask > 0)]) + bias); wt: BF16 [COUT][kpad(CIN)]
 // with k = t CIN + ci and zeros for k >= 27 CIN.  With out0 != NULL only
 // output channel 0 is stored, in FP32, to out0[sample][voxel] (out unused).
@@ -159,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3(const bf16 *__restrict__ in,
   constexpr int VS = vstride(CIN), KP = kpad(CIN), KS = kstride(CIN), NT = COUT / 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   bf16 *in_s = reinterpret_cast<bf16 *>(smem_raw);
-  bf16 *w_s = in_s + 1000 * VS;
+  bf16 *w_s = in_s + 2 * 1000 * VS;  // after the two input bricks
   bf16 *zero_s = w_s + COUT * KS;
   for (int idx = threadIdx.x; idx < COUT * (KP / 8); idx += kThreads) {
     const int row = idx / (KP / 8), ch = idx % (KP / 8);
@@ -183,11 +205,28 @@ __global__ void __launch_bounds__(kThreads) k_conv3(const bf16 *__restrict__ in,
     bv[nt][1] = bias ? __ldg(bias + nt * 8 + 2 * tq + 1) : 0.0f;
   }
 
+  // without a mask the input bricks are double-buffered: brick b + gridDim.x
+  // is copied asynchronously while brick b is multiplied
+  int buf = 0;
+  if (!mask && blockIdx.x < total) {
+    stage_brick_async<CIN, VS>(in_s, in, N, brick_of(blockIdx.x, nb, N));
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
   for (int b = blockIdx.x; b < total; b += gridDim.x) {
     const Brick bk = brick_of(b, nb, N);
-    __syncthreads();  // the previous brick's fragments are consumed
-    stage_brick<CIN, VS>(in_s, in, mask, N, bk);
+    if (mask) {
+      __syncthreads();  // the previous brick's fragments are consumed
+      stage_brick<CIN, VS>(in_s, in, mask, N, bk);
+    } else {
+      // the other buffer was last read by the previous brick's fragments
+      __syncthreads();
+      if (b + (int)gridDim.x < total)
+        stage_brick_async<CIN, VS>(in_s + (buf ^ 1) * 1000 * VS, in, N, brick_of(b + gridDim.x, nb, N));
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this brick's copies
+    }
     __syncthreads();
+    const uint32_t in_b = in_a + (uint32_t)(buf * 1000 * VS) * 2u;
     float acc[4][NT][4];
 #pragma unroll
     for (int mt = 0; mt < 4; ++mt)
@@ -216,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3(const bf16 *__restrict__ in,
 #pragma unroll
       for (int mt = 0; mt < 4; ++mt) {
         const int hv = a_base + mt * 20 + toff;
-        const uint32_t addr = real ? in_a + (uint32_t)(hv * VS + c0) * 2u : zero_a;
+        const uint32_t addr = real ? in_b + (uint32_t)(hv * VS + c0) * 2u : zero_a;
         uint32_t a[4];
         ldsm_x4(a, addr);
 #pragma unroll
@@ -251,7 +290,9 @@ __global__ void __launch_bounds__(kThreads) k_conv3(const bf16 *__restrict__ in,
           }
         }
     }
+    if (!mask) buf ^= 1;
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy left in flight at exit
 }
 
 // Per-block partial sums of one layer's weight and bias gradients over the
