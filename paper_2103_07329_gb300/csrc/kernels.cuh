@@ -324,7 +324,7 @@ __device__ __forceinline__ void vstore(T *p, const Vec<T, VEC> &r) {
 // storage order (no reduction adds), and a chunk's tail takes exactly as many
 // FMAs as it has entries.  With scaled (bf16) values the products are summed
 // first and the row scale applied once: v = init +/- s_i * sum_k q_ik x_k.
-template <class TB, class TV, int NV, int VEC, int SL, bool NEG, int EPI>
+template <class TB, class TV, int NV, int VEC, int SL, bool NEG, int EPI, int XW = 1>
 __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
   using VL = ValueLoad<TV>;
   using V = Vec<TB, VEC>;
@@ -345,15 +345,23 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
   const int sl = (lane / G) % SL;   // slice of the row
   const int grp = lane / (G * SL);  // row of the warp
   const int gbase = (lane / G) * G;
-  const int64_t warp0 = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const int64_t wstride = (int64_t)gridDim.x * kWarps;
+  // XW > 1 (a row already fills a warp): XW warps of a block share one row,
+  // warp slice wx taking the entry rounds wx, wx + XW, ...; their partial
+  // sums are added in a fixed order through shared memory, so the row loop is
+  // block-uniform: block step b covers rows b * kWarps / XW + warp / XW
+  static_assert(XW == 1 || (RPW == 1 && SL == 1), "warps per row need one row per warp");
+  constexpr int RPB = kWarps / XW;
+  const int wx = (threadIdx.x >> 5) % XW;
+  const int64_t warp0 =
+      XW == 1 ? (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5) : (int64_t)blockIdx.x * RPB;
+  const int64_t wstride = XW == 1 ? (int64_t)gridDim.x * kWarps : (int64_t)gridDim.x * RPB;
   const int32_t *__restrict__ col = op.col;
   const TB *__restrict__ src = op.src;
   double dsum[VEC], dsum2[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; ++v) dsum[v] = dsum2[v] = 0.0;
   for (int64_t base = warp0 * RPW; base < op.n; base += wstride * RPW) {
-    const int64_t i = base + grp;
+    const int64_t i = base + (XW == 1 ? grp : (threadIdx.x >> 5) / XW);
     const bool valid = i < op.n;
     const int64_t e = i * NV + c0;
     int start = 0, len = 0;
@@ -366,18 +374,20 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
       start = __ldg(op.rowptr + i);
       len = __ldg(op.rowptr + i + 1) - start;
       if constexpr (VL::idx16) meta = __ldg(op.rowmeta + i);
-      if (!VL::scaled && op.init && sl == 0) acc = vload<TB, VEC>(op.init + e);
-      if constexpr (EPI == EPI_Y_DN || EPI == EPI_Y_XDP || EPI == EPI_MID || xlast)
-        dpv = vload<TB, VEC>(op.dp + e);
-      if constexpr (EPI == EPI_Y_D0 || EPI == EPI_Y_DN || EPI == EPI_MID || xlast) wv = op.w[i];
-      if constexpr (EPI == EPI_Y_XDP || EPI == EPI_MID || xlast) xv = vload<TB, VEC>(op.x + e);
+      if (wx == 0) {
+        if (!VL::scaled && op.init && sl == 0) acc = vload<TB, VEC>(op.init + e);
+        if constexpr (EPI == EPI_Y_DN || EPI == EPI_Y_XDP || EPI == EPI_MID || xlast)
+          dpv = vload<TB, VEC>(op.dp + e);
+        if constexpr (EPI == EPI_Y_D0 || EPI == EPI_Y_DN || EPI == EPI_MID || xlast) wv = op.w[i];
+        if constexpr (EPI == EPI_Y_XDP || EPI == EPI_MID || xlast) xv = vload<TB, VEC>(op.x + e);
+      }
     }
     const int maxlen = (RPW == 1 && SL == 1) ? len : __reduce_max_sync(0xffffffffu, len);
     // slice sl takes rounds sl, sl + SL, ...; every slice runs the same number
     // of rounds (entries past the row's end are zeros), so the shuffles stay
     // warp-uniform
-    for (int kb0 = 0; kb0 < maxlen; kb0 += G * K * SL) {
-      const int kb = kb0 + sl * G * K;
+    for (int kb0 = 0; kb0 < maxlen; kb0 += G * K * SL * XW) {
+      const int kb = kb0 + (sl + wx * SL) * G * K;
       // the group fetches G*K entries per round: slot q of lane g holds entry
       // kb + q*G + g (coalesced across the group for every q)
       int cl[K];
@@ -445,7 +455,22 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
 #pragma unroll
         for (int o = G; o < G * SL; o <<= 1) acc.v[v] += __shfl_xor_sync(0xffffffffu, acc.v[v], o);
     }
-    if (valid && sl == 0) {
+    if constexpr (XW > 1) {
+      // slice 0 (which holds the init value) adds slices 1 .. XW-1 in order
+      __shared__ TB xw_red[kWarps][32 * VEC];
+      const int w = threadIdx.x >> 5;
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) xw_red[w][lane * VEC + v] = acc.v[v];
+      __syncthreads();
+      if (wx == 0) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v)
+#pragma unroll
+          for (int j = 1; j < XW; ++j) acc.v[v] += xw_red[w + j][lane * VEC + v];
+      }
+      __syncthreads();
+    }
+    if (valid && sl == 0 && wx == 0) {
       if constexpr (VL::scaled) {
         V in;
 #pragma unroll
@@ -475,7 +500,7 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
       if constexpr (xlast) {
         V xn;
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) xn.v[v] = (xv.v[v] + dpv.v[v]) + fma(op.c1, dpv.v[v], wv * acc.v[v]);
+        for (int v = 0; v < VEC; ++v) xn.v[v] = fma(wv, acc.v[v], fma(op.c1 + (TB)1, dpv.v[v], xv.v[v]));
         vstore<TB, VEC>(op.x + e, xn);
         if constexpr (EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2) {
 #pragma unroll
@@ -736,6 +761,9 @@ template <class TB, class TV, int NV, int S, bool NEG, int EPI>
 __global__ void __launch_bounds__(kBlock, 4) k_rows(RowOpT<TB> op) {
   if constexpr (S == 1) {
     rows_vec<TB, TV, NV, row_vec<TB, NV>(), 1, NEG, EPI>(op);
+  } else if constexpr (NV > 1 && S < 0) {
+    // a row fills a warp: -S warps per row
+    rows_vec<TB, TV, NV, row_vec<TB, NV>(), 1, NEG, EPI, -S>(op);
   } else if constexpr (NV > 1) {
     rows_vec<TB, TV, NV, row_vec<TB, NV>(), S, NEG, EPI>(op);
   } else {

@@ -73,6 +73,11 @@ struct VParts {
 // (kStreamShort), 1 / 512 (kStreamMid), 2 / 512 (kStreamPair), 1 / 1024
 // (kStreamLong), 4 / 1024 (kStreamQuad) or 32 / 1024 (kStreamWarp), or 16
 // lanes per row with the row's entries dealt round-robin (kSliced16).
+// Warps sharing one row in the wide split of blocks whose row already fills a
+// warp (32 FP64 columns): the dense Galerkin levels have too few rows to
+// fill the GPU one row per warp.
+constexpr int kWarpsPerRow = 4;
+
 constexpr int kStreamShort = -1, kStreamLong = -2, kStreamQuad = -3, kStreamWarp = -4, kStreamMid = -5,
               kStreamPair = -6, kSliced16 = 16;
 

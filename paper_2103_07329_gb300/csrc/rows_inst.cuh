@@ -22,8 +22,7 @@ using TBx = double;
 // S < 0: an m = 1 stream-kernel variant (StreamCfg<S>).
 template <class TV, int NV, int S, bool NEG, int EPI>
 int rows_t(const RowOpT<TBx> &op, cudaStream_t st) {
-  if constexpr (S < 0) {
-    static_assert(NV == 1, "the stream kernel is the m = 1 split");
+  if constexpr (S < 0 && NV == 1) {
     constexpr int LPR = StreamCfg<S>::LPR, R = StreamCfg<S>::R;
     constexpr int smem = kWarps * stream_warp_bytes<TV, R>();
     auto kern = k_rows_stream<TBx, TV, LPR, R, NEG, EPI>;
@@ -51,8 +50,9 @@ int rows_t(const RowOpT<TBx> &op, cudaStream_t st) {
         b = 1;
       max_grid = std::min(kMaxGrid, b * device_sm_count());
     }
-    constexpr int lanes_per_row = NV == 1 ? (S > 0 ? S : 1) : (NV / row_vec<TBx, NV>()) * S;
-    constexpr int rows_per_block = kWarps * (32 / lanes_per_row);
+    // S < 0 (NV > 1): -S warps per row
+    constexpr int lanes_per_row = NV == 1 ? S : (NV / row_vec<TBx, NV>()) * (S > 0 ? S : 1);
+    constexpr int rows_per_block = S < 0 ? kWarps / -S : kWarps * (32 / lanes_per_row);
     const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
     k_rows<TBx, TV, NV, S, NEG, EPI><<<grid, kBlock, 0, st>>>(op);
@@ -119,8 +119,10 @@ int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t 
   constexpr int WS = 32 / (XAMG_NV / row_vec<TBx, XAMG_NV>());
   if constexpr (WS > 1) {
     if (slices > 1) return rows_e<TV, XAMG_NV, WS>(op, neg, epi, st);
+  } else {
+    // a row already fills the warp: the wide split gives it kWarpsPerRow warps
+    if (slices > 1) return rows_e<TV, XAMG_NV, -kWarpsPerRow>(op, neg, epi, st);
   }
-  (void)slices;
   return rows_e<TV, XAMG_NV, 1>(op, neg, epi, st);
 #endif
 }

@@ -127,7 +127,7 @@ def test_bf16_index_compression_paths(which):
 
 
 @pytest.mark.parametrize("prec", [B.PREC_FP64, B.PREC_FP32, B.PREC_BF16])
-@pytest.mark.parametrize("m", [1, 2, 16])
+@pytest.mark.parametrize("m", [1, 2, 16, 32])
 def test_autotuned_splits_keep_the_results(prec, m):
     # a fresh hierarchy: tuning stores its choices in the hierarchy
     A = P.diffusion7(24, P.lognormal_cells(24, 1.0, 1))

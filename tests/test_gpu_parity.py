@@ -146,6 +146,36 @@ def test_spmm_m1_every_split(cand):
                     pr.g.set_split(1, B.PREC_FP64, l, which, -1)
 
 
+@pytest.mark.parametrize("m", [16, 32])
+@pytest.mark.parametrize("cand", [0, 1])
+def test_spmm_wide_blocks_every_split(m, cand):
+    # FP64 blocks of 16 and 32 columns under both splits on every level and
+    # operator (32 columns, split 1: four warps share a row), the 7-point and
+    # 27-point hierarchies with their dense Galerkin levels
+    for name, N in (("p7", 33), ("p27", 20)):
+        pr = pair(name, N)
+        rng = np.random.default_rng(100 + cand)
+        for l in range(pr.o.nlev):
+            lv = pr.o.level(l)
+            ops = [(0, csr_of(lv.A, lv.n), lv.n)]
+            if lv.P is not None:
+                nc = pr.o.level(l + 1).n
+                ops += [(1, P.CSR(lv.n, *lv.P), nc), (2, P.CSR(nc, *lv.R), lv.n)]
+            for which, M, ncols in ops:
+                pr.g.set_split(m, B.PREC_FP64, l, which, cand)
+                try:
+                    X = rng.integers(-50, 51, size=(ncols, m)).astype(np.float64)
+                    Y = torch.empty((M.n, m), dtype=torch.float64, device="cuda")
+                    pr.g.spmm(l, which, dev(X), Y)
+                    ref = oracle.spmm(M, X, ncols=ncols)
+                    if l == 0 and which == 0:
+                        assert np.array_equal(Y.cpu().numpy(), ref), (name, l, which)
+                    else:
+                        assert colrel(Y.cpu().numpy(), ref).max() <= RTOL, (name, l, which)
+                finally:
+                    pr.g.set_split(m, B.PREC_FP64, l, which, -1)
+
+
 def test_set_split_rejects_bad_arguments(cfg0):
     g = cfg0.g
     L = cfg0.o.nlev
