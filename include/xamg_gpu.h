@@ -192,6 +192,24 @@ int xamg_setup_hierarchy(const xamg_csr *A, const xamg_amg_params *p, xamg_hier 
 /* Releases the handle and every device buffer it owns.  NULL is accepted. */
 int xamg_destroy(xamg_hier *h);
 
+/* The frozen hierarchy as a byte blob (the "hierarchy as input" of the
+ * solve phase): the setup parameters and every level's A, P, R, coarse /
+ * fine flags, inverse diagonal and Chebyshev interval, plus the coarsest
+ * LU factors, written field by field in this host's byte order behind a
+ * magic string and a format version.  *bytes receives the blob's size; with
+ * blob = NULL nothing else happens (size query), else the blob is written to
+ * the caller's buffer of `capacity` bytes (XAMG_ERR_INVALID_ARG if smaller).
+ * Host only. */
+int xamg_hier_save(const xamg_hier *h, void *blob, size_t capacity, size_t *bytes);
+
+/* A hierarchy from a blob of xamg_hier_save, uploaded to the current device
+ * when its saved parameters ask for it (device_upload), exactly as after
+ * xamg_setup_hierarchy: solves on it equal those on the saved hierarchy bit
+ * for bit.  XAMG_ERR_INVALID_ARG if the blob is not a complete, well-formed
+ * hierarchy of this format (every length, offset and index is checked).
+ * The caller's blob is only read. */
+int xamg_hier_load(const void *blob, size_t bytes, xamg_hier **out);
+
 /* Number of levels and the row count, nnz of A, nnz of P of level `level`
  * (nnz_p = 0 on the coarsest level).  Any output pointer may be NULL. */
 int xamg_hier_info(const xamg_hier *h, int32_t *levels, double *op_complexity);

@@ -38,7 +38,8 @@ MAX_RHS = 32
 # every entry point declared in include/xamg_gpu.h
 EXPORTS = [
     "xamg_strerror", "xamg_amg_params_default", "xamg_solve_opts_default",
-    "xamg_setup_hierarchy", "xamg_destroy", "xamg_hier_info", "xamg_level_info",
+    "xamg_setup_hierarchy", "xamg_destroy", "xamg_hier_save", "xamg_hier_load", "xamg_hier_info",
+    "xamg_level_info",
     "xamg_level_export", "xamg_coarse_export", "xamg_workspace_bytes", "xamg_solve",
     "xamg_solve_host", "xamg_level_spmm", "xamg_smooth", "xamg_vcycle", "xamg_vcycle_precond",
     "xamg_coarse_solve",
@@ -118,6 +119,8 @@ def _load():
         "xamg_solve_opts_default": ([C.POINTER(SolveOptsT)], None),
         "xamg_setup_hierarchy": ([C.POINTER(CsrT), C.POINTER(AmgParamsT), C.POINTER(vp)], C.c_int),
         "xamg_destroy": ([vp], C.c_int),
+        "xamg_hier_save": ([vp, vp, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
+        "xamg_hier_load": ([vp, C.c_size_t, C.POINTER(vp)], C.c_int),
         "xamg_hier_info": ([vp, C.POINTER(i32), C.POINTER(dbl)], C.c_int),
         "xamg_level_info": ([vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64)], C.c_int),
         "xamg_level_export": ([vp, i32, vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
@@ -244,6 +247,34 @@ class Hierarchy:
         self._h = h
         self.n = A.n
         self.on_device = bool(prm.device_upload)
+
+    def save(self) -> bytes:
+        """xamg_hier_save: the frozen hierarchy as bytes."""
+        L = _load()
+        n = C.c_size_t()
+        _check(L.xamg_hier_save(self._h, None, 0, C.byref(n)), "xamg_hier_save")
+        buf = C.create_string_buffer(n.value)
+        _check(L.xamg_hier_save(self._h, buf, n.value, C.byref(n)), "xamg_hier_save")
+        return buf.raw[:n.value]
+
+    @classmethod
+    def load(cls, blob: bytes) -> "Hierarchy":
+        """xamg_hier_load: a hierarchy from the bytes of save()."""
+        L = _load()
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        h = C.c_void_p()
+        _check(L.xamg_hier_load(buf, len(blob), C.byref(h)), "xamg_hier_load")
+        self = cls.__new__(cls)
+        self._h = h
+        n = C.c_int32()
+        na = C.c_int64()
+        npn = C.c_int64()
+        _check(L.xamg_level_info(h, 0, C.byref(n), C.byref(na), C.byref(npn)), "xamg_level_info")
+        self.n = n.value
+        # graphs are on by default; re-enabling them changes nothing and is
+        # accepted only by a hierarchy on the device
+        self.on_device = L.xamg_set_graphs(h, 1) == 0
+        return self
 
     def close(self):
         if getattr(self, "_h", None):

@@ -30,7 +30,7 @@ def _nvcc() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("setup.cpp", "kernels.cu", "capi.cu", "noalloc.cu",
+    return [os.path.join(CSRC, f) for f in ("setup.cpp", "hier_io.cpp", "kernels.cu", "capi.cu", "noalloc.cu",
                                             "rows_nv1.cu", "rows_nv2.cu", "rows_nv4.cu",
                                             "rows_nv8.cu", "rows_nv16.cu", "rows_nv32.cu",
                                             "rowsf_nv1.cu", "rowsf_nv2.cu", "rowsf_nv4.cu",

@@ -1499,6 +1499,8 @@ void xamg_solve_opts_default(xamg_solve_opts *o) {
   o->workspace_bytes = 0;
 }
 
+static int attach_device(xamg_hier *h, xamg_hier **out);
+
 int xamg_setup_hierarchy(const xamg_csr *A, const xamg_amg_params *p, xamg_hier **out) {
   if (!A || !out) return XAMG_ERR_INVALID_ARG;
   *out = nullptr;
@@ -1513,6 +1515,37 @@ int xamg_setup_hierarchy(const xamg_csr *A, const xamg_amg_params *p, xamg_hier 
     delete h;
     return rc;
   }
+  return attach_device(h, out);
+}
+
+int xamg_hier_save(const xamg_hier *h, void *blob, size_t capacity, size_t *bytes) {
+  if (!h || !bytes) return XAMG_ERR_INVALID_ARG;
+  const std::vector<char> b = save_hier(h->prm, h->host);
+  *bytes = b.size();
+  if (!blob) return XAMG_OK;
+  if (capacity < b.size()) return XAMG_ERR_INVALID_ARG;
+  std::memcpy(blob, b.data(), b.size());
+  return XAMG_OK;
+}
+
+int xamg_hier_load(const void *blob, size_t bytes, xamg_hier **out) {
+  if (!blob || !out) return XAMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  xamg_hier *h = new (std::nothrow) xamg_hier();
+  if (!h) return XAMG_ERR_OOM;
+  const int rc = load_hier(blob, bytes, h->prm, h->host);
+  if (rc != XAMG_OK) {
+    delete h;
+    return rc;
+  }
+  return attach_device(h, out);
+}
+
+// Uploads a built (or loaded) host hierarchy when its parameters ask for it
+// and hands it out; on failure frees it.
+static int attach_device(xamg_hier *h, xamg_hier **out) {
+  int rc = XAMG_OK;
+  const xamg_amg_params &prm = h->prm;
   if (prm.device_upload) {
     if (cudaGetDevice(&h->device) != cudaSuccess) {
       delete h;

@@ -1,6 +1,7 @@
 // Host-side AMG hierarchy of the library (built once, then frozen and
 // uploaded).  Internal to the library.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <vector>
 
@@ -35,5 +36,11 @@ struct HostHier {
 
 // Builds the hierarchy.  Returns an XAMG_* code.
 int build_hierarchy(const xamg_csr &A, const xamg_amg_params &p, HostHier &h);
+
+// The setup parameters and the frozen hierarchy as a byte blob, and back
+// (hier_io.cpp); load_hier returns XAMG_ERR_INVALID_ARG for a blob that is
+// not a complete, well-formed hierarchy of this format.
+std::vector<char> save_hier(const xamg_amg_params &p, const HostHier &h);
+int load_hier(const void *blob, size_t bytes, xamg_amg_params &p, HostHier &h);
 
 }  // namespace xamg
