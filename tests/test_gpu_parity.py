@@ -321,6 +321,24 @@ def test_edge_cases(cfg0):
         cfg0.g.solve(dev(np.zeros((n, 33))), torch.empty((n, 33), dtype=torch.float64, device="cuda"))
 
 
+def test_breakdown_on_a_negative_definite_matrix():
+    # -A of the 7-point Laplacian: p^T A p < 0 for every p, so the first alpha
+    # step flags every column as broken down (the reading of the breakdown
+    # rule), X stays at its zero start, and the call returns XAMG_BREAKDOWN,
+    # all as in the oracle (its coarsening stalls: one dense level)
+    A = P.poisson7(8)
+    An = P.CSR(A.n, A.rowptr, A.col, -A.val)
+    g = B.Hierarchy(An)
+    o = oracle.Hierarchy(An)
+    Bm = P.rhs_uniform(A.n, 3, 1)
+    X = torch.full((A.n, 3), 7.0, dtype=torch.float64, device="cuda")
+    st = g.solve(dev(Bm), X, tol=1e-8, maxit=50)
+    ref = o.pcg(Bm, 1e-8, 50)
+    assert st.rc == B.BREAKDOWN
+    assert np.array_equal(st.status, ref.status) and np.array_equal(st.iters, ref.iters)
+    assert np.all(X.cpu().numpy() == 0.0)
+
+
 def test_host_buffers_match_device(cfg0):
     Bm = P.rhs_uniform(cfg0.A.n, 4, 5)
     Xd = torch.empty_like(dev(Bm))
