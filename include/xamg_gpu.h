@@ -327,7 +327,7 @@ int xamg_coldot_noalloc(const double *U, const double *V, int64_t n, int32_t m, 
  * XAMG_PREC_FP32 / XAMG_PREC_BF16: FP32 blocks with FP32 / bf16 values of A)
  * under every row split -- for m > 1 the default (a group of lanes per row,
  * several rows per warp) and one row per warp with its entries split over the
- * lanes (32 FP64 columns: four warps per row); for m = 1 the stream kernel (the warp's entries staged in shared
+ * lanes (16 and 32 FP64 columns: four warps per row); for m = 1 the stream kernel (the warp's entries staged in shared
  * memory) with one lane per row and a 256-, 512- or 1024-entry window, 2, 4
  * or 32 lanes per row, and 16 lanes per row without staging -- and keeps
  * the fastest in the hierarchy; later solves and V-cycles of
@@ -347,8 +347,8 @@ int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_
  * window; 1 = 16 lanes per row; 2, 3, 4 = stream kernel with a 1024-entry
  * window and 1 lane, 4 lanes or a warp per row; 5, 6 = stream kernel with a
  * 512-entry window and 1 or 2 lanes per row; m > 1: 0 = a
- * group of lanes per row, 1 = one row per warp (for FP64 blocks of 32
- * columns, whose row already fills a warp: four warps per row).  Results do not depend on the split
+ * group of lanes per row, 1 = one row per warp (for FP64 blocks of 16 and
+ * 32 columns: four warps per row).  Results do not depend on the split
  * beyond the order of each row's sums.  XAMG_ERR_INVALID_ARG for any other
  * value.  Host only.  No counterpart in the paper. */
 int xamg_set_split(xamg_hier *h, int32_t m, int32_t precond, int32_t level, int32_t which,

@@ -490,9 +490,10 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
   // row's entries split over the warp
   const int vec = fp32 ? (nv >= 4 ? 4 : nv) : 1;
   const double warps = (double)M.n / (32 / (nv / vec));
-  // a row that already fills a warp (32 FP64 columns) gets four warps below
-  // two waves of rows: measured faster from 5 739 rows (1 537 entries) down
-  const double waves = nv / vec == 32 ? 2.0 : 1.0;
+  // FP64 blocks of 16 and 32 columns, whose wide split spreads a row over
+  // four warps, take it below two waves of narrow warps: measured faster from
+  // 11 696 rows (1 025 entries) down at 16 columns and 5 739 (1 537) at 32
+  const double waves = (!fp32 && nv >= 16) ? 2.0 : 1.0;
   if (avg >= 32.0 && warps < waves * 32.0 * device_sm_count()) return 2;
   return 1;
 }

@@ -349,7 +349,7 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
   // warp slice wx taking the entry rounds wx, wx + XW, ...; their partial
   // sums are added in a fixed order through shared memory, so the row loop is
   // block-uniform: block step b covers rows b * kWarps / XW + warp / XW
-  static_assert(XW == 1 || (RPW == 1 && SL == 1), "warps per row need one row per warp");
+  static_assert(XW == 1 || RPW == 1, "warps per row need one row per warp");
   constexpr int RPB = kWarps / XW;
   const int wx = (threadIdx.x >> 5) % XW;
   const int64_t warp0 =
@@ -762,8 +762,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_rows(RowOpT<TB> op) {
   if constexpr (S == 1) {
     rows_vec<TB, TV, NV, row_vec<TB, NV>(), 1, NEG, EPI>(op);
   } else if constexpr (NV > 1 && S < 0) {
-    // a row fills a warp: -S warps per row
-    rows_vec<TB, TV, NV, row_vec<TB, NV>(), 1, NEG, EPI, -S>(op);
+    // one row per warp (in 32 / (NV / VEC) slices), -S warps per row
+    rows_vec<TB, TV, NV, row_vec<TB, NV>(), 32 / (NV / row_vec<TB, NV>()), NEG, EPI, -S>(op);
   } else if constexpr (NV > 1) {
     rows_vec<TB, TV, NV, row_vec<TB, NV>(), S, NEG, EPI>(op);
   } else {

@@ -118,6 +118,10 @@ int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t 
   // warp; with 32 FP64 columns a row already fills the warp)
   constexpr int WS = 32 / (XAMG_NV / row_vec<TBx, XAMG_NV>());
   if constexpr (WS > 1) {
+#if !XAMG_FLOAT && XAMG_NV == 16
+    // 16 FP64 columns: the row's two slices in each of kWarpsPerRow warps
+    if (slices > 1) return rows_e<TV, XAMG_NV, -kWarpsPerRow>(op, neg, epi, st);
+#endif
     if (slices > 1) return rows_e<TV, XAMG_NV, WS>(op, neg, epi, st);
   } else {
     // a row already fills the warp: the wide split gives it kWarpsPerRow warps
