@@ -31,8 +31,6 @@ struct HierLevelView {
 
 struct HierView {
   int L = 0, nc = 0, cheb_steps = 0, device = 0;
-  const double *lu = nullptr;
-  const int32_t *piv = nullptr;
   const double *ainv = nullptr;  // inverse of the coarsest operator (nc x nc)
   HierLevelView lv[kBatchMaxLevels];
 };

@@ -112,8 +112,6 @@ struct xamg_hier {
   bool on_device = false;
   int device = 0;
   std::vector<DevLevel> lv;
-  double *lu = nullptr;
-  int32_t *piv = nullptr;
   double *ainv = nullptr;     // inverse of the coarsest operator (nc x nc, row-major)
   std::vector<void *> owned;  // device allocations of the hierarchy
   void *ws = nullptr;         // cached solve workspace
@@ -1180,9 +1178,7 @@ int hier_view(xamg_hier *h, HierView *v) {
   v->nc = h->host.nc;
   v->cheb_steps = h->host.cheb_steps;
   v->device = h->device;
-  v->lu = h->lu;
   v->ainv = h->ainv;
-  v->piv = h->piv;
   for (int l = 0; l < L; ++l) {
     const DevLevel &D = h->lv[l];
     HierLevelView &o = v->lv[l];
@@ -1555,8 +1551,6 @@ static int attach_device(xamg_hier *h, xamg_hier **out) {
     const int L = (int)h->host.lv.size();
     h->lv.resize(L);
     for (int l = 0; l < L && rc == XAMG_OK; ++l) rc = upload_level(h, l);
-    if (rc == XAMG_OK) rc = dev_upload(h, &h->lu, h->host.lu.data(), h->host.lu.size());
-    if (rc == XAMG_OK) rc = dev_upload(h, &h->piv, h->host.piv.data(), h->host.piv.size());
     if (rc == XAMG_OK) {
       // the coarsest solve runs as a dense product with the explicit inverse
       // (its columns: the LU solves of the unit vectors)
