@@ -115,3 +115,29 @@ def test_loaded_hierarchy_solves_bitwise():
         s2 = g.solve(Bm, X2, precond=prec)
         assert torch.equal(X1, X2) and np.array_equal(s1.iters, s2.iters)
         assert s1.rc == 0
+
+
+def test_device_blob_without_a_device_fails_cleanly():
+    # a host-only blob with its upload flag set: where no GPU is present the
+    # load returns XAMG_ERR_CUDA (no crash, nothing leaked); with a GPU it
+    # uploads like any other load
+    import ctypes as C
+    blob = bytearray(host_hier(P.poisson7(6)).save())
+    flag = 8 + 4 + 4 + 8 + 4 * 4 + 8 + 8 + 4 + 4  # magic, version, order, parameters before device_upload
+    assert struct.unpack_from("<i", blob, flag)[0] == 0
+    blob[flag:flag + 4] = struct.pack("<i", 1)
+    L = B.lib()
+    out = C.c_void_p()
+    buf = C.create_string_buffer(bytes(blob), len(blob))
+    rc = L.xamg_hier_load(buf, len(blob), C.byref(out))
+    has_gpu = False
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        pass
+    if has_gpu:
+        assert rc == 0
+        L.xamg_destroy(out)
+    else:
+        assert rc == B.ERR_CUDA and not out.value
