@@ -83,7 +83,9 @@ extern "C" {
  *                   FP32 scale s_i = max_j |a_ij|: a_ij ~ s_i bf16(a_ij / s_i);
  *                   where every row's columns lie in two consecutive windows
  *                   of 65536 columns, A's column indices are also stored as
- *                   uint16 (low 16 bits plus one per-row window word) */
+ *                   uint16 (low 16 bits plus one per-row window word), read
+ *                   by the products on blocks of two or more columns (m = 1
+ *                   reads the 32-bit indices) */
 #define XAMG_PREC_FP64 0
 #define XAMG_PREC_FP32 1
 #define XAMG_PREC_BF16 2
@@ -120,8 +122,9 @@ typedef struct {
  *   nthreads      host threads for the setup (0 = all hardware threads)
  *   device_upload 1 (default): upload the hierarchy to the current CUDA
  *                 device; 0: build the host-side hierarchy only (no CUDA
- *                 call is made; only the xamg_*info / xamg_level_export
- *                 entry points accept such a handle) */
+ *                 call is made; only the xamg_*info, xamg_level_export,
+ *                 xamg_coarse_export and xamg_hier_save entry points accept
+ *                 such a handle) */
 typedef struct {
   double theta;
   int32_t max_coarse;
