@@ -141,3 +141,22 @@ def test_device_blob_without_a_device_fails_cleanly():
         L.xamg_destroy(out)
     else:
         assert rc == B.ERR_CUDA and not out.value
+
+
+def test_random_corruptions_never_crash():
+    # seeded single-byte corruptions and random-length prefixes anywhere in the
+    # blob: every load either succeeds (a value changed but the structure
+    # still checks out), returns XAMG_ERR_INVALID_ARG, or -- when the byte
+    # set the upload flag and no GPU is present -- XAMG_ERR_CUDA
+    blob = host_hier(P.poisson7(7)).save()
+    ok = (0, B.ERR_INVALID_ARG, B.ERR_CUDA)
+    rng = np.random.default_rng(2024)
+    for _ in range(300):
+        bad = bytearray(blob)
+        pos = int(rng.integers(0, len(blob)))
+        bad[pos] = int(rng.integers(0, 256))
+        assert load_code(bytes(bad)) in ok, pos
+    for _ in range(100):
+        cut = int(rng.integers(0, len(blob)))
+        tail = bytes(rng.integers(0, 256, size=int(rng.integers(0, 64)), dtype=np.uint8))
+        assert load_code(blob[:cut] + tail) in ok, cut
