@@ -84,7 +84,7 @@ typedef struct {
   int nc;
   /* reduced-precision copies for the FP32 preconditioner (built on first use) */
   int lp_ready;
-  float *af[ORC_MAXLEV], *pf[ORC_MAXLEV], *rf[ORC_MAXLEV], *dinvf[ORC_MAXLEV];
+  float *af[ORC_MAXLEV], *pf[ORC_MAXLEV], *rf[ORC_MAXLEV];
   uint16_t *aq[ORC_MAXLEV];  /* bf16 bits of fl32(a_ij) / s_i */
   float *as[ORC_MAXLEV];     /* s_i = fl32(max_j |a_ij|) */
 } ohier;
@@ -519,7 +519,7 @@ void orc_free(ohier *h) {
   for (l = 0; l < ORC_MAXLEV; ++l) {
     csr_free(&h->A[l]); csr_free(&h->P[l]); csr_free(&h->R[l]);
     free(h->cf[l]); free(h->dinv[l]);
-    free(h->af[l]); free(h->pf[l]); free(h->rf[l]); free(h->dinvf[l]); free(h->aq[l]); free(h->as[l]);
+    free(h->af[l]); free(h->pf[l]); free(h->rf[l]); free(h->aq[l]); free(h->as[l]);
   }
   free(h->lu); free(h->piv);
   free(h);
@@ -736,13 +736,19 @@ int orc_vcycle(const ohier *h, int m, const double *b, double *x) {
 /* ------------------------------------------------------------------ */
 /* Reduced-precision preconditioner (paper Sec. 2.3, "mixed-precision": a
  * reduced floating-point type inside part of the multigrid hierarchy, the
- * basic precision for the result).  Reading: every value of A, P, R, D^-1 and
- * every Chebyshev coefficient is rounded once to FP32 and the V-cycle runs in
- * FP32 arithmetic (each operation rounded to FP32), except the coarsest
- * solve, which widens its FP32 input, solves with the FP64 LU factors and
- * rounds the result back.  In the bf16 variant A's values are stored as
- * q_ij = bf16(fl32(a_ij) / s_i), s_i = fl32(max_j |a_ij|), and a row product
- * is s_i * sum_j q_ij x_j. */
+ * basic precision for the result).  Reading R9: every value of A, P and R is
+ * rounded once to FP32; so is each Chebyshev step's row weight
+ * w_k,i = coef_k * (D^-1)_ii (coef_0 = 1/theta, coef_k = 2 rho_k / delta,
+ * formed in FP64 like the FP64 smoother's coefficients) and each step
+ * coefficient c1_k = rho_k rho_{k-1}.  The V-cycle then runs in FP32
+ * arithmetic: a row product accumulates its terms in the row's storage order,
+ * each term added with one rounding (IEEE 754 fusedMultiplyAdd, the FP32
+ * accumulation of the multiply-add units), and every other operation -- the
+ * residual update r - t, d = c1 d + w r, x + d, the bf16 row scale -- rounds
+ * once per operation in the order written.  The coarsest solve widens its
+ * FP32 input, solves with the FP64 LU factors and rounds the result back.  In
+ * the bf16 variant A's values are stored as q_ij = bf16(fl32(a_ij) / s_i),
+ * s_i = fl32(max_j |a_ij|), and a row product is s_i * (sum_j q_ij x_j). */
 
 /* bf16 bits of a float: IEEE 754 roundTiesToEven on the 16 dropped
  * mantissa bits (NaN stays NaN). */
@@ -778,10 +784,9 @@ static int build_lowp(ohier *h) {
   for (l = 0; l < h->nlev; ++l) {
     const ocsr *A = &h->A[l];
     h->af[l] = to_f32(A->val, nnz_of(A));
-    h->dinvf[l] = to_f32(h->dinv[l], A->n);
     h->aq[l] = (uint16_t *)malloc((size_t)(nnz_of(A) > 0 ? nnz_of(A) : 1) * sizeof(uint16_t));
     h->as[l] = (float *)malloc((size_t)A->n * sizeof(float));
-    if (!h->af[l] || !h->dinvf[l] || !h->aq[l] || !h->as[l]) return ORC_ERR_OOM;
+    if (!h->af[l] || !h->aq[l] || !h->as[l]) return ORC_ERR_OOM;
     for (i = 0; i < A->n; ++i) {
       double mx = 0.0;
       for (p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) if (fabs(A->val[p]) > mx) mx = fabs(A->val[p]);
@@ -812,14 +817,16 @@ static void spmm_f(const ohier *h, int l, int which, int bf16, int m, const floa
     for (p = M->rowptr[i]; p < M->rowptr[i + 1]; ++p) {
       const float a = (which == 0 && bf16) ? bf16_value(h->aq[l][p]) : v[p];
       const float *x = X + (size_t)M->col[p] * m;
-      for (j = 0; j < m; ++j) y[j] = y[j] + a * x[j];
+      for (j = 0; j < m; ++j) y[j] = fmaf(a, x[j], y[j]);
     }
     if (which == 0 && bf16)
       for (j = 0; j < m; ++j) y[j] = h->as[l][i] * y[j];
   }
 }
 
-/* FP32 Chebyshev smoothing: the recurrence of cheb_smooth with FP32 data. */
+/* FP32 Chebyshev smoothing: the recurrence of cheb_smooth with FP32 data
+ * (reading R9): d_0 = w_0 r_0, d_k = c1_k d_{k-1} + w_k r_k, with the row
+ * weights w_k,i = fl32(coef_k (D^-1)_ii) and c1_k = fl32(rho_k rho_{k-1}). */
 static int cheb_smooth_f(const ohier *h, int l, int bf16, int m, const float *b, float *x, int x_zero,
                          float *r_out) {
   const ocsr *A = &h->A[l];
@@ -827,9 +834,8 @@ static int cheb_smooth_f(const ohier *h, int l, int bf16, int m, const float *b,
   int i, j, k, steps = h->cheb_steps;
   double lo = h->cheb_lo[l], hi = h->cheb_hi[l];
   double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
-  double rho = 1.0 / sigma, rho_new;
-  const float c0 = (float)(1.0 / theta);
-  const float *dv = h->dinvf[l];
+  double rho = 1.0 / sigma, rho_new, coef;
+  const double *dv = h->dinv[l];
   float *r = (float *)malloc(N * sizeof(float));
   float *d = (float *)malloc(N * sizeof(float));
   float *t = (float *)malloc(N * sizeof(float));
@@ -840,25 +846,30 @@ static int cheb_smooth_f(const ohier *h, int l, int bf16, int m, const float *b,
     spmm_f(h, l, 0, bf16, m, x, t);
     for (e = 0; e < N; ++e) r[e] = b[e] - t[e];
   }
-  for (i = 0; i < A->n; ++i)
+  coef = 1.0 / theta;
+  for (i = 0; i < A->n; ++i) {
+    const float w = (float)(coef * dv[i]);
     for (j = 0; j < m; ++j) {
       e = (size_t)i * m + j;
-      d[e] = c0 * (dv[i] * r[e]);
+      d[e] = w * r[e];
       x[e] = x[e] + d[e];
     }
+  }
   for (k = 1; k < steps; ++k) {
-    float c1, c2;
+    float c1;
     spmm_f(h, l, 0, bf16, m, d, t);
     for (e = 0; e < N; ++e) r[e] = r[e] - t[e];
     rho_new = 1.0 / (2.0 * sigma - rho);
     c1 = (float)(rho_new * rho);
-    c2 = (float)(2.0 * rho_new / delta);
-    for (i = 0; i < A->n; ++i)
+    coef = 2.0 * rho_new / delta;
+    for (i = 0; i < A->n; ++i) {
+      const float w = (float)(coef * dv[i]);
       for (j = 0; j < m; ++j) {
         e = (size_t)i * m + j;
-        d[e] = c1 * d[e] + c2 * (dv[i] * r[e]);
+        d[e] = c1 * d[e] + w * r[e];
         x[e] = x[e] + d[e];
       }
+    }
     rho = rho_new;
   }
   if (r_out) {

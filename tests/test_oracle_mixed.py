@@ -118,3 +118,54 @@ def test_flexible_pcg_iterations_and_accuracy():
         r = h.pcg(B, tol=1e-8, prec=prec)
         assert np.all(r.status == 0) and np.all(r.relres <= 1e-8)
         assert np.all(r.iters <= r64.iters + (1 if prec == 1 else 3))
+
+
+def _rn32(q):
+    """Nearest FP32 value of the rational q, ties to even (normal range)."""
+    from fractions import Fraction
+    if q == 0:
+        return 0.0
+    sgn = -1 if q < 0 else 1
+    a = abs(q)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    elif Fraction(2) ** (e + 1) <= a:
+        e += 1
+    assert -126 <= e <= 127
+    m = a / Fraction(2) ** (e - 23)              # in [2^23, 2^24)
+    f = m.numerator // m.denominator
+    rem = m - f
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and f % 2 == 1):
+        f += 1
+    return sgn * float(Fraction(f) * Fraction(2) ** (e - 23))
+
+
+def test_fp32_accumulation_is_one_rounding_per_term_in_storage_order():
+    # reading R9: each term of a row product is added with one rounding (a
+    # fused multiply-add), in the row's storage order.  Brute force with exact
+    # rational arithmetic and an independent round-to-nearest-even, on the
+    # non-integer values of a Galerkin level and of P and R
+    from fractions import Fraction
+    A, h = fine_hier(8)
+    rng = np.random.default_rng(5)
+    separate_differs = False
+    for l, which in [(1, 0), (0, 1), (0, 2)]:
+        lv = h.level(l)
+        rp, ci, v = lv.A if which == 0 else (lv.P if which == 1 else lv.R)
+        ncols = h.level(l + 1).n if which == 1 else lv.n
+        X = rng.standard_normal((ncols, 2)).astype(np.float32)
+        Y = h.spmm_f(l, which, X)
+        v32 = v.astype(np.float32)
+        for i in range(0, len(rp) - 1, 7):
+            for j in range(2):
+                y = Fraction(0)
+                ys = np.float32(0)
+                for p in range(rp[i], rp[i + 1]):
+                    term = Fraction(float(v32[p])) * Fraction(float(X[ci[p], j]))
+                    y = Fraction(_rn32(term + y))
+                    ys = np.float32(ys + np.float32(v32[p] * X[ci[p], j]))
+                assert Y[i, j] == np.float32(float(y)), (l, which, i, j)
+                separate_differs |= bool(ys != Y[i, j])
+    # the check can tell a fused chain from a multiply-then-add chain
+    assert separate_differs
