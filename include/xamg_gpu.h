@@ -266,6 +266,62 @@ int xamg_solve_host(xamg_hier *h, const double *B, double *X, int32_t m, double 
 int xamg_level_spmm(xamg_hier *h, int32_t level, int32_t which, const double *X, double *Y,
                     int32_t m, void *stream);
 
+/* Y = M X on level `level` in the reduced precision `precond`
+ * (XAMG_PREC_FP32: FP32 values of M; XAMG_PREC_BF16: for M = A the bf16
+ * values with their FP32 row scales, y_i = s_i (sum_k q_ik x_k), and FP32
+ * values of P and R): the product of the preconditioner's V-cycle (paper
+ * Sec. 2.3, "mixed-precision" and index compression), with the same split and
+ * 16-bit index choice the V-cycle makes for blocks of pad(m) columns.  X is
+ * rounded to FP32 (exactly, when it holds FP32 values), every term is added
+ * to the FP32 row sum with one rounding, and the FP32 result is widened into
+ * Y.  which, level, X and Y as for xamg_level_spmm: DEVICE FP64 row-major
+ * blocks with m columns, 1 <= m <= XAMG_MAX_RHS, caller-owned.  The first
+ * reduced-precision call uploads the FP32/bf16 copies of the hierarchy.
+ * Errors: INVALID_ARG (bad level, operator, m or precond), CUDA, OOM. */
+int xamg_level_spmm_precond(xamg_hier *h, int32_t precond, int32_t level, int32_t which,
+                            const double *X, double *Y, int32_t m, void *stream);
+
+/* Fused coarse tail of the V(1,1) cycle (on by default, max_elems = 131072).
+ * The levels whose n x pad(m) blocks hold at most max_elems elements -- from
+ * the first such level down to the coarsest and back up to its first
+ * post-smoothing step, at most ten levels, blocks of two or more columns,
+ * two Chebyshev steps -- run as one cooperative kernel launch with a
+ * grid-wide barrier between stages (paper Sec. 2.1: the V-cycle; the fusion
+ * is this library's).  Each stage computes exactly what its separate launch
+ * would, so results are bitwise those of the unfused cycle; small systems,
+ * whose cycles are bound by launch latency, gain the most.  max_elems = 0
+ * turns the fusion off.  Every barrier wait is bounded by wait_limit_s
+ * seconds (0 < wait_limit_s <= 60; default 2): a wait that runs out ends the
+ * kernel, and the solve or V-cycle returns XAMG_ERR_TIMEOUT (X then holds no
+ * meaningful result; the device stays usable).  extra_arrivals > 0 adds
+ * arrivals that never come to every barrier: fault injection for testing
+ * the bounded waits (0 in normal use).  Drops the cached CUDA graphs.  Host
+ * only.  Errors: INVALID_ARG. */
+int xamg_set_tail(xamg_hier *h, int64_t max_elems, double wait_limit_s, int32_t extra_arrivals);
+
+/* First level of the fused coarse tail for blocks of pad(m) columns, or -1
+ * when the cycle runs unfused, written to *first_level.  Host only.
+ * Errors: INVALID_ARG. */
+int xamg_tail_info(const xamg_hier *h, int32_t m, int32_t *first_level);
+
+/* 16-bit column indices of the reduced-precision products (paper Sec. 2.3:
+ * CSR index types reduced to uint16_t), off by default: on GB300 the decode
+ * lengthens each row's index -> operand-gather chain by more than the two
+ * bytes per entry it saves, measured at every block width.  Each operator that
+ * fits the segmented form -- rows cut into tiles of 32, each tile with at
+ * most four segment bases that cover every column of its rows within 65535
+ * -- stores its columns as 16-bit offsets and is read that way by blocks of
+ * two or more columns; decoding is exact, so results do not depend on the
+ * setting.  enable = 0 reads the 32-bit indices everywhere (it drops the
+ * cached CUDA graphs).  Host only.  No counterpart of the switch in the
+ * paper. */
+int xamg_set_index16(xamg_hier *h, int32_t enable);
+
+/* Which operators of level `level` have 16-bit column indices: bit 0 = A,
+ * bit 1 = P, bit 2 = R, written to *mask.  Uploads the reduced-precision
+ * copies of the hierarchy on first use.  Errors: INVALID_ARG, CUDA, OOM. */
+int xamg_index16_info(xamg_hier *h, int32_t level, int32_t *mask);
+
 /* Chebyshev smoothing on level `level` (< levels-1): cheb_steps steps on X
  * for right-hand side B.  x_zero = 1 takes X = 0 on entry (pre-smoothing)
  * and then, if R is not NULL, writes the residual B - A X after the last
@@ -297,7 +353,8 @@ int xamg_coarse_solve(xamg_hier *h, const double *B, double *X, int32_t m, void 
  * n x m row-major blocks (the paper's "blas" dot products, Sec. 2.3), into the
  * DEVICE array out[m].  The sum is reduced in a fixed order, so repeated
  * calls give identical bits.  Allocates (and frees) its own device scratch
- * for the per-block partial sums. */
+ * for the per-block partial sums.  A CUDA error that earlier work left
+ * pending in the runtime is reported as XAMG_ERR_CUDA (and cleared). */
 int xamg_coldot(const double *U, const double *V, int64_t n, int32_t m, double *out,
                 void *stream);
 
@@ -315,7 +372,11 @@ int xamg_coldot(const double *U, const double *V, int64_t n, int32_t m, double *
  * [1, XAMG_MAX_RHS] (else XAMG_ERR_INVALID_ARG, nothing launched).  The call
  * makes no cudaMalloc, cudaFree or other allocating call.  Its first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current); make that first call before any stream capture.  All
+ * device current); make that first call before any stream capture.  The
+ * address is kept for the life of the process, so the library must not be
+ * used across a cudaDeviceReset of that device.  A CUDA error that earlier
+ * work left pending in the runtime is reported by this call as
+ * XAMG_ERR_CUDA (and cleared), like any launch error of its own.  All
  * calls share the array and it keeps the last call's contents: calls whose
  * device work overlaps (other streams, other threads) race on it and must be
  * serialised by the caller.  Results are reduced in a fixed order; they may

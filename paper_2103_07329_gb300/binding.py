@@ -41,7 +41,8 @@ EXPORTS = [
     "xamg_setup_hierarchy", "xamg_destroy", "xamg_hier_save", "xamg_hier_load", "xamg_hier_info",
     "xamg_level_info",
     "xamg_level_export", "xamg_coarse_export", "xamg_workspace_bytes", "xamg_solve",
-    "xamg_solve_host", "xamg_level_spmm", "xamg_smooth", "xamg_vcycle", "xamg_vcycle_precond",
+    "xamg_solve_host", "xamg_level_spmm", "xamg_level_spmm_precond", "xamg_set_index16",
+    "xamg_index16_info", "xamg_set_tail", "xamg_tail_info", "xamg_smooth", "xamg_vcycle", "xamg_vcycle_precond",
     "xamg_coarse_solve",
     "xamg_coldot", "xamg_timing_enable", "xamg_timing_read", "xamg_kernel_launches",
     "xamg_coldot_noalloc",
@@ -130,6 +131,11 @@ def _load():
         "xamg_solve_host": ([vp, vp, vp, i32, dbl, i32, C.POINTER(SolveOptsT), C.POINTER(StatsT)],
                             C.c_int),
         "xamg_level_spmm": ([vp, i32, i32, vp, vp, i32, vp], C.c_int),
+        "xamg_level_spmm_precond": ([vp, i32, i32, i32, vp, vp, i32, vp], C.c_int),
+        "xamg_set_index16": ([vp, i32], C.c_int),
+        "xamg_index16_info": ([vp, i32, C.POINTER(i32)], C.c_int),
+        "xamg_set_tail": ([vp, i64, dbl, i32], C.c_int),
+        "xamg_tail_info": ([vp, i32, C.POINTER(i32)], C.c_int),
         "xamg_smooth": ([vp, i32, vp, vp, vp, i32, i32, vp], C.c_int),
         "xamg_vcycle": ([vp, vp, vp, i32, vp], C.c_int),
         "xamg_vcycle_precond": ([vp, i32, vp, vp, i32, vp], C.c_int),
@@ -379,6 +385,33 @@ class Hierarchy:
         m = X.shape[1]
         _check(_load().xamg_level_spmm(self._h, level, which, _ptr(X), _ptr(Y), m, _stream(stream)),
                "xamg_level_spmm")
+
+    def spmm_precond(self, precond: int, level: int, which: int, X, Y, stream=None):
+        """xamg_level_spmm_precond: the reduced-precision product of the
+        V-cycle (FP64 blocks in and out, FP32 inside)."""
+        m = X.shape[1]
+        _check(_load().xamg_level_spmm_precond(self._h, precond, level, which, _ptr(X), _ptr(Y), m,
+                                               _stream(stream)), "xamg_level_spmm_precond")
+
+    def set_tail(self, max_elems: int = 131072, wait_limit_s: float = 2.0, extra_arrivals: int = 0):
+        """xamg_set_tail: the fused coarse tail of the V-cycle (0 turns it off)."""
+        _check(_load().xamg_set_tail(self._h, max_elems, wait_limit_s, extra_arrivals), "xamg_set_tail")
+
+    def tail_info(self, m: int) -> int:
+        """xamg_tail_info: first level of the fused tail for pad(m) columns, or -1."""
+        f = C.c_int32()
+        _check(_load().xamg_tail_info(self._h, m, C.byref(f)), "xamg_tail_info")
+        return f.value
+
+    def set_index16(self, on: bool = True):
+        """xamg_set_index16: 16-bit column indices of the reduced-precision products on or off."""
+        _check(_load().xamg_set_index16(self._h, 1 if on else 0), "xamg_set_index16")
+
+    def index16_info(self, level: int) -> int:
+        """xamg_index16_info: bit mask of level's operators (A 1, P 2, R 4) with 16-bit indices."""
+        mk = C.c_int32()
+        _check(_load().xamg_index16_info(self._h, level, C.byref(mk)), "xamg_index16_info")
+        return mk.value
 
     def smooth(self, level: int, B, X, R=None, x_zero=True, stream=None):
         m = B.shape[1]

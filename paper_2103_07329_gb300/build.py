@@ -37,12 +37,13 @@ def sources():
                                             "rowsf_nv8.cu", "rowsf_nv16.cu", "rowsf_nv32.cu",
                                             "net.cu", "batch.cu", "batch_stage1.cu",
                                             "batch_stage2.cu", "batch_stage3.cu",
-                                            "bicg_variants.cu")]
+                                            "bicg_variants.cu", "vtail_f64.cu", "vtail_f32.cu")]
 
 
 def _deps():
     return sources() + [os.path.join(CSRC, f) for f in ("hier_host.h", "launch.h", "kernels.cuh",
                                                               "rows_inst.cuh", "elem.cuh", "batch.h",
+                                                              "vtail.cuh", "vtail_kern.cuh",
                                                               "batch_stage.cuh")] + [
         os.path.join(ROOT, "include", "xamg_gpu.h")]
 

@@ -307,7 +307,7 @@ void compute_grids(xamg_batch *b) {
   b->g_post0 = stage_grid(b, BS_POST2_DOT2, 0);
   int64_t emax = 1;
   for (const BSys &S : b->sys_h) emax = std::max<int64_t>(emax, S.n0 * S.nv);
-  b->g_elem = (int)std::max<int64_t>(1, std::min<int64_t>((emax + kBlock - 1) / kBlock, (int64_t)device_sm_count() * 8));
+  b->g_elem = (int)std::max<int64_t>(1, std::min<int64_t>((emax + kBlock - 1) / kBlock, std::min<int64_t>((int64_t)device_sm_count() * 8, kMaxGrid)));
 }
 
 template <class TB>

@@ -7,12 +7,14 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
 #include "batch.h"
 #include "hier_host.h"
 #include "launch.h"
+#include "vtail.cuh"
 
 using namespace xamg;
 
@@ -34,8 +36,12 @@ struct DevLevel {
   float *a32 = nullptr, *p32 = nullptr, *r32 = nullptr;
   __nv_bfloat16 *a16 = nullptr;  // bf16(fl32(a_ij) / s_i)
   float *a16s = nullptr;         // s_i = fl32(max_j |a_ij|)
-  uint16_t *a16w = nullptr;      // low 16 bits of A's columns (if every row fits two windows)
-  uint32_t *a16meta = nullptr;   // per row: first window << 16 | entries in it
+  // 16-bit column indices of A, P, R (index 0, 1, 2) in the segmented form
+  // of kernels.cuh (offsets, row boundaries, tile bases), where the operator
+  // fits it (else null)
+  uint16_t *w16[3] = {nullptr, nullptr, nullptr};
+  uint32_t *m16[3] = {nullptr, nullptr, nullptr};
+  int32_t *t16[3] = {nullptr, nullptr, nullptr};
   float *w32[4] = {nullptr, nullptr, nullptr, nullptr};
   float c1f[4] = {0, 0, 0, 0};
   // row split of the sparse products chosen by xamg_autotune, per values
@@ -121,6 +127,9 @@ struct xamg_hier {
   Flags *flags_h = nullptr;   // mapped pinned counters
   Flags *flags_d = nullptr;
   bool lowp_ready = false;    // reduced-precision copies uploaded
+  // 16-bit column indices in the reduced-precision products (off by default:
+  // measured slower at every block width, xamg_set_index16)
+  bool use_idx16 = false;
   bool timing = false;
   std::vector<TimerRec> pending;
   std::vector<cudaEvent_t> event_pool;
@@ -130,6 +139,20 @@ struct xamg_hier {
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
   std::vector<GraphRec> graphs;
+  // fused coarse tail of the V-cycle (vtail.cuh): levels whose blocks hold at
+  // most tail_elems elements (rows x block width) run as one cooperative
+  // launch; 0 turns it off.  tail_limit_s bounds each grid-barrier wait;
+  // tail_extra is added to the barrier's expected arrivals (fault injection)
+  int64_t tail_elems = 131072;
+  double tail_limit_s = 2.0;
+  int tail_extra = 0;
+  TailSync *tail_sync = nullptr;  // device barrier words
+  // while a tail program is being recorded: the program (TailProg<TB> of the
+  // recording vcycle's block scalar) and whether every stage fit it
+  void *rec = nullptr;
+  bool rec_ok = true;
+  std::unique_ptr<TailProg<double>> tp64;
+  std::unique_ptr<TailProg<float>> tp32;
 };
 
 namespace {
@@ -226,6 +249,62 @@ int upload_level(xamg_hier *h, int l) {
   return XAMG_OK;
 }
 
+// 16-bit column indices of one operator in the segmented form of
+// kernels.cuh (seg16_col; paper Sec. 2.3: CSR index types reduced to
+// uint16_t).  Each tile of kSegTile rows takes its segment bases greedily
+// over the sorted columns of its rows: a base is the first column not covered
+// by the previous segment [b, b + 65535].  The operator keeps its 32-bit
+// indices (*w, *m, *tb stay null) when a tile needs more than kSegs
+// segments or a row's boundary lies at an entry position beyond 1022.
+int upload_idx16(xamg_hier *h, const HostCsr &M, uint16_t **w, uint32_t **m, int32_t **tb) {
+  *w = nullptr;
+  *m = nullptr;
+  *tb = nullptr;
+  if (M.n == 0 || M.col.empty()) return XAMG_OK;
+  const int tiles = (M.n + kSegTile - 1) / kSegTile;
+  std::vector<uint16_t> off(M.col.size());
+  std::vector<uint32_t> meta((size_t)M.n);
+  std::vector<int32_t> base((size_t)tiles * kSegs, 0);
+  std::vector<int32_t> cols;
+  for (int t = 0; t < tiles; ++t) {
+    const int r0 = t * kSegTile, r1 = std::min(M.n, r0 + kSegTile);
+    cols.assign(M.col.begin() + M.rowptr[r0], M.col.begin() + M.rowptr[r1]);
+    std::sort(cols.begin(), cols.end());
+    int nseg = 0;
+    int32_t *b = &base[(size_t)t * kSegs];
+    for (int32_t c : cols) {
+      if (nseg == 0 || (int64_t)c - b[nseg - 1] > 65535) {
+        if (nseg == kSegs) return XAMG_OK;
+        b[nseg++] = c;
+      }
+    }
+    for (int s = std::max(nseg, 1); s < kSegs; ++s) b[s] = b[s - 1];
+    for (int i = r0; i < r1; ++i) {
+      uint32_t e[3] = {(uint32_t)kSegNone, (uint32_t)kSegNone, (uint32_t)kSegNone};
+      int seg = 0;
+      // a row past position 1022 decodes as segment 0 only when the tile has
+      // one segment
+      if (nseg > 1 && M.rowptr[i + 1] - M.rowptr[i] > kSegNone) return XAMG_OK;
+      for (int p = M.rowptr[i]; p < M.rowptr[i + 1]; ++p) {
+        const int k = p - M.rowptr[i];
+        while (seg + 1 < nseg && M.col[p] >= b[seg + 1]) {
+          ++seg;
+          if (k >= kSegNone) return XAMG_OK;
+          e[seg - 1] = (uint32_t)k;  // entries before k lie below segment seg
+        }
+        off[p] = (uint16_t)(M.col[p] - b[seg]);
+      }
+      // a boundary that no entry of the row crosses stays kSegNone, above
+      // every position of the row
+      meta[i] = e[0] | e[1] << 10 | e[2] << 20;
+    }
+  }
+  int rc;
+  if ((rc = dev_upload(h, w, off.data(), off.size())) != XAMG_OK) return rc;
+  if ((rc = dev_upload(h, m, meta.data(), meta.size())) != XAMG_OK) return rc;
+  return dev_upload(h, tb, base.data(), base.size());
+}
+
 // Reduced-precision copies of the hierarchy for the FP32-block preconditioner:
 // fl32 of every value of A, P, R; bf16 values of A relative to the row scale
 // s_i = fl32(max_j |a_ij|), q_ij = bf16_rne(fl32(a_ij) / s_i); the Chebyshev
@@ -252,37 +331,15 @@ int upload_lowp(xamg_hier *h) {
     if (q.size() & 1) q.push_back(__float2bfloat16_rn(0.0f));
     if ((rc = dev_upload(h, &D.a16, q.data(), q.size())) != XAMG_OK) return rc;
     if ((rc = dev_upload(h, &D.a16s, s.data(), s.size())) != XAMG_OK) return rc;
-    // 16-bit column indices: usable when every row's columns lie in two
-    // consecutive windows of 65536 columns (and a row has < 65536 entries in
-    // its first window); otherwise the level keeps its 32-bit indices
-    {
-      std::vector<uint16_t> lw(H.A.col.size());
-      std::vector<uint32_t> meta((size_t)H.A.n);
-      bool ok = true;
-      for (int i = 0; i < H.A.n && ok; ++i) {
-        const int p0 = H.A.rowptr[i], p1 = H.A.rowptr[i + 1];
-        const uint32_t hw = p1 > p0 ? (uint32_t)H.A.col[p0] >> 16 : 0u;
-        uint32_t split = 0;
-        for (int p = p0; p < p1; ++p) {
-          const uint32_t w = (uint32_t)H.A.col[p] >> 16;
-          if (w == hw) ++split;
-          else if (w != hw + 1) ok = false;
-          lw[p] = (uint16_t)(H.A.col[p] & 0xffff);
-        }
-        if (split > 0xffffu || hw > 0xffffu) ok = false;
-        meta[i] = hw << 16 | split;
-      }
-      if (ok) {
-        if ((rc = dev_upload(h, &D.a16w, lw.data(), lw.size())) != XAMG_OK) return rc;
-        if ((rc = dev_upload(h, &D.a16meta, meta.data(), meta.size())) != XAMG_OK) return rc;
-      }
-    }
+    if ((rc = upload_idx16(h, H.A, &D.w16[0], &D.m16[0], &D.t16[0])) != XAMG_OK) return rc;
     if (l + 1 == L) continue;
     std::vector<float> pf(H.P.val.size()), rf(H.R.val.size());
     for (size_t k = 0; k < pf.size(); ++k) pf[k] = (float)H.P.val[k];
     for (size_t k = 0; k < rf.size(); ++k) rf[k] = (float)H.R.val[k];
     if ((rc = dev_upload(h, &D.p32, pf.data(), pf.size())) != XAMG_OK) return rc;
     if ((rc = dev_upload(h, &D.r32, rf.data(), rf.size())) != XAMG_OK) return rc;
+    if ((rc = upload_idx16(h, H.P, &D.w16[1], &D.m16[1], &D.t16[1])) != XAMG_OK) return rc;
+    if ((rc = upload_idx16(h, H.R, &D.w16[2], &D.m16[2], &D.t16[2])) != XAMG_OK) return rc;
     const double theta = 0.5 * (H.hi + H.lo), delta = 0.5 * (H.hi - H.lo), sigma = theta / delta;
     double rho = 1.0 / sigma;
     std::vector<float> w(H.dinv.size());
@@ -517,7 +574,7 @@ double row_bytes(const DevCsr &M, const RowOpT<TB> &op, int nv, double val_bytes
   const double idx_bytes = op.colw ? 2.0 : 4.0;
   double b = (idx_bytes + val_bytes) * (double)M.nnz + 4.0 * (M.n + 1) + (double)M.ncols * nv * sizeof(TB);
   if (op.rscale) b += 4.0 * M.n;
-  if (op.rowmeta) b += 4.0 * M.n;
+  if (op.rowmeta) b += 4.0 * M.n + 16.0 * ((M.n + kSegTile - 1) / kSegTile);
   if (op.init) b += blk;
   if (op.y) b += blk;
   if (op.dp) b += blk;
@@ -546,20 +603,52 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
     op.rscale = nullptr;
   } else {
     vbytes = 4.0;
+    // 16-bit column indices (wider blocks; m = 1 reads the 32-bit ones)
+    const bool i16 = h->use_idx16 && D.w16[which] && nv > 1;
+    if (i16) {
+      op.colw = D.w16[which];
+      op.rowmeta = D.m16[which];
+      op.tbase = D.t16[which];
+    }
     if (which == 0 && prec == XAMG_PREC_BF16) {
       op.val = D.a16;
       op.rscale = D.a16s;
-      vt = 1;
+      vt = i16 ? 2 : 1;
       vbytes = 2.0;
-      if (D.a16w && nv > 1) {
-        op.colw = D.a16w;
-        op.rowmeta = D.a16meta;
-        vt = 2;
-      }
     } else {
       op.val = which == 0 ? D.a32 : which == 1 ? D.p32 : D.r32;
       op.rscale = nullptr;
+      vt = i16 ? 3 : 0;
     }
+  }
+  if (h->rec) {
+    // recording a tail program: the stage runs later inside the cooperative
+    // kernel, with the split this launch would take and 32-bit indices
+    int sl = slices_for(M, nv, sizeof(TB) == 4);
+    int lg = 0;
+    while ((1 << lg) < nv) ++lg;
+    const int t = D.split[sizeof(TB) == 8 ? 2 : ((vt == 1 || vt == 2) ? 1 : 0)][which][lg];
+    if (t >= 0) sl = split_slices(nv, t);
+    op.colw = nullptr;
+    op.rowmeta = nullptr;
+    op.tbase = nullptr;
+    int kind = -1;
+    if (which == 0 && neg && epi == EPI_Y_DN) kind = TK_A_YDN;
+    else if (which == 0 && neg && epi == EPI_Y_XDP) kind = TK_A_YXDP;
+    else if (which == 0 && neg && epi == EPI_Y_D0) kind = TK_A_YD0;
+    else if (which == 0 && neg && epi == EPI_XLAST) kind = TK_A_XLAST;
+    else if (which != 0 && !neg && epi == EPI_Y) kind = TK_PR_Y;
+    else if (which == 2 && !neg && epi == EPI_Y_D0) kind = TK_PR_YD0;
+    TailProg<TB> *prog = static_cast<TailProg<TB> *>(h->rec);
+    if (kind < 0 || nv < 2 || prog->nstages >= kTailMaxStages) {
+      h->rec_ok = false;
+      return 1;
+    }
+    TailStage<TB> &s = prog->st[prog->nstages++];
+    s.op = op;
+    s.kind = kind;
+    s.wide = sl > 1 ? 1 : 0;
+    return 1;
   }
   cudaEvent_t a = nullptr, b = nullptr;
   if (h->timing) {
@@ -579,7 +668,7 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
     int sl = slices_for(M, nv, true);
     int lg = 0;
     while ((1 << lg) < nv) ++lg;
-    const int t = D.split[vt ? 1 : 0][which][lg];
+    const int t = D.split[(vt == 1 || vt == 2) ? 1 : 0][which][lg];
     if (t >= 0) sl = split_slices(nv, t);
     g = launch_rows_f(op, nv, sl, neg, epi, vt, st);
   }
@@ -637,20 +726,25 @@ struct Dots {
   int *grid = nullptr;
 };
 
-// Post-smoothing of x (r is scratch).
+// Post-smoothing of x (r is scratch), in two parts: the first step (r = b -
+// A x, d_0 = w_0 r), then the rest (the fused coarse tail ends between them).
 template <class TB>
-int postsmooth(xamg_hier *h, Work &W, int prec, int l, const TB *b, TB *x, TB *r, cudaStream_t st,
-               const Dots &dots) {
+int postsmooth_first(xamg_hier *h, Work &W, int prec, int l, const TB *b, TB *x, TB *r, cudaStream_t st) {
+  using BL = Blocks<TB>;
+  const DevLevel &D = h->lv[l];
+  RowOpT<TB> o = blank<TB>();
+  o.init = b; o.src = x; o.y = r; o.w = BL::w(D, 0); o.dnext = BL::d(W, l);
+  return rows<TB>(h, l, 0, prec, o, W.nv, true, EPI_Y_D0, st) < 0 ? XAMG_ERR_CUDA : XAMG_OK;
+}
+
+template <class TB>
+int postsmooth_rest(xamg_hier *h, Work &W, int prec, int l, TB *x, TB *r, cudaStream_t st,
+                    const Dots &dots) {
   using BL = Blocks<TB>;
   const int nv = W.nv;
   const int s = h->host.cheb_steps;
   const DevLevel &D = h->lv[l];
   TB *dA = BL::d(W, l), *dB = BL::d2(W, l);
-  {
-    RowOpT<TB> o = blank<TB>();
-    o.init = b; o.src = x; o.y = r; o.w = BL::w(D, 0); o.dnext = dA;
-    if (rows<TB>(h, l, 0, prec, o, nv, true, EPI_Y_D0, st) < 0) return XAMG_ERR_CUDA;
-  }
   if (s == 1) {
     const int g = elem_grid(D.A.n, nv);
     if constexpr (sizeof(TB) == 8) {
@@ -693,6 +787,93 @@ int postsmooth(xamg_hier *h, Work &W, int prec, int l, const TB *b, TB *x, TB *r
   return XAMG_OK;
 }
 
+// ---- fused coarse tail (vtail.cuh) ----
+// First level of the tail for blocks of nv columns: the smallest l such that
+// every level from l down holds at most tail_elems block elements, with at
+// least one level above the coarsest and its stages within kTailMaxStages;
+// -1: no tail (off, m = 1, or a smoother other than two Chebyshev steps).
+int tail_start(const xamg_hier *h, int nv) {
+  const int L = (int)h->lv.size();
+  // (timing measures the unfused row launches, so it takes the plain cycle)
+  if (h->tail_elems <= 0 || h->timing || nv < 2 || h->host.cheb_steps != 2 || L < 2) return -1;
+  int l = L - 1;
+  while (l > 0 && (int64_t)h->lv[l - 1].A.n * nv <= h->tail_elems && 6 * (L - l) <= kTailMaxStages) --l;
+  return l <= L - 2 ? l : -1;
+}
+
+template <class TB> TailProg<TB> &tail_prog(xamg_hier *h);
+template <> TailProg<double> &tail_prog<double>(xamg_hier *h) {
+  if (!h->tp64) h->tp64.reset(new TailProg<double>());
+  return *h->tp64;
+}
+template <> TailProg<float> &tail_prog<float>(xamg_hier *h) {
+  if (!h->tp32) h->tp32.reset(new TailProg<float>());
+  return *h->tp32;
+}
+
+template <class TB>
+int vcycle(xamg_hier *h, Work &W, int prec, int l, const TB *b, TB *x, cudaStream_t st,
+           const Dots &dots);
+
+// The cycle from level l with its coarse part fused: the stages from the
+// pre-smoothing of l down to the coarsest and back up to the first
+// post-smoothing step of l are recorded (rows() in record mode) and run as one
+// cooperative launch; the last post-smoothing step of l, which may carry the
+// caller's dots, is launched as usual.  XAMG_ERR_SETUP: a stage did not fit
+// the tail program (nothing was launched).
+template <class TB>
+int vcycle_tail(xamg_hier *h, Work &W, int prec, int l, const TB *b, TB *x, cudaStream_t st,
+                const Dots &dots) {
+  using BL = Blocks<TB>;
+  const int nv = W.nv;
+  if (!h->tail_sync) {
+    void *p = nullptr;
+    XCK(cudaMalloc(&p, sizeof(TailSync)));
+    h->owned.push_back(p);
+    h->tail_sync = static_cast<TailSync *>(p);
+  }
+  TailProg<TB> &prog = tail_prog<TB>(h);
+  prog.nstages = 0;
+  prog.extra = h->tail_extra;
+  prog.limit_ns = (unsigned long long)(h->tail_limit_s * 1e9);
+  prog.sync = h->tail_sync;
+  prog.err_host = &h->flags_d->tail_err;
+  h->rec = &prog;
+  h->rec_ok = true;
+  TB *r = BL::r(W, l);
+  int rc = presmooth<TB>(h, W, prec, l, b, x, r, st);
+  if (rc == XAMG_OK) {
+    const bool next_coarsest = l + 2 == (int)h->lv.size();
+    RowOpT<TB> o = blank<TB>();
+    o.src = r; o.y = BL::b(W, l + 1);
+    if (!next_coarsest) {
+      o.w = BL::w(h->lv[l + 1], 0);
+      o.dnext = BL::x(W, l + 1);
+    }
+    rows<TB>(h, l, 2, prec, o, nv, false, next_coarsest ? EPI_Y : EPI_Y_D0, st);
+    rc = vcycle<TB>(h, W, prec, l + 1, BL::b(W, l + 1), BL::x(W, l + 1), st, Dots());
+  }
+  if (rc == XAMG_OK) {
+    RowOpT<TB> o = blank<TB>();
+    o.init = x; o.src = BL::x(W, l + 1); o.y = x;
+    rows<TB>(h, l, 1, prec, o, nv, false, EPI_Y, st);
+    rc = postsmooth_first<TB>(h, W, prec, l, b, x, r, st);
+  }
+  h->rec = nullptr;
+  if (rc != XAMG_OK) return rc;
+  if (!h->rec_ok) return XAMG_ERR_SETUP;
+  XCK(cudaMemsetAsync(h->tail_sync, 0, sizeof(TailSync), st));
+  int g;
+  if constexpr (sizeof(TB) == 8) {
+    g = launch_vtail_f64(prog, nv, st);
+  } else {
+    g = launch_vtail_f32(prog, nv, prec == XAMG_PREC_BF16 ? 1 : 0, st);
+  }
+  if (g < 0) return XAMG_ERR_CUDA;
+  if ((rc = postsmooth_rest<TB>(h, W, prec, l, x, r, st, dots)) != XAMG_OK) return rc;
+  return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
+}
+
 // ---- V(1,1) Chebyshev cycle ----
 // On entry x holds w0 .* b (the first smoother iterate) unless `level` is the
 // coarsest.  TB = double: the FP64 preconditioner; TB = float: the
@@ -706,6 +887,22 @@ int vcycle(xamg_hier *h, Work &W, int prec, int l, const TB *b, TB *x, cudaStrea
   const int L = (int)h->lv.size();
   if (l == L - 1) {
     const int nc = h->host.nc;
+    if (h->rec) {
+      TailProg<TB> *prog = static_cast<TailProg<TB> *>(h->rec);
+      if (dots.part || prog->nstages >= kTailMaxStages) {
+        h->rec_ok = false;
+        return XAMG_OK;
+      }
+      TailStage<TB> &t = prog->st[prog->nstages++];
+      std::memset(&t.op, 0, sizeof(t.op));
+      t.op.n = nc;
+      t.op.val = h->ainv;
+      t.op.src = b;
+      t.op.y = x;
+      t.kind = TK_COARSE;
+      t.wide = 0;
+      return XAMG_OK;
+    }
     const double *xd;
     if constexpr (sizeof(TB) == 8) {
       launch_coarse(nv, nc, h->ainv, b, x, st);
@@ -722,6 +919,10 @@ int vcycle(xamg_hier *h, Work &W, int prec, int l, const TB *b, TB *x, cudaStrea
       *dots.grid = g;
     }
     return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
+  }
+  if (!h->rec && tail_start(h, nv) == l) {
+    const int rc = vcycle_tail<TB>(h, W, prec, l, b, x, st, dots);
+    if (rc != XAMG_ERR_SETUP) return rc;  // else: the tail does not fit; the plain cycle below
   }
   TB *r = BL::r(W, l);
   int rc = presmooth<TB>(h, W, prec, l, b, x, r, st);
@@ -746,8 +947,8 @@ int vcycle(xamg_hier *h, Work &W, int prec, int l, const TB *b, TB *x, cudaStrea
     o.init = x; o.src = BL::x(W, l + 1); o.y = x;
     if (rows<TB>(h, l, 1, prec, o, nv, false, EPI_Y, st) < 0) return XAMG_ERR_CUDA;
   }
-  rc = postsmooth<TB>(h, W, prec, l, b, x, r, st, dots);
-  if (rc != XAMG_OK) return rc;
+  if ((rc = postsmooth_first<TB>(h, W, prec, l, b, x, r, st)) != XAMG_OK) return rc;
+  if ((rc = postsmooth_rest<TB>(h, W, prec, l, x, r, st, dots)) != XAMG_OK) return rc;
   return cudaPeekAtLastError() == cudaSuccess ? XAMG_OK : XAMG_ERR_CUDA;
 }
 
@@ -1407,6 +1608,7 @@ int solve_impl(xamg_hier *h, const double *B, double *X, int m, double tol, int 
   int rc = ensure_workspace(h, c.nv, o.method, c.prec, &o, c.W);
   if (rc != XAMG_OK) return rc;
   h->flags_h->active = 0;
+  h->flags_h->tail_err = 0;
   if (o.method == XAMG_PCG)
     rc = c.prec == XAMG_PREC_FP64 ? solve_pcg(c, B, X, stats) : solve_fpcg(c, B, X, stats);
   else if (o.method == XAMG_BICGSTAB_REORDERED)
@@ -1418,6 +1620,11 @@ int solve_impl(xamg_hier *h, const double *B, double *X, int m, double tol, int 
   if (h->timing && rc < 0) {
     cudaStreamSynchronize(c.st);
     flush_timing(h);
+  }
+  if (h->flags_h->tail_err) {  // a grid-barrier wait of the fused tail ran out
+    cudaStreamSynchronize(c.st);
+    h->flags_h->tail_err = 0;
+    return XAMG_ERR_TIMEOUT;
   }
   return rc;
 }
@@ -1723,6 +1930,70 @@ int xamg_level_spmm(xamg_hier *h, int32_t level, int32_t which, const double *X,
   return XAMG_OK;
 }
 
+int xamg_level_spmm_precond(xamg_hier *h, int32_t precond, int32_t level, int32_t which, const double *X,
+                            double *Y, int32_t m, void *stream) {
+  if (!h || !h->on_device || !X || !Y || m < 1 || m > XAMG_MAX_RHS || level < 0 ||
+      level >= (int)h->lv.size() || which < 0 || which > 2)
+    return XAMG_ERR_INVALID_ARG;
+  if (which > 0 && level + 1 >= (int)h->lv.size()) return XAMG_ERR_INVALID_ARG;
+  if (precond != XAMG_PREC_FP32 && precond != XAMG_PREC_BF16) return XAMG_ERR_INVALID_ARG;
+  XCK(cudaSetDevice(h->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nv = pad_nv(m);
+  Work W;
+  // the level-0 FP32 blocks of the workspace hold the operand and the result
+  // (every level's operators have at most n_0 rows and columns)
+  int rc = ensure_workspace(h, nv, XAMG_PCG, precond, nullptr, W);
+  if (rc != XAMG_OK) return rc;
+  DevLevel &D = h->lv[level];
+  const DevCsr &M = which == 0 ? D.A : which == 1 ? D.P : D.R;
+  launch_pad_in(nv, M.ncols, X, m, W.Bn, elem_grid(M.ncols, nv), st);
+  launch_to_f32(nv, M.ncols, W.Bn, W.R32, nullptr, nullptr, elem_grid(M.ncols, nv), st);
+  RowOpF o = blank<float>();
+  o.src = W.R32;
+  o.y = W.Z32;
+  if (rows<float>(h, level, which, precond, o, nv, false, EPI_Y, st) < 0) return XAMG_ERR_CUDA;
+  launch_to_f64(nv, M.n, W.Z32, W.X, elem_grid(M.n, nv), st);
+  launch_copy_out(nv, M.n, W.X, Y, m, elem_grid(M.n, nv), st);
+  XCK(cudaStreamSynchronize(st));
+  XCK(cudaGetLastError());
+  if (h->timing) flush_timing(h);
+  return XAMG_OK;
+}
+
+int xamg_set_tail(xamg_hier *h, int64_t max_elems, double wait_limit_s, int32_t extra_arrivals) {
+  if (!h || max_elems < 0 || !(wait_limit_s > 0.0) || wait_limit_s > 60.0 || extra_arrivals < 0)
+    return XAMG_ERR_INVALID_ARG;
+  clear_graphs(h);  // the captured tail launches hold the old settings
+  h->tail_elems = max_elems;
+  h->tail_limit_s = wait_limit_s;
+  h->tail_extra = extra_arrivals;
+  return XAMG_OK;
+}
+
+int xamg_tail_info(const xamg_hier *h, int32_t m, int32_t *first_level) {
+  if (!h || !h->on_device || !first_level || m < 1 || m > XAMG_MAX_RHS) return XAMG_ERR_INVALID_ARG;
+  *first_level = tail_start(h, pad_nv(m));
+  return XAMG_OK;
+}
+
+int xamg_set_index16(xamg_hier *h, int32_t enable) {
+  if (!h) return XAMG_ERR_INVALID_ARG;
+  if (h->use_idx16 != (enable != 0)) clear_graphs(h);
+  h->use_idx16 = enable != 0;
+  return XAMG_OK;
+}
+
+int xamg_index16_info(xamg_hier *h, int32_t level, int32_t *mask) {
+  if (!h || !h->on_device || !mask || level < 0 || level >= (int)h->lv.size()) return XAMG_ERR_INVALID_ARG;
+  XCK(cudaSetDevice(h->device));
+  int rc = upload_lowp(h);
+  if (rc != XAMG_OK) return rc;
+  const DevLevel &D = h->lv[level];
+  *mask = (D.w16[0] ? 1 : 0) | (D.w16[1] ? 2 : 0) | (D.w16[2] ? 4 : 0);
+  return XAMG_OK;
+}
+
 int xamg_smooth(xamg_hier *h, int32_t level, const double *B, double *X, double *R, int32_t x_zero,
                 int32_t m, void *stream) {
   if (!h || !h->on_device || !B || !X || m < 1 || m > XAMG_MAX_RHS || level < 0 ||
@@ -1746,7 +2017,8 @@ int xamg_smooth(xamg_hier *h, int32_t level, const double *B, double *X, double 
     if (R) launch_copy_out(nv, n, r, R, m, ge, st);
   } else {
     launch_pad_in(nv, n, X, m, x, ge, st);
-    if ((rc = postsmooth<double>(h, W, XAMG_PREC_FP64, level, W.Bn, x, r, st, Dots())) != XAMG_OK)
+    if ((rc = postsmooth_first<double>(h, W, XAMG_PREC_FP64, level, W.Bn, x, r, st)) != XAMG_OK ||
+        (rc = postsmooth_rest<double>(h, W, XAMG_PREC_FP64, level, x, r, st, Dots())) != XAMG_OK)
       return rc;
   }
   launch_copy_out(nv, n, x, X, m, ge, st);
@@ -1759,6 +2031,7 @@ int xamg_smooth(xamg_hier *h, int32_t level, const double *B, double *X, double 
 int xamg_vcycle(xamg_hier *h, const double *B, double *X, int32_t m, void *stream) {
   if (!h || !h->on_device || !B || !X || m < 1 || m > XAMG_MAX_RHS) return XAMG_ERR_INVALID_ARG;
   XCK(cudaSetDevice(h->device));
+  h->flags_h->tail_err = 0;
   cudaStream_t st = (cudaStream_t)stream;
   const int nv = pad_nv(m);
   Work W;
@@ -1772,6 +2045,10 @@ int xamg_vcycle(xamg_hier *h, const double *B, double *X, int32_t m, void *strea
   launch_copy_out(nv, n, W.X, X, m, ge, st);
   XCK(cudaStreamSynchronize(st));
   XCK(cudaGetLastError());
+  if (h->flags_h->tail_err) {  // a grid-barrier wait of the fused tail ran out
+    h->flags_h->tail_err = 0;
+    return XAMG_ERR_TIMEOUT;
+  }
   if (h->timing) flush_timing(h);
   return XAMG_OK;
 }
@@ -1782,6 +2059,7 @@ int xamg_vcycle_precond(xamg_hier *h, int32_t precond, const double *B, double *
   if (precond == XAMG_PREC_FP64) return xamg_vcycle(h, B, X, m, stream);
   if (precond != XAMG_PREC_FP32 && precond != XAMG_PREC_BF16) return XAMG_ERR_INVALID_ARG;
   XCK(cudaSetDevice(h->device));
+  h->flags_h->tail_err = 0;
   cudaStream_t st = (cudaStream_t)stream;
   const int nv = pad_nv(m);
   Work W;
@@ -1796,6 +2074,10 @@ int xamg_vcycle_precond(xamg_hier *h, int32_t precond, const double *B, double *
   launch_copy_out(nv, n, W.X, X, m, ge, st);
   XCK(cudaStreamSynchronize(st));
   XCK(cudaGetLastError());
+  if (h->flags_h->tail_err) {  // a grid-barrier wait of the fused tail ran out
+    h->flags_h->tail_err = 0;
+    return XAMG_ERR_TIMEOUT;
+  }
   if (h->timing) flush_timing(h);
   return XAMG_OK;
 }

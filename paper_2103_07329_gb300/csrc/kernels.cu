@@ -14,20 +14,30 @@ namespace xamg {
 
 std::atomic<int64_t> g_launches{0};
 
+// SM count of the current device, cached per device ordinal (atomics: the
+// library may be called from several host threads).
 int device_sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-      sms = 1;
+  constexpr int kDevs = 64;
+  static std::atomic<int> cache[kDevs];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const int slot = dev >= 0 && dev < kDevs ? dev : -1;
+  if (slot >= 0) {
+    const int c = cache[slot].load(std::memory_order_relaxed);
+    if (c > 0) return c;
   }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  if (slot >= 0) cache[slot].store(sms, std::memory_order_relaxed);
   return sms;
 }
 
+// Elementwise grid: at most 8 blocks per SM and never more than kMaxGrid, the
+// block count the per-block partial-sum buffers are sized for.
 int elem_grid(int64_t n, int nv) {
   const int64_t need = (n * nv + kBlock - 1) / kBlock;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)device_sm_count() * 8));
+  const int64_t cap = std::min<int64_t>((int64_t)device_sm_count() * 8, kMaxGrid);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, cap));
 }
 
 // ------------------------------------------------------------------ rows
@@ -464,7 +474,8 @@ void launch_zero_rhs_cols(int nv, int64_t n, double *X, const ColState *cs, int 
 int coldot_rt_grid(int64_t n, int m) {
   const int per = kBlock / m;
   const int64_t need = (n + per - 1) / per;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)device_sm_count() * 8));
+  const int64_t cap = std::min<int64_t>((int64_t)device_sm_count() * 8, kMaxGrid);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, cap));
 }
 void launch_coldot_rt(int64_t n, int m, const double *U, const double *V, double *part, int grid,
                       cudaStream_t st) {

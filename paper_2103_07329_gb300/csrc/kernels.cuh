@@ -39,8 +39,9 @@ struct RowOpT {
   const int32_t *col;
   const void *val;       // matrix values (TV)
   const float *rscale;   // per-row scale of bf16 values
-  const uint16_t *colw;  // 16-bit column indices (Bf16Idx16)
-  const uint32_t *rowmeta;  // per row: first window << 16 | entries in it (Bf16Idx16)
+  const uint16_t *colw;     // 16-bit column offsets (Bf16Idx16, F32Idx16; see Seg16)
+  const uint32_t *rowmeta;  // per row: segment boundaries (Seg16)
+  const int32_t *tbase;     // per tile of kSegTile rows: kSegs segment bases (Seg16)
   const TB *src;
   const TB *init;
   TB *y;
@@ -116,6 +117,59 @@ __device__ __forceinline__ void block_colsum_store_vec(const double (&v)[VEC], d
   }
 }
 
+// Epilogue arithmetic.  FP64 blocks fuse it into FMAs (their bound is the
+// FP64 issue rate).  FP32 blocks round once per operation in the order the
+// Chebyshev recurrence is written -- t = sum_k m_ik x_k (a fused multiply-add
+// chain from zero in storage order), v = init +/- t, d = c1 d + w v,
+// x = x + d -- so that the reduced-precision cycle rounds at the points of its
+// definition, not at points the fusion would choose; the FP32 path is bound
+// by memory, so the extra operations cost nothing.
+template <class TB>
+__device__ __forceinline__ TB ep_add(TB a, TB b) {
+  if constexpr (sizeof(TB) == 4) return __fadd_rn(a, b);
+  else return a + b;
+}
+template <class TB>
+__device__ __forceinline__ TB ep_mul(TB a, TB b) {
+  if constexpr (sizeof(TB) == 4) return __fmul_rn(a, b);
+  else return a * b;
+}
+// c1 d + w v
+template <class TB>
+__device__ __forceinline__ TB ep_dn(TB c1, TB d, TB w, TB v) {
+  if constexpr (sizeof(TB) == 4) return __fadd_rn(__fmul_rn(c1, d), __fmul_rn(w, v));
+  else return fma(c1, d, w * v);
+}
+// x + d + (c1 d + w v): FP32 as (x + d) + (c1 d + w v); FP64 as
+// (x + (1 + c1) d) + w v, two FMAs (1 + c1 is the same for every element)
+template <class TB>
+__device__ __forceinline__ TB ep_xlast(TB x, TB c1, TB d, TB w, TB v) {
+  if constexpr (sizeof(TB) == 4) return __fadd_rn(__fadd_rn(x, d), ep_dn(c1, d, w, v));
+  else return fma(w, v, fma(c1 + (TB)1, d, x));
+}
+// The row's value from its product sum t (accumulated from zero, with the
+// sign of NEG already applied) and, when has_init, its init value `in`:
+// in + s t with the row scale s of scaled values, else in + t.  FP64 blocks
+// with unscaled values start their sums from the init value instead.
+template <class TB, bool SCALED>
+__device__ __forceinline__ TB ep_combine(TB t, TB s, bool has_init, TB in) {
+  if constexpr (SCALED) {
+    if constexpr (sizeof(TB) == 4) {
+      const TB st = __fmul_rn(s, t);
+      return has_init ? __fadd_rn(in, st) : st;
+    } else {
+      return fma(s, t, has_init ? in : (TB)0);
+    }
+  } else {
+    return has_init ? ep_add(in, t) : t;
+  }
+}
+// FP64 blocks with unscaled values begin the product sum at the init value.
+template <class TB, bool SCALED>
+__device__ __forceinline__ constexpr bool sum_from_init() {
+  return !SCALED && sizeof(TB) == 8;
+}
+
 // Epilogue of a row kernel, fixed at compile time so that no floating-point
 // operation of an unused branch is executed (v is the row's product sum):
 enum Epi : int {
@@ -141,17 +195,15 @@ __device__ __forceinline__ void row_epilogue(const RowOpT<TB> &op, int64_t i, in
   if constexpr (EPI != EPI_XLAST && EPI != EPI_XLAST_DOT && EPI != EPI_XLAST_DOT2) {
     if (op.y) op.y[e] = acc;
   }
-  if constexpr (EPI == EPI_Y_D0) op.dnext[e] = wv * acc;
-  if constexpr (EPI == EPI_Y_DN) op.dnext[e] = fma(op.c1, dpv, wv * acc);
-  if constexpr (EPI == EPI_Y_XDP) op.x[e] = xv + dpv;
+  if constexpr (EPI == EPI_Y_D0) op.dnext[e] = ep_mul(wv, acc);
+  if constexpr (EPI == EPI_Y_DN) op.dnext[e] = ep_dn(op.c1, dpv, wv, acc);
+  if constexpr (EPI == EPI_Y_XDP) op.x[e] = ep_add(xv, dpv);
   if constexpr (EPI == EPI_MID) {
-    op.dnext[e] = fma(op.c1, dpv, wv * acc);
-    op.x[e] = xv + dpv;
+    op.dnext[e] = ep_dn(op.c1, dpv, wv, acc);
+    op.x[e] = ep_add(xv, dpv);
   }
   if constexpr (EPI == EPI_XLAST || EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2) {
-    // x + d + (c1 d + w v) = (x + (1 + c1) d) + w v: two FMAs per element
-    // (1 + c1 is the same for every element)
-    const TB xn = fma(wv, acc, fma(op.c1 + (TB)1, dpv, xv));
+    const TB xn = ep_xlast(xv, op.c1, dpv, wv, acc);
     op.x[e] = xn;
     if constexpr (EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2) dsum = fma(du, (double)xn, dsum);
     if constexpr (EPI == EPI_XLAST_DOT2) dsum2 = fma(du2, (double)xn, dsum2);
@@ -209,11 +261,23 @@ template <> struct ValueLoad<__nv_bfloat16> {
     return __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(v) + k));
   }
 };
-// bf16 values with 16-bit column indices: entry k of row i holds the low 16
-// bits of its column; the row's entries lie in two consecutive windows of
-// 65536 columns, the first `split` entries in window `hw` and the rest in
-// hw + 1, packed as rowmeta[i] = hw << 16 | split (paper Sec. 2.3: CSR index
-// types reduced to uint16_t).
+// 16-bit column indices (paper Sec. 2.3: CSR index types reduced to
+// uint16_t), in a segmented form that 3-D stencil rows (three planes far
+// apart) and Galerkin rows fit: the rows are cut into tiles of kSegTile
+// consecutive rows, and each tile has up to kSegs segment bases b_s such that
+// every column of its rows lies in [b_s, b_s + 65535] for the segment s of
+// that entry.  Entry k of row i stores col - b_s as uint16; rowmeta[i] packs
+// the row's segment boundaries e1 | e2 << 10 | e3 << 20 (entries before e1
+// are in segment 0, before e2 in segment 1, before e3 in segment 2, the rest
+// in segment 3; a field of 1023 means no boundary), and tbase[t * kSegs + s]
+// is b_s of tile t.  Decoding is exact.
+constexpr int kSegTile = 32, kSegs = 4, kSegNone = 1023;
+__device__ __forceinline__ int seg16_col(const int4 &b, uint32_t meta, int k, uint16_t off) {
+  const int e1 = (int)(meta & 1023u), e2 = (int)((meta >> 10) & 1023u), e3 = (int)((meta >> 20) & 1023u);
+  const int base = k < e1 ? b.x : k < e2 ? b.y : k < e3 ? b.z : b.w;
+  return base + (int)off;
+}
+// bf16 values with 16-bit column indices.
 struct Bf16Idx16 {};
 template <> struct ValueLoad<Bf16Idx16> {
   using T = __nv_bfloat16;
@@ -223,11 +287,22 @@ template <> struct ValueLoad<Bf16Idx16> {
     return __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(v) + k));
   }
 };
+// FP32 values with the same 16-bit column indices.
+struct F32Idx16 {};
+template <> struct ValueLoad<F32Idx16> {
+  using T = float;
+  static constexpr bool scaled = false;
+  static constexpr bool idx16 = true;
+  __device__ __forceinline__ static float get(const void *v, int k) {
+    return __ldg(static_cast<const float *>(v) + k);
+  }
+};
 
 template <bool NEG, class TB>
 __device__ __forceinline__ TB fmadd(TB a, TB x, TB acc) {
   return NEG ? fma(-a, x, acc) : fma(a, x, acc);
 }
+
 
 // Exactly `rem` (1..7) further products of one chunk, in order.
 template <bool NEG, class TB>
@@ -324,7 +399,7 @@ __device__ __forceinline__ void vstore(T *p, const Vec<T, VEC> &r) {
 // storage order (no reduction adds), and a chunk's tail takes exactly as many
 // FMAs as it has entries.  With scaled (bf16) values the products are summed
 // first and the row scale applied once: v = init +/- s_i * sum_k q_ik x_k.
-template <class TB, class TV, int NV, int VEC, int SL, bool NEG, int EPI, int XW = 1>
+template <class TB, class TV, int NV, int VEC, int SL, bool NEG, int EPI, int XW = 1, bool COH = false>
 __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
   using VL = ValueLoad<TV>;
   using V = Vec<TB, VEC>;
@@ -366,16 +441,24 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
     const int64_t e = i * NV + c0;
     int start = 0, len = 0;
     uint32_t meta = 0;
-    V acc, dpv, xv;
+    int4 tb = make_int4(0, 0, 0, 0);
+    V acc, dpv, xv, in0;
     TB wv = 0;
 #pragma unroll
-    for (int v = 0; v < VEC; ++v) acc.v[v] = dpv.v[v] = xv.v[v] = 0;
+    for (int v = 0; v < VEC; ++v) acc.v[v] = dpv.v[v] = xv.v[v] = in0.v[v] = 0;
     if (valid) {
       start = __ldg(op.rowptr + i);
       len = __ldg(op.rowptr + i + 1) - start;
-      if constexpr (VL::idx16) meta = __ldg(op.rowmeta + i);
+      if constexpr (VL::idx16) {
+        meta = __ldg(op.rowmeta + i);
+        tb = __ldg(reinterpret_cast<const int4 *>(op.tbase) + i / kSegTile);
+      }
       if (wx == 0) {
-        if (!VL::scaled && op.init && sl == 0) acc = vload<TB, VEC>(op.init + e);
+        // the init value: the start of the product sum (FP64, unscaled
+        // values), else added after it; loaded before the product loop either
+        // way, so that its latency hides behind the gathers
+        if (sum_from_init<TB, VL::scaled>() && op.init && sl == 0) acc = vload<TB, VEC>(op.init + e);
+        if (!sum_from_init<TB, VL::scaled>() && op.init && sl == 0) in0 = vload<TB, VEC>(op.init + e);
         if constexpr (EPI == EPI_Y_DN || EPI == EPI_Y_XDP || EPI == EPI_MID || xlast)
           dpv = vload<TB, VEC>(op.dp + e);
         if constexpr (EPI == EPI_Y_D0 || EPI == EPI_Y_DN || EPI == EPI_MID || xlast) wv = op.w[i];
@@ -397,9 +480,7 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
         const bool own = kb + q * G + gl < len;
         if constexpr (VL::idx16) {
           const int kl = kb + q * G + gl;
-          cl[q] = own ? (int)((((meta >> 16) + (kl >= (int)(meta & 0xffffu) ? 1u : 0u)) << 16) |
-                             __ldg(op.colw + start + kl))
-                      : 0;
+          cl[q] = own ? seg16_col(tb, meta, kl, __ldg(op.colw + start + kl)) : 0;
         } else {
           cl[q] = own ? __ldg(col + start + kb + q * G + gl) : 0;
         }
@@ -420,7 +501,11 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
             const int cc = __shfl_sync(0xffffffffu, cl[q], from);
             as[u] = __shfl_sync(0xffffffffu, av[q], from);
             if (t + u < cq && kq + t + u < len) {
-              xs[u] = vldg<TB, VEC>(src + (int64_t)cc * NV + c0);
+              // COH: the operand block was written earlier in the same kernel
+              // (the fused coarse tail), so it is read through the coherent
+              // path, not the read-only one
+              xs[u] = COH ? vload<TB, VEC>(src + (int64_t)cc * NV + c0)
+                          : vldg<TB, VEC>(src + (int64_t)cc * NV + c0);
             } else {
 #pragma unroll
               for (int v = 0; v < VEC; ++v) xs[u].v[v] = 0;
@@ -471,14 +556,10 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
       __syncthreads();
     }
     if (valid && sl == 0 && wx == 0) {
-      if constexpr (VL::scaled) {
-        V in;
+      if constexpr (!sum_from_init<TB, VL::scaled>()) {
+        const TB s = VL::scaled ? (TB)op.rscale[i] : (TB)1;
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) in.v[v] = 0;
-        if (op.init) in = vload<TB, VEC>(op.init + e);
-        const TB s = (TB)op.rscale[i];
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) acc.v[v] = fma(s, acc.v[v], in.v[v]);
+        for (int v = 0; v < VEC; ++v) acc.v[v] = ep_combine<TB, VL::scaled>(acc.v[v], s, op.init != nullptr, in0.v[v]);
       }
       // epilogue (see enum Epi)
       if constexpr (!xlast) {
@@ -488,19 +569,19 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
         V dn;
 #pragma unroll
         for (int v = 0; v < VEC; ++v)
-          dn.v[v] = EPI == EPI_Y_D0 ? wv * acc.v[v] : fma(op.c1, dpv.v[v], wv * acc.v[v]);
+          dn.v[v] = EPI == EPI_Y_D0 ? ep_mul(wv, acc.v[v]) : ep_dn(op.c1, dpv.v[v], wv, acc.v[v]);
         vstore<TB, VEC>(op.dnext + e, dn);
       }
       if constexpr (EPI == EPI_Y_XDP || EPI == EPI_MID) {
         V xn;
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) xn.v[v] = xv.v[v] + dpv.v[v];
+        for (int v = 0; v < VEC; ++v) xn.v[v] = ep_add(xv.v[v], dpv.v[v]);
         vstore<TB, VEC>(op.x + e, xn);
       }
       if constexpr (xlast) {
         V xn;
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) xn.v[v] = fma(wv, acc.v[v], fma(op.c1 + (TB)1, dpv.v[v], xv.v[v]));
+        for (int v = 0; v < VEC; ++v) xn.v[v] = ep_xlast(xv.v[v], op.c1, dpv.v[v], wv, acc.v[v]);
         vstore<TB, VEC>(op.x + e, xn);
         if constexpr (EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2) {
 #pragma unroll
@@ -557,7 +638,7 @@ __device__ __forceinline__ void rows_sliced(const RowOpT<TB> &op) {
     TB acc = 0, dpv = 0, wv = 0, xv = 0;
     double du = 0.0, du2 = 0.0;
     if (valid) {
-      if (!VL::scaled && op.init && s == 0) acc = op.init[i * NV + c];
+      if (sum_from_init<TB, VL::scaled>() && op.init && s == 0) acc = op.init[i * NV + c];
       row_operands<TB, NV, EPI>(op, i, c, dpv, wv, xv, du, du2);
       int k = __ldg(op.rowptr + i) + s;
       const int end = __ldg(op.rowptr + i + 1);
@@ -580,8 +661,10 @@ __device__ __forceinline__ void rows_sliced(const RowOpT<TB> &op) {
     }
 #pragma unroll
     for (int o = NV; o < G; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if constexpr (VL::scaled) {
-      if (valid) acc = fma((TB)op.rscale[i], acc, op.init ? op.init[i * NV + c] : (TB)0);
+    if constexpr (!sum_from_init<TB, VL::scaled>()) {
+      if (valid)
+        acc = ep_combine<TB, VL::scaled>(acc, VL::scaled ? (TB)op.rscale[i] : (TB)1, op.init != nullptr,
+                                         op.init ? op.init[i * NV + c] : (TB)0);
     }
     if (valid && s == 0) row_epilogue<TB, NV, EPI>(op, i, c, acc, dpv, wv, xv, du, du2, dsum, dsum2);
   }
@@ -669,9 +752,9 @@ __device__ __forceinline__ void rows_stream(const RowOpT<TB> &op, unsigned char 
       nre = __ldg(op.rowptr + min(r0 + step + g + 1, n));
     }
     const int e0 = __shfl_sync(0xffffffffu, rs, 0), e1 = __shfl_sync(0xffffffffu, re, 31);
-    // the owner lane starts from the init value (unscaled values), so that
-    // no FP64 add is spent on it
-    TB acc = VL::scaled ? (TB)0 : iv;
+    // the owner lane starts from the init value (FP64, unscaled values), so
+    // that no FP64 add is spent on it
+    TB acc = sum_from_init<TB, VL::scaled>() ? iv : (TB)0;
     for (int wb = e0; wb < e1; wb += R) {
       const int we = min(e1, wb + R);
       const int vb = pairs ? (wb & ~1) : wb;  // first value in the window's buffer
@@ -719,7 +802,7 @@ __device__ __forceinline__ void rows_stream(const RowOpT<TB> &op, unsigned char 
     }
 #pragma unroll
     for (int o = 1; o < LPR; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if constexpr (VL::scaled) acc = fma((TB)rsc, acc, iv);
+    if constexpr (!sum_from_init<TB, VL::scaled>()) acc = ep_combine<TB, VL::scaled>(acc, (TB)rsc, op.init != nullptr, iv);
     if (owner) row_epilogue<TB, 1, EPI>(op, i, 0, acc, dpv, wv, xv, du, du2, dsum, dsum2);
     rs = nrs;
     re = nre;

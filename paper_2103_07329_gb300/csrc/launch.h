@@ -35,6 +35,7 @@ struct Flags {
   int32_t frozen;       // columns frozen by the recursive residual test
   int32_t reactivated;  // columns restarted by the last confirmation
   int32_t breakdown;
+  int32_t tail_err;     // 1: a grid-barrier wait of the fused coarse tail ran out
 };
 
 enum ScalarMode : int {
@@ -94,7 +95,9 @@ int launch_rows_nv4(const RowOp &op, int slices, bool neg, int epi, cudaStream_t
 int launch_rows_nv8(const RowOp &op, int slices, bool neg, int epi, cudaStream_t st);
 int launch_rows_nv16(const RowOp &op, int slices, bool neg, int epi, cudaStream_t st);
 int launch_rows_nv32(const RowOp &op, int slices, bool neg, int epi, cudaStream_t st);
-// FP32 blocks; vt 0 = float values, 1 = bf16 values with per-row FP32 scale.
+// FP32 blocks; vt 0 = float values, 1 = bf16 values with per-row FP32 scale,
+// 2 = bf16 values with 16-bit column indices, 3 = float values with 16-bit
+// column indices.
 int launch_rows_f(const RowOpF &op, int nv, int slices, bool neg, int epi, int vt, cudaStream_t st);
 int launch_rowsf_nv1(const RowOpF &op, int slices, bool neg, int epi, int vt, cudaStream_t st);
 int launch_rowsf_nv2(const RowOpF &op, int slices, bool neg, int epi, int vt, cudaStream_t st);

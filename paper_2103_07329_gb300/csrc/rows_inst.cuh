@@ -138,9 +138,10 @@ int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t 
 
 #if XAMG_FLOAT
 // vt: 0 = float values, 1 = bf16 values with per-row scale, 2 = the same with
-// 16-bit column indices
+// 16-bit column indices, 3 = float values with 16-bit column indices
 int XAMG_CAT(launch_rowsf_nv, XAMG_NV)(const RowOpF &op, int slices, bool neg, int epi, int vt,
                                         cudaStream_t st) {
+  if (vt == 3) return rows_any<F32Idx16>(op, slices, neg, epi, st);
   if (vt == 2) return rows_any<Bf16Idx16>(op, slices, neg, epi, st);
   return vt == 1 ? rows_any<__nv_bfloat16>(op, slices, neg, epi, st)
                  : rows_any<float>(op, slices, neg, epi, st);

@@ -111,3 +111,25 @@ def test_invalid_batches(systems):
     assert e.value.code == B.ERR_INVALID_ARG
     with pytest.raises(B.XamgError):
         B.Batch([systems[0][2]], [33])
+
+
+def test_batch_at_the_workload_sizes_matches_the_oracle():
+    # systems of the benchmark's size range side by side: an 80^3 system with
+    # 32 right-hand sides (512 000 unknowns, many blocks per system in every
+    # fine-level stage), a 64^3 one with 7 and a 16^3 one with 4
+    spec = [(80, 32), (16, 4), (64, 7)]
+    sys_ = []
+    for s, (edge, m) in enumerate(spec):
+        A, Bm = P.batch_system(edge, m, 40 + s)
+        sys_.append((A, Bm, B.Hierarchy(A)))
+    _, Xs, st = solve_batch(sys_)
+    for (A, Bm, h), X, s in zip(sys_, Xs, st):
+        assert s.rc == 0 and np.all(s.status == 0)
+        rr = np.linalg.norm(Bm - oracle.spmm(A, X), axis=0) / np.linalg.norm(Bm, axis=0)
+        assert np.all(rr <= 1e-8), rr
+        ref = oracle.Hierarchy(A).pcg(Bm, tol=1e-8, prec=B.PREC_FP32)
+        assert np.all(np.abs(s.iters - ref.iters) <= 1), (s.iters, ref.iters)
+        X1 = torch.empty_like(dev(Bm))
+        s1 = h.solve(dev(Bm), X1, tol=1e-8, maxit=100, precond=B.PREC_FP32)
+        assert np.all(np.abs(s.iters - s1.iters) <= 1)
+        assert colrel(X, X1.cpu().numpy()).max() <= 1e-9

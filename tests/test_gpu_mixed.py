@@ -96,27 +96,35 @@ def test_reduced_precision_edge_cases():
         g.solve(dev(Bm), X, precond=7)
 
 
-def _long_range(N, stride):
-    """7-point Poisson plus a symmetric coupling of every row to the row
-    `stride` away (diagonally dominant, so still SPD): with a stride beyond
-    two index windows of 65536 the rows cannot use 16-bit column indices."""
+def _long_range(N, *strides):
+    """7-point Poisson plus a symmetric coupling of every row to the rows
+    `stride` away (diagonally dominant, so still SPD).  Each stride adds two
+    column clusters far from the row's own: one stride beyond 65536 needs
+    three 16-bit segments per row tile, two such strides five, more than the
+    segmented form holds."""
     import scipy.sparse as sp
     A0 = P.poisson7(N)
     M = sp.csr_matrix((A0.val, A0.col, A0.rowptr), shape=(A0.n, A0.n))
     n = A0.n
-    E = sp.diags([np.full(n - stride, -0.1), np.full(n - stride, -0.1)], [stride, -stride], shape=(n, n))
-    M = (M + E + sp.identity(n) * 0.2).tocsr()
+    for stride in strides:
+        E = sp.diags([np.full(n - stride, -0.1), np.full(n - stride, -0.1)], [stride, -stride],
+                     shape=(n, n))
+        M = M + E + sp.identity(n) * 0.2
+    M = M.tocsr()
     M.sort_indices()
     return P.CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data)
 
 
-@pytest.mark.parametrize("which", ["windows", "fallback"])
+@pytest.mark.parametrize("which", ["windows", "segments", "fallback"])
 def test_bf16_index_compression_paths(which):
-    # n = 262144 spans four windows; the 7-point rows cross window borders but
-    # fit two windows (16-bit indices).  The long-range variant does not fit
-    # and keeps 32-bit indices.  Both must match the oracle's bf16 V-cycle.
-    A = P.poisson7(64) if which == "windows" else _long_range(64, 140000)
+    # n = 262144 spans four 65536-column windows: the 7-point rows fit one
+    # 16-bit segment per tile, the one-stride long-range rows three; the
+    # two-stride rows of the 72^3 grid need five and keep 32-bit indices.  All
+    # must match the oracle's bf16 V-cycle.
+    A = {"windows": P.poisson7(64), "segments": _long_range(64, 70000),
+         "fallback": _long_range(72, 70000, 140000)}[which]
     g, o = B.Hierarchy(A), oracle.Hierarchy(A)
+    g.set_index16(True)
     Bm = P.rhs_uniform(A.n, 8, 0, m_draw=32)
     X = torch.empty((A.n, 8), dtype=torch.float64, device="cuda")
     g.vcycle_precond(B.PREC_BF16, dev(Bm), X)
@@ -173,3 +181,146 @@ def test_m1_splits_of_the_reduced_precision_vcycle(prec, cand):
     s = g.solve(dev(Bm), X, tol=1e-8, maxit=100, precond=prec)
     rr = np.linalg.norm(Bm - oracle.spmm(A, X.cpu().numpy()), axis=0) / np.linalg.norm(Bm, axis=0)
     assert s.rc == 0 and np.all(rr <= 1e-8)
+
+
+# ---- products and cycles that must equal the oracle bit for bit ----------
+#
+# The FP32 row kernels round where the reduced-precision cycle is defined to
+# round (one rounding per term of a row sum, in storage order; one per
+# elementwise operation), so with the storage-order split on every product
+# (tuning candidate 0: a lane group per row, or at m = 1 the stream kernel
+# with one lane per row) the GPU and the oracle compute identical bits.  A
+# kernel that accumulated in FP64, fused differently or summed in another
+# order would fail these tests (the FP32-vs-FP64 gap of the cycle is 1-2e-7,
+# and merely fusing the products differently moves it by 1e-7).
+
+def _storage_order(g, m, prec):
+    for l in range(g.levels):
+        for which in (0, 1, 2):
+            if which == 0 or l + 1 < g.levels:
+                g.set_split(m, prec, l, which, 0)
+
+
+def _fp32_block(rows, m, seed):
+    return np.random.default_rng(seed).standard_normal((rows, m)).astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("key", ["p7_32", "var_24", "p27_16"])
+@pytest.mark.parametrize("prec", [B.PREC_FP32, B.PREC_BF16])
+@pytest.mark.parametrize("m", [1, 4, 32])
+def test_reduced_products_bitwise_in_storage_order(key, prec, m):
+    A, _, o = pair(key)
+    g = B.Hierarchy(A)
+    _storage_order(g, m, prec)
+    for l in range(g.levels):
+        n = g.level_info(l)[0]
+        nc = g.level_info(l + 1)[0] if l + 1 < g.levels else 0
+        for which in ((0, 1, 2) if l + 1 < g.levels else (0,)):
+            cols, rows = {0: (n, n), 1: (nc, n), 2: (n, nc)}[which]
+            X = _fp32_block(cols, m, 100 * l + which)
+            Y = torch.empty((rows, m), dtype=torch.float64, device="cuda")
+            g.spmm_precond(prec, l, which, dev(X), Y)
+            ref = o.spmm_f(l, which, X, bf16=(prec == B.PREC_BF16 and which == 0))
+            assert np.array_equal(Y.cpu().numpy(), ref.astype(np.float64)), (l, which)
+
+
+@pytest.mark.parametrize("key", ["p7_32", "var_24", "p27_16"])
+@pytest.mark.parametrize("prec", [B.PREC_FP32, B.PREC_BF16])
+@pytest.mark.parametrize("m", [1, 4, 32])
+def test_reduced_vcycle_bitwise_in_storage_order(key, prec, m):
+    A, _, o = pair(key)
+    g = B.Hierarchy(A)
+    _storage_order(g, m, prec)
+    Bm = P.rhs_uniform(A.n, m, 0, m_draw=32)
+    X = torch.empty((A.n, m), dtype=torch.float64, device="cuda")
+    g.vcycle_precond(prec, dev(Bm), X)
+    Xg = X.cpu().numpy()
+    ref = o.vcycle_prec(prec, Bm)
+    assert np.array_equal(Xg, ref), colrel(Xg, ref).max()
+    # and the cycle is genuinely reduced precision: it sits well away from
+    # the FP64 cycle (FP32: 1e-7 relative; bf16 values: 1e-3)
+    X64 = torch.empty_like(X)
+    g.vcycle(dev(Bm), X64)
+    gap = colrel(Xg, X64.cpu().numpy()).min()
+    assert gap > (3e-8 if prec == B.PREC_FP32 else 1e-4), gap
+
+
+@pytest.mark.parametrize("key", ["p7_32", "p27_16"])
+@pytest.mark.parametrize("prec", [B.PREC_FP32, B.PREC_BF16])
+@pytest.mark.parametrize("m", [4, 32])
+def test_reduced_products_within_summation_bound_every_split(key, prec, m):
+    # the default and the one-row-per-warp splits add a row's terms in another
+    # order: each result is within the FP32 summation bound of the oracle's,
+    # 2 gamma_k sum |m_ik| |x_k| (k terms, both sides within gamma_k of the
+    # exact sum of the same stored values)
+    import scipy.sparse as sp
+    A, _, o = pair(key)
+    g = B.Hierarchy(A)
+    u = 2.0 ** -24
+    for cand in (-1, 1):
+        for l in range(g.levels):
+            for which in ((0, 1, 2) if l + 1 < g.levels else (0,)):
+                g.set_split(m, prec, l, which, cand)
+                rp, ci, v = _ops(o, l)[which]
+                rows, cols = len(rp) - 1, (o.level(l + 1).n if which == 1 else o.level(l).n)
+                X = _fp32_block(cols, m, 7 * l + which)
+                Y = torch.empty((rows, m), dtype=torch.float64, device="cuda")
+                g.spmm_precond(prec, l, which, dev(X), Y)
+                ref = o.spmm_f(l, which, X, bf16=(prec == B.PREC_BF16 and which == 0)).astype(np.float64)
+                Mabs = sp.csr_matrix((np.abs(v) * (1.01 if prec == B.PREC_BF16 else 1.0), ci, rp),
+                                     shape=(rows, cols))
+                k = int(np.diff(rp).max()) + 1
+                bound = 2 * k * u / (1 - k * u) * (Mabs @ np.abs(X))
+                assert np.all(np.abs(Y.cpu().numpy() - ref) <= bound + 1e-40), (cand, l, which)
+
+
+def _ops(o, l):
+    lv = o.level(l)
+    return {0: lv.A, 1: lv.P if l + 1 < o.nlev else None, 2: lv.R if l + 1 < o.nlev else None}
+
+
+@pytest.mark.parametrize("kind", ["p7_64", "long_70000"])
+@pytest.mark.parametrize("prec", [B.PREC_FP32, B.PREC_BF16])
+@pytest.mark.parametrize("m", [2, 4, 32])
+def test_index16_products_and_cycle_equal_index32(kind, prec, m):
+    # 16-bit column offsets decode exactly: with them on or off every product
+    # and the whole cycle give identical bits.  n = 262144 spans four 65536
+    # windows; the 7-point tiles take one segment, the long-range ones three
+    A = P.poisson7(64) if kind == "p7_64" else _long_range(64, 70000)
+    g = B.Hierarchy(A)
+    masks = [g.index16_info(l) for l in range(g.levels)]
+    assert masks[0] & 1 and masks[0] & 2 and masks[0] & 4, masks
+    Bm = P.rhs_uniform(A.n, m, 0, m_draw=32)
+    outs = []
+    for on in (True, False):
+        g.set_index16(on)
+        ys = []
+        for l in range(g.levels - 1):
+            for which in (0, 1, 2):
+                lv = g.level_info(l)[0]
+                nc = g.level_info(l + 1)[0]
+                cols, rows = {0: (lv, lv), 1: (nc, lv), 2: (lv, nc)}[which]
+                X = _fp32_block(cols, m, l * 3 + which)
+                Y = torch.empty((rows, m), dtype=torch.float64, device="cuda")
+                g.spmm_precond(prec, l, which, dev(X), Y)
+                ys.append(Y.cpu().numpy())
+        Z = torch.empty((A.n, m), dtype=torch.float64, device="cuda")
+        g.vcycle_precond(prec, dev(Bm), Z)
+        ys.append(Z.cpu().numpy())
+        outs.append(ys)
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_index16_falls_back_where_rows_do_not_fit():
+    # two long-range strides need five segments per tile in the middle rows
+    # (n = 373248 > 2 x 140000): level 0's A keeps 32-bit indices, and its
+    # products still match the oracle's
+    A = _long_range(72, 70000, 140000)
+    g, o = B.Hierarchy(A), oracle.Hierarchy(A)
+    assert not (g.index16_info(0) & 1)
+    _storage_order(g, 8, B.PREC_FP32)
+    X = _fp32_block(A.n, 8, 3)
+    Y = torch.empty((A.n, 8), dtype=torch.float64, device="cuda")
+    g.spmm_precond(B.PREC_FP32, 0, 0, dev(X), Y)
+    assert np.array_equal(Y.cpu().numpy(), o.spmm_f(0, 0, X).astype(np.float64))
