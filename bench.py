@@ -38,8 +38,8 @@ sys.path.insert(0, ROOT)
 METRIC = "RHS solved/s to 1e-8 residual, plain FP64 vs mixed/batched/warm; SpMM %HBM"
 UNIT = "RHS/s"
 # FP64 FMA peak derived from the part's unit counts and clock: 152 SMs x 2 FP64
-# FMA lanes per SM per clock x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s; a
-# DFMA-only probe on this GPU measured 1.19 TFLOP/s under load).
+# FMA lanes per SM per clock x 2 flop x 2.07 GHz (1.259 TFLOP/s; ncu reports
+# the same two DFMA per SM per clock as the FP64 pipe's sustained peak).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
@@ -80,13 +80,25 @@ def parse():
     ap.add_argument("--sweep-ms", default="1,2,4,8,16,32", help="--sweep: comma-separated m values")
     ap.add_argument("--sweep-methods", default="pcg,bicgstab",
                     help="--sweep: comma-separated methods (also bicgstab_reordered, bicgstab_pipelined)")
+    ap.add_argument("--fp32-split", type=int, default=-1,
+                    help="--sweep: force this split candidate on every FP32-block product "
+                         "(-1: the default rule)")
+    ap.add_argument("--index16", action="store_true",
+                    help="--sweep: 16-bit column indices in the reduced-precision products")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=100)
-    ap.add_argument("--cpu-cols", type=int, default=1, help="columns in the oracle's sample")
+    ap.add_argument("--cpu-cols", type=int, default=8,
+                    help="cpu_baseline: columns of the oracle's sample (one multi-column solve)")
+    ap.add_argument("--ref-cols", type=int, default=1,
+                    help="--impl reference: columns the oracle solves per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision and warm forms")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned-initial-guess form")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the variable-coefficient precision workload")
+    ap.add_argument("--precision-grid", type=int, default=192,
+                    help="grid edge of the variable-coefficient precision workload")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched form")
     ap.add_argument("--batch-count", type=int, default=64, help="systems of the batched form")
     ap.add_argument("--batch-only", action="store_true",
@@ -100,8 +112,11 @@ def parse():
                     help="measurement mode: every row split of every level's FP64 product y = M x "
                          "on --m columns, microseconds per product, one JSON line per operator")
     ap.add_argument("--spmm-only", action="store_true",
-                    help="profiling mode: four level-0 products y = A x on --m columns with the "
-                         "default row split, nothing else (the case for kernel captures)")
+                    help="profiling mode: four products y = A x of level --level on --m columns "
+                         "with the default row split, nothing else (the case for kernel captures)")
+    ap.add_argument("--level", type=int, default=0, help="--spmm-only: the level")
+    ap.add_argument("--precond", default="fp64", choices=["fp64", "fp32", "bf16"],
+                    help="--spmm-only: FP64 blocks, or FP32 blocks with FP32 / bf16 values of A")
     a = ap.parse_args()
     if a.grid is None:
         a.grid = 160 if a.matrix == "poisson27" else 192
@@ -189,7 +204,7 @@ def measured_hbm():
 
 
 KERNEL_SOURCES = ("paper_2103_07329_gb300/csrc/kernels.cuh", "paper_2103_07329_gb300/csrc/rows_inst.cuh")
-TRAFFIC_FILE = "profiles/traffic_k_rows_poisson7_192_m32.txt"
+TRAFFIC_FILE = "profiles/traffic_k_rows_poisson7_96_m32.txt"
 
 
 def kernel_source_hash() -> str:
@@ -200,11 +215,15 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def kernel_traffic(a):
-    """Average DRAM bytes (read + write) per row-kernel launch from the committed
-    ncu capture of the default workload, or None when the capture is missing,
-    was taken on another workload, or the kernel sources changed since."""
-    if (a.matrix, a.grid, a.m, a.method) != ("poisson7", 192, 32, "pcg"):
+def kernel_traffic(a, algorithmic_bytes_per_launch):
+    """DRAM bytes (read + write) per row-kernel launch of the FP64 solve,
+    scaled from the committed ncu capture of the same solve on the 96^3 grid
+    (the 192^3 solve holds too much device memory for a capture) by the
+    algorithmic bytes per launch: traffic = captured DRAM bytes x (this run's
+    algorithmic bytes / the captured run's).  None when the capture is
+    missing, the workload is not the 7-point m = 32 PCG solve, or the kernel
+    sources changed since the capture."""
+    if (a.matrix, a.m, a.method) != ("poisson7", 32, "pcg"):
         return None
     try:
         kv = {}
@@ -214,7 +233,8 @@ def kernel_traffic(a):
                 kv[k.strip()] = v.strip()
         if kv.get("source_sha256") != kernel_source_hash():
             return None
-        return float(kv["dram_bytes_per_launch"])
+        ratio = float(kv["dram_bytes_per_launch"]) / float(kv["algorithmic_bytes_per_launch"])
+        return round(ratio * algorithmic_bytes_per_launch)
     except Exception:
         return None
 
@@ -352,7 +372,7 @@ def run_reference(a):
     oracle.build()
     A = make_matrix(a)
     h = oracle.Hierarchy(A)
-    Bm = P.rhs_uniform(A.n, a.cpu_cols, 0, m_draw=max(a.m, a.cpu_cols))
+    Bm = P.rhs_uniform(A.n, a.ref_cols, 0, m_draw=max(a.m, a.ref_cols))
 
     def solve(Bm, tol, maxit):
         return oracle_solve(h, a, Bm)
@@ -367,7 +387,9 @@ def run_reference(a):
     total = sum(times)
     value = solved / total
     cores = oracle_threads()
-    sample = f"{a.cpu_cols} of the {a.m} columns per step, full matrix, oracle setup untimed"
+    sample = (f"{a.ref_cols} of the {a.m} columns per step (a per-column rate: the oracle's "
+              f"multi-column solve runs at about the same rate per column), full matrix, oracle "
+              f"setup untimed")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -413,115 +435,152 @@ def run_ours(a):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def solves(hh, Bb, Xb, steps, prec=B.PREC_FP64, meth=method):
+        """`steps` complete solves on the current stream, bracketed by CUDA
+        events; returns (ms, columns that reached tol, last stats)."""
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ok, st = 0, None
+        for _ in range(steps):
+            st = hh.solve(Bb, Xb, a.tol, a.maxit, meth, precond=prec)
+            ok += int(np.sum((st.status == 0) & (st.relres <= a.tol)))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), ok, st
+
+    def row_timing(hh, base):
+        """Totals and per-level A-product figures of the row kernel launches
+        recorded since timing was enabled (base 0: FP64 blocks, 3: FP32)."""
+        tot = dict(launches=0, ms=0.0, flops=0.0, bytes=0.0)
+        levels = []
+        for l in range(hh.levels):
+            for which in (0, 1, 2):
+                if which and l + 1 == hh.levels:
+                    continue
+                r = hh.timing_read(l, base + which)
+                for k in tot:
+                    tot[k] += r[k]
+                if which == 0 and r["launches"]:
+                    levels.append(dict(level=l, launches=r["launches"], ms=round(r["ms"], 3),
+                                       tflops=round(r["flops"] / r["ms"] / 1e9, 4),
+                                       gbs=round(r["bytes"] / r["ms"] / 1e6, 1)))
+        return tot, levels
+
     for _ in range(a.warmup):
         h.solve(Bd, X, a.tol, a.maxit, method)
-    # timed region: K complete solves
+    # timed region: K complete solves on the product path (CUDA graphs of the
+    # steady iteration, no per-launch events)
     clocks = Clocks(local)
-    h.timing_enable(True)
     barrier()
     clocks.start()
     l0 = B.kernel_launches()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    solved = 0
-    stats = []
-    for _ in range(a.steps):
-        st = h.solve(Bd, X, a.tol, a.maxit, method)
-        solved += int(np.sum((st.status == 0) & (st.relres <= a.tol)))
-        stats.append(st)
-    ev1.record(stream)
+    ms, solved, st = solves(h, Bd, X, a.steps)
     barrier()
     launches = B.kernel_launches() - l0
     ck = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
+    stats = [st]
     value, t_max, solved_all = MR.job_throughput(ms / 1e3, solved, dist, "cuda")
 
-    # dominant kernel: the fused sparse row kernel on the A operators of all levels
-    tot = dict(launches=0, ms=0.0, flops=0.0, bytes=0.0)
-    per_level = []
-    for l in range(h.levels):
-        for which in (0, 1, 2):
-            if which and l + 1 == h.levels:
-                continue
-            r = h.timing_read(l, which)
-            for k in tot:
-                tot[k] += r[k]
-            if which == 0 and r["launches"]:
-                per_level.append(dict(level=l, launches=r["launches"], ms=round(r["ms"], 3),
-                                      tflops=round(r["flops"] / r["ms"] / 1e9, 4),
-                                      gbs=round(r["bytes"] / r["ms"] / 1e6, 1)))
+    # roofline of the dominant kernel, the fused sparse row kernel (A, P, R of
+    # all levels): a separate instrumented pass of the same K solves, every
+    # row launch bracketed by CUDA events on the solve's stream
+    h.timing_enable(True)
+    barrier()
+    ms_i, solved_i, _ = solves(h, Bd, X, a.steps)
+    tot, per_level = row_timing(h, 0)
     h.timing_enable(False)
     achieved_tf = tot["flops"] / tot["ms"] / 1e9 if tot["ms"] > 0 else 0.0
     achieved_gbs = tot["bytes"] / tot["ms"] / 1e6 if tot["ms"] > 0 else 0.0
     hbm, hbm_kind = measured_hbm()
-    traffic = kernel_traffic(a)
+    traffic = kernel_traffic(a, tot["bytes"] / max(1, tot["launches"]))
     roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4),
-                "traffic": traffic, "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+                "traffic": traffic,
+                "traffic_unit": ("bytes per launch (DRAM read + write, ncu on the 96^3 solve, scaled "
+                                 "by algorithmic bytes per launch)"),
                 "algorithmic_bytes_per_launch": round(tot["bytes"] / max(1, tot["launches"])),
                 "kernel": "k_rows<NV=32> fused SpMM row kernel, all levels (A, P, R)",
                 "launches": tot["launches"], "avg_launch_ms": round(tot["ms"] / max(1, tot["launches"]), 4),
                 "peak_kind": "derived FP64 FMA peak (152 SM x 2 DFMA/clk x 2.07 GHz)",
                 "hbm": {"achieved_gbs": round(achieved_gbs, 1), "peak_gbs": hbm,
                         "frac": round(achieved_gbs / hbm, 4), "peak_kind": hbm_kind},
-                "share_of_step": round(tot["ms"] / ms, 4)}
+                "share_of_step": round(tot["ms"] / ms_i, 4),
+                "pass": "instrumented pass of the same solves (per-launch CUDA events, no graphs)",
+                "instrumented_value": round(solved_i / (ms_i / 1e3), 3)}
 
-    # the same workload with the reduced-precision preconditioner (FP32 blocks;
-    # FP32 or bf16 values of A) inside the FP64 outer loop, same tolerance
+    def precision_forms(hh, Bb, Xb, value64, X64, index16=False):
+        """The FP32 and bf16 preconditioners inside the FP64 outer loop on the
+        same system: RHS/s (product path), the FP32 row kernel's algorithmic
+        GB/s from an instrumented pass, and per column the relative error
+        ||X_form - X_fp64|| / ||X_fp64|| against the FP64 GPU solution.  With
+        index16 also both forms with 16-bit column indices."""
+        out = {}
+        x64 = X64.cpu().numpy()
+        variants = [("fp32", B.PREC_FP32, False), ("bf16", B.PREC_BF16, False)]
+        if index16:
+            variants += [("fp32_index16", B.PREC_FP32, True), ("bf16_index16", B.PREC_BF16, True)]
+        for name, prec, i16 in variants:
+            hh.set_index16(i16)
+            hh.solve(Bb, Xb, a.tol, a.maxit, method, precond=prec)
+            barrier()
+            fms, fok, fst = solves(hh, Bb, Xb, a.steps, prec)
+            fv, ft, _ = MR.job_throughput(fms / 1e3, fok, dist, "cuda")
+            xf = Xb.cpu().numpy()
+            err = np.linalg.norm(xf - x64, axis=0) / np.linalg.norm(x64, axis=0)
+            hh.timing_enable(True)
+            barrier()
+            ims, _, _ = solves(hh, Bb, Xb, a.steps, prec)
+            f32, flev = row_timing(hh, 3)
+            hh.timing_enable(False)
+            gbs = f32["bytes"] / f32["ms"] / 1e6 if f32["ms"] > 0 else 0.0
+            out["mixed_" + name] = {
+                "value": fv, "speedup_vs_fp64": fv / value64, "ms_per_step": 1e3 * ft / a.steps,
+                "iters": fst.iters.tolist(), "max_relres": float(fst.relres.max()),
+                "error_vs_fp64_per_column": [float(f"{e:.3e}") for e in err],
+                "precond_row_kernel": {"bound": "hbm", "achieved_gbs": round(gbs, 1), "peak_gbs": hbm,
+                                       "frac": round(gbs / hbm, 4), "launches": f32["launches"],
+                                       "share_of_step": round(f32["ms"] / ims, 4),
+                                       "pass": "instrumented pass of the same solves"},
+                "roofline_levels": flev}
+        hh.set_index16(False)
+        return out
+
+    def precision_workload():
+        """The precision workload: 3-D 7-point variable-coefficient diffusion
+        on precision_grid^3 cells with lognormal (sigma 1, seed 1) cell
+        coefficients and m = 16, plain FP64 against the FP32 and bf16
+        preconditioners (outer FP64 flexible PCG, same tolerance)."""
+        g = a.precision_grid
+        Av = P.diffusion7(g, P.lognormal_cells(g, 1.0, 1))
+        t0 = time.perf_counter()
+        hv = B.Hierarchy(Av)
+        t_set = time.perf_counter() - t0
+        Bv = P.rhs_uniform(Av.n, 16, MR.rhs_seed(rank), m_draw=32)
+        Bvd = torch.from_numpy(Bv).cuda()
+        Xv = torch.empty_like(Bvd)
+        hv.solve(Bvd, Xv, a.tol, a.maxit, method)
+        barrier()
+        vms, vok, vst = solves(hv, Bvd, Xv, a.steps)
+        v64, vt, _ = MR.job_throughput(vms / 1e3, vok, dist, "cuda")
+        out = {"workload": (f"3-D 7-point variable-coefficient diffusion {g}^3 (n={Av.n}, nnz={Av.nnz}), "
+                            f"cell k lognormal sigma=1 seed 1, m=16 RHS uniform[-1,1) seed 0, "
+                            f"{a.method.upper()} + classical RS AMG V(1,1) Chebyshev-2, tol {a.tol:g}"),
+               "levels": hv.levels, "op_complexity": round(hv.op_complexity, 4), "setup_s": round(t_set, 2),
+               "fp64": {"value": v64, "ms_per_step": 1e3 * vt / a.steps, "iters": vst.iters.tolist(),
+                        "max_relres": float(vst.relres.max())}}
+        out.update(precision_forms(hv, Bvd, Xv, v64, Xv.clone(), index16=True))
+        hv.close()
+        del Bvd, Xv
+        return out
+
     forms = None
     if not a.no_forms:
-        forms = {}
-        for name, prec in (("mixed_fp32", B.PREC_FP32), ("mixed_bf16", B.PREC_BF16)):
-            # the default row splits, then the autotuned ones (tuning is setup, untimed)
-            h.solve(Bd, X, a.tol, a.maxit, method, precond=prec)
-            barrier()
-            u0 = torch.cuda.Event(enable_timing=True)
-            u1 = torch.cuda.Event(enable_timing=True)
-            u0.record(stream)
-            su = 0
-            for _ in range(a.steps):
-                st = h.solve(Bd, X, a.tol, a.maxit, method, precond=prec)
-                su += int(np.sum((st.status == 0) & (st.relres <= a.tol)))
-            u1.record(stream)
-            barrier()
-            untuned, _, _ = MR.job_throughput(u0.elapsed_time(u1) / 1e3, su, dist, "cuda")
-            t0 = time.perf_counter()
-            tuned_ops, wide_ops = h.autotune(a.m, prec)
-            t_tune = time.perf_counter() - t0
-            h.solve(Bd, X, a.tol, a.maxit, method, precond=prec)
-            h.timing_enable(True)
-            barrier()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            s3 = 0
-            for _ in range(a.steps):
-                st = h.solve(Bd, X, a.tol, a.maxit, method, precond=prec)
-                s3 += int(np.sum((st.status == 0) & (st.relres <= a.tol)))
-            e1.record(stream)
-            barrier()
-            fv, ft, _ = MR.job_throughput(e0.elapsed_time(e1) / 1e3, s3, dist, "cuda")
-            f32 = dict(launches=0, ms=0.0, flops=0.0, bytes=0.0)
-            for l in range(h.levels):
-                for which in (3, 4, 5):
-                    if which > 3 and l + 1 == h.levels:
-                        continue
-                    r = h.timing_read(l, which)
-                    for k in f32:
-                        f32[k] += r[k]
-            h.timing_enable(False)
-            gbs = f32["bytes"] / f32["ms"] / 1e6 if f32["ms"] > 0 else 0.0
-            forms[name] = {"value": fv, "speedup_vs_fp64": fv / value, "ms_per_step": 1e3 * ft / a.steps,
-                           "value_default_splits": untuned,
-                           "autotune": {"products": tuned_ops, "one_row_per_warp": wide_ops,
-                                        "seconds": round(t_tune, 3)},
-                           "iters": st.iters.tolist()[:4], "max_relres": float(st.relres.max()),
-                           "precond_row_kernel": {"bound": "hbm", "achieved_gbs": round(gbs, 1),
-                                                  "peak_gbs": measured_hbm()[0],
-                                                  "frac": round(gbs / measured_hbm()[0], 4),
-                                                  "launches": f32["launches"],
-                                                  "share_of_step": round(f32["ms"] / (1e3 * ft), 4)}}
+        X64 = X.clone()
+        forms = precision_forms(h, Bd, X, value, X64)
+        del X64
+        if not a.no_precision:
+            forms["precision_var%d" % a.precision_grid] = precision_workload()
 
     # learned initial guess: held-out 64^3 GRF-coefficient diffusion systems,
     # 32 smooth right-hand sides each, solved from X0 = 0 and from the trained
@@ -572,10 +631,11 @@ def run_ours(a):
         del Bd, X
         v, info = cpu_baseline(a, A)
         cpu = {"value": v, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-               "sample": f"{a.cpu_cols} of the {a.m} columns of the same workload solved to "
-                         f"{a.tol:g} (oracle setup {info['t_setup']:.1f} s untimed, solve "
-                         f"{info['t_solve']:.1f} s, iterations {info['iters']}); OpenMP over "
-                         f"the SpMM row loops, the rest single-threaded"}
+               "sample": f"the first {a.cpu_cols} of the {a.m} columns of the same workload, "
+                         f"one {a.cpu_cols}-column oracle solve to {a.tol:g} (oracle setup "
+                         f"{info['t_setup']:.1f} s untimed, solve {info['t_solve']:.1f} s, "
+                         f"iterations {info['iters']}); OpenMP over the SpMM row loops, the "
+                         f"rest single-threaded"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -616,6 +676,8 @@ def run_sweep(a):
     t0 = time.perf_counter()
     h = B.Hierarchy(A)
     setup = time.perf_counter() - t0
+    if a.index16:
+        h.set_index16(True)
     hbm = measured_hbm()[0]
     for m in [int(v) for v in a.sweep_ms.split(",")]:
         Bm = P.rhs_uniform(A.n, m, 0, m_draw=32)
@@ -627,6 +689,14 @@ def run_sweep(a):
                                ("mixed_bf16", B.PREC_BF16)):
                 if method == B.BICGSTAB_PIPELINED and prec != B.PREC_FP64:
                     continue  # its recurrences need a linear preconditioner
+                if prec != B.PREC_FP64 and a.fp32_split >= 0:
+                    for l in range(h.levels):
+                        for which in (0, 1, 2):
+                            if which == 0 or l + 1 < h.levels:
+                                try:
+                                    h.set_split(m, prec, l, which, a.fp32_split)
+                                except B.XamgError:
+                                    pass
                 h.solve(Bd, X, a.tol, a.maxit, method, precond=prec)
                 h.timing_enable(True)
                 torch.cuda.synchronize()
@@ -650,6 +720,7 @@ def run_sweep(a):
                                        "gbs": round(r["bytes"] / r["ms"] / 1e6, 1)})
                 h.timing_enable(False)
                 print(json.dumps({"matrix": a.matrix, "grid": a.grid, "n": A.n, "m": m,
+                                  "index16": a.index16, "fp32_split": a.fp32_split,
                                   "method": method_name, "form": form,
                                   "rhs_per_s": round(solved / (ms * a.steps / 1e3), 2),
                                   "ms_per_solve": round(ms, 3), "iters": int(st.iters.max()),
@@ -708,7 +779,8 @@ def run_split_table(a):
 
 
 def run_spmm_only(a):
-    """Four level-0 products y = A x with the default split, for kernel captures."""
+    """Four products y = A_l x with the default split, for kernel captures
+    (FP32 blocks for --precond fp32 / bf16: the preconditioner's product)."""
     import torch
 
     from paper_2103_07329_gb300 import binding as B
@@ -717,13 +789,18 @@ def run_spmm_only(a):
     build_mod.build()
     A = make_matrix(a)
     h = B.Hierarchy(A)
-    X = torch.rand(A.n, a.m, dtype=torch.float64, device="cuda")
-    Y = torch.empty(A.n, a.m, dtype=torch.float64, device="cuda")
+    n, nnz, _ = h.level_info(a.level)
+    X = torch.rand(n, a.m, dtype=torch.float64, device="cuda")
+    Y = torch.empty(n, a.m, dtype=torch.float64, device="cuda")
+    prec = {"fp64": B.PREC_FP64, "fp32": B.PREC_FP32, "bf16": B.PREC_BF16}[a.precond]
     for _ in range(4):
-        h.spmm(0, 0, X, Y)
+        if prec == B.PREC_FP64:
+            h.spmm(a.level, 0, X, Y)
+        else:
+            h.spmm_precond(prec, a.level, 0, X, Y)
     torch.cuda.synchronize()
-    print(json.dumps({"matrix": a.matrix, "grid": a.grid, "n": A.n, "nnz": A.nnz, "m": a.m,
-                      "products": 4}))
+    print(json.dumps({"matrix": a.matrix, "grid": a.grid, "level": a.level, "n": n, "nnz": nnz, "m": a.m,
+                      "precond": a.precond, "products": 4}))
     return 0
 
 

@@ -281,16 +281,20 @@ int xamg_level_spmm(xamg_hier *h, int32_t level, int32_t which, const double *X,
 int xamg_level_spmm_precond(xamg_hier *h, int32_t precond, int32_t level, int32_t which,
                             const double *X, double *Y, int32_t m, void *stream);
 
-/* Fused coarse tail of the V(1,1) cycle (on by default, max_elems = 131072).
- * The levels whose n x pad(m) blocks hold at most max_elems elements -- from
+/* Fused coarse tail of the V(1,1) cycle (off by default; max_elems = 131072
+ * is the tested setting).  The levels whose n x pad(m) blocks hold at most
+ * max_elems elements -- from
  * the first such level down to the coarsest and back up to its first
  * post-smoothing step, at most ten levels, blocks of two or more columns,
  * two Chebyshev steps -- run as one cooperative kernel launch with a
  * grid-wide barrier between stages (paper Sec. 2.1: the V-cycle; the fusion
  * is this library's).  Each stage computes exactly what its separate launch
- * would, so results are bitwise those of the unfused cycle; small systems,
- * whose cycles are bound by launch latency, gain the most.  max_elems = 0
- * turns the fusion off.  Every barrier wait is bounded by wait_limit_s
+ * would, so results are bitwise those of the unfused cycle.  On GB300 it
+ * measured slower than the separate launches replayed from a CUDA graph
+ * (a stage with its grid barrier took about 12 us against about 5 us per
+ * launch: the barrier itself costs 2 us, and the cooperative kernel holds
+ * only two blocks per SM), hence off by default.  max_elems = 0 turns the
+ * fusion off.  Every barrier wait is bounded by wait_limit_s
  * seconds (0 < wait_limit_s <= 60; default 2): a wait that runs out ends the
  * kernel, and the solve or V-cycle returns XAMG_ERR_TIMEOUT (X then holds no
  * meaningful result; the device stays usable).  extra_arrivals > 0 adds
@@ -412,8 +416,11 @@ int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_
  * window and 1 lane, 4 lanes or a warp per row; 5, 6 = stream kernel with a
  * 512-entry window and 1 or 2 lanes per row; m > 1: 0 = a
  * group of lanes per row, 1 = one row per warp (for FP64 blocks of 16 and
- * 32 columns: four warps per row).  Results do not depend on the split
- * beyond the order of each row's sums.  XAMG_ERR_INVALID_ARG for any other
+ * 32 columns: four warps per row), and for FP32 blocks of 8 or more columns
+ * 2 = a group of lanes per row with the operand rows staged through shared
+ * memory by asynchronous copies (the sums of candidate 0, bit for bit; an
+ * operator whose warp row groups exceed the staging window takes 0).
+ * Results do not depend on the split beyond the order of each row's sums.  XAMG_ERR_INVALID_ARG for any other
  * value.  Host only.  No counterpart in the paper. */
 int xamg_set_split(xamg_hier *h, int32_t m, int32_t precond, int32_t level, int32_t which,
                    int32_t candidate);

@@ -23,6 +23,9 @@ namespace {
 struct DevCsr {
   int n = 0, ncols = 0;
   int64_t nnz = 0;
+  // entries of the longest aligned group of 4, 8 and 16 consecutive rows (the
+  // rows one warp of the staged FP32 kernel takes at 32, 16 and 8 columns)
+  int span[3] = {0, 0, 0};
   int32_t *rowptr = nullptr;
   int32_t *col = nullptr;
   double *val = nullptr;
@@ -141,9 +144,10 @@ struct xamg_hier {
   std::vector<GraphRec> graphs;
   // fused coarse tail of the V-cycle (vtail.cuh): levels whose blocks hold at
   // most tail_elems elements (rows x block width) run as one cooperative
-  // launch; 0 turns it off.  tail_limit_s bounds each grid-barrier wait;
-  // tail_extra is added to the barrier's expected arrivals (fault injection)
-  int64_t tail_elems = 131072;
+  // launch; 0 (the default: measured slower than graph-replayed launches)
+  // turns it off.  tail_limit_s bounds each grid-barrier wait; tail_extra is
+  // added to the barrier's expected arrivals (fault injection)
+  int64_t tail_elems = 0;
   double tail_limit_s = 2.0;
   int tail_extra = 0;
   TailSync *tail_sync = nullptr;  // device barrier words
@@ -189,6 +193,13 @@ int upload_csr(xamg_hier *h, const HostCsr &a, DevCsr &d) {
   d.n = a.n;
   d.ncols = a.ncols;
   d.nnz = a.nnz();
+  for (int t = 0; t < 3; ++t) {
+    const int rpw = 4 << t;
+    int mx = 0;
+    for (int r0 = 0; r0 < a.n; r0 += rpw)
+      mx = std::max(mx, a.rowptr[std::min(a.n, r0 + rpw)] - a.rowptr[r0]);
+    d.span[t] = mx;
+  }
   int rc;
   if ((rc = dev_upload(h, &d.rowptr, a.rowptr.data(), a.rowptr.size())) != XAMG_OK) return rc;
   if ((rc = dev_upload(h, &d.col, a.col.data(), a.col.size())) != XAMG_OK) return rc;
@@ -528,6 +539,15 @@ void flush_timing(xamg_hier *h) {
 }
 
 // ---- row kernel wrapper ----
+// Whether the staged FP32 narrow kernel (rows_async) can take operator M on
+// blocks of nv columns: every aligned group of a warp's rows fits its window.
+bool async_fits(const DevCsr &M, int nv, bool fp32) {
+  if (!fp32 || nv < 8) return false;
+  const int t = nv == 32 ? 0 : nv == 16 ? 1 : 2;
+  const int window[3] = {async_window<32>(), async_window<16>(), async_window<8>()};
+  return M.span[t] <= window[t];
+}
+
 // m = 1: 4 or 16 lanes per row.  FP32 blocks of >= 16 columns with long rows
 // (the dense coarse Galerkin levels): one row per warp, split into slices.
 int slices_for(const DevCsr &M, int nv, bool fp32) {
@@ -550,20 +570,22 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
   // 11 696 rows (1 025 entries) down at 16 columns and 5 739 (1 537) at 32
   const double waves = (!fp32 && nv >= 16) ? 2.0 : 1.0;
   if (avg >= 32.0 && warps < waves * 32.0 * device_sm_count()) return 2;
+  // (the staged narrow split, kAsyncNarrow, is a tuning candidate only: it
+  // measured slower than this one on every level it fits)
   return 1;
 }
 
 // Row split of tuning candidate t: m = 1 has seven (the stream-kernel
 // variants and 16 lanes per row, launch.h), wider blocks two (narrow, one row
 // per warp).
-int split_candidates(int nv) { return nv == 1 ? 7 : 2; }
+int split_candidates(int nv, bool fp32) { return nv == 1 ? 7 : (fp32 && nv >= 8 ? 3 : 2); }
 int split_slices(int nv, int t) {
   if (nv == 1) {
     static const int c[7] = {kStreamShort, kSliced16, kStreamLong, kStreamQuad, kStreamWarp, kStreamMid,
                              kStreamPair};
     return c[t];
   }
-  return t ? 2 : 1;
+  return t == 2 ? kAsyncNarrow : t ? 2 : 1;
 }
 
 // Algorithmic bytes of one fused row launch: the matrix once, the operand
@@ -647,7 +669,7 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
     TailStage<TB> &s = prog->st[prog->nstages++];
     s.op = op;
     s.kind = kind;
-    s.wide = sl > 1 ? 1 : 0;
+    s.wide = sl > 1 && sl != kAsyncNarrow ? 1 : 0;
     return 1;
   }
   cudaEvent_t a = nullptr, b = nullptr;
@@ -670,6 +692,7 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
     while ((1 << lg) < nv) ++lg;
     const int t = D.split[(vt == 1 || vt == 2) ? 1 : 0][which][lg];
     if (t >= 0) sl = split_slices(nv, t);
+    if (sl == kAsyncNarrow && !async_fits(M, nv, true)) sl = 1;
     g = launch_rows_f(op, nv, sl, neg, epi, vt, st);
   }
   if (h->timing) {
@@ -1641,7 +1664,7 @@ int tune_product(xamg_hier *h, int l, int which, int precond, RowOpT<TB> o, int 
                  cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int *wide) {
   float best = 1e30f;
   int best_opt = 0;
-  for (int opt = 0; opt < split_candidates(nv); ++opt) {
+  for (int opt = 0; opt < split_candidates(nv, sizeof(TB) == 4); ++opt) {
     slot = (signed char)opt;
     if (rows<TB>(h, l, which, precond, o, nv, false, EPI_Y, st) < 0) return XAMG_ERR_CUDA;
     cudaEventRecord(e0, st);
@@ -2184,7 +2207,7 @@ int xamg_set_split(xamg_hier *h, int32_t m, int32_t precond, int32_t level, int3
   if (level < 0 || level >= L || which < 0 || which > 2 || (which > 0 && level + 1 >= L))
     return XAMG_ERR_INVALID_ARG;
   const int nv = pad_nv(m);
-  if (candidate < -1 || candidate >= split_candidates(nv)) return XAMG_ERR_INVALID_ARG;
+  if (candidate < -1 || candidate >= split_candidates(nv, precond != XAMG_PREC_FP64)) return XAMG_ERR_INVALID_ARG;
   int lg = 0;
   while ((1 << lg) < nv) ++lg;
   const int pc = precond == XAMG_PREC_BF16 ? 1 : precond == XAMG_PREC_FP32 ? 0 : 2;

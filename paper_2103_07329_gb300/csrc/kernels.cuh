@@ -388,6 +388,66 @@ __device__ __forceinline__ void vstore(T *p, const Vec<T, VEC> &r) {
   }
 }
 
+// The epilogue of the vector row kernels for row i (e = i NV + c0): the
+// product sum acc (from zero, or from the init value for FP64 unscaled
+// values) becomes v, and v is written and combined as enum Epi says.
+template <class TB, class TV, int NV, int VEC, int EPI>
+__device__ __forceinline__ void vec_epilogue(const RowOpT<TB> &op, int64_t i, int64_t e, Vec<TB, VEC> acc,
+                                             const Vec<TB, VEC> &in0, const Vec<TB, VEC> &dpv, TB wv,
+                                             const Vec<TB, VEC> &xv, double (&dsum)[VEC],
+                                             double (&dsum2)[VEC]) {
+  using VL = ValueLoad<TV>;
+  using V = Vec<TB, VEC>;
+  constexpr bool xlast = EPI == EPI_XLAST || EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2;
+  if constexpr (!sum_from_init<TB, VL::scaled>()) {
+    const TB s = VL::scaled ? (TB)op.rscale[i] : (TB)1;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc.v[v] = ep_combine<TB, VL::scaled>(acc.v[v], s, op.init != nullptr, in0.v[v]);
+  }
+  // epilogue (see enum Epi)
+  if constexpr (!xlast) {
+    if (op.y) vstore<TB, VEC>(op.y + e, acc);
+  }
+  if constexpr (EPI == EPI_Y_D0 || EPI == EPI_Y_DN || EPI == EPI_MID) {
+    V dn;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v)
+      dn.v[v] = EPI == EPI_Y_D0 ? ep_mul(wv, acc.v[v]) : ep_dn(op.c1, dpv.v[v], wv, acc.v[v]);
+    vstore<TB, VEC>(op.dnext + e, dn);
+  }
+  if constexpr (EPI == EPI_Y_XDP || EPI == EPI_MID) {
+    V xn;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) xn.v[v] = ep_add(xv.v[v], dpv.v[v]);
+    vstore<TB, VEC>(op.x + e, xn);
+  }
+  if constexpr (xlast) {
+    V xn;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) xn.v[v] = ep_xlast(xv.v[v], op.c1, dpv.v[v], wv, acc.v[v]);
+    vstore<TB, VEC>(op.x + e, xn);
+    if constexpr (EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) dsum[v] = fma(op.dot_u[e + v], (double)xn.v[v], dsum[v]);
+    }
+    if constexpr (EPI == EPI_XLAST_DOT2) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) dsum2[v] = fma(op.dot_u2[e + v], (double)xn.v[v], dsum2[v]);
+    }
+  }
+  if constexpr (EPI == EPI_Y_DOT) {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) dsum[v] = fma(op.dot_u[e + v], (double)acc.v[v], dsum[v]);
+  }
+  if constexpr (EPI == EPI_Y_DOT2) {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      if (op.dot_u) dsum[v] = fma(op.dot_u[e + v], (double)acc.v[v], dsum[v]);
+      dsum2[v] = fma((double)acc.v[v], (double)acc.v[v], dsum2[v]);
+    }
+  }
+}
+
 // Row kernel, S = 1.  A group of G = NV/VEC lanes owns one row (32/G rows per
 // warp); lane g of the group holds the VEC adjacent columns g*VEC .. g*VEC+VEC-1
 // and moves them with one 8/16-byte access, so a warp keeps 32/G rows' gathers
@@ -555,55 +615,150 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
       }
       __syncthreads();
     }
-    if (valid && sl == 0 && wx == 0) {
-      if constexpr (!sum_from_init<TB, VL::scaled>()) {
-        const TB s = VL::scaled ? (TB)op.rscale[i] : (TB)1;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) acc.v[v] = ep_combine<TB, VL::scaled>(acc.v[v], s, op.init != nullptr, in0.v[v]);
-      }
-      // epilogue (see enum Epi)
-      if constexpr (!xlast) {
-        if (op.y) vstore<TB, VEC>(op.y + e, acc);
-      }
-      if constexpr (EPI == EPI_Y_D0 || EPI == EPI_Y_DN || EPI == EPI_MID) {
-        V dn;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v)
-          dn.v[v] = EPI == EPI_Y_D0 ? ep_mul(wv, acc.v[v]) : ep_dn(op.c1, dpv.v[v], wv, acc.v[v]);
-        vstore<TB, VEC>(op.dnext + e, dn);
-      }
-      if constexpr (EPI == EPI_Y_XDP || EPI == EPI_MID) {
-        V xn;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) xn.v[v] = ep_add(xv.v[v], dpv.v[v]);
-        vstore<TB, VEC>(op.x + e, xn);
-      }
-      if constexpr (xlast) {
-        V xn;
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) xn.v[v] = ep_xlast(xv.v[v], op.c1, dpv.v[v], wv, acc.v[v]);
-        vstore<TB, VEC>(op.x + e, xn);
-        if constexpr (EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2) {
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) dsum[v] = fma(op.dot_u[e + v], (double)xn.v[v], dsum[v]);
-        }
-        if constexpr (EPI == EPI_XLAST_DOT2) {
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) dsum2[v] = fma(op.dot_u2[e + v], (double)xn.v[v], dsum2[v]);
-        }
-      }
-      if constexpr (EPI == EPI_Y_DOT) {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) dsum[v] = fma(op.dot_u[e + v], (double)acc.v[v], dsum[v]);
-      }
-      if constexpr (EPI == EPI_Y_DOT2) {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-          if (op.dot_u) dsum[v] = fma(op.dot_u[e + v], (double)acc.v[v], dsum[v]);
-          dsum2[v] = fma((double)acc.v[v], (double)acc.v[v], dsum2[v]);
-        }
-      }
+    if (valid && sl == 0 && wx == 0) vec_epilogue<TB, TV, NV, VEC, EPI>(op, i, e, acc, in0, dpv, wv, xv, dsum, dsum2);
+  }
+  if constexpr (epi_has_dot<EPI>()) {
+    if (EPI != EPI_Y_DOT2 || op.dot_u) block_colsum_store_vec<NV, VEC>(dsum, op.partials);
+    if constexpr (EPI == EPI_Y_DOT2 || EPI == EPI_XLAST_DOT2) {
+      __syncthreads();
+      block_colsum_store_vec<NV, VEC>(dsum2, op.partials2);
     }
+  }
+}
+
+// Asynchronous 4- and 8-byte global -> shared copies (no registers held while
+// they are in flight).
+__device__ __forceinline__ void cp_async_4(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// ---- FP32 row kernel with operand rows staged through shared memory ----
+// 16-byte asynchronous global -> shared copy (cached in L1, like the
+// read-only gathers it replaces), and the group bookkeeping of cp.async.
+__device__ __forceinline__ void cp_async_16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Depth of the operand ring (entries in flight per lane) and the per-warp
+// window of staged column indices and values: 32 entries per row of the
+// warp's row group on average (the host takes this kernel only for levels
+// whose every aligned group of rows fits).
+constexpr int kAsyncDepth = 8;
+template <int NV>
+__host__ __device__ constexpr int async_rows_per_warp() { return 32 / (NV / 4); }
+template <int NV>
+__host__ __device__ constexpr int async_window() { return 32 * async_rows_per_warp<NV>(); }
+template <class TV, int NV>
+__host__ __device__ constexpr int async_warp_bytes() {
+  return kAsyncDepth * 32 * 16 + async_window<NV>() * 4 +
+         ((async_window<NV>() + 2) * (int)sizeof(typename ValueLoad<TV>::T) + 15) / 16 * 16;
+}
+
+// The narrow split of FP32 blocks (NV >= 8: a group of G = NV/4 lanes per
+// row, each lane holding 4 adjacent columns) with deeper memory parallelism.
+// A warp's RPW consecutive rows own one contiguous range of the CSR arrays:
+// the warp first copies that range's column indices and values into its
+// shared window (cp.async, 32 consecutive entries per instruction), then each
+// lane streams its 16-byte slice of the rows' operand rows through a private
+// ring of kAsyncDepth slots in shared memory -- entry k + depth is in flight
+// while entry k is multiplied -- so a lane keeps depth gathers outstanding
+// without holding their registers.  Each lane reads back only what it copied
+// itself, so the ring needs no synchronization beyond the lane's own
+// cp.async groups.  The products are added in storage order from zero
+// exactly as rows_vec's narrow split adds them, so the results are bitwise
+// the same; the epilogue is vec_epilogue.
+template <class TB, class TV, int NV, bool NEG, int EPI>
+__device__ __forceinline__ void rows_async(const RowOpT<TB> &op, unsigned char *smem) {
+  static_assert(sizeof(TB) == 4 && NV >= 8, "FP32 blocks of 8 or more columns");
+  using VL = ValueLoad<TV>;
+  using TS = typename VL::T;
+  static_assert(!VL::idx16, "the staged kernel reads 32-bit column indices");
+  constexpr int VEC = 4, G = NV / VEC, RPW = 32 / G, W = async_window<NV>(), D = kAsyncDepth;
+  constexpr bool pairs = sizeof(TS) == 2;
+  constexpr bool xlast = EPI == EPI_XLAST || EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2;
+  using V = Vec<TB, VEC>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gl = lane % G, c0 = gl * VEC, grp = lane / G;
+  unsigned char *wsm = smem + warp * async_warp_bytes<TV, NV>();
+  float4 *ring = reinterpret_cast<float4 *>(wsm);                  // [D][32]
+  int32_t *s_col = reinterpret_cast<int32_t *>(wsm + D * 32 * 16);  // [W]
+  TS *s_val = reinterpret_cast<TS *>(s_col + W);                   // [W + 2]
+  const TS *gval = static_cast<const TS *>(op.val);
+  const int64_t warp0 = (int64_t)blockIdx.x * kWarps + warp;
+  const int64_t wstride = (int64_t)gridDim.x * kWarps;
+  double dsum[VEC], dsum2[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) dsum[v] = dsum2[v] = 0.0;
+  for (int64_t base = warp0 * RPW; base < op.n; base += wstride * RPW) {
+    const int64_t i = base + grp;
+    const bool valid = i < op.n;
+    const int64_t e = i * NV + c0;
+    int start = 0, len = 0;
+    V acc, dpv, xv, in0;
+    TB wv = 0;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc.v[v] = dpv.v[v] = xv.v[v] = in0.v[v] = 0;
+    if (valid) {
+      start = __ldg(op.rowptr + i);
+      len = __ldg(op.rowptr + i + 1) - start;
+      if (op.init) in0 = vload<TB, VEC>(op.init + e);
+      if constexpr (EPI == EPI_Y_DN || EPI == EPI_Y_XDP || EPI == EPI_MID || xlast)
+        dpv = vload<TB, VEC>(op.dp + e);
+      if constexpr (EPI == EPI_Y_D0 || EPI == EPI_Y_DN || EPI == EPI_MID || xlast) wv = op.w[i];
+      if constexpr (EPI == EPI_Y_XDP || EPI == EPI_MID || xlast) xv = vload<TB, VEC>(op.x + e);
+    }
+    // the warp's contiguous range of entries [wb, we) (at most W: host rule)
+    const int wb = (int)__reduce_min_sync(0xffffffffu, valid ? (unsigned)start : 0x7fffffffu);
+    const int we = (int)__reduce_max_sync(0xffffffffu, valid ? (unsigned)(start + len) : 0u);
+    const int vb = pairs ? (wb & ~1) : wb;
+    __syncwarp();  // every lane is done with the previous window
+    for (int k = wb + lane; k < we; k += 32) cp_async_4(s_col + (k - wb), op.col + k);
+    if constexpr (pairs) {
+      for (int k = vb + 2 * lane; k < we; k += 64) cp_async_4(s_val + (k - vb), gval + k);
+    } else {
+      for (int k = wb + lane; k < we; k += 32) cp_async_4(s_val + (k - vb), gval + k);
+    }
+    cp_async_commit();
+    cp_async_wait_group<0>();
+    __syncwarp();
+    const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+    const int off = start - wb, voff = start - vb;
+    // prologue: the first D entries of the lane's row in flight
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      if (d < len) cp_async_16(&ring[d * 32 + lane], op.src + (int64_t)s_col[off + d] * NV + c0);
+      cp_async_commit();
+    }
+    for (int k = 0; k < maxlen; ++k) {
+      cp_async_wait_group<D - 1>();  // entry k of this lane has landed
+      const int slot = (k % D) * 32 + lane;
+      if (k < len) {
+        const float4 q = ring[slot];
+        const TB a = pairs ? (TB)__bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(s_val + voff + k))
+                           : (TB)s_val[voff + k];
+        acc.v[0] = fmadd<NEG>(a, (TB)q.x, acc.v[0]);
+        acc.v[1] = fmadd<NEG>(a, (TB)q.y, acc.v[1]);
+        acc.v[2] = fmadd<NEG>(a, (TB)q.z, acc.v[2]);
+        acc.v[3] = fmadd<NEG>(a, (TB)q.w, acc.v[3]);
+      }
+      // refill the slot just read (its products above consumed it first)
+      if (k + D < len) cp_async_16(&ring[slot], op.src + (int64_t)s_col[off + k + D] * NV + c0);
+      cp_async_commit();
+    }
+    cp_async_wait_group<0>();
+    if (valid) vec_epilogue<TB, TV, NV, VEC, EPI>(op, i, e, acc, in0, dpv, wv, xv, dsum, dsum2);
   }
   if constexpr (epi_has_dot<EPI>()) {
     if (EPI != EPI_Y_DOT2 || op.dot_u) block_colsum_store_vec<NV, VEC>(dsum, op.partials);
@@ -678,17 +833,6 @@ __device__ __forceinline__ void rows_sliced(const RowOpT<TB> &op) {
 }
 
 // ---- m = 1 stream kernel ----
-// Asynchronous 4- and 8-byte global -> shared copies (no registers held while
-// they are in flight).
-__device__ __forceinline__ void cp_async_4(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_8(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Shared-memory bytes of one warp's window of R entries: R column indices,
 // then R + 2 values (bf16 values are copied in aligned pairs, so a window may
@@ -852,6 +996,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_rows(RowOpT<TB> op) {
   } else {
     rows_sliced<TB, TV, NV, S, NEG, EPI>(op);
   }
+}
+
+// The staged FP32 kernel (rows_async): kWarps windows of
+// async_warp_bytes<TV, NV>() bytes of dynamic shared memory per block.
+template <class TB, class TV, int NV, bool NEG, int EPI>
+__global__ void __launch_bounds__(kBlock, 3) k_rows_async(RowOpT<TB> op) {
+  extern __shared__ __align__(16) unsigned char xamg_async_smem[];
+  if constexpr (sizeof(TB) == 4 && NV >= 8 && !ValueLoad<TV>::idx16) rows_async<TB, TV, NV, NEG, EPI>(op, xamg_async_smem);
 }
 
 // The m = 1 stream kernel: window of R entries per warp in dynamic shared

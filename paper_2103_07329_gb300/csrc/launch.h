@@ -81,6 +81,9 @@ constexpr int kWarpsPerRow = 4;
 
 constexpr int kStreamShort = -1, kStreamLong = -2, kStreamQuad = -3, kStreamWarp = -4, kStreamMid = -5,
               kStreamPair = -6, kSliced16 = 16;
+// FP32 blocks of 8 or more columns: the narrow split with operand rows staged
+// through shared memory (rows_async); the `slices` code of the row launchers.
+constexpr int kAsyncNarrow = 100;
 
 int device_sm_count();
 extern std::atomic<int64_t> g_launches;  // kernels launched by the library

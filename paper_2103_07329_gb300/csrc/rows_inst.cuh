@@ -22,7 +22,24 @@ using TBx = double;
 // S < 0: an m = 1 stream-kernel variant (StreamCfg<S>).
 template <class TV, int NV, int S, bool NEG, int EPI>
 int rows_t(const RowOpT<TBx> &op, cudaStream_t st) {
-  if constexpr (S < 0 && NV == 1) {
+  if constexpr (S == kAsyncNarrow) {
+    constexpr int smem = kWarps * async_warp_bytes<TV, NV>();
+    auto kern = k_rows_async<TBx, TV, NV, NEG, EPI>;
+    static int max_grid = 0;
+    if (!max_grid) {
+      int b = 0;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kBlock, smem) != cudaSuccess || b < 1)
+        b = 1;
+      max_grid = std::min(kMaxGrid, b * device_sm_count());
+    }
+    constexpr int rows_per_block = kWarps * async_rows_per_warp<NV>();
+    const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
+    kern<<<grid, kBlock, smem, st>>>(op);
+    g_launches++;
+    return cudaPeekAtLastError() == cudaSuccess ? grid : -1;
+  } else if constexpr (S < 0 && NV == 1) {
     constexpr int LPR = StreamCfg<S>::LPR, R = StreamCfg<S>::R;
     constexpr int smem = kWarps * stream_warp_bytes<TV, R>();
     auto kern = k_rows_stream<TBx, TV, LPR, R, NEG, EPI>;
@@ -114,6 +131,13 @@ int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t 
     }
   }
 #else
+#if XAMG_FLOAT && XAMG_NV >= 8
+  // the narrow split with operand rows staged through shared memory
+  if constexpr (!ValueLoad<TV>::idx16) {
+    if (slices == kAsyncNarrow) return rows_e<TV, XAMG_NV, kAsyncNarrow>(op, neg, epi, st);
+  }
+#endif
+  if (slices == kAsyncNarrow) slices = 1;
   // long rows: every group of the warp takes a slice of one row (one row per
   // warp; with 32 FP64 columns a row already fills the warp)
   constexpr int WS = 32 / (XAMG_NV / row_vec<TBx, XAMG_NV>());

@@ -194,11 +194,14 @@ def test_m1_splits_of_the_reduced_precision_vcycle(prec, cand):
 # order would fail these tests (the FP32-vs-FP64 gap of the cycle is 1-2e-7,
 # and merely fusing the products differently moves it by 1e-7).
 
-def _storage_order(g, m, prec):
+def _storage_order(g, m, prec, cand=0):
+    # candidate 0: the register narrow split; 2 (FP32 blocks of >= 8
+    # columns): the same sums with the operand rows staged through shared
+    # memory (operators whose row groups exceed its window fall back to 0)
     for l in range(g.levels):
         for which in (0, 1, 2):
             if which == 0 or l + 1 < g.levels:
-                g.set_split(m, prec, l, which, 0)
+                g.set_split(m, prec, l, which, cand)
 
 
 def _fp32_block(rows, m, seed):
@@ -207,11 +210,11 @@ def _fp32_block(rows, m, seed):
 
 @pytest.mark.parametrize("key", ["p7_32", "var_24", "p27_16"])
 @pytest.mark.parametrize("prec", [B.PREC_FP32, B.PREC_BF16])
-@pytest.mark.parametrize("m", [1, 4, 32])
-def test_reduced_products_bitwise_in_storage_order(key, prec, m):
+@pytest.mark.parametrize("m,cand", [(1, 0), (4, 0), (32, 0), (8, 2), (16, 2), (32, 2)])
+def test_reduced_products_bitwise_in_storage_order(key, prec, m, cand):
     A, _, o = pair(key)
     g = B.Hierarchy(A)
-    _storage_order(g, m, prec)
+    _storage_order(g, m, prec, cand)
     for l in range(g.levels):
         n = g.level_info(l)[0]
         nc = g.level_info(l + 1)[0] if l + 1 < g.levels else 0
@@ -226,11 +229,11 @@ def test_reduced_products_bitwise_in_storage_order(key, prec, m):
 
 @pytest.mark.parametrize("key", ["p7_32", "var_24", "p27_16"])
 @pytest.mark.parametrize("prec", [B.PREC_FP32, B.PREC_BF16])
-@pytest.mark.parametrize("m", [1, 4, 32])
-def test_reduced_vcycle_bitwise_in_storage_order(key, prec, m):
+@pytest.mark.parametrize("m,cand", [(1, 0), (4, 0), (32, 0), (8, 2), (16, 2), (32, 2)])
+def test_reduced_vcycle_bitwise_in_storage_order(key, prec, m, cand):
     A, _, o = pair(key)
     g = B.Hierarchy(A)
-    _storage_order(g, m, prec)
+    _storage_order(g, m, prec, cand)
     Bm = P.rhs_uniform(A.n, m, 0, m_draw=32)
     X = torch.empty((A.n, m), dtype=torch.float64, device="cuda")
     g.vcycle_precond(prec, dev(Bm), X)
@@ -324,3 +327,13 @@ def test_index16_falls_back_where_rows_do_not_fit():
     Y = torch.empty((A.n, 8), dtype=torch.float64, device="cuda")
     g.spmm_precond(B.PREC_FP32, 0, 0, dev(X), Y)
     assert np.array_equal(Y.cpu().numpy(), o.spmm_f(0, 0, X).astype(np.float64))
+
+
+def test_staged_split_is_rejected_where_it_does_not_exist():
+    # the staged narrow split is a candidate of FP32 blocks of >= 8 columns only
+    g = B.Hierarchy(P.poisson7(12))
+    with pytest.raises(B.XamgError):
+        g.set_split(4, B.PREC_FP32, 0, 0, 2)
+    with pytest.raises(B.XamgError):
+        g.set_split(32, B.PREC_FP64, 0, 0, 2)
+    g.set_split(8, B.PREC_BF16, 0, 0, 2)

@@ -57,6 +57,8 @@ def cycle(g, prec, Bm):
 def test_fused_tail_cycle_is_bitwise_the_unfused_one(key, m, prec):
     A = system(key)
     g = B.Hierarchy(A)
+    assert g.tail_info(m) == -1          # off by default
+    g.set_tail(131072)
     first = g.tail_info(m)
     assert 0 <= first <= g.levels - 2
     Bm = P.rhs_uniform(A.n, m, 0, m_draw=32)
@@ -75,6 +77,7 @@ def test_tail_covers_the_whole_cycle_of_a_small_system():
     # 7-point 32^3 with four right-hand sides: every level's block holds at
     # most 131072 elements, so the cycle from level 0 is one launch
     g = B.Hierarchy(system("p7_32"))
+    g.set_tail(131072)
     assert g.tail_info(4) == 0
     assert g.tail_info(1) == -1          # m = 1 keeps the stream kernels
     g.set_tail(4096)
@@ -105,6 +108,7 @@ def test_fused_tail_solve_is_bitwise_the_unfused_one(prec, method):
 def test_tail_barrier_wait_runs_out_and_the_device_stays_usable():
     A = system("p7_32")
     g = B.Hierarchy(A)
+    g.set_tail(131072)
     Bm = P.rhs_uniform(A.n, 4, 0, m_draw=32)
     ref = cycle(g, B.PREC_FP64, Bm)
     # every barrier now expects one arrival that never comes: each wait ends
