@@ -111,6 +111,10 @@ def parse():
     ap.add_argument("--split-table", action="store_true",
                     help="measurement mode: every row split of every level's FP64 product y = M x "
                          "on --m columns, microseconds per product, one JSON line per operator")
+    ap.add_argument("--tail-table", action="store_true",
+                    help="measurement mode: small solves (7-point 32^3 and 64^3, m = 4 and 32; "
+                         "variable-coefficient 64^3, m = 32) with the fused coarse tail on and off, "
+                         "FP64 and FP32 preconditioners, one JSON line each")
     ap.add_argument("--spmm-only", action="store_true",
                     help="profiling mode: four products y = A x of level --level on --m columns "
                          "with the default row split, nothing else (the case for kernel captures)")
@@ -599,6 +603,8 @@ def run_ours(a):
             "speedup_vs_plain": r["speedup"], "speedup_smoothed_vs_plain": r["speedup_smooth"],
             "iters_plain": [x["iters_plain"] for x in recs], "iters_warm": [x["iters_warm"] for x in recs],
             "iters_warm_smoothed": [x["iters_warm_smooth"] for x in recs],
+            "mean_iters_per_column_plain": [round(x["mean_iters_plain"], 3) for x in recs],
+            "mean_iters_per_column_warm": [round(x["mean_iters_warm"], 3) for x in recs],
             "x0_anorm_error": [round(x["x0_anorm_error"], 4) for x in recs],
             "x0_relres": [round(x["x0_relres"], 4) for x in recs],
             "ms_predict": [round(x["ms_predict"], 3) for x in recs],
@@ -789,6 +795,8 @@ def run_spmm_only(a):
     build_mod.build()
     A = make_matrix(a)
     h = B.Hierarchy(A)
+    if a.index16:
+        h.set_index16(True)
     n, nnz, _ = h.level_info(a.level)
     X = torch.rand(n, a.m, dtype=torch.float64, device="cuda")
     Y = torch.empty(n, a.m, dtype=torch.float64, device="cuda")
@@ -800,7 +808,50 @@ def run_spmm_only(a):
             h.spmm_precond(prec, a.level, 0, X, Y)
     torch.cuda.synchronize()
     print(json.dumps({"matrix": a.matrix, "grid": a.grid, "level": a.level, "n": n, "nnz": nnz, "m": a.m,
-                      "precond": a.precond, "products": 4}))
+                      "precond": a.precond, "index16": a.index16, "products": 4}))
+    return 0
+
+
+def run_tail_table(a):
+    """Milliseconds per PCG solve (tol 1e-8) of small systems with the fused
+    coarse tail (xamg_set_tail, 131072 elements) and without it, CUDA graphs
+    on, after five warm-up solves; CUDA events around max(steps, 20) solves."""
+    import torch
+
+    from paper_2103_07329_gb300 import binding as B
+    from paper_2103_07329_gb300 import build as build_mod
+    from paper_2103_07329_gb300 import problems as P
+
+    build_mod.build()
+    cases = [("poisson7", 32, 4), ("poisson7", 32, 32), ("poisson7", 64, 4), ("poisson7", 64, 32),
+             ("diffusion7", 64, 32)]
+    steps = max(a.steps, 20)
+    for kind, grid, m in cases:
+        A = P.poisson7(grid) if kind == "poisson7" else P.diffusion7(grid, P.lognormal_cells(grid, 1.0, 1))
+        Bm = P.rhs_uniform(A.n, m, 0, m_draw=32)
+        Bd = torch.from_numpy(Bm).cuda()
+        X = torch.empty_like(Bd)
+        for prec in (B.PREC_FP64, B.PREC_FP32):
+            for elems in (131072, 0):
+                h = B.Hierarchy(A)
+                h.set_tail(elems)
+                for _ in range(5):
+                    st = h.solve(Bd, X, a.tol, a.maxit, precond=prec)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                l0 = B.kernel_launches()
+                e0.record()
+                for _ in range(steps):
+                    st = h.solve(Bd, X, a.tol, a.maxit, precond=prec)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                print(json.dumps({"matrix": kind, "grid": grid, "m": m, "precond": "fp64" if prec == 0 else "fp32",
+                                  "tail_first_level": h.tail_info(m), "ms_per_solve": round(ms, 4),
+                                  "rhs_per_s": round(m / ms * 1e3, 1), "iters": int(st.iters.max()),
+                                  "launches_per_solve": (B.kernel_launches() - l0) // steps}), flush=True)
+                h.close()
     return 0
 
 
@@ -814,6 +865,8 @@ def main():
         return run_split_table(a)
     if a.spmm_only:
         return run_spmm_only(a)
+    if a.tail_table:
+        return run_tail_table(a)
     if a.batch_only:
         return run_batch_only(a)
     return run_ours(a)
