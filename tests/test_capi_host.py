@@ -74,6 +74,22 @@ def test_host_only_handle_refuses_device_calls():
     assert e.value.code == B.ERR_INVALID_ARG
     rc = B.lib().xamg_solve(h.handle, 1, 1, 1, 1e-8, 10, None, None)
     assert rc == B.ERR_INVALID_ARG
+    # the reduced-precision product, the 16-bit index and tail queries need the device copy
+    assert B.lib().xamg_level_spmm_precond(h.handle, B.PREC_FP32, 0, 0, 1, 1, 1, None) == B.ERR_INVALID_ARG
+    with pytest.raises(B.XamgError) as e:
+        h.index16_info(0)
+    assert e.value.code == B.ERR_INVALID_ARG
+    with pytest.raises(B.XamgError) as e:
+        h.tail_info(4)
+    assert e.value.code == B.ERR_INVALID_ARG
+    # host-side settings are accepted, with their arguments checked
+    h.set_index16(True)
+    h.set_tail(131072, 0.5, 0)
+    h.set_tail(0)
+    for bad in [(-1, 2.0, 0), (131072, 0.0, 0), (131072, 61.0, 0), (131072, 2.0, -1)]:
+        with pytest.raises(B.XamgError) as e:
+            h.set_tail(*bad)
+        assert e.value.code == B.ERR_INVALID_ARG
 
 
 def assert_same_hierarchy(A, **kw):
