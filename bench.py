@@ -538,6 +538,7 @@ def run_ours(a):
             f32, flev = row_timing(hh, 3)
             hh.timing_enable(False)
             gbs = f32["bytes"] / f32["ms"] / 1e6 if f32["ms"] > 0 else 0.0
+            lv0 = [x for x in flev if x["level"] == 0]
             out["mixed_" + name] = {
                 "value": fv, "speedup_vs_fp64": fv / value64, "ms_per_step": 1e3 * ft / a.steps,
                 "iters": fst.iters.tolist(), "max_relres": float(fst.relres.max()),
@@ -545,6 +546,7 @@ def run_ours(a):
                 "precond_row_kernel": {"bound": "hbm", "achieved_gbs": round(gbs, 1), "peak_gbs": hbm,
                                        "frac": round(gbs / hbm, 4), "launches": f32["launches"],
                                        "share_of_step": round(f32["ms"] / ims, 4),
+                                       "level0_frac": round(lv0[0]["gbs"] / hbm, 4) if lv0 else None,
                                        "pass": "instrumented pass of the same solves"},
                 "roofline_levels": flev}
         hh.set_index16(False)
@@ -578,10 +580,58 @@ def run_ours(a):
         del Bvd, Xv
         return out
 
+    def spmm_form():
+        """The fine-level sparse product alone, y = A x on the benchmark's
+        blocks (m columns), FP64 blocks and FP32 blocks (FP32 and bf16 values of
+        A): algorithmic GB/s of the row kernel by CUDA events over 20 products
+        after 3 warm-ups, against the measured HBM copy peak."""
+        out = {}
+        Yd = torch.empty_like(Bd)
+        for name, prec in (("fp64", B.PREC_FP64), ("fp32", B.PREC_FP32), ("bf16", B.PREC_BF16)):
+            def prod():
+                if prec == B.PREC_FP64:
+                    h.spmm(0, 0, Bd, Yd)
+                else:
+                    h.spmm_precond(prec, 0, 0, Bd, Yd)
+            for _ in range(3):
+                prod()
+            h.timing_enable(True)
+            for _ in range(20):
+                prod()
+            r = h.timing_read(0, 0 if prec == B.PREC_FP64 else 3)
+            h.timing_enable(False)
+            gbs = r["bytes"] / r["ms"] / 1e6
+            out[name] = {"launches": r["launches"], "us_per_product": round(1e3 * r["ms"] / r["launches"], 1),
+                         "achieved_gbs": round(gbs, 1), "peak_gbs": hbm, "frac_of_hbm": round(gbs / hbm, 4),
+                         "tflops": round(r["flops"] / r["ms"] / 1e9, 4),
+                         "algorithmic_bytes_per_product": round(r["bytes"] / r["launches"])}
+        del Yd
+        return out
+
+    def parity_case_form():
+        """The small parity workload: 7-point Poisson 32^3, m = 4 (seed 0), PCG
+        to tol, plain FP64 and with the FP32 preconditioner; RHS/s over
+        max(steps, 20) solves after 3 warm-ups (CUDA graphs on)."""
+        As = P.poisson7(32)
+        hs = B.Hierarchy(As)
+        Bs = torch.from_numpy(P.rhs_uniform(As.n, 4, 0)).cuda()
+        Xs = torch.empty_like(Bs)
+        out = {"workload": (f"3-D 7-point Poisson 32^3 (n={As.n}, nnz={As.nnz}), m=4 RHS uniform[-1,1) "
+                            f"seed 0, PCG + classical RS AMG V(1,1) Chebyshev-2, tol {a.tol:g}")}
+        for name, prec in (("fp64", B.PREC_FP64), ("fp32", B.PREC_FP32)):
+            for _ in range(3):
+                hs.solve(Bs, Xs, a.tol, a.maxit, method, precond=prec)
+            pms, pok, pst = solves(hs, Bs, Xs, max(a.steps, 20), prec)
+            out[name] = {"value": pok / (pms / 1e3), "ms_per_solve": pms / max(a.steps, 20),
+                         "iters": pst.iters.tolist(), "max_relres": float(pst.relres.max())}
+        hs.close()
+        return out
+
     forms = None
     if not a.no_forms:
+        forms = {"spmm_level0": spmm_form(), "parity_case_32": parity_case_form()}
         X64 = X.clone()
-        forms = precision_forms(h, Bd, X, value, X64)
+        forms.update(precision_forms(h, Bd, X, value, X64))
         del X64
         if not a.no_precision:
             forms["precision_var%d" % a.precision_grid] = precision_workload()

@@ -12,7 +12,7 @@ def run_reference(env_extra):
     env = dict(os.environ)
     env.update(env_extra)
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--grid", "8",
-                          "--m", "2", "--cpu-cols", "2", "--steps", "1", "--warmup", "1"],
+                          "--m", "2", "--ref-cols", "2", "--steps", "1", "--warmup", "1"],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
