@@ -1516,7 +1516,6 @@ int solve_rbicgstab(SolveCtx &c, const double *B, double *Xuser, xamg_stats *sta
 // out = A (M u) for the FP64 preconditioner; tmp receives M u.
 int apply_B(SolveCtx &c, const double *u, double *tmp, double *out) {
   xamg_hier *h = c.h;
-  Work &W = c.W;
   const int64_t n = h->lv[0].A.n;
   if (h->lv.size() > 1) launch_scale_rows(c.nv, n, h->lv[0].w[0], u, tmp, elem_grid(n, c.nv), c.st);
   int rc = apply_precond(c, u, tmp);

@@ -459,7 +459,8 @@ __device__ __forceinline__ void vec_epilogue(const RowOpT<TB> &op, int64_t i, in
 // storage order (no reduction adds), and a chunk's tail takes exactly as many
 // FMAs as it has entries.  With scaled (bf16) values the products are summed
 // first and the row scale applied once: v = init +/- s_i * sum_k q_ik x_k.
-template <class TB, class TV, int NV, int VEC, int SL, bool NEG, int EPI, int XW = 1, bool COH = false>
+template <class TB, class TV, int NV, int VEC, int SL, bool NEG, int EPI, int XW = 1, bool COH = false,
+          int CHX = 0>
 __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
   using VL = ValueLoad<TV>;
   using V = Vec<TB, VEC>;
@@ -470,7 +471,7 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
   // already fill the registers; never more than the G lanes of a row group
   // hold, since a chunk's shuffles broadcast the group's own entries (narrow
   // blocks, m = 2..8, would otherwise spend most shuffles on empty slots)
-  constexpr int CH0 = sizeof(TB) == 4 ? 4 : 8;
+  constexpr int CH0 = CHX > 0 ? CHX : (sizeof(TB) == 4 ? 4 : 8);
   constexpr int CH = CH0 < G ? CH0 : G;
   constexpr int K = 32 / G < 4 ? 32 / G : 4;  // entries each lane fetches per round
   constexpr bool xlast = EPI == EPI_XLAST || EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2;

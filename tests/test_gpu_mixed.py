@@ -337,3 +337,5 @@ def test_staged_split_is_rejected_where_it_does_not_exist():
     with pytest.raises(B.XamgError):
         g.set_split(32, B.PREC_FP64, 0, 0, 2)
     g.set_split(8, B.PREC_BF16, 0, 0, 2)
+    with pytest.raises(B.XamgError):
+        g.set_split(32, B.PREC_FP32, 0, 0, 3)
