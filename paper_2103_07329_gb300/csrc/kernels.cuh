@@ -394,13 +394,13 @@ __device__ __forceinline__ void vstore(T *p, const Vec<T, VEC> &r) {
 template <class TB, class TV, int NV, int VEC, int EPI>
 __device__ __forceinline__ void vec_epilogue(const RowOpT<TB> &op, int64_t i, int64_t e, Vec<TB, VEC> acc,
                                              const Vec<TB, VEC> &in0, const Vec<TB, VEC> &dpv, TB wv,
-                                             const Vec<TB, VEC> &xv, double (&dsum)[VEC],
+                                             const Vec<TB, VEC> &xv, TB s, double (&dsum)[VEC],
                                              double (&dsum2)[VEC]) {
   using VL = ValueLoad<TV>;
   using V = Vec<TB, VEC>;
   constexpr bool xlast = EPI == EPI_XLAST || EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2;
+  // s: the row scale of scaled (bf16) values, loaded before the product loop
   if constexpr (!sum_from_init<TB, VL::scaled>()) {
-    const TB s = VL::scaled ? (TB)op.rscale[i] : (TB)1;
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc.v[v] = ep_combine<TB, VL::scaled>(acc.v[v], s, op.init != nullptr, in0.v[v]);
   }
@@ -504,12 +504,13 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
     uint32_t meta = 0;
     int4 tb = make_int4(0, 0, 0, 0);
     V acc, dpv, xv, in0;
-    TB wv = 0;
+    TB wv = 0, rs = 1;
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc.v[v] = dpv.v[v] = xv.v[v] = in0.v[v] = 0;
     if (valid) {
       start = __ldg(op.rowptr + i);
       len = __ldg(op.rowptr + i + 1) - start;
+      if constexpr (VL::scaled) rs = (TB)__ldg(op.rscale + i);
       if constexpr (VL::idx16) {
         meta = __ldg(op.rowmeta + i);
         tb = __ldg(reinterpret_cast<const int4 *>(op.tbase) + i / kSegTile);
@@ -616,7 +617,7 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
       }
       __syncthreads();
     }
-    if (valid && sl == 0 && wx == 0) vec_epilogue<TB, TV, NV, VEC, EPI>(op, i, e, acc, in0, dpv, wv, xv, dsum, dsum2);
+    if (valid && sl == 0 && wx == 0) vec_epilogue<TB, TV, NV, VEC, EPI>(op, i, e, acc, in0, dpv, wv, xv, rs, dsum, dsum2);
   }
   if constexpr (epi_has_dot<EPI>()) {
     if (EPI != EPI_Y_DOT2 || op.dot_u) block_colsum_store_vec<NV, VEC>(dsum, op.partials);
@@ -708,12 +709,13 @@ __device__ __forceinline__ void rows_async(const RowOpT<TB> &op, unsigned char *
     const int64_t e = i * NV + c0;
     int start = 0, len = 0;
     V acc, dpv, xv, in0;
-    TB wv = 0;
+    TB wv = 0, rs = 1;
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc.v[v] = dpv.v[v] = xv.v[v] = in0.v[v] = 0;
     if (valid) {
       start = __ldg(op.rowptr + i);
       len = __ldg(op.rowptr + i + 1) - start;
+      if constexpr (VL::scaled) rs = (TB)__ldg(op.rscale + i);
       if (op.init) in0 = vload<TB, VEC>(op.init + e);
       if constexpr (EPI == EPI_Y_DN || EPI == EPI_Y_XDP || EPI == EPI_MID || xlast)
         dpv = vload<TB, VEC>(op.dp + e);
@@ -759,7 +761,7 @@ __device__ __forceinline__ void rows_async(const RowOpT<TB> &op, unsigned char *
       cp_async_commit();
     }
     cp_async_wait_group<0>();
-    if (valid) vec_epilogue<TB, TV, NV, VEC, EPI>(op, i, e, acc, in0, dpv, wv, xv, dsum, dsum2);
+    if (valid) vec_epilogue<TB, TV, NV, VEC, EPI>(op, i, e, acc, in0, dpv, wv, xv, rs, dsum, dsum2);
   }
   if constexpr (epi_has_dot<EPI>()) {
     if (EPI != EPI_Y_DOT2 || op.dot_u) block_colsum_store_vec<NV, VEC>(dsum, op.partials);
@@ -791,10 +793,13 @@ __device__ __forceinline__ void rows_sliced(const RowOpT<TB> &op) {
   for (int64_t base = warp0 * RPW; base < op.n; base += wstride * RPW) {
     const int64_t i = base + grp;
     const bool valid = i < op.n;
-    TB acc = 0, dpv = 0, wv = 0, xv = 0;
+    TB acc = 0, dpv = 0, wv = 0, xv = 0, rs = 1, iv = 0;
     double du = 0.0, du2 = 0.0;
     if (valid) {
       if (sum_from_init<TB, VL::scaled>() && op.init && s == 0) acc = op.init[i * NV + c];
+      // the row scale and (for sums from zero) the init value, before the loop
+      if constexpr (VL::scaled) rs = (TB)__ldg(op.rscale + i);
+      if (!sum_from_init<TB, VL::scaled>() && op.init) iv = op.init[i * NV + c];
       row_operands<TB, NV, EPI>(op, i, c, dpv, wv, xv, du, du2);
       int k = __ldg(op.rowptr + i) + s;
       const int end = __ldg(op.rowptr + i + 1);
@@ -818,9 +823,7 @@ __device__ __forceinline__ void rows_sliced(const RowOpT<TB> &op) {
 #pragma unroll
     for (int o = NV; o < G; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if constexpr (!sum_from_init<TB, VL::scaled>()) {
-      if (valid)
-        acc = ep_combine<TB, VL::scaled>(acc, VL::scaled ? (TB)op.rscale[i] : (TB)1, op.init != nullptr,
-                                         op.init ? op.init[i * NV + c] : (TB)0);
+      if (valid) acc = ep_combine<TB, VL::scaled>(acc, rs, op.init != nullptr, iv);
     }
     if (valid && s == 0) row_epilogue<TB, NV, EPI>(op, i, c, acc, dpv, wv, xv, du, du2, dsum, dsum2);
   }
