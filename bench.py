@@ -83,6 +83,12 @@ def parse():
     ap.add_argument("--fp32-split", type=int, default=-1,
                     help="--sweep: force this split candidate on every FP32-block product "
                          "(-1: the default rule)")
+    ap.add_argument("--fp64-split", type=int, default=-1,
+                    help="--sweep: force this split candidate on every FP64 product of the "
+                         "levels averaging at most --split-max-row entries per row")
+    ap.add_argument("--split-max-row", type=float, default=1e9,
+                    help="--sweep: the forced splits apply to levels with at most this many "
+                         "entries per row on average")
     ap.add_argument("--index16", action="store_true",
                     help="--sweep: 16-bit column indices in the reduced-precision products")
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -745,12 +751,16 @@ def run_sweep(a):
                                ("mixed_bf16", B.PREC_BF16)):
                 if method == B.BICGSTAB_PIPELINED and prec != B.PREC_FP64:
                     continue  # its recurrences need a linear preconditioner
-                if prec != B.PREC_FP64 and a.fp32_split >= 0:
+                force = a.fp64_split if prec == B.PREC_FP64 else a.fp32_split
+                if force >= 0:
                     for l in range(h.levels):
+                        n_l, nnz_l, _ = h.level_info(l)
+                        if nnz_l / max(n_l, 1) > a.split_max_row:
+                            continue
                         for which in (0, 1, 2):
                             if which == 0 or l + 1 < h.levels:
                                 try:
-                                    h.set_split(m, prec, l, which, a.fp32_split)
+                                    h.set_split(m, prec, l, which, force)
                                 except B.XamgError:
                                     pass
                 h.solve(Bd, X, a.tol, a.maxit, method, precond=prec)
@@ -776,7 +786,8 @@ def run_sweep(a):
                                        "gbs": round(r["bytes"] / r["ms"] / 1e6, 1)})
                 h.timing_enable(False)
                 print(json.dumps({"matrix": a.matrix, "grid": a.grid, "n": A.n, "m": m,
-                                  "index16": a.index16, "fp32_split": a.fp32_split,
+                                  "index16": a.index16, "fp32_split": a.fp32_split, "fp64_split": a.fp64_split,
+                                  "split_max_row": a.split_max_row,
                                   "method": method_name, "form": form,
                                   "rhs_per_s": round(solved / (ms * a.steps / 1e3), 2),
                                   "ms_per_solve": round(ms, 3), "iters": int(st.iters.max()),

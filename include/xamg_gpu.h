@@ -419,7 +419,9 @@ int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_
  * 32 columns: four warps per row), and for FP32 blocks of 8 or more columns
  * 2 = a group of lanes per row with the operand rows staged through shared
  * memory by asynchronous copies (the sums of candidate 0, bit for bit; an
- * operator whose warp row groups exceed the staging window takes 0).
+ * operator whose warp row groups exceed the staging window takes 0), and
+ * for blocks of 2 or 4 columns 2 = the stream kernel of m = 1 with one lane
+ * per row holding the row's columns (the sums of candidate 0).
  * Results do not depend on the split beyond the order of each row's sums.  XAMG_ERR_INVALID_ARG for any other
  * value.  Host only.  No counterpart in the paper. */
 int xamg_set_split(xamg_hier *h, int32_t m, int32_t precond, int32_t level, int32_t which,

@@ -539,6 +539,10 @@ void flush_timing(xamg_hier *h) {
 }
 
 // ---- row kernel wrapper ----
+// Blocks of 2 or 4 columns (8- to 32-byte rows) can take the stream kernel
+// with one lane per row (rows_stream_v).
+bool stream_v_ok(int nv, bool /*fp32*/) { return nv == 2 || nv == 4; }
+
 // Whether the staged FP32 narrow kernel (rows_async) can take operator M on
 // blocks of nv columns: every aligned group of a warp's rows fits its window.
 bool async_fits(const DevCsr &M, int nv, bool fp32) {
@@ -570,6 +574,11 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
   // 11 696 rows (1 025 entries) down at 16 columns and 5 739 (1 537) at 32
   const double waves = (!fp32 && nv >= 16) ? 2.0 : 1.0;
   if (avg >= 32.0 && warps < waves * 32.0 * device_sm_count()) return 2;
+  // 2- and 4-column blocks on sparse levels: one lane per row over the warp's
+  // staged entries (measured per level at m = 2 and 4 on the 7- and 27-point
+  // hierarchies: FP64 faster up to 27 entries per row and slower at 35; FP32
+  // faster from 19 to 35 and slower at 7)
+  if (stream_v_ok(nv, fp32) && (fp32 ? (avg > 10.0 && avg <= 40.0) : avg <= 30.0)) return kStreamV1024;
   // (the staged narrow split, kAsyncNarrow, is a tuning candidate only: it
   // measured slower than this one on every level it fits)
   return 1;
@@ -578,14 +587,19 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
 // Row split of tuning candidate t: m = 1 has seven (the stream-kernel
 // variants and 16 lanes per row, launch.h), wider blocks two (narrow, one row
 // per warp).
-int split_candidates(int nv, bool fp32) { return nv == 1 ? 7 : (fp32 && nv >= 8 ? 3 : 2); }
+// Blocks of 8 or more FP32 columns have the staged narrow split as a third
+// tuning candidate, blocks with 8- or 16-byte rows the stream kernel.
+int split_candidates(int nv, bool fp32) {
+  return nv == 1 ? 7 : ((fp32 && nv >= 8) || stream_v_ok(nv, fp32)) ? 3 : 2;
+}
 int split_slices(int nv, int t) {
   if (nv == 1) {
     static const int c[7] = {kStreamShort, kSliced16, kStreamLong, kStreamQuad, kStreamWarp, kStreamMid,
                              kStreamPair};
     return c[t];
   }
-  return t == 2 ? kAsyncNarrow : t ? 2 : 1;
+  if (t == 2) return nv >= 8 ? kAsyncNarrow : kStreamV1024;
+  return t ? 2 : 1;
 }
 
 // Algorithmic bytes of one fused row launch: the matrix once, the operand
@@ -669,7 +683,7 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
     TailStage<TB> &s = prog->st[prog->nstages++];
     s.op = op;
     s.kind = kind;
-    s.wide = sl > 1 && sl != kAsyncNarrow ? 1 : 0;
+    s.wide = sl > 1 && sl < kAsyncNarrow ? 1 : 0;  // the staged / stream codes sum as the narrow split
     return 1;
   }
   cudaEvent_t a = nullptr, b = nullptr;

@@ -340,6 +340,14 @@ __device__ __forceinline__ Vec<T, VEC> vload(const T *p) {
   Vec<T, VEC> r;
   if constexpr (VEC == 1) {
     r.v[0] = *p;
+  } else if constexpr (sizeof(T) * VEC == 32) {
+    // two 16-byte halves
+    const Vec<T, VEC / 2> lo = vload<T, VEC / 2>(p), hi = vload<T, VEC / 2>(p + VEC / 2);
+#pragma unroll
+    for (int k = 0; k < VEC / 2; ++k) {
+      r.v[k] = lo.v[k];
+      r.v[k + VEC / 2] = hi.v[k];
+    }
   } else if constexpr (sizeof(T) * VEC == 16) {
     if constexpr (sizeof(T) == 4) {
       const float4 q = *reinterpret_cast<const float4 *>(p);
@@ -360,6 +368,13 @@ __device__ __forceinline__ Vec<T, VEC> vldg(const T *p) {
   Vec<T, VEC> r;
   if constexpr (VEC == 1) {
     r.v[0] = __ldg(p);
+  } else if constexpr (sizeof(T) * VEC == 32) {
+    const Vec<T, VEC / 2> lo = vldg<T, VEC / 2>(p), hi = vldg<T, VEC / 2>(p + VEC / 2);
+#pragma unroll
+    for (int k = 0; k < VEC / 2; ++k) {
+      r.v[k] = lo.v[k];
+      r.v[k + VEC / 2] = hi.v[k];
+    }
   } else if constexpr (sizeof(T) * VEC == 16) {
     if constexpr (sizeof(T) == 4) {
       const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
@@ -378,6 +393,15 @@ template <class T, int VEC>
 __device__ __forceinline__ void vstore(T *p, const Vec<T, VEC> &r) {
   if constexpr (VEC == 1) {
     *p = r.v[0];
+  } else if constexpr (sizeof(T) * VEC == 32) {
+    Vec<T, VEC / 2> lo, hi;
+#pragma unroll
+    for (int k = 0; k < VEC / 2; ++k) {
+      lo.v[k] = r.v[k];
+      hi.v[k] = r.v[k + VEC / 2];
+    }
+    vstore<T, VEC / 2>(p, lo);
+    vstore<T, VEC / 2>(p + VEC / 2, hi);
   } else if constexpr (sizeof(T) * VEC == 16) {
     if constexpr (sizeof(T) == 4)
       *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
@@ -964,6 +988,120 @@ __device__ __forceinline__ void rows_stream(const RowOpT<TB> &op, unsigned char 
   }
 }
 
+// The stream kernel for narrow blocks of NV = 2 or 4 columns (8 to 32 bytes of
+// block row: FP64 with 2 or 4 columns, FP32 with 2 or 4): one lane per row holds
+// the row's NV columns, and the warp's entries are staged in shared memory
+// exactly as at m = 1, so the lane walks its row from the window and gathers
+// one NV-wide operand row per entry (one 8- or 16-byte access, two for 32
+// bytes).  Each
+// column's products are added in storage order, as in the narrow split; the
+// epilogue is vec_epilogue on the lane's NV columns.
+template <class TB, class TV, int NV, int R, bool NEG, int EPI>
+__device__ __forceinline__ void rows_stream_v(const RowOpT<TB> &op, unsigned char *smem) {
+  using VL = ValueLoad<TV>;
+  using TS = typename VL::T;
+  using V = Vec<TB, NV>;
+  static_assert(!VL::idx16, "the stream kernel reads 32-bit column indices");
+  static_assert(NV * sizeof(TB) == 8 || NV * sizeof(TB) == 16 || NV * sizeof(TB) == 32,
+                "8-, 16- or 32-byte block rows");
+  constexpr bool pairs = sizeof(TS) == 2;
+  constexpr bool xlast = EPI == EPI_XLAST || EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t *s_col = reinterpret_cast<int32_t *>(smem + warp * stream_warp_bytes<TV, R>());
+  TS *s_val = reinterpret_cast<TS *>(s_col + R);
+  const int64_t n = op.n;
+  const int64_t step = (int64_t)gridDim.x * kWarps * 32;
+  const TS *gval = static_cast<const TS *>(op.val);
+  double dsum[NV], dsum2[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) dsum[v] = dsum2[v] = 0.0;
+  int64_t r0 = ((int64_t)blockIdx.x * kWarps + warp) * 32;
+  int rs = 0, re = 0;
+  if (r0 < n) {
+    rs = __ldg(op.rowptr + min(r0 + lane, n));
+    re = __ldg(op.rowptr + min(r0 + lane + 1, n));
+  }
+  for (; r0 < n; r0 += step) {
+    const int64_t i = r0 + lane;
+    const bool valid = i < n;
+    const int64_t e = i * NV;
+    V acc, dpv, xv, in0;
+    TB wv = 0, rsc = 1;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc.v[v] = dpv.v[v] = xv.v[v] = in0.v[v] = 0;
+    if (valid) {
+      if (op.init) in0 = vload<TB, NV>(op.init + e);
+      if constexpr (VL::scaled) rsc = (TB)__ldg(op.rscale + i);
+      if constexpr (EPI == EPI_Y_DN || EPI == EPI_Y_XDP || EPI == EPI_MID || xlast) dpv = vload<TB, NV>(op.dp + e);
+      if constexpr (EPI == EPI_Y_D0 || EPI == EPI_Y_DN || EPI == EPI_MID || xlast) wv = op.w[i];
+      if constexpr (EPI == EPI_Y_XDP || EPI == EPI_MID || xlast) xv = vload<TB, NV>(op.x + e);
+    }
+    // FP64 unscaled values start the sums at the init value (no FP64 add)
+    if constexpr (sum_from_init<TB, VL::scaled>()) acc = in0;
+    int nrs = 0, nre = 0;
+    if (r0 + step < n) {
+      nrs = __ldg(op.rowptr + min(r0 + step + lane, n));
+      nre = __ldg(op.rowptr + min(r0 + step + lane + 1, n));
+    }
+    const int e0 = __shfl_sync(0xffffffffu, rs, 0), e1 = __shfl_sync(0xffffffffu, re, 31);
+    for (int wb = e0; wb < e1; wb += R) {
+      const int we = min(e1, wb + R);
+      const int vb = pairs ? (wb & ~1) : wb;
+      __syncwarp();
+      for (int k = wb + lane; k < we; k += 32) cp_async_4(s_col + (k - wb), op.col + k);
+      if constexpr (pairs) {
+        for (int k = vb + 2 * lane; k < we; k += 64) cp_async_4(s_val + (k - vb), gval + k);
+      } else if constexpr (sizeof(TS) == 8) {
+        for (int k = wb + lane; k < we; k += 32) cp_async_8(s_val + (k - vb), gval + k);
+      } else {
+        for (int k = wb + lane; k < we; k += 32) cp_async_4(s_val + (k - vb), gval + k);
+      }
+      cp_async_wait_all();
+      __syncwarp();
+      const int lo = max(rs, wb), hi = min(re, we);
+      const int cnt = hi > lo ? hi - lo : 0;
+      const int wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
+      // blocks of four entries (their gathers in flight together), then a
+      // warp-uniform tail of exactly wmax % 4 (a masked lane adds 0 * 0)
+      for (int q = 0; q < wmax; q += 4) {
+        TB a[4];
+        V xg[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a[u] = (TB)0;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) xg[u].v[v] = (TB)0;
+          const int k = lo + q + u;
+          if (k < hi) {
+            const int c = s_col[k - wb];
+            if constexpr (pairs) a[u] = __bfloat162float(s_val[k - vb]);
+            else a[u] = (TB)s_val[k - vb];
+            xg[u] = vldg<TB, NV>(op.src + (int64_t)c * NV);
+          }
+        }
+        const int rem = min(4, wmax - q);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (u < rem) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc.v[v] = fmadd<NEG>(a[u], xg[u].v[v], acc.v[v]);
+          }
+        }
+      }
+    }
+    if (valid) vec_epilogue<TB, TV, NV, NV, EPI>(op, i, e, acc, in0, dpv, wv, xv, rsc, dsum, dsum2);
+    rs = nrs;
+    re = nre;
+  }
+  if constexpr (epi_has_dot<EPI>()) {
+    if (EPI != EPI_Y_DOT2 || op.dot_u) block_colsum_store_vec<NV, NV>(dsum, op.partials);
+    if constexpr (EPI == EPI_Y_DOT2 || EPI == EPI_XLAST_DOT2) {
+      __syncthreads();
+      block_colsum_store_vec<NV, NV>(dsum2, op.partials2);
+    }
+  }
+}
+
 // Stream-kernel variants of the m = 1 split (the S < 0 codes of the row
 // launchers): lanes per row and window entries.
 template <int S> struct StreamCfg;
@@ -1000,6 +1138,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_rows(RowOpT<TB> op) {
   } else {
     rows_sliced<TB, TV, NV, S, NEG, EPI>(op);
   }
+}
+
+// The stream kernel for 2- and 4-column blocks (rows_stream_v), window of R
+// entries per warp as at m = 1.
+template <class TB, class TV, int NV, int R, bool NEG, int EPI>
+__global__ void __launch_bounds__(kBlock, R <= 512 ? 4 : 2) k_rows_stream_v(RowOpT<TB> op) {
+  extern __shared__ __align__(16) unsigned char xamg_stream_v_smem[];
+  if constexpr ((NV * sizeof(TB) == 8 || NV * sizeof(TB) == 16 || (sizeof(TB) == 8 && NV == 4)) &&
+                !ValueLoad<TV>::idx16)
+    rows_stream_v<TB, TV, NV, R, NEG, EPI>(op, xamg_stream_v_smem);
 }
 
 // The staged FP32 kernel (rows_async): kWarps windows of

@@ -84,6 +84,9 @@ constexpr int kStreamShort = -1, kStreamLong = -2, kStreamQuad = -3, kStreamWarp
 // FP32 blocks of 8 or more columns: the narrow split with operand rows staged
 // through shared memory (rows_async); the `slices` code of the row launchers.
 constexpr int kAsyncNarrow = 100;
+// Blocks of 2 or 4 columns (8 or 16 bytes per block row): the stream kernel
+// with one lane per row and a 256- or 1024-entry window (rows_stream_v).
+constexpr int kStreamV256 = 200, kStreamV1024 = 201;
 
 int device_sm_count();
 extern std::atomic<int64_t> g_launches;  // kernels launched by the library

@@ -22,7 +22,25 @@ using TBx = double;
 // S < 0: an m = 1 stream-kernel variant (StreamCfg<S>).
 template <class TV, int NV, int S, bool NEG, int EPI>
 int rows_t(const RowOpT<TBx> &op, cudaStream_t st) {
-  if constexpr (S == kAsyncNarrow) {
+  if constexpr (S == kStreamV256 || S == kStreamV1024) {
+    constexpr int R = S == kStreamV256 ? 256 : 1024;
+    constexpr int smem = kWarps * stream_warp_bytes<TV, R>();
+    auto kern = k_rows_stream_v<TBx, TV, NV, R, NEG, EPI>;
+    static int max_grid = 0;
+    if (!max_grid) {
+      int b = 0;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kBlock, smem) != cudaSuccess || b < 1)
+        b = 1;
+      max_grid = std::min(kMaxGrid, b * device_sm_count());
+    }
+    constexpr int rows_per_block = kWarps * 32;
+    const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
+    kern<<<grid, kBlock, smem, st>>>(op);
+    g_launches++;
+    return cudaPeekAtLastError() == cudaSuccess ? grid : -1;
+  } else if constexpr (S == kAsyncNarrow) {
     constexpr int smem = kWarps * async_warp_bytes<TV, NV>();
     auto kern = k_rows_async<TBx, TV, NV, NEG, EPI>;
     static int max_grid = 0;
@@ -131,6 +149,14 @@ int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t 
     }
   }
 #else
+#if XAMG_NV == 2 || XAMG_NV == 4
+  // one lane per row over the warp's staged entries (8- to 32-byte block rows)
+  if constexpr (!ValueLoad<TV>::idx16) {
+    if (slices == kStreamV256) return rows_e<TV, XAMG_NV, kStreamV256>(op, neg, epi, st);
+    if (slices == kStreamV1024) return rows_e<TV, XAMG_NV, kStreamV1024>(op, neg, epi, st);
+  }
+#endif
+  if (slices == kStreamV256 || slices == kStreamV1024) slices = 1;
 #if XAMG_FLOAT && XAMG_NV >= 8
   // the narrow split with operand rows staged through shared memory
   if constexpr (!ValueLoad<TV>::idx16) {

@@ -197,7 +197,8 @@ def test_m1_splits_of_the_reduced_precision_vcycle(prec, cand):
 def _storage_order(g, m, prec, cand=0):
     # candidate 0: the register narrow split; 2 (FP32 blocks of >= 8
     # columns): the same sums with the operand rows staged through shared
-    # memory (operators whose row groups exceed its window fall back to 0)
+    # memory (operators whose row groups exceed its window fall back to 0);
+    # 2 for 2 and 4 columns: the stream kernel with one lane per row
     for l in range(g.levels):
         for which in (0, 1, 2):
             if which == 0 or l + 1 < g.levels:
@@ -210,7 +211,7 @@ def _fp32_block(rows, m, seed):
 
 @pytest.mark.parametrize("key", ["p7_32", "var_24", "p27_16"])
 @pytest.mark.parametrize("prec", [B.PREC_FP32, B.PREC_BF16])
-@pytest.mark.parametrize("m,cand", [(1, 0), (4, 0), (32, 0), (8, 2), (16, 2), (32, 2)])
+@pytest.mark.parametrize("m,cand", [(1, 0), (4, 0), (32, 0), (8, 2), (16, 2), (32, 2), (2, 2), (4, 2)])
 def test_reduced_products_bitwise_in_storage_order(key, prec, m, cand):
     A, _, o = pair(key)
     g = B.Hierarchy(A)
@@ -229,7 +230,7 @@ def test_reduced_products_bitwise_in_storage_order(key, prec, m, cand):
 
 @pytest.mark.parametrize("key", ["p7_32", "var_24", "p27_16"])
 @pytest.mark.parametrize("prec", [B.PREC_FP32, B.PREC_BF16])
-@pytest.mark.parametrize("m,cand", [(1, 0), (4, 0), (32, 0), (8, 2), (16, 2), (32, 2)])
+@pytest.mark.parametrize("m,cand", [(1, 0), (4, 0), (32, 0), (8, 2), (16, 2), (32, 2), (2, 2), (4, 2)])
 def test_reduced_vcycle_bitwise_in_storage_order(key, prec, m, cand):
     A, _, o = pair(key)
     g = B.Hierarchy(A)
@@ -329,13 +330,14 @@ def test_index16_falls_back_where_rows_do_not_fit():
     assert np.array_equal(Y.cpu().numpy(), o.spmm_f(0, 0, X).astype(np.float64))
 
 
-def test_staged_split_is_rejected_where_it_does_not_exist():
-    # the staged narrow split is a candidate of FP32 blocks of >= 8 columns only
+def test_third_split_candidate_exists_where_documented():
+    # candidate 2: the staged narrow split for FP32 blocks of >= 8 columns, the
+    # stream kernel for 2 and 4 columns; nothing for wider FP64 blocks
     g = B.Hierarchy(P.poisson7(12))
-    with pytest.raises(B.XamgError):
-        g.set_split(4, B.PREC_FP32, 0, 0, 2)
-    with pytest.raises(B.XamgError):
-        g.set_split(32, B.PREC_FP64, 0, 0, 2)
-    g.set_split(8, B.PREC_BF16, 0, 0, 2)
-    with pytest.raises(B.XamgError):
-        g.set_split(32, B.PREC_FP32, 0, 0, 3)
+    for m, prec in [(2, B.PREC_FP32), (4, B.PREC_FP32), (8, B.PREC_BF16), (32, B.PREC_FP32),
+                    (2, B.PREC_FP64), (4, B.PREC_FP64)]:
+        g.set_split(m, prec, 0, 0, 2)
+        g.set_split(m, prec, 0, 0, -1)
+    for m, prec, cand in [(32, B.PREC_FP64, 2), (8, B.PREC_FP64, 2), (32, B.PREC_FP32, 3)]:
+        with pytest.raises(B.XamgError):
+            g.set_split(m, prec, 0, 0, cand)

@@ -176,10 +176,57 @@ def test_spmm_wide_blocks_every_split(m, cand):
                     pr.g.set_split(m, B.PREC_FP64, l, which, -1)
 
 
+@pytest.mark.parametrize("m", [2, 4])
+def test_narrow_block_stream_split_is_bitwise_the_narrow_split(m):
+    # 2- and 4-column FP64 blocks: the stream kernel (one lane per row over the
+    # warp's staged entries, candidate 2) adds each column's products in
+    # storage order like the narrow split (candidate 0), on every level and
+    # operator, so products and the V-cycle agree bit for bit; the solve's
+    # fused dot products reduce in another lane and block order, so its
+    # iterates agree to rounding
+    for name, N in (("p7", 33), ("p27", 20)):
+        pr = pair(name, N)
+        rng = np.random.default_rng(7)
+        outs = []
+        for cand in (0, 2):
+            for l in range(pr.o.nlev):
+                for which in (0, 1, 2):
+                    if which == 0 or l + 1 < pr.o.nlev:
+                        pr.g.set_split(m, B.PREC_FP64, l, which, cand)
+            ys = []
+            for l in range(pr.o.nlev):
+                lv = pr.o.level(l)
+                ops = [(0, lv.n, lv.n)]
+                if lv.P is not None:
+                    nc = pr.o.level(l + 1).n
+                    ops += [(1, lv.n, nc), (2, nc, lv.n)]
+                for which, rows, ncols in ops:
+                    X = np.random.default_rng(10 * l + which).standard_normal((ncols, m))
+                    Y = torch.empty((rows, m), dtype=torch.float64, device="cuda")
+                    pr.g.spmm(l, which, dev(X), Y)
+                    ys.append(Y.cpu().numpy())
+            Bm = P.rhs_uniform(pr.A.n, m, 0)
+            Z = torch.empty((pr.A.n, m), dtype=torch.float64, device="cuda")
+            pr.g.vcycle(dev(Bm), Z)
+            ys.append(Z.cpu().numpy())
+            st = pr.g.solve(dev(Bm), Z, tol=1e-8, maxit=100)
+            assert st.rc == 0
+            outs.append((ys, Z.cpu().numpy(), st.iters.copy()))
+        for l in range(pr.o.nlev):
+            for which in (0, 1, 2):
+                if which == 0 or l + 1 < pr.o.nlev:
+                    pr.g.set_split(m, B.PREC_FP64, l, which, -1)
+        (ya, xa, ia), (yb, xb, ib) = outs
+        for a, b in zip(ya, yb):
+            assert np.array_equal(a, b), name
+        assert np.array_equal(ia, ib) and colrel(xa, xb).max() <= 1e-12
+
+
 def test_set_split_rejects_bad_arguments(cfg0):
     g = cfg0.g
     L = cfg0.o.nlev
-    for args in [(1, B.PREC_FP64, 0, 0, 7), (2, B.PREC_FP64, 0, 0, 2), (1, 9, 0, 0, 0),
+    for args in [(1, B.PREC_FP64, 0, 0, 7), (8, B.PREC_FP64, 0, 0, 2), (2, B.PREC_FP64, 0, 0, 3),
+                 (1, 9, 0, 0, 0),
                  (1, B.PREC_FP64, L, 0, 0), (1, B.PREC_FP64, L - 1, 1, 0), (1, B.PREC_FP64, 0, 3, 0),
                  (0, B.PREC_FP64, 0, 0, 0), (33, B.PREC_FP64, 0, 0, 0), (1, B.PREC_FP64, 0, 0, -2)]:
         with pytest.raises(B.XamgError):
