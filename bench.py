@@ -115,8 +115,9 @@ def parse():
                     help="measurement mode: m in 1..32, PCG and BiCGStab, FP64/FP32/bf16 "
                          "preconditioner, one JSON line each (not the benchmark line)")
     ap.add_argument("--split-table", action="store_true",
-                    help="measurement mode: every row split of every level's FP64 product y = M x "
-                         "on --m columns, microseconds per product, one JSON line per operator")
+                    help="measurement mode: every row split of every level's product y = M x "
+                         "on --m columns (--precond), microseconds per product, one JSON line per "
+                         "operator")
     ap.add_argument("--tail-table", action="store_true",
                     help="measurement mode: small solves (7-point 32^3 and 64^3, m = 4 and 32; "
                          "variable-coefficient 64^3, m = 32) with the fused coarse tail on and off, "
@@ -126,7 +127,8 @@ def parse():
                          "with the default row split, nothing else (the case for kernel captures)")
     ap.add_argument("--level", type=int, default=0, help="--spmm-only: the level")
     ap.add_argument("--precond", default="fp64", choices=["fp64", "fp32", "bf16"],
-                    help="--spmm-only: FP64 blocks, or FP32 blocks with FP32 / bf16 values of A")
+                    help="--spmm-only, --split-table: FP64 blocks, or FP32 blocks with FP32 / bf16 "
+                         "values of A")
     a = ap.parse_args()
     if a.grid is None:
         a.grid = 160 if a.matrix == "poisson27" else 192
@@ -801,9 +803,22 @@ SPLIT_NAMES = {1: ["stream1x256", "lanes16", "stream1x1024", "stream4x1024", "st
                0: ["narrow", "row_per_warp"]}
 
 
+def split_names(m, prec_fp64):
+    """Names of the row-split candidates of xamg_set_split for m columns."""
+    if m == 1:
+        return SPLIT_NAMES[1]
+    mp = 1 << (m - 1).bit_length()
+    if mp in (2, 4):
+        return SPLIT_NAMES[0] + ["stream_lane_per_row"]
+    if not prec_fp64 and mp >= 8:
+        return SPLIT_NAMES[0] + ["staged"]
+    return SPLIT_NAMES[0]
+
+
 def run_split_table(a):
-    """Microseconds per FP64 product y = M x of every level and operator under
-    every row split (xamg_set_split), 20 timed products after 3 warm-ups."""
+    """Microseconds per product y = M x of every level and operator under
+    every row split (xamg_set_split), 20 timed products after 3 warm-ups: FP64
+    blocks, or with --precond fp32 / bf16 the preconditioner's FP32 blocks."""
     import torch
 
     from paper_2103_07329_gb300 import binding as B
@@ -814,7 +829,15 @@ def run_split_table(a):
     h = B.Hierarchy(A)
     L = h.levels
     info = [h.level_info(l) for l in range(L)]
-    names = SPLIT_NAMES[1] if a.m == 1 else SPLIT_NAMES[0]
+    prec = {"fp64": B.PREC_FP64, "fp32": B.PREC_FP32, "bf16": B.PREC_BF16}[a.precond]
+    names = split_names(a.m, prec == B.PREC_FP64)
+
+    def product(l, which, X, Y):
+        if prec == B.PREC_FP64:
+            h.spmm(l, which, X, Y)
+        else:
+            h.spmm_precond(prec, l, which, X, Y)
+
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     for l in range(L):
@@ -827,19 +850,19 @@ def run_split_table(a):
             Y = torch.empty(n_out, a.m, dtype=torch.float64, device="cuda")
             us = {}
             for c, name in enumerate(names):
-                h.set_split(a.m, B.PREC_FP64, l, which, c)
+                h.set_split(a.m, prec, l, which, c)
                 for _ in range(3):
-                    h.spmm(l, which, X, Y)
+                    product(l, which, X, Y)
                 torch.cuda.synchronize()
                 e0.record()
                 for _ in range(20):
-                    h.spmm(l, which, X, Y)
+                    product(l, which, X, Y)
                 e1.record()
                 torch.cuda.synchronize()
                 us[name] = round(e0.elapsed_time(e1) / 20 * 1e3, 1)
-            h.set_split(a.m, B.PREC_FP64, l, which, -1)
+            h.set_split(a.m, prec, l, which, -1)
             nnz = info[l][1] if which == 0 else info[l][2]
-            print(json.dumps({"matrix": a.matrix, "grid": a.grid, "m": a.m, "level": l,
+            print(json.dumps({"matrix": a.matrix, "grid": a.grid, "m": a.m, "precond": a.precond, "level": l,
                               "op": "APR"[which], "rows": n_out, "nnz": nnz,
                               "avg_row": round(nnz / max(n_out, 1), 1), "us": us}), flush=True)
     return 0

@@ -577,8 +577,17 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
   // 2- and 4-column blocks on sparse levels: one lane per row over the warp's
   // staged entries (measured per level at m = 2 and 4 on the 7- and 27-point
   // hierarchies: FP64 faster up to 27 entries per row and slower at 35; FP32
-  // faster from 19 to 35 and slower at 7)
-  if (stream_v_ok(nv, fp32) && (fp32 ? (avg > 10.0 && avg <= 40.0) : avg <= 30.0)) return kStreamV1024;
+  // faster from 19 to 35 and slower at 7).  FP64 levels below 131 072 rows
+  // keep the narrow split: its blocks hold a quarter (m = 4) or half (m = 2)
+  // of the stream kernel's 256 rows, so small levels still fill the GPU
+  // (CUDA-graph solves of the 7-point 32^3 and 48^3 cases, m = 4, measured
+  // 5 % faster that way; 64^3 and above at most 1 % apart).  FP32 levels of
+  // short rows below 131 072 rows take the stream kernel, latency-bound
+  // there (2 % faster solves at 32^3 and 48^3, 2 % slower at 96^3)
+  const bool small = M.n < 131072;
+  if (stream_v_ok(nv, fp32) &&
+      (fp32 ? ((avg > 10.0 || small) && avg <= 40.0) : (avg <= 30.0 && !small)))
+    return kStreamV1024;
   // (the staged narrow split, kAsyncNarrow, is a tuning candidate only: it
   // measured slower than this one on every level it fits)
   return 1;
