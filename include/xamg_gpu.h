@@ -394,15 +394,16 @@ int xamg_coldot_noalloc(const double *U, const double *V, int64_t n, int32_t m, 
  * of the precision `precond` selects (XAMG_PREC_FP64: FP64 blocks;
  * XAMG_PREC_FP32 / XAMG_PREC_BF16: FP32 blocks with FP32 / bf16 values of A)
  * under every row split -- for m > 1 the default (a group of lanes per row,
- * several rows per warp) and one row per warp with its entries split over the
- * lanes (16 and 32 FP64 columns: four warps per row); for m = 1 the stream kernel (the warp's entries staged in shared
- * memory) with one lane per row and a 256-, 512- or 1024-entry window, 2, 4
- * or 32 lanes per row, and 16 lanes per row without staging -- and keeps
- * the fastest in the hierarchy; later solves and V-cycles of
- * that block width and precision use it.  Results do not depend on the split
- * beyond the order of each row's sums.  ops_tuned / ops_wide (may be NULL):
- * products tuned and how many chose a split other than the first candidate
- * (m > 1: one row per warp).  Uses the hierarchy's cached
+ * several rows per warp), one row per warp with its entries split over the
+ * lanes (16 and 32 FP64 columns: four warps per row) and the third
+ * candidate where xamg_set_split lists one; for m = 1 the stream kernel (the
+ * warp's entries staged in shared memory) with one lane per row and a 256-,
+ * 512- or 1024-entry window, 2, 4 or 32 lanes per row, and 16 lanes per row
+ * without staging -- and keeps the fastest in the hierarchy; later solves
+ * and V-cycles of that block width and precision use it.  Results do not
+ * depend on the split beyond the order of each row's sums.  ops_tuned /
+ * ops_wide (may be NULL): products tuned and how many chose a split other
+ * than the first candidate.  Uses the hierarchy's cached
  * workspace; synchronizes `stream`.  No counterpart in the paper. */
 int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_t *ops_tuned,
                   int32_t *ops_wide);
@@ -419,9 +420,12 @@ int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_
  * 32 columns: four warps per row), and for FP32 blocks of 8 or more columns
  * 2 = a group of lanes per row with the operand rows staged through shared
  * memory by asynchronous copies (the sums of candidate 0, bit for bit; an
- * operator whose warp row groups exceed the staging window takes 0), and
- * for blocks of 2 or 4 columns 2 = the stream kernel of m = 1 with one lane
- * per row holding the row's columns (the sums of candidate 0).
+ * operator whose warp row groups exceed the staging window takes 0), for
+ * blocks of 2 or 4 columns 2 = the stream kernel of m = 1 with one lane
+ * per row holding the row's columns (the sums of candidate 0), and for FP64
+ * blocks of 16 or 32 columns 2 = candidate 0 with its row loop
+ * software-pipelined (the next rows' column indices and row pointers
+ * loaded while a row's operand rows are gathered; the sums of candidate 0).
  * Results do not depend on the split beyond the order of each row's sums.  XAMG_ERR_INVALID_ARG for any other
  * value.  Host only.  No counterpart in the paper. */
 int xamg_set_split(xamg_hier *h, int32_t m, int32_t precond, int32_t level, int32_t which,

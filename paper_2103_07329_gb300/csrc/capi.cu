@@ -542,6 +542,8 @@ void flush_timing(xamg_hier *h) {
 // Blocks of 2 or 4 columns (8- to 32-byte rows) can take the stream kernel
 // with one lane per row (rows_stream_v).
 bool stream_v_ok(int nv, bool /*fp32*/) { return nv == 2 || nv == 4; }
+// FP64 blocks of 16 or 32 columns can take the pipelined narrow split.
+bool pipe_ok(int nv, bool fp32) { return !fp32 && nv >= 16; }
 
 // Whether the staged FP32 narrow kernel (rows_async) can take operator M on
 // blocks of nv columns: every aligned group of a warp's rows fits its window.
@@ -588,6 +590,12 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
   if (stream_v_ok(nv, fp32) &&
       (fp32 ? ((avg > 10.0 || small) && avg <= 40.0) : (avg <= 30.0 && !small)))
     return kStreamV1024;
+  // FP64 blocks of 16 and 32 columns on levels of more than 10 entries per
+  // row: the pipelined narrow split (measured 3 to 7 % faster per launch on
+  // levels 1 to 6 of the 7-point 192^3 hierarchy at m = 32, 3 % slower on
+  // level 0 with its 7 entries per row, where the fourth block per SM pays
+  // more than the pipeline)
+  if (pipe_ok(nv, fp32) && avg > 10.0) return kPipeNarrow;
   // (the staged narrow split, kAsyncNarrow, is a tuning candidate only: it
   // measured slower than this one on every level it fits)
   return 1;
@@ -595,19 +603,19 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
 
 // Row split of tuning candidate t: m = 1 has seven (the stream-kernel
 // variants and 16 lanes per row, launch.h), wider blocks two (narrow, one row
-// per warp).
-// Blocks of 8 or more FP32 columns have the staged narrow split as a third
-// tuning candidate, blocks with 8- or 16-byte rows the stream kernel.
+// per warp) and a third where one exists: blocks of 8 or more FP32 columns
+// the staged narrow split, blocks of 2 or 4 columns the stream kernel, FP64
+// blocks of 16 or 32 columns the pipelined narrow split.
 int split_candidates(int nv, bool fp32) {
-  return nv == 1 ? 7 : ((fp32 && nv >= 8) || stream_v_ok(nv, fp32)) ? 3 : 2;
+  return nv == 1 ? 7 : ((fp32 && nv >= 8) || stream_v_ok(nv, fp32) || pipe_ok(nv, fp32)) ? 3 : 2;
 }
-int split_slices(int nv, int t) {
+int split_slices(int nv, int t, bool fp32) {
   if (nv == 1) {
     static const int c[7] = {kStreamShort, kSliced16, kStreamLong, kStreamQuad, kStreamWarp, kStreamMid,
                              kStreamPair};
     return c[t];
   }
-  if (t == 2) return nv >= 8 ? kAsyncNarrow : kStreamV1024;
+  if (t == 2) return fp32 && nv >= 8 ? kAsyncNarrow : stream_v_ok(nv, fp32) ? kStreamV1024 : kPipeNarrow;
   return t ? 2 : 1;
 }
 
@@ -673,7 +681,7 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
     int lg = 0;
     while ((1 << lg) < nv) ++lg;
     const int t = D.split[sizeof(TB) == 8 ? 2 : ((vt == 1 || vt == 2) ? 1 : 0)][which][lg];
-    if (t >= 0) sl = split_slices(nv, t);
+    if (t >= 0) sl = split_slices(nv, t, sizeof(TB) == 4);
     op.colw = nullptr;
     op.rowmeta = nullptr;
     op.tbase = nullptr;
@@ -692,7 +700,7 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
     TailStage<TB> &s = prog->st[prog->nstages++];
     s.op = op;
     s.kind = kind;
-    s.wide = sl > 1 && sl < kAsyncNarrow ? 1 : 0;  // the staged / stream codes sum as the narrow split
+    s.wide = sl > 1 && sl < kAsyncNarrow ? 1 : 0;  // the staged / stream / pipelined codes sum as the narrow split
     return 1;
   }
   cudaEvent_t a = nullptr, b = nullptr;
@@ -707,14 +715,14 @@ int rows(xamg_hier *h, int level, int which, int prec, RowOpT<TB> op, int nv, bo
     int lg = 0;
     while ((1 << lg) < nv) ++lg;
     const int t = D.split[2][which][lg];
-    if (t >= 0) sl = split_slices(nv, t);
+    if (t >= 0) sl = split_slices(nv, t, false);
     g = launch_rows(op, nv, sl, neg, epi, st);
   } else {
     int sl = slices_for(M, nv, true);
     int lg = 0;
     while ((1 << lg) < nv) ++lg;
     const int t = D.split[(vt == 1 || vt == 2) ? 1 : 0][which][lg];
-    if (t >= 0) sl = split_slices(nv, t);
+    if (t >= 0) sl = split_slices(nv, t, true);
     if (sl == kAsyncNarrow && !async_fits(M, nv, true)) sl = 1;
     g = launch_rows_f(op, nv, sl, neg, epi, vt, st);
   }

@@ -17,6 +17,9 @@ namespace xamg {
 
 constexpr int kBlock = 256;  // threads per block of the row and element kernels
 constexpr int kWarps = kBlock / 32;
+// `slices` code of the row launchers for the narrow split with its row loop
+// software-pipelined (FP64 blocks of 16 or 32 columns; k_rows, rows_vec)
+constexpr int kPipeNarrow = 300;
 
 // One fused row operation (paper Sec. 2.2-2.3: the "blas2" SpMV-like group,
 // here with m columns at once).  For every row i of the sparse matrix M and
@@ -484,7 +487,7 @@ __device__ __forceinline__ void vec_epilogue(const RowOpT<TB> &op, int64_t i, in
 // FMAs as it has entries.  With scaled (bf16) values the products are summed
 // first and the row scale applied once: v = init +/- s_i * sum_k q_ik x_k.
 template <class TB, class TV, int NV, int VEC, int SL, bool NEG, int EPI, int XW = 1, bool COH = false,
-          int CHX = 0>
+          int CHX = 0, bool PIPE = false>
 __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
   using VL = ValueLoad<TV>;
   using V = Vec<TB, VEC>;
@@ -520,7 +523,40 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
   double dsum[VEC], dsum2[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; ++v) dsum[v] = dsum2[v] = 0.0;
-  for (int64_t base = warp0 * RPW; base < op.n; base += wstride * RPW) {
+  // a round of a row's column indices / values: slot q of lane g holds entry
+  // kb + q*G + g
+  auto load_cols = [&](int (&cl)[K], int start, int len, int kb) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) cl[q] = kb + q * G + gl < len ? __ldg(col + start + kb + q * G + gl) : 0;
+  };
+  auto load_vals = [&](TB (&av)[K], int start, int len, int kb) {
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+      av[q] = kb + q * G + gl < len ? (TB)VL::get(op.val, start + kb + q * G + gl) : (TB)0;
+  };
+  // PIPE: software pipeline of the row loop (one warp per row group, 32-bit
+  // indices).  While a row's operand rows are gathered, the next row's first
+  // round of column indices and the row pointers of the row after it are
+  // already in flight, so the dependent chain row pointer -> index -> operand
+  // row costs one memory latency per row instead of three.  The sums are
+  // those of the unpipelined loop, bit for bit.
+  constexpr bool PF = PIPE && XW == 1 && !VL::idx16 && !COH;
+  const int64_t rstep = wstride * RPW;
+  int pf_s1 = 0, pf_l1 = 0, pf_s2 = 0, pf_l2 = 0;
+  int pf_cl[K];
+  if constexpr (PF) {
+    const int64_t i0 = warp0 * RPW + grp;
+    if (i0 < op.n) {
+      pf_s1 = __ldg(op.rowptr + i0);
+      pf_l1 = __ldg(op.rowptr + i0 + 1) - pf_s1;
+    }
+    if (i0 + rstep < op.n) {
+      pf_s2 = __ldg(op.rowptr + i0 + rstep);
+      pf_l2 = __ldg(op.rowptr + i0 + rstep + 1) - pf_s2;
+    }
+    load_cols(pf_cl, pf_s1, pf_l1, sl * G * K);
+  }
+  for (int64_t base = warp0 * RPW; base < op.n; base += rstep) {
     const int64_t i = base + (XW == 1 ? grp : (threadIdx.x >> 5) / XW);
     const bool valid = i < op.n;
     const int64_t e = i * NV + c0;
@@ -529,11 +565,30 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
     int4 tb = make_int4(0, 0, 0, 0);
     V acc, dpv, xv, in0;
     TB wv = 0, rs = 1;
+    int cl0[K];
+    TB av0[K];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc.v[v] = dpv.v[v] = xv.v[v] = in0.v[v] = 0;
+    if constexpr (PF) {
+      start = pf_s1;
+      len = pf_l1;
+#pragma unroll
+      for (int q = 0; q < K; ++q) cl0[q] = pf_cl[q];
+      load_vals(av0, start, len, sl * G * K);
+      pf_s1 = pf_s2;
+      pf_l1 = pf_l2;
+      load_cols(pf_cl, pf_s1, pf_l1, sl * G * K);
+      pf_s2 = pf_l2 = 0;
+      if (i + 2 * rstep < op.n) {
+        pf_s2 = __ldg(op.rowptr + i + 2 * rstep);
+        pf_l2 = __ldg(op.rowptr + i + 2 * rstep + 1) - pf_s2;
+      }
+    }
     if (valid) {
-      start = __ldg(op.rowptr + i);
-      len = __ldg(op.rowptr + i + 1) - start;
+      if constexpr (!PF) {
+        start = __ldg(op.rowptr + i);
+        len = __ldg(op.rowptr + i + 1) - start;
+      }
       if constexpr (VL::scaled) rs = (TB)__ldg(op.rscale + i);
       if constexpr (VL::idx16) {
         meta = __ldg(op.rowmeta + i);
@@ -561,16 +616,23 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
       // kb + q*G + g (coalesced across the group for every q)
       int cl[K];
       TB av[K];
+      if (PF && kb0 == 0) {
 #pragma unroll
-      for (int q = 0; q < K; ++q) {
-        const bool own = kb + q * G + gl < len;
-        if constexpr (VL::idx16) {
-          const int kl = kb + q * G + gl;
-          cl[q] = own ? seg16_col(tb, meta, kl, __ldg(op.colw + start + kl)) : 0;
-        } else {
-          cl[q] = own ? __ldg(col + start + kb + q * G + gl) : 0;
+        for (int q = 0; q < K; ++q) {
+          cl[q] = cl0[q];
+          av[q] = av0[q];
         }
-        av[q] = own ? (TB)VL::get(op.val, start + kb + q * G + gl) : (TB)0;
+      } else if constexpr (VL::idx16) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          const int kl = kb + q * G + gl;
+          const bool own = kl < len;
+          cl[q] = own ? seg16_col(tb, meta, kl, __ldg(op.colw + start + kl)) : 0;
+          av[q] = own ? (TB)VL::get(op.val, start + kl) : (TB)0;
+        }
+      } else {
+        load_cols(cl, start, len, kb);
+        load_vals(av, start, len, kb);
       }
       const int cnt = min(G * K, maxlen - kb0);  // uniform over the warp
 #pragma unroll
@@ -1125,10 +1187,15 @@ __host__ __device__ constexpr int row_vec() {
 // row -> block map (and with it the order of the partial dot sums) depends
 // only on n and the grid size.  At most 64 registers per thread (four
 // 256-thread blocks per SM): measured faster than the uncapped build, whose
-// wider epilogues took 80 registers and three blocks per SM.
+// wider epilogues took 80 registers and three blocks per SM.  The pipelined
+// narrow split (kPipeNarrow) holds the next rows' indices and row pointers
+// as well and takes the 80 registers.
 template <class TB, class TV, int NV, int S, bool NEG, int EPI>
-__global__ void __launch_bounds__(kBlock, 4) k_rows(RowOpT<TB> op) {
-  if constexpr (S == 1) {
+__global__ void __launch_bounds__(kBlock, S == kPipeNarrow ? 3 : 4) k_rows(RowOpT<TB> op) {
+  if constexpr (S == kPipeNarrow) {
+    // the pipelined narrow split: 80 registers, three blocks per SM
+    rows_vec<TB, TV, NV, row_vec<TB, NV>(), 1, NEG, EPI, 1, false, 0, true>(op);
+  } else if constexpr (S == 1) {
     rows_vec<TB, TV, NV, row_vec<TB, NV>(), 1, NEG, EPI>(op);
   } else if constexpr (NV > 1 && S < 0) {
     // one row per warp (in 32 / (NV / VEC) slices), -S warps per row

@@ -85,9 +85,10 @@ int rows_t(const RowOpT<TBx> &op, cudaStream_t st) {
         b = 1;
       max_grid = std::min(kMaxGrid, b * device_sm_count());
     }
-    // S < 0 (NV > 1): -S warps per row
-    constexpr int lanes_per_row = NV == 1 ? S : (NV / row_vec<TBx, NV>()) * (S > 0 ? S : 1);
-    constexpr int rows_per_block = S < 0 ? kWarps / -S : kWarps * (32 / lanes_per_row);
+    // S < 0 (NV > 1): -S warps per row; kPipeNarrow: the narrow split
+    constexpr int SS = S == kPipeNarrow ? 1 : S;
+    constexpr int lanes_per_row = NV == 1 ? SS : (NV / row_vec<TBx, NV>()) * (SS > 0 ? SS : 1);
+    constexpr int rows_per_block = SS < 0 ? kWarps / -SS : kWarps * (32 / lanes_per_row);
     const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
     k_rows<TBx, TV, NV, S, NEG, EPI><<<grid, kBlock, 0, st>>>(op);
@@ -164,6 +165,11 @@ int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t 
   }
 #endif
   if (slices == kAsyncNarrow) slices = 1;
+#if !XAMG_FLOAT && XAMG_NV >= 16
+  // the narrow split with its row loop software-pipelined
+  if (slices == kPipeNarrow) return rows_e<TV, XAMG_NV, kPipeNarrow>(op, neg, epi, st);
+#endif
+  if (slices == kPipeNarrow) slices = 1;
   // long rows: every group of the warp takes a slice of one row (one row per
   // warp; with 32 FP64 columns a row already fills the warp)
   constexpr int WS = 32 / (XAMG_NV / row_vec<TBx, XAMG_NV>());

@@ -147,11 +147,12 @@ def test_spmm_m1_every_split(cand):
 
 
 @pytest.mark.parametrize("m", [16, 32])
-@pytest.mark.parametrize("cand", [0, 1])
+@pytest.mark.parametrize("cand", [0, 1, 2])
 def test_spmm_wide_blocks_every_split(m, cand):
-    # FP64 blocks of 16 and 32 columns under both splits on every level and
-    # operator (32 columns, split 1: four warps share a row), the 7-point and
-    # 27-point hierarchies with their dense Galerkin levels
+    # FP64 blocks of 16 and 32 columns under every split on every level and
+    # operator (32 columns, split 1: four warps share a row; split 2: the
+    # pipelined narrow split), the 7-point and 27-point hierarchies with their
+    # dense Galerkin levels
     for name, N in (("p7", 33), ("p27", 20)):
         pr = pair(name, N)
         rng = np.random.default_rng(100 + cand)
@@ -176,10 +177,11 @@ def test_spmm_wide_blocks_every_split(m, cand):
                     pr.g.set_split(m, B.PREC_FP64, l, which, -1)
 
 
-@pytest.mark.parametrize("m", [2, 4])
-def test_narrow_block_stream_split_is_bitwise_the_narrow_split(m):
-    # 2- and 4-column FP64 blocks: the stream kernel (one lane per row over the
-    # warp's staged entries, candidate 2) adds each column's products in
+@pytest.mark.parametrize("m", [2, 4, 16, 32])
+def test_third_fp64_split_is_bitwise_the_narrow_split(m):
+    # FP64 candidate 2 -- for 2- and 4-column blocks the stream kernel (one
+    # lane per row over the warp's staged entries), for 16 and 32 columns the
+    # software-pipelined narrow split -- adds each column's products in
     # storage order like the narrow split (candidate 0), on every level and
     # operator, so products and the V-cycle agree bit for bit; the solve's
     # fused dot products reduce in another lane and block order, so its
