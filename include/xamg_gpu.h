@@ -425,7 +425,9 @@ int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_
  * per row holding the row's columns (the sums of candidate 0), and for FP64
  * blocks of 16 or 32 columns 2 = candidate 0 with its row loop
  * software-pipelined (the next rows' column indices and row pointers
- * loaded while a row's operand rows are gathered; the sums of candidate 0).
+ * loaded while a row's operand rows are gathered; the sums of candidate 0),
+ * 3 = candidate 0 and 4 = candidate 2 with two adjacent columns per lane,
+ * so that a warp works on two rows at once (the sums of candidate 0).
  * Results do not depend on the split beyond the order of each row's sums.  XAMG_ERR_INVALID_ARG for any other
  * value.  Host only.  No counterpart in the paper. */
 int xamg_set_split(xamg_hier *h, int32_t m, int32_t precond, int32_t level, int32_t which,

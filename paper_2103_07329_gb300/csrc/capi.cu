@@ -590,12 +590,19 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
   if (stream_v_ok(nv, fp32) &&
       (fp32 ? ((avg > 10.0 || small) && avg <= 40.0) : (avg <= 30.0 && !small)))
     return kStreamV1024;
-  // FP64 blocks of 16 and 32 columns on levels of more than 10 entries per
-  // row: the pipelined narrow split (measured 3 to 7 % faster per launch on
+  // FP64 blocks of 16 and 32 columns: the pipelined narrow split on levels of
+  // more than 10 entries per row (measured 3 to 7 % faster per launch on
   // levels 1 to 6 of the 7-point 192^3 hierarchy at m = 32, 3 % slower on
   // level 0 with its 7 entries per row, where the fourth block per SM pays
-  // more than the pipeline)
-  if (pipe_ok(nv, fp32) && avg > 10.0) return kPipeNarrow;
+  // more than the pipeline).  Two columns per lane (a warp on two rows) on
+  // the sparser levels: level 0 6-8 % faster at m = 16 and 32, level 1
+  // (18.8 entries per row) 4 % at m = 32 and 21 % at m = 16, level 2 (34.7)
+  // 8 % at m = 16 but 3 % slower at m = 32, the denser levels 4-13 % slower
+  if (pipe_ok(nv, fp32)) {
+    if (avg <= 10.0) return kNarrow2;
+    if (avg <= 20.0 || (nv == 16 && avg <= 40.0)) return kPipeNarrow2;
+    return kPipeNarrow;
+  }
   // (the staged narrow split, kAsyncNarrow, is a tuning candidate only: it
   // measured slower than this one on every level it fits)
   return 1;
@@ -605,9 +612,12 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
 // variants and 16 lanes per row, launch.h), wider blocks two (narrow, one row
 // per warp) and a third where one exists: blocks of 8 or more FP32 columns
 // the staged narrow split, blocks of 2 or 4 columns the stream kernel, FP64
-// blocks of 16 or 32 columns the pipelined narrow split.
+// blocks of 16 or 32 columns the pipelined narrow split, and for those two
+// more, the narrow split and its pipelined form with two columns per lane.
 int split_candidates(int nv, bool fp32) {
-  return nv == 1 ? 7 : ((fp32 && nv >= 8) || stream_v_ok(nv, fp32) || pipe_ok(nv, fp32)) ? 3 : 2;
+  if (nv == 1) return 7;
+  if (pipe_ok(nv, fp32)) return 5;
+  return ((fp32 && nv >= 8) || stream_v_ok(nv, fp32)) ? 3 : 2;
 }
 int split_slices(int nv, int t, bool fp32) {
   if (nv == 1) {
@@ -616,6 +626,8 @@ int split_slices(int nv, int t, bool fp32) {
     return c[t];
   }
   if (t == 2) return fp32 && nv >= 8 ? kAsyncNarrow : stream_v_ok(nv, fp32) ? kStreamV1024 : kPipeNarrow;
+  if (t == 3) return kNarrow2;
+  if (t == 4) return kPipeNarrow2;
   return t ? 2 : 1;
 }
 

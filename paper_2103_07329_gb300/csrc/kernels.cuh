@@ -17,9 +17,12 @@ namespace xamg {
 
 constexpr int kBlock = 256;  // threads per block of the row and element kernels
 constexpr int kWarps = kBlock / 32;
-// `slices` code of the row launchers for the narrow split with its row loop
-// software-pipelined (FP64 blocks of 16 or 32 columns; k_rows, rows_vec)
-constexpr int kPipeNarrow = 300;
+// `slices` codes of the row launchers for FP64 blocks of 16 or 32 columns
+// (k_rows, rows_vec): the narrow split with its row loop software-pipelined
+// (kPipeNarrow), and the narrow split and its pipelined form with two
+// adjacent columns per lane, so that a warp holds two rows (kNarrow2,
+// kPipeNarrow2)
+constexpr int kPipeNarrow = 300, kNarrow2 = 310, kPipeNarrow2 = 311;
 
 // One fused row operation (paper Sec. 2.2-2.3: the "blas2" SpMV-like group,
 // here with m columns at once).  For every row i of the sparse matrix M and
@@ -493,12 +496,13 @@ __device__ __forceinline__ void rows_vec(const RowOpT<TB> &op) {
   using V = Vec<TB, VEC>;
   constexpr int G = NV / VEC;
   constexpr int RPW = 32 / (G * SL);
-  // entries gathered per chunk: 8 for FP64 (exact-count tails keep the FP64
-  // FMA count at the algorithmic one); 4 for FP32, whose 16-byte gathers
+  // entries gathered per chunk: 8 for FP64 with one column per lane
+  // (exact-count tails keep the FP64 FMA count at the algorithmic one); 4
+  // for FP32 and for FP64 with two columns per lane, whose 16-byte gathers
   // already fill the registers; never more than the G lanes of a row group
   // hold, since a chunk's shuffles broadcast the group's own entries (narrow
   // blocks, m = 2..8, would otherwise spend most shuffles on empty slots)
-  constexpr int CH0 = CHX > 0 ? CHX : (sizeof(TB) == 4 ? 4 : 8);
+  constexpr int CH0 = CHX > 0 ? CHX : (sizeof(TB) == 4 || VEC == 2 ? 4 : 8);
   constexpr int CH = CH0 < G ? CH0 : G;
   constexpr int K = 32 / G < 4 ? 32 / G : 4;  // entries each lane fetches per round
   constexpr bool xlast = EPI == EPI_XLAST || EPI == EPI_XLAST_DOT || EPI == EPI_XLAST_DOT2;
@@ -1182,6 +1186,12 @@ __host__ __device__ constexpr int row_vec() {
   if constexpr (sizeof(TB) == 4) return NV >= 4 ? 4 : NV;
   return 1;
 }
+// Columns per lane of the row kernel with `slices` code S: two for the
+// kNarrow2 / kPipeNarrow2 forms, else row_vec.
+template <class TB, int NV, int S>
+__host__ __device__ constexpr int split_vec() {
+  return (S == kNarrow2 || S == kPipeNarrow2) ? 2 : row_vec<TB, NV>();
+}
 
 // The fused row kernel.  Warps walk the rows in a grid-stride loop, so the
 // row -> block map (and with it the order of the partial dot sums) depends
@@ -1191,10 +1201,12 @@ __host__ __device__ constexpr int row_vec() {
 // narrow split (kPipeNarrow) holds the next rows' indices and row pointers
 // as well and takes the 80 registers.
 template <class TB, class TV, int NV, int S, bool NEG, int EPI>
-__global__ void __launch_bounds__(kBlock, S == kPipeNarrow ? 3 : 4) k_rows(RowOpT<TB> op) {
-  if constexpr (S == kPipeNarrow) {
+__global__ void __launch_bounds__(kBlock, (S == kPipeNarrow || S == kPipeNarrow2) ? 3 : 4) k_rows(RowOpT<TB> op) {
+  if constexpr (S == kPipeNarrow || S == kPipeNarrow2) {
     // the pipelined narrow split: 80 registers, three blocks per SM
-    rows_vec<TB, TV, NV, row_vec<TB, NV>(), 1, NEG, EPI, 1, false, 0, true>(op);
+    rows_vec<TB, TV, NV, split_vec<TB, NV, S>(), 1, NEG, EPI, 1, false, 0, true>(op);
+  } else if constexpr (S == kNarrow2) {
+    rows_vec<TB, TV, NV, 2, 1, NEG, EPI>(op);
   } else if constexpr (S == 1) {
     rows_vec<TB, TV, NV, row_vec<TB, NV>(), 1, NEG, EPI>(op);
   } else if constexpr (NV > 1 && S < 0) {

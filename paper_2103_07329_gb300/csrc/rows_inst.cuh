@@ -85,9 +85,10 @@ int rows_t(const RowOpT<TBx> &op, cudaStream_t st) {
         b = 1;
       max_grid = std::min(kMaxGrid, b * device_sm_count());
     }
-    // S < 0 (NV > 1): -S warps per row; kPipeNarrow: the narrow split
-    constexpr int SS = S == kPipeNarrow ? 1 : S;
-    constexpr int lanes_per_row = NV == 1 ? SS : (NV / row_vec<TBx, NV>()) * (SS > 0 ? SS : 1);
+    // S < 0 (NV > 1): -S warps per row; kPipeNarrow, kNarrow2, kPipeNarrow2:
+    // the narrow split (with split_vec columns per lane)
+    constexpr int SS = (S == kPipeNarrow || S == kNarrow2 || S == kPipeNarrow2) ? 1 : S;
+    constexpr int lanes_per_row = NV == 1 ? SS : (NV / split_vec<TBx, NV, S>()) * (SS > 0 ? SS : 1);
     constexpr int rows_per_block = SS < 0 ? kWarps / -SS : kWarps * (32 / lanes_per_row);
     const int64_t need = ((int64_t)op.n + rows_per_block - 1) / rows_per_block;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, max_grid));
@@ -166,10 +167,13 @@ int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t 
 #endif
   if (slices == kAsyncNarrow) slices = 1;
 #if !XAMG_FLOAT && XAMG_NV >= 16
-  // the narrow split with its row loop software-pipelined
+  // the narrow split with its row loop software-pipelined, and both with two
+  // columns per lane
   if (slices == kPipeNarrow) return rows_e<TV, XAMG_NV, kPipeNarrow>(op, neg, epi, st);
+  if (slices == kNarrow2) return rows_e<TV, XAMG_NV, kNarrow2>(op, neg, epi, st);
+  if (slices == kPipeNarrow2) return rows_e<TV, XAMG_NV, kPipeNarrow2>(op, neg, epi, st);
 #endif
-  if (slices == kPipeNarrow) slices = 1;
+  if (slices == kPipeNarrow || slices == kNarrow2 || slices == kPipeNarrow2) slices = 1;
   // long rows: every group of the warp takes a slice of one row (one row per
   // warp; with 32 FP64 columns a row already fills the warp)
   constexpr int WS = 32 / (XAMG_NV / row_vec<TBx, XAMG_NV>());

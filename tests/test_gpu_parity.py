@@ -147,12 +147,13 @@ def test_spmm_m1_every_split(cand):
 
 
 @pytest.mark.parametrize("m", [16, 32])
-@pytest.mark.parametrize("cand", [0, 1, 2])
+@pytest.mark.parametrize("cand", [0, 1, 2, 3, 4])
 def test_spmm_wide_blocks_every_split(m, cand):
     # FP64 blocks of 16 and 32 columns under every split on every level and
     # operator (32 columns, split 1: four warps share a row; split 2: the
-    # pipelined narrow split), the 7-point and 27-point hierarchies with their
-    # dense Galerkin levels
+    # pipelined narrow split; 3 and 4: the narrow split and its pipelined
+    # form with two columns per lane), the 7-point and 27-point hierarchies
+    # with their dense Galerkin levels
     for name, N in (("p7", 33), ("p27", 20)):
         pr = pair(name, N)
         rng = np.random.default_rng(100 + cand)
@@ -178,19 +179,20 @@ def test_spmm_wide_blocks_every_split(m, cand):
 
 
 @pytest.mark.parametrize("m", [2, 4, 16, 32])
-def test_third_fp64_split_is_bitwise_the_narrow_split(m):
+def test_alternative_fp64_splits_are_bitwise_the_narrow_split(m):
     # FP64 candidate 2 -- for 2- and 4-column blocks the stream kernel (one
     # lane per row over the warp's staged entries), for 16 and 32 columns the
-    # software-pipelined narrow split -- adds each column's products in
-    # storage order like the narrow split (candidate 0), on every level and
-    # operator, so products and the V-cycle agree bit for bit; the solve's
-    # fused dot products reduce in another lane and block order, so its
-    # iterates agree to rounding
+    # software-pipelined narrow split -- and for 16 and 32 columns candidates
+    # 3 and 4 (two columns per lane) add each column's products in storage
+    # order like the narrow split (candidate 0), on every level and operator,
+    # so products and the V-cycle agree bit for bit; the solve's fused dot
+    # products reduce in another lane and block order, so its iterates agree
+    # to rounding
     for name, N in (("p7", 33), ("p27", 20)):
         pr = pair(name, N)
         rng = np.random.default_rng(7)
         outs = []
-        for cand in (0, 2):
+        for cand in ((0, 2) if m <= 4 else (0, 2, 3, 4)):
             for l in range(pr.o.nlev):
                 for which in (0, 1, 2):
                     if which == 0 or l + 1 < pr.o.nlev:
@@ -218,10 +220,11 @@ def test_third_fp64_split_is_bitwise_the_narrow_split(m):
             for which in (0, 1, 2):
                 if which == 0 or l + 1 < pr.o.nlev:
                     pr.g.set_split(m, B.PREC_FP64, l, which, -1)
-        (ya, xa, ia), (yb, xb, ib) = outs
-        for a, b in zip(ya, yb):
-            assert np.array_equal(a, b), name
-        assert np.array_equal(ia, ib) and colrel(xa, xb).max() <= 1e-12
+        ya, xa, ia = outs[0]
+        for yb, xb, ib in outs[1:]:
+            for a, b in zip(ya, yb):
+                assert np.array_equal(a, b), name
+            assert np.array_equal(ia, ib) and colrel(xa, xb).max() <= 1e-12
 
 
 def test_set_split_rejects_bad_arguments(cfg0):
