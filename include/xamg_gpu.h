@@ -423,7 +423,7 @@ int xamg_autotune(xamg_hier *h, int32_t m, int32_t precond, void *stream, int32_
  * operator whose warp row groups exceed the staging window takes 0), for
  * blocks of 2 or 4 columns 2 = the stream kernel of m = 1 with one lane
  * per row holding the row's columns (the sums of candidate 0), and for FP64
- * blocks of 16 or 32 columns 2 = candidate 0 with its row loop
+ * blocks of 8, 16 or 32 columns 2 = candidate 0 with its row loop
  * software-pipelined (the next rows' column indices and row pointers
  * loaded while a row's operand rows are gathered; the sums of candidate 0),
  * 3 = candidate 0 and 4 = candidate 2 with two adjacent columns per lane,

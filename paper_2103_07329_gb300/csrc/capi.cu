@@ -542,8 +542,8 @@ void flush_timing(xamg_hier *h) {
 // Blocks of 2 or 4 columns (8- to 32-byte rows) can take the stream kernel
 // with one lane per row (rows_stream_v).
 bool stream_v_ok(int nv, bool /*fp32*/) { return nv == 2 || nv == 4; }
-// FP64 blocks of 16 or 32 columns can take the pipelined narrow split.
-bool pipe_ok(int nv, bool fp32) { return !fp32 && nv >= 16; }
+// FP64 blocks of 8 or more columns can take the pipelined narrow split.
+bool pipe_ok(int nv, bool fp32) { return !fp32 && nv >= 8; }
 
 // Whether the staged FP32 narrow kernel (rows_async) can take operator M on
 // blocks of nv columns: every aligned group of a warp's rows fits its window.
@@ -590,17 +590,18 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
   if (stream_v_ok(nv, fp32) &&
       (fp32 ? ((avg > 10.0 || small) && avg <= 40.0) : (avg <= 30.0 && !small)))
     return kStreamV1024;
-  // FP64 blocks of 16 and 32 columns: the pipelined narrow split on levels of
-  // more than 10 entries per row (measured 3 to 7 % faster per launch on
+  // FP64 blocks of 8, 16 and 32 columns: the pipelined narrow split on levels
+  // of more than 10 entries per row (measured 3 to 7 % faster per launch on
   // levels 1 to 6 of the 7-point 192^3 hierarchy at m = 32, 3 % slower on
   // level 0 with its 7 entries per row, where the fourth block per SM pays
   // more than the pipeline).  Two columns per lane (a warp on two rows) on
-  // the sparser levels: level 0 6-8 % faster at m = 16 and 32, level 1
-  // (18.8 entries per row) 4 % at m = 32 and 21 % at m = 16, level 2 (34.7)
-  // 8 % at m = 16 but 3 % slower at m = 32, the denser levels 4-13 % slower
+  // the sparser levels: level 0 6-9 % faster at m = 8, 16 and 32, level 1
+  // (18.8 entries per row) 4 % at m = 32, 17 % at m = 8 and 21 % at m = 16,
+  // level 2 (34.7) 8-10 % at m = 8 and 16 but 3 % slower at m = 32, the
+  // denser levels 4-13 % slower at m = 16 and 32
   if (pipe_ok(nv, fp32)) {
     if (avg <= 10.0) return kNarrow2;
-    if (avg <= 20.0 || (nv == 16 && avg <= 40.0)) return kPipeNarrow2;
+    if (avg <= 20.0 || (nv <= 16 && avg <= 40.0)) return kPipeNarrow2;
     return kPipeNarrow;
   }
   // (the staged narrow split, kAsyncNarrow, is a tuning candidate only: it
@@ -612,7 +613,7 @@ int slices_for(const DevCsr &M, int nv, bool fp32) {
 // variants and 16 lanes per row, launch.h), wider blocks two (narrow, one row
 // per warp) and a third where one exists: blocks of 8 or more FP32 columns
 // the staged narrow split, blocks of 2 or 4 columns the stream kernel, FP64
-// blocks of 16 or 32 columns the pipelined narrow split, and for those two
+// blocks of 8 or more columns the pipelined narrow split, and for those two
 // more, the narrow split and its pipelined form with two columns per lane.
 int split_candidates(int nv, bool fp32) {
   if (nv == 1) return 7;

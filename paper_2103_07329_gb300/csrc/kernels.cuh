@@ -17,7 +17,7 @@ namespace xamg {
 
 constexpr int kBlock = 256;  // threads per block of the row and element kernels
 constexpr int kWarps = kBlock / 32;
-// `slices` codes of the row launchers for FP64 blocks of 16 or 32 columns
+// `slices` codes of the row launchers for FP64 blocks of 8 or more columns
 // (k_rows, rows_vec): the narrow split with its row loop software-pipelined
 // (kPipeNarrow), and the narrow split and its pipelined form with two
 // adjacent columns per lane, so that a warp holds two rows (kNarrow2,

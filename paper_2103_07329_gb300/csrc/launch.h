@@ -87,8 +87,9 @@ constexpr int kAsyncNarrow = 100;
 // Blocks of 2 or 4 columns (8 or 16 bytes per block row): the stream kernel
 // with one lane per row and a 256- or 1024-entry window (rows_stream_v).
 constexpr int kStreamV256 = 200, kStreamV1024 = 201;
-// (kPipeNarrow, the pipelined narrow split of FP64 blocks of 16 or 32
-// columns, is defined with the row kernel in kernels.cuh.)
+// (kPipeNarrow, kNarrow2 and kPipeNarrow2, the other narrow splits of FP64
+// blocks of 8 or more columns, are defined with the row kernel in
+// kernels.cuh.)
 
 int device_sm_count();
 extern std::atomic<int64_t> g_launches;  // kernels launched by the library

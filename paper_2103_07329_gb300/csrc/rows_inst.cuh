@@ -166,7 +166,7 @@ int rows_any(const RowOpT<TBx> &op, int slices, bool neg, int epi, cudaStream_t 
   }
 #endif
   if (slices == kAsyncNarrow) slices = 1;
-#if !XAMG_FLOAT && XAMG_NV >= 16
+#if !XAMG_FLOAT && XAMG_NV >= 8
   // the narrow split with its row loop software-pipelined, and both with two
   // columns per lane
   if (slices == kPipeNarrow) return rows_e<TV, XAMG_NV, kPipeNarrow>(op, neg, epi, st);

@@ -333,16 +333,16 @@ def test_index16_falls_back_where_rows_do_not_fit():
 def test_third_split_candidate_exists_where_documented():
     # candidate 2: the staged narrow split for FP32 blocks of >= 8 columns, the
     # stream kernel for 2 and 4 columns, the pipelined narrow split for FP64
-    # blocks of 16 and 32 columns (which also have 3 and 4, two columns per
-    # lane); nothing for 8 FP64 columns
+    # blocks of 8 or more columns (which also have 3 and 4, two columns per
+    # lane)
     g = B.Hierarchy(P.poisson7(12))
     for m, prec, cand in [(2, B.PREC_FP32, 2), (4, B.PREC_FP32, 2), (8, B.PREC_BF16, 2),
                           (32, B.PREC_FP32, 2), (2, B.PREC_FP64, 2), (4, B.PREC_FP64, 2),
-                          (16, B.PREC_FP64, 4), (32, B.PREC_FP64, 4)]:
+                          (8, B.PREC_FP64, 4), (16, B.PREC_FP64, 4), (32, B.PREC_FP64, 4)]:
         for c in range(2, cand + 1):
             g.set_split(m, prec, 0, 0, c)
         g.set_split(m, prec, 0, 0, -1)
-    for m, prec, cand in [(32, B.PREC_FP64, 5), (8, B.PREC_FP64, 2), (32, B.PREC_FP32, 3),
+    for m, prec, cand in [(32, B.PREC_FP64, 5), (8, B.PREC_FP64, 5), (32, B.PREC_FP32, 3),
                           (4, B.PREC_FP64, 3)]:
         with pytest.raises(B.XamgError):
             g.set_split(m, prec, 0, 0, cand)

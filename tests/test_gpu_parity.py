@@ -146,10 +146,10 @@ def test_spmm_m1_every_split(cand):
                     pr.g.set_split(1, B.PREC_FP64, l, which, -1)
 
 
-@pytest.mark.parametrize("m", [16, 32])
+@pytest.mark.parametrize("m", [8, 16, 32])
 @pytest.mark.parametrize("cand", [0, 1, 2, 3, 4])
 def test_spmm_wide_blocks_every_split(m, cand):
-    # FP64 blocks of 16 and 32 columns under every split on every level and
+    # FP64 blocks of 8, 16 and 32 columns under every split on every level and
     # operator (32 columns, split 1: four warps share a row; split 2: the
     # pipelined narrow split; 3 and 4: the narrow split and its pipelined
     # form with two columns per lane), the 7-point and 27-point hierarchies
@@ -178,11 +178,11 @@ def test_spmm_wide_blocks_every_split(m, cand):
                     pr.g.set_split(m, B.PREC_FP64, l, which, -1)
 
 
-@pytest.mark.parametrize("m", [2, 4, 16, 32])
+@pytest.mark.parametrize("m", [2, 4, 8, 16, 32])
 def test_alternative_fp64_splits_are_bitwise_the_narrow_split(m):
     # FP64 candidate 2 -- for 2- and 4-column blocks the stream kernel (one
-    # lane per row over the warp's staged entries), for 16 and 32 columns the
-    # software-pipelined narrow split -- and for 16 and 32 columns candidates
+    # lane per row over the warp's staged entries), for 8 to 32 columns the
+    # software-pipelined narrow split -- and for 8 to 32 columns candidates
     # 3 and 4 (two columns per lane) add each column's products in storage
     # order like the narrow split (candidate 0), on every level and operator,
     # so products and the V-cycle agree bit for bit; the solve's fused dot
@@ -230,7 +230,7 @@ def test_alternative_fp64_splits_are_bitwise_the_narrow_split(m):
 def test_set_split_rejects_bad_arguments(cfg0):
     g = cfg0.g
     L = cfg0.o.nlev
-    for args in [(1, B.PREC_FP64, 0, 0, 7), (8, B.PREC_FP64, 0, 0, 2), (2, B.PREC_FP64, 0, 0, 3),
+    for args in [(1, B.PREC_FP64, 0, 0, 7), (8, B.PREC_FP64, 0, 0, 5), (2, B.PREC_FP64, 0, 0, 3),
                  (1, 9, 0, 0, 0),
                  (1, B.PREC_FP64, L, 0, 0), (1, B.PREC_FP64, L - 1, 1, 0), (1, B.PREC_FP64, 0, 3, 0),
                  (0, B.PREC_FP64, 0, 0, 0), (33, B.PREC_FP64, 0, 0, 0), (1, B.PREC_FP64, 0, 0, -2)]:
