@@ -812,6 +812,8 @@ def split_names(m, prec_fp64):
         return SPLIT_NAMES[0] + ["stream_lane_per_row"]
     if not prec_fp64 and mp >= 8:
         return SPLIT_NAMES[0] + ["staged"]
+    if prec_fp64 and mp >= 8:
+        return SPLIT_NAMES[0] + ["pipelined", "narrow_2col", "pipelined_2col"]
     return SPLIT_NAMES[0]
 
 

@@ -40,3 +40,19 @@ def test_oracle_threads_follows_the_environment(monkeypatch):
     assert bench.oracle_threads() == 3
     monkeypatch.delenv("OMP_NUM_THREADS")
     assert bench.oracle_threads() == os.cpu_count()
+
+
+def test_split_table_names_match_the_candidate_counts():
+    # --split-table times one product per xamg_set_split candidate; the
+    # counts documented there: 7 at m = 1, 3 for 2 or 4 columns (the stream
+    # kernel) and for FP32 blocks of 8 or more (the staged split), 5 for FP64
+    # blocks of 8 or more (pipelined, and both with two columns per lane)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert len(bench.split_names(1, True)) == 7
+    for m in (2, 3, 4):
+        assert len(bench.split_names(m, True)) == 3 and len(bench.split_names(m, False)) == 3
+    for m in (5, 8, 16, 17, 32):
+        assert len(bench.split_names(m, False)) == 3
+        assert len(bench.split_names(m, True)) == 5
+    assert len(set(bench.split_names(32, True))) == 5
